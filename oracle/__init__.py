@@ -1,0 +1,283 @@
+"""CPU oracle for the HPL / HPL-MxP dense LU solve (test infrastructure).
+
+This package is the plain, slow, FP64 statement of what the GPU library
+computes, written from the paper (arXiv 2604.09517, Sec. III-A.1 for HPL,
+Sec. III-A.2 for HPL-MxP, Sec. II-B for GMRES-based refinement) and from the
+published methods it names. Only the tests, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it. The GPU library never
+calls it and shares no code with it.
+
+The arithmetic lives in ``oracle.c`` (plain C, OpenMP); this module builds it
+with gcc and exposes thin numpy wrappers. All matrices are numpy arrays in
+Fortran (column-major) order.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB_PATH = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# Stream tags of the generator (see oracle.c).
+STREAM_A = 0
+STREAM_B = 1
+STREAM_BATCH_SIZES = 2
+
+
+def batch_stream_a(s: int) -> int:
+    return 16 + 2 * s
+
+
+def batch_stream_b(s: int) -> int:
+    return 17 + 2 * s
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into a shared library (gcc, -O3, OpenMP).
+
+    FMA contraction is off so the oracle gives the same bits on x86 and Arm.
+    """
+    os.makedirs(os.path.dirname(_LIB_PATH), exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    cmd = ["gcc", "-O3", "-std=gnu11", "-fopenmp", "-ffp-contract=off", "-fno-fast-math",
+           "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        build()
+        lib = ctypes.CDLL(_LIB_PATH)
+        i64, u64, dp, fp, ip = (ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_float), ctypes.POINTER(ctypes.c_int32))
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        intp = ctypes.POINTER(ctypes.c_int)
+        sig = {
+            "orc_sm64_next": (u64, [u64, u64]),
+            "orc_stream_key": (u64, [u64, u64]),
+            "orc_raw": (u64, [u64, u64]),
+            "orc_uniform": (ctypes.c_double, [u64, u64]),
+            "orc_generate": (None, [u64, u64, i64, i64, ctypes.c_int, dp, i64]),
+            "orc_getrf": (i64, [i64, dp, i64, ip, dp]),
+            "orc_getrs": (None, [i64, i64, dp, i64, ip, ctypes.c_int, dp, i64]),
+            "orc_scaled_residual": (ctypes.c_double, [i64, dp, i64, dp, dp]),
+            "orc_scaled_residual_gen": (ctypes.c_double, [u64, i64, ctypes.c_int, dp, dp]),
+            "orc_perm_from_ipiv": (None, [i64, ip, i64p]),
+            "orc_lu_sample_diff": (None, [u64, i64, ctypes.c_int, dp, i64, i64p, i64, i64p, i64p, dp]),
+            "orc_round_bf16": (ctypes.c_float, [ctypes.c_float]),
+            "orc_round_e4m3": (ctypes.c_float, [ctypes.c_float]),
+            "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, fp, i64]),
+            "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, fp, i64, dp, dp, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
+            "orc_adjoint": (i64, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64]),
+            "orc_batch_sizes": (None, [u64, i64, i64p]),
+            "orc_num_threads": (ctypes.c_int, []),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _i64p(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+def _fortran(a, dtype):
+    a = np.asarray(a, dtype=dtype)
+    return np.asfortranarray(a)
+
+
+def num_threads() -> int:
+    return int(_load().orc_num_threads())
+
+
+# --- generator -------------------------------------------------------------
+
+def sm64_next(state: int, c: int) -> int:
+    """c-th SplitMix64 output (c >= 1) from initial state ``state``."""
+    return int(_load().orc_sm64_next(state & (2**64 - 1), c & (2**64 - 1)))
+
+
+def stream_key(seed: int, stream: int) -> int:
+    return int(_load().orc_stream_key(seed, stream))
+
+
+def raw(key: int, idx: int) -> int:
+    return int(_load().orc_raw(key, idx))
+
+
+def generate(seed: int, stream: int, m: int, ncols: int, dominant: bool = False) -> np.ndarray:
+    """m x ncols matrix of stream ``stream`` (Fortran order)."""
+    A = np.empty((m, ncols), dtype=np.float64, order="F")
+    _load().orc_generate(seed, stream, m, ncols, int(bool(dominant)), _dp(A), max(m, 1))
+    return A
+
+
+def batch_sizes(seed: int, count: int) -> np.ndarray:
+    out = np.empty(count, dtype=np.int64)
+    _load().orc_batch_sizes(seed, count, _i64p(out))
+    return out
+
+
+# --- HPL ---------------------------------------------------------------------
+
+def getrf(A):
+    """LU with partial pivoting. Returns (LU, ipiv, info, min_gap)."""
+    LU = _fortran(A, np.float64).copy(order="F")
+    n = LU.shape[0]
+    assert LU.shape == (n, n)
+    ipiv = np.zeros(n, dtype=np.int32)
+    gap = ctypes.c_double(0.0)
+    info = _load().orc_getrf(n, _dp(LU), max(n, 1), _ip(ipiv), ctypes.byref(gap))
+    return LU, ipiv, int(info), float(gap.value)
+
+
+def getrs(LU, ipiv, B, trans: int = 0):
+    LU = _fortran(LU, np.float64)
+    X = _fortran(B, np.float64).copy(order="F")
+    vec = X.ndim == 1
+    if vec:
+        X = X.reshape(-1, 1, order="F")
+    n, nrhs = X.shape
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    _load().orc_getrs(n, nrhs, _dp(LU), max(n, 1), _ip(ipiv), int(trans), _dp(X), max(n, 1))
+    return X[:, 0].copy() if vec else X
+
+
+def solve(A, B):
+    LU, ipiv, info, _ = getrf(A)
+    return getrs(LU, ipiv, B), info
+
+
+def scaled_residual(A, x, b) -> float:
+    A = _fortran(A, np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = A.shape[0]
+    return float(_load().orc_scaled_residual(n, _dp(A), max(n, 1), _dp(x), _dp(b)))
+
+
+def scaled_residual_gen(seed: int, n: int, dominant: bool, x, b) -> float:
+    """Scaled residual with A regenerated from (seed, stream 0)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    return float(_load().orc_scaled_residual_gen(seed, n, int(bool(dominant)), _dp(x), _dp(b)))
+
+
+def perm_from_ipiv(ipiv) -> np.ndarray:
+    ipiv = np.ascontiguousarray(ipiv, dtype=np.int32)
+    out = np.empty(ipiv.shape[0], dtype=np.int64)
+    _load().orc_perm_from_ipiv(ipiv.shape[0], _ip(ipiv), _i64p(out))
+    return out
+
+
+def lu_sample_diff(seed: int, n: int, dominant: bool, LU, ipiv, si, sj) -> np.ndarray:
+    """(PA - LU)_ij at sampled (i,j), A regenerated, for factors too big to redo."""
+    LU = _fortran(LU, np.float64)
+    rowmap = perm_from_ipiv(ipiv)
+    si = np.ascontiguousarray(si, dtype=np.int64)
+    sj = np.ascontiguousarray(sj, dtype=np.int64)
+    out = np.empty(si.shape[0], dtype=np.float64)
+    _load().orc_lu_sample_diff(seed, n, int(bool(dominant)), _dp(LU), LU.shape[0], _i64p(rowmap),
+                               si.shape[0], _i64p(si), _i64p(sj), _dp(out))
+    return out
+
+
+# --- HPL-MxP ------------------------------------------------------------------
+
+PREC_BF16 = 0
+PREC_FP8 = 1
+PREC_FP32 = 2
+
+
+def round_bf16(x: float) -> float:
+    return float(_load().orc_round_bf16(float(x)))
+
+
+def round_e4m3(x: float) -> float:
+    return float(_load().orc_round_e4m3(float(x)))
+
+
+def mxp_factor(A, nb: int, prec: int = PREC_BF16):
+    """Blocked unpivoted low-precision LU of FP32(A). Returns (F, info)."""
+    F = np.asfortranarray(np.asarray(A, dtype=np.float64).astype(np.float32))
+    n = F.shape[0]
+    info = _load().orc_mxp_factor(n, nb, prec, _fp(F), max(n, 1))
+    return F, int(info)
+
+
+def mxp_refine(A, F, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0):
+    """Refine with the FP32 factor F. Returns dict(x, status, iters, inner, sr, hist)."""
+    A = _fortran(A, np.float64)
+    F = np.asfortranarray(F, dtype=np.float32)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    n = A.shape[0]
+    x = np.zeros(n, dtype=np.float64)
+    it, inner = ctypes.c_int(0), ctypes.c_int(0)
+    sr = ctypes.c_double(0.0)
+    hist = np.full(max_iter + 1, np.nan)
+    st = _load().orc_mxp_refine(n, _dp(A), max(n, 1), _fp(F), max(n, 1), _dp(b), _dp(x), int(refine),
+                                int(max_iter), int(gmres_m), float(tol), ctypes.byref(it),
+                                ctypes.byref(inner), ctypes.byref(sr), _dp(hist))
+    return dict(x=x, status=int(st), iters=int(it.value), inner=int(inner.value), sr=float(sr.value),
+                hist=hist[: it.value + 1])
+
+
+def mxp_solve(A, b, nb: int, prec: int = PREC_BF16, refine: int = 1, max_iter: int = 50,
+              gmres_m: int = 30, tol: float = 16.0):
+    F, info = mxp_factor(A, nb, prec)
+    out = mxp_refine(A, F, b, refine, max_iter, gmres_m, tol)
+    out["F"] = F
+    out["info"] = info
+    return out
+
+
+# --- adjoint -------------------------------------------------------------------
+
+def adjoint(A, X, G, want_grad_a: bool = True):
+    """grad_B = A^-T G, grad_A = -grad_B X^T (FP64 LU of A)."""
+    A = _fortran(A, np.float64)
+    X = _fortran(X, np.float64)
+    G = _fortran(G, np.float64)
+    n, nrhs = G.shape
+    gB = np.empty((n, nrhs), dtype=np.float64, order="F")
+    gA = np.empty((n, n), dtype=np.float64, order="F") if want_grad_a else None
+    _load().orc_adjoint(n, nrhs, _dp(A), n, _dp(X), n, _dp(G), n, _dp(gB), n,
+                        _dp(gA) if gA is not None else None, n)
+    return gB, gA
+
+
+def flops(n: int) -> float:
+    """Operation count credited to one solve: 2n^3/3 + 2n^2."""
+    return 2.0 * n ** 3 / 3.0 + 2.0 * n ** 2

@@ -1,0 +1,641 @@
+/*
+ * CPU oracle for the dense LU solve of HPL and HPL-MxP.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes. Only the test suite, the smoke
+ * check and the CPU-baseline leg of the benchmark may load it. The product
+ * path (the CUDA library and its Python binding) never calls into it, and the
+ * two share no code: no headers, helpers, tables or constants.
+ *
+ * Everything is FP64 unless the method fixes a lower precision (the HPL-MxP
+ * emulation below). Matrices are column-major with a leading dimension, pivot
+ * vectors are 0-based int32 with LAPACK semantics (row k was swapped with row
+ * ipiv[k] >= k, in order k = 0, 1, ...).
+ *
+ * Paper references (arXiv 2604.09517, "Sustaining Exascale Performance:
+ * Lessons from HPL and HPL-MxP on Aurora"):
+ *   Sec. III-A.1 (HPL): solve Ax=b, A dense random FP64, by LU with partial
+ *     pivoting followed by triangular solves; flop count 2/3 N^3 + O(N^2).
+ *   Sec. III-A.2 (HPL-MxP): the same structure with factorization and trailing
+ *     updates in low precision, no pivoting, residual and corrections in FP64.
+ *   Sec. II-B: HPL-MxP refines with a non-stationary (GMRES-based) method and
+ *     uses a scalable generator for its input matrix.
+ * Where the paper is silent the readings are listed at each function.
+ *
+ * Parity status of each function (what pins it, in tests/):
+ *   orc_sm64_next / orc_uniform / orc_generate : published SplitMix64 outputs,
+ *       exact-rational diagonal sums, distribution moments.
+ *   orc_getrf / orc_getrs : exact rational elimination (n <= 6), Cramer's rule,
+ *       LAPACK getrf via scipy, closed forms, ||PA-LU|| invariant.
+ *   orc_scaled_residual(_gen) : closed forms and a hand-computed case.
+ *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine).
+ *   orc_mxp_factor : FP32 mode equals unpivoted LU; BF16 mode error bound.
+ *   orc_mxp_solve : converged x equals the FP64 LU solution; iteration
+ *       behaviour with an exact preconditioner (one step).
+ *   orc_adjoint : central finite differences and torch.linalg.solve autograd.
+ *   FP8 operand encoding (prec = 1): element rounding pinned; the per-block
+ *       scale choice is this build's reading, parity for FP8 iteration
+ *       counts is unpinned (only convergence is checked).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORC_GAMMA 0x9E3779B97F4A7C15ULL
+
+/* ------------------------------------------------------------------------ */
+/* Generator: SplitMix64 (Steele, Lea & Flood, "Fast splittable pseudorandom
+ * number generators", OOPSLA 2014), used as a counter-based generator.
+ * The paper only says the entries are random (Sec. III-A.1) and that HPL-MxP
+ * has a scalable generator (Sec. II-B); this definition is the build's own. */
+
+/* The SplitMix64 output function (the variant-13 mixer of the paper above). */
+static uint64_t orc_mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+/* c-th output (c >= 1) of a SplitMix64 generator whose state starts at s:
+ * the state advances by GAMMA before each output. */
+uint64_t orc_sm64_next(uint64_t s, uint64_t c) { return orc_mix64(s + c * ORC_GAMMA); }
+
+/* Key of stream `stream` under `seed`: output number stream+1 of the
+ * generator seeded with `seed`. Stream tags: A = 0, b/B = 1, batch sizes = 2,
+ * batched system s: A = 16 + 2s, b = 17 + 2s. */
+uint64_t orc_stream_key(uint64_t seed, uint64_t stream) { return orc_sm64_next(seed, stream + 1); }
+
+/* Raw 64-bit draw number idx (0-based) of a stream. */
+uint64_t orc_raw(uint64_t key, uint64_t idx) { return orc_sm64_next(key, idx + 1); }
+
+/* Entry draw: top 53 bits scaled to [0,1), shifted to [-0.5, 0.5). Exact. */
+double orc_uniform(uint64_t key, uint64_t idx) {
+    uint64_t h = orc_raw(key, idx);
+    return (double)(h >> 11) * 0x1p-53 - 0.5;
+}
+
+/* |entry| as an integer multiple of 2^-53 (exact): |(h>>11) - 2^52|. */
+static uint64_t orc_abs_units(uint64_t key, uint64_t idx) {
+    uint64_t m = orc_raw(key, idx) >> 11;
+    const uint64_t half = 1ULL << 52;
+    return m >= half ? m - half : half - m;
+}
+
+/* Fill the m x ncols column-major matrix A (leading dimension lda) with the
+ * i.i.d. uniform[-0.5,0.5) entries of stream `stream`; entry (i,j) is draw
+ * number j*m + i. With dominant != 0 (square only), the diagonal entry of each
+ * row is replaced by the sum over that row of |a_ij| (the original |a_ii|
+ * included), summed exactly in 128-bit integers and rounded once to double
+ * (round to nearest even). This is the diagonally dominant HPL-MxP input. */
+void orc_generate(uint64_t seed, uint64_t stream, int64_t m, int64_t ncols, int dominant,
+                  double* A, int64_t lda) {
+    uint64_t key = orc_stream_key(seed, stream);
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < ncols; j++)
+        for (int64_t i = 0; i < m; i++)
+            A[j * lda + i] = orc_uniform(key, (uint64_t)(j * m + i));
+    if (dominant && m == ncols) {
+#pragma omp parallel for schedule(static)
+        for (int64_t i = 0; i < m; i++) {
+            unsigned __int128 s = 0;
+            for (int64_t j = 0; j < ncols; j++) s += orc_abs_units(key, (uint64_t)(j * m + i));
+            A[i * lda + i] = (double)s * 0x1p-53; /* one rounding: int128 -> double */
+        }
+    }
+}
+
+/* Entry (i,j) of the generated n x n matrix without storing the matrix. For a
+ * dominant matrix the caller supplies the row's diagonal value. */
+static double orc_entry(uint64_t key, int64_t n, int64_t i, int64_t j) {
+    return orc_uniform(key, (uint64_t)(j * n + i));
+}
+
+static double orc_row_diag(uint64_t key, int64_t n, int64_t i) {
+    unsigned __int128 s = 0;
+    for (int64_t j = 0; j < n; j++) s += orc_abs_units(key, (uint64_t)(j * n + i));
+    return (double)s * 0x1p-53;
+}
+
+/* ------------------------------------------------------------------------ */
+/* HPL: LU with partial pivoting (Sec. III-A.1), unblocked, LAPACK dgetf2
+ * semantics. Readings: the pivot is the first index attaining the largest
+ * |a_ik| (as BLAS idamax); full rows are swapped (factored L columns too);
+ * multipliers use true division by the pivot; a zero pivot records
+ * info = k+1 (first occurrence, 1-based) and the column is left unscaled.
+ * min_gap (optional) receives min over k of (max - second max)/max of the
+ * candidate magnitudes, which flags near-ties that rounding order can flip. */
+int64_t orc_getrf(int64_t n, double* A, int64_t lda, int32_t* ipiv, double* min_gap) {
+    int64_t info = 0;
+    double gap_min = INFINITY;
+    for (int64_t k = 0; k < n; k++) {
+        double* colk = A + k * lda;
+        int64_t p = k;
+        double vmax = fabs(colk[k]);
+        for (int64_t i = k + 1; i < n; i++) {
+            double v = fabs(colk[i]);
+            if (v > vmax) { vmax = v; p = i; }
+        }
+        if (min_gap && vmax > 0.0 && n - k > 1) {
+            double second = 0.0;
+            for (int64_t i = k; i < n; i++)
+                if (i != p && fabs(colk[i]) > second) second = fabs(colk[i]);
+            double g = (vmax - second) / vmax;
+            if (g < gap_min) gap_min = g;
+        }
+        ipiv[k] = (int32_t)p;
+        if (p != k) {
+            for (int64_t j = 0; j < n; j++) {
+                double t = A[j * lda + k];
+                A[j * lda + k] = A[j * lda + p];
+                A[j * lda + p] = t;
+            }
+        }
+        double piv = colk[k];
+        if (piv != 0.0) {
+            for (int64_t i = k + 1; i < n; i++) colk[i] = colk[i] / piv;
+        } else if (info == 0) {
+            info = k + 1;
+        }
+        if (piv != 0.0) {
+#pragma omp parallel for schedule(static) if (n - k > 256)
+            for (int64_t j = k + 1; j < n; j++) {
+                double* colj = A + j * lda;
+                double ukj = colj[k];
+                for (int64_t i = k + 1; i < n; i++) colj[i] -= colk[i] * ukj;
+            }
+        }
+    }
+    if (min_gap) *min_gap = gap_min;
+    return info;
+}
+
+/* Triangular solves after getrf (Sec. III-A.1 "followed by triangular
+ * solves"). trans = 0 solves A X = B: apply the interchanges to B in order,
+ * then L (unit lower) forward and U backward. trans = 1 solves A^T X = B:
+ * U^T forward, L^T backward, then the interchanges in reverse order. */
+void orc_getrs(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const int32_t* ipiv,
+               int trans, double* B, int64_t ldb) {
+#pragma omp parallel for schedule(dynamic) if (nrhs > 1)
+    for (int64_t c = 0; c < nrhs; c++) {
+        double* b = B + c * ldb;
+        if (!trans) {
+            for (int64_t k = 0; k < n; k++) {
+                int64_t p = ipiv[k];
+                if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+            }
+            for (int64_t i = 0; i < n; i++) {
+                double s = b[i];
+                for (int64_t j = 0; j < i; j++) s -= LU[j * lda + i] * b[j];
+                b[i] = s;
+            }
+            for (int64_t i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int64_t j = i + 1; j < n; j++) s -= LU[j * lda + i] * b[j];
+                b[i] = s / LU[i * lda + i];
+            }
+        } else {
+            /* U^T z = b: U^T is lower, (U^T)_ij = U_ji = LU[i*lda + j]. */
+            for (int64_t i = 0; i < n; i++) {
+                double s = b[i];
+                for (int64_t j = 0; j < i; j++) s -= LU[i * lda + j] * b[j];
+                b[i] = s / LU[i * lda + i];
+            }
+            /* L^T w = z: unit upper, (L^T)_ij = L_ji = LU[i*lda + j], j > i. */
+            for (int64_t i = n - 1; i >= 0; i--) {
+                double s = b[i];
+                for (int64_t j = i + 1; j < n; j++) s -= LU[i * lda + j] * b[j];
+                b[i] = s;
+            }
+            for (int64_t k = n - 1; k >= 0; k--) {
+                int64_t p = ipiv[k];
+                if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* HPL scaled residual (the acceptance test; the paper prints no formula, this
+ * is the standard HPL check): ||Ax-b||_inf / (eps (||A||_inf ||x||_inf +
+ * ||b||_inf) n) with eps = 2^-53. Each r_i = sum_j a_ij x_j - b_i in FP64. */
+static double orc_norm_inf_vec(int64_t n, const double* v) {
+    double m = 0.0;
+    for (int64_t i = 0; i < n; i++) if (fabs(v[i]) > m) m = fabs(v[i]);
+    return m;
+}
+
+double orc_scaled_residual(int64_t n, const double* A, int64_t lda, const double* x, const double* b) {
+    double rmax = 0.0, amax = 0.0;
+#pragma omp parallel for schedule(static) reduction(max : rmax, amax)
+    for (int64_t i = 0; i < n; i++) {
+        double r = 0.0, s = 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            double a = A[j * lda + i];
+            r += a * x[j];
+            s += fabs(a);
+        }
+        r -= b[i];
+        if (fabs(r) > rmax) rmax = fabs(r);
+        if (s > amax) amax = s;
+    }
+    double eps = 0x1p-53;
+    return rmax / (eps * (amax * orc_norm_inf_vec(n, x) + orc_norm_inf_vec(n, b)) * (double)n);
+}
+
+/* The same residual with A regenerated from (seed, stream 0) row by row, for
+ * sizes whose matrix is not kept. */
+double orc_scaled_residual_gen(uint64_t seed, int64_t n, int dominant, const double* x, const double* b) {
+    uint64_t key = orc_stream_key(seed, 0);
+    double rmax = 0.0, amax = 0.0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : rmax, amax)
+    for (int64_t i = 0; i < n; i++) {
+        double r = 0.0, s = 0.0;
+        double dii = dominant ? orc_row_diag(key, n, i) : 0.0;
+        for (int64_t j = 0; j < n; j++) {
+            double a = (dominant && j == i) ? dii : orc_entry(key, n, i, j);
+            r += a * x[j];
+            s += fabs(a);
+        }
+        r -= b[i];
+        if (fabs(r) > rmax) rmax = fabs(r);
+        if (s > amax) amax = s;
+    }
+    double eps = 0x1p-53;
+    return rmax / (eps * (amax * orc_norm_inf_vec(n, x) + orc_norm_inf_vec(n, b)) * (double)n);
+}
+
+/* Sampled factorization check for sizes the oracle cannot factor: for each
+ * sample (i,j) returns (PA)_ij - (LU)_ij with A regenerated, P from ipiv and
+ * L, U read from the factored matrix. rowmap[i] must give the original row of
+ * A that sits in position i after the interchanges (computed by the caller
+ * from ipiv, see orc_perm_from_ipiv). */
+void orc_perm_from_ipiv(int64_t n, const int32_t* ipiv, int64_t* rowmap) {
+    for (int64_t i = 0; i < n; i++) rowmap[i] = i;
+    for (int64_t k = 0; k < n; k++) {
+        int64_t p = ipiv[k];
+        if (p != k) { int64_t t = rowmap[k]; rowmap[k] = rowmap[p]; rowmap[p] = t; }
+    }
+}
+
+void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU, int64_t lda,
+                        const int64_t* rowmap, int64_t count, const int64_t* si, const int64_t* sj,
+                        double* diff) {
+    uint64_t key = orc_stream_key(seed, 0);
+#pragma omp parallel for schedule(dynamic)
+    for (int64_t t = 0; t < count; t++) {
+        int64_t i = si[t], j = sj[t];
+        int64_t r = rowmap[i];
+        double a = (dominant && r == j) ? orc_row_diag(key, n, r) : orc_entry(key, n, r, j);
+        int64_t kmax = i < j ? i : j;
+        double s = 0.0;
+        for (int64_t k = 0; k < kmax; k++) s += LU[k * lda + i] * LU[j * lda + k];
+        s += (i <= j) ? LU[j * lda + i] : LU[j * lda + i] * LU[j * lda + j];
+        diff[t] = a - s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* HPL-MxP emulation (Sec. III-A.2: low-precision factor and update, no
+ * pivoting, FP64 residual and corrections; Sec. II-B: GMRES-based refinement).
+ * Readings, none of which the paper fixes:
+ *   - working storage FP32 (FP64 -> FP32 round to nearest);
+ *   - per block step of width nb: the diagonal block is factored unpivoted in
+ *     FP32; its unit-lower and upper factors are inverted in FP32; the panel
+ *     products U12 = inv(L11) A12 and L21 = A21 inv(U11) and the trailing
+ *     update A22 -= L21 U12 take their operands rounded to the low precision
+ *     and accumulate in FP32, in increasing k;
+ *   - low precision prec = 0: BF16, round to nearest even;
+ *     prec = 1: FP8 E4M3 (finite, max 448), round to nearest even, with one
+ *     power-of-two scale per 32 consecutive elements along the contraction
+ *     index, the smallest one that keeps amax/scale <= 448;
+ *     prec = 2: no rounding (FP32 operands), a reference mode.           */
+
+/* BF16 round-to-nearest-even of a float: keep 8 significant bits. Written from
+ * the format definition (1 sign, 8 exponent, 7 stored fraction bits). */
+float orc_round_bf16(float x) {
+    if (x == 0.0f || !isfinite(x)) return x;
+    int e;
+    double f = frexp((double)x, &e);            /* x = f * 2^e, 0.5 <= |f| < 1 */
+    double q = nearbyint(ldexp(f, 8));          /* 8 significant bits, RNE */
+    double r = ldexp(q, e - 8);
+    if (fabs(r) > 3.3895313892515355e38) r = copysign(INFINITY, r); /* overflow */
+    return (float)r;
+}
+
+/* FP8 E4M3 (OCP "fn" variant) round-to-nearest-even with saturation to
+ * +-448: normals 2^-6 .. 448 with 3 fraction bits, subnormals k * 2^-9. */
+float orc_round_e4m3(float x) {
+    if (x == 0.0f) return x;
+    double a = fabs((double)x);
+    double spacing;
+    if (a < 0x1p-6) spacing = 0x1p-9;
+    else {
+        int e;
+        frexp(a, &e);                           /* a in [2^(e-1), 2^e) */
+        spacing = ldexp(1.0, e - 1 - 3);
+    }
+    double q = nearbyint(a / spacing) * spacing;
+    if (q > 448.0) q = 448.0;
+    return (float)copysign(q, (double)x);
+}
+
+/* Scale exponent for a block with max magnitude amax: smallest e with
+ * amax * 2^-e <= 448. Returns 0 for an all-zero block. */
+static int orc_e4m3_block_exp(double amax) {
+    if (amax == 0.0) return 0;
+    int e = (int)ceil(log2(amax / 448.0));
+    while (ldexp(amax, -e) > 448.0) e++;
+    while (e > -127 && ldexp(amax, -(e - 1)) <= 448.0) e--;
+    return e;
+}
+
+/* Round an operand to the low precision. X is r x c column-major (ld);
+ * kdim_is_rows says whether the contraction index runs along rows (the B
+ * operand, k x ncols) or along columns (the A operand, mrows x k). The result
+ * is the dequantised value, stored as float. */
+static void orc_round_operand(int prec, float* X, int64_t r, int64_t c, int64_t ld, int kdim_is_rows) {
+    if (prec == 2) return;
+    if (prec == 0) {
+        for (int64_t j = 0; j < c; j++)
+            for (int64_t i = 0; i < r; i++) X[j * ld + i] = orc_round_bf16(X[j * ld + i]);
+        return;
+    }
+    /* FP8 with a scale per 32 contraction elements. */
+    if (kdim_is_rows) {
+        for (int64_t j = 0; j < c; j++)
+            for (int64_t i0 = 0; i0 < r; i0 += 32) {
+                int64_t i1 = i0 + 32 < r ? i0 + 32 : r;
+                double amax = 0.0;
+                for (int64_t i = i0; i < i1; i++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
+                int e = orc_e4m3_block_exp(amax);
+                for (int64_t i = i0; i < i1; i++)
+                    X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+            }
+    } else {
+        for (int64_t i = 0; i < r; i++)
+            for (int64_t j0 = 0; j0 < c; j0 += 32) {
+                int64_t j1 = j0 + 32 < c ? j0 + 32 : c;
+                double amax = 0.0;
+                for (int64_t j = j0; j < j1; j++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
+                int e = orc_e4m3_block_exp(amax);
+                for (int64_t j = j0; j < j1; j++)
+                    X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+            }
+    }
+}
+
+/* C (m x n, ldc) = sub ? C - A*B : A*B, with A (m x k, lda) and B (k x n, ldb)
+ * float, products accumulated in FP32 in increasing k. */
+static void orc_gemm32(int64_t m, int64_t n, int64_t k, const float* A, int64_t lda,
+                       const float* B, int64_t ldb, float* C, int64_t ldc, int sub) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = 0; i < m; i++) {
+            float acc = 0.0f;
+            for (int64_t p = 0; p < k; p++) acc += A[p * lda + i] * B[j * ldb + p];
+            C[j * ldc + i] = sub ? C[j * ldc + i] - acc : acc;
+        }
+}
+
+/* Blocked unpivoted low-precision LU of the FP32 matrix A (in place). Also
+ * returns, if Linv/Uinv are non-NULL (n x nb each, block b at column offset
+ * b*nb... stored as nb-wide slices, ld = n), the FP32 inverses of the diagonal
+ * factors. Returns info = first zero pivot (1-based) or 0. */
+int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, float* A, int64_t lda) {
+    int64_t info = 0;
+    float* Li = (float*)malloc(sizeof(float) * nb * nb);
+    float* Ui = (float*)malloc(sizeof(float) * nb * nb);
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        int64_t kb = n - k0 < nb ? n - k0 : nb;
+        float* D = A + k0 * lda + k0;
+        /* 1. unpivoted FP32 getrf of the diagonal block */
+        for (int64_t c = 0; c < kb; c++) {
+            float piv = D[c * lda + c];
+            if (piv == 0.0f) { if (!info) info = k0 + c + 1; continue; }
+            for (int64_t i = c + 1; i < kb; i++) D[c * lda + i] = D[c * lda + i] / piv;
+            for (int64_t j = c + 1; j < kb; j++)
+                for (int64_t i = c + 1; i < kb; i++) D[j * lda + i] -= D[c * lda + i] * D[j * lda + c];
+        }
+        int64_t m = n - k0 - kb;
+        if (m == 0) break;
+        /* 2. inverses of the unit-lower and upper factors, column by column */
+        for (int64_t j = 0; j < kb; j++) {
+            for (int64_t i = 0; i < kb; i++) {           /* L x = e_j, forward */
+                float s = (i == j) ? 1.0f : 0.0f;
+                for (int64_t p = 0; p < i; p++) s -= D[p * lda + i] * Li[j * kb + p];
+                Li[j * kb + i] = s;
+            }
+            for (int64_t i = kb - 1; i >= 0; i--) {      /* U x = e_j, backward */
+                float s = (i == j) ? 1.0f : 0.0f;
+                for (int64_t p = i + 1; p < kb; p++) s -= D[p * lda + i] * Ui[j * kb + p];
+                Ui[j * kb + i] = s / D[i * lda + i];
+            }
+        }
+        /* 3. panel products with low-precision operands, FP32 accumulate */
+        float* A12 = A + (k0 + kb) * lda + k0;            /* kb x m */
+        float* A21 = A + k0 * lda + k0 + kb;              /* m x kb */
+        float* A22 = A + (k0 + kb) * lda + k0 + kb;       /* m x m  */
+        float* t12 = (float*)malloc(sizeof(float) * kb * m);
+        float* t21 = (float*)malloc(sizeof(float) * m * kb);
+        float* Lq = (float*)malloc(sizeof(float) * kb * kb);
+        float* Uq = (float*)malloc(sizeof(float) * kb * kb);
+        memcpy(Lq, Li, sizeof(float) * kb * kb);
+        memcpy(Uq, Ui, sizeof(float) * kb * kb);
+        for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
+        for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
+        orc_round_operand(prec, Lq, kb, kb, kb, 0);      /* A operand: k along columns */
+        orc_round_operand(prec, t12, kb, m, kb, 1);      /* B operand: k along rows    */
+        orc_round_operand(prec, t21, m, kb, m, 0);
+        orc_round_operand(prec, Uq, kb, kb, kb, 1);
+        orc_gemm32(kb, m, kb, Lq, kb, t12, kb, A12, lda, 0);   /* U12 = inv(L11) A12 */
+        orc_gemm32(m, kb, kb, t21, m, Uq, kb, A21, lda, 0);    /* L21 = A21 inv(U11) */
+        /* 4. trailing update with the rounded panels */
+        for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
+        for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
+        orc_round_operand(prec, t21, m, kb, m, 0);
+        orc_round_operand(prec, t12, kb, m, kb, 1);
+        orc_gemm32(m, m, kb, t21, m, t12, kb, A22, lda, 1);
+        free(t12); free(t21); free(Lq); free(Uq);
+    }
+    free(Li); free(Ui);
+    return info;
+}
+
+/* Preconditioner M^-1 v = U^-1 L^-1 v with the FP32 factor: v rounded to FP32,
+ * unit-lower forward and upper backward substitution in FP32, result widened. */
+static void orc_precond(int64_t n, const float* F, int64_t ldf, const double* v, double* out, float* tmp) {
+    for (int64_t i = 0; i < n; i++) tmp[i] = (float)v[i];
+    for (int64_t i = 0; i < n; i++) {
+        float s = tmp[i];
+        for (int64_t j = 0; j < i; j++) s -= F[j * ldf + i] * tmp[j];
+        tmp[i] = s;
+    }
+    for (int64_t i = n - 1; i >= 0; i--) {
+        float s = tmp[i];
+        for (int64_t j = i + 1; j < n; j++) s -= F[j * ldf + i] * tmp[j];
+        tmp[i] = s / F[i * ldf + i];
+    }
+    for (int64_t i = 0; i < n; i++) out[i] = (double)tmp[i];
+}
+
+static void orc_matvec(int64_t n, const double* A, int64_t lda, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++) s += A[j * lda + i] * x[j];
+        y[i] = s;
+    }
+}
+
+static double orc_dot(int64_t n, const double* a, const double* b) {
+    double s = 0.0;
+    for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
+    return s;
+}
+
+/* Refinement to FP64 accuracy with the low-precision factor F (Sec. III-A.2,
+ * Sec. II-B). x0 = M^-1 b. Each outer iteration computes r = b - A x in FP64
+ * and the scaled residual; it stops once that is below tol. Otherwise the
+ * correction d solves A d = r either by one preconditioner application
+ * (refine = 0, classic iterative refinement) or by GMRES with at most gmres_m
+ * Arnoldi steps, right-preconditioned by M^-1, modified Gram-Schmidt and
+ * Givens rotations in FP64, stopping early once the estimated residual is
+ * below 1e-10 of ||r||_2 (refine = 1, GMRES-IR after Carson & Higham, SIAM J.
+ * Sci. Comput. 2018, with the preconditioner on the right). Then x += d.
+ * Returns 0 when converged, 4 when max_iter corrections did not get there.
+ * iters = corrections applied, inner = preconditioner applications inside
+ * GMRES (equal to iters for refine = 0). hist (optional, max_iter+1) receives
+ * the scaled residual before each correction. */
+int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int64_t ldf,
+                   const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
+                   int* iters, int* inner, double* final_sr, double* hist) {
+    double eps = 0x1p-53;
+    double anorm = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++) s += fabs(A[j * lda + i]);
+        if (s > anorm) anorm = s;
+    }
+    double bnorm = orc_norm_inf_vec(n, b);
+    float* tmp = (float*)malloc(sizeof(float) * n);
+    double* r = (double*)malloc(sizeof(double) * n);
+    double* d = (double*)malloc(sizeof(double) * n);
+    int m = gmres_m > 0 ? gmres_m : 1;
+    double* V = (double*)malloc(sizeof(double) * n * (m + 1));
+    double* Z = (double*)malloc(sizeof(double) * n * m);
+    double* H = (double*)calloc((size_t)(m + 1) * m, sizeof(double));
+    double* cs = (double*)malloc(sizeof(double) * m);
+    double* sn = (double*)malloc(sizeof(double) * m);
+    double* g = (double*)malloc(sizeof(double) * (m + 1));
+    double* y = (double*)malloc(sizeof(double) * m);
+    orc_precond(n, F, ldf, b, x, tmp);
+    int it = 0, inn = 0, status = 4;
+    double sr = INFINITY;
+    for (;;) {
+        orc_matvec(n, A, lda, x, r);
+        for (int64_t i = 0; i < n; i++) r[i] = b[i] - r[i];
+        sr = orc_norm_inf_vec(n, r) / (eps * (anorm * orc_norm_inf_vec(n, x) + bnorm) * (double)n);
+        if (hist) hist[it] = sr;
+        if (sr < tol) { status = 0; break; }
+        if (it >= max_iter) break;
+        if (refine == 0) {
+            orc_precond(n, F, ldf, r, d, tmp);
+            inn++;
+        } else {
+            double beta = sqrt(orc_dot(n, r, r));
+            for (int64_t i = 0; i < n; i++) V[i] = r[i] / beta;
+            for (int i = 0; i <= m; i++) g[i] = 0.0;
+            g[0] = beta;
+            int j, kk = 0;
+            for (j = 0; j < m; j++) {
+                double* vj = V + (int64_t)j * n;
+                double* zj = Z + (int64_t)j * n;
+                double* w = V + (int64_t)(j + 1) * n;
+                orc_precond(n, F, ldf, vj, zj, tmp);
+                inn++;
+                orc_matvec(n, A, lda, zj, w);
+                for (int i = 0; i <= j; i++) {
+                    double h = orc_dot(n, w, V + (int64_t)i * n);
+                    H[j * (m + 1) + i] = h;
+                    for (int64_t q = 0; q < n; q++) w[q] -= h * V[(int64_t)i * n + q];
+                }
+                double hn = sqrt(orc_dot(n, w, w));
+                H[j * (m + 1) + j + 1] = hn;
+                if (hn != 0.0) for (int64_t q = 0; q < n; q++) w[q] /= hn;
+                for (int i = 0; i < j; i++) {          /* previous rotations */
+                    double a = H[j * (m + 1) + i], c = H[j * (m + 1) + i + 1];
+                    H[j * (m + 1) + i] = cs[i] * a + sn[i] * c;
+                    H[j * (m + 1) + i + 1] = -sn[i] * a + cs[i] * c;
+                }
+                double a = H[j * (m + 1) + j], c = H[j * (m + 1) + j + 1];
+                double rho = hypot(a, c);
+                cs[j] = a / rho;
+                sn[j] = c / rho;
+                H[j * (m + 1) + j] = rho;
+                H[j * (m + 1) + j + 1] = 0.0;
+                g[j + 1] = -sn[j] * g[j];
+                g[j] = cs[j] * g[j];
+                kk = j + 1;
+                if (fabs(g[j + 1]) <= 1e-10 * beta || hn == 0.0) break;
+            }
+            for (int i = kk - 1; i >= 0; i--) {       /* back substitution H y = g */
+                double s = g[i];
+                for (int q = i + 1; q < kk; q++) s -= H[q * (m + 1) + i] * y[q];
+                y[i] = s / H[i * (m + 1) + i];
+            }
+            for (int64_t q = 0; q < n; q++) d[q] = 0.0;
+            for (int i = 0; i < kk; i++)
+                for (int64_t q = 0; q < n; q++) d[q] += y[i] * Z[(int64_t)i * n + q];
+        }
+        for (int64_t i = 0; i < n; i++) x[i] += d[i];
+        it++;
+    }
+    if (iters) *iters = it;
+    if (inner) *inner = inn;
+    if (final_sr) *final_sr = sr;
+    free(tmp); free(r); free(d); free(V); free(Z); free(H); free(cs); free(sn); free(g); free(y);
+    return status;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of x = A^-1 b (not in the paper; the differentiable form of the
+ * solve): grad_B = A^-T G and grad_A = -grad_B X^T, with the FP64 LU of A. */
+int64_t orc_adjoint(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
+                    const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA, int64_t ldga) {
+    double* LU = (double*)malloc(sizeof(double) * n * n);
+    int32_t* ipiv = (int32_t*)malloc(sizeof(int32_t) * n);
+    for (int64_t j = 0; j < n; j++) memcpy(LU + j * n, A + j * lda, sizeof(double) * n);
+    int64_t info = orc_getrf(n, LU, n, ipiv, NULL);
+    for (int64_t c = 0; c < nrhs; c++) memcpy(gradB + c * ldgb, G + c * ldg, sizeof(double) * n);
+    orc_getrs(n, nrhs, LU, n, ipiv, 1, gradB, ldgb);
+    if (gradA) {
+#pragma omp parallel for schedule(static)
+        for (int64_t j = 0; j < n; j++)
+            for (int64_t i = 0; i < n; i++) {
+                double s = 0.0;
+                for (int64_t c = 0; c < nrhs; c++) s += gradB[c * ldgb + i] * X[c * ldx + j];
+                gradA[j * ldga + i] = -s;
+            }
+    }
+    free(LU); free(ipiv);
+    return info;
+}
+
+/* Batched workload sizes: n_s = 32 + (draw s of stream 2 mod 481), i.e.
+ * uniform on [32, 512] up to a modulo bias below 1e-16. */
+void orc_batch_sizes(uint64_t seed, int64_t count, int64_t* nout) {
+    uint64_t key = orc_stream_key(seed, 2);
+    for (int64_t s = 0; s < count; s++) nout[s] = 32 + (int64_t)(orc_raw(key, (uint64_t)s) % 481ULL);
+}
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,431 @@
+"""Pins of the CPU oracle against facts that do not come from the oracle.
+
+Each test checks one oracle function against an external fact: a published
+value, exact rational arithmetic, Cramer's rule, a library routine (LAPACK
+through scipy, PyTorch casts and autograd), a closed form or an invariant.
+"""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+EPS = 2.0 ** -53
+
+
+def _read_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(line)
+    return rows
+
+
+# --- generator ---------------------------------------------------------------
+
+def test_splitmix64_published_outputs(orc):
+    want = [int(v, 16) for v in _read_golden("splitmix64_state0.txt")]
+    got = [orc.sm64_next(0, c) for c in (1, 2, 3)]
+    assert got == want
+
+
+def test_uniform_entries_on_53bit_grid(orc):
+    A = orc.generate(7, orc.STREAM_A, 300, 200)
+    assert A.min() >= -0.5 and A.max() < 0.5
+    units = (A + 0.5) * 2.0 ** 53
+    assert np.all(units == np.floor(units))
+    # the entry is the top 53 bits of the raw draw (stream key, then draw j*m+i)
+    key = orc.stream_key(7, orc.STREAM_A)
+    for (i, j) in [(0, 0), (5, 3), (299, 199)]:
+        assert A[i, j] == (orc.raw(key, j * 300 + i) >> 11) * 2.0 ** -53 - 0.5
+
+
+def test_uniform_moments(orc):
+    A = orc.generate(11, orc.STREAM_A, 1000, 1000)
+    N = A.size
+    assert abs(A.mean()) < 5 * math.sqrt(1 / 12 / N)
+    assert abs(A.var() - 1 / 12) < 5 * math.sqrt(1 / 180 / N)
+    # different streams / seeds are different draws
+    B = orc.generate(11, orc.STREAM_B, 1000, 1)
+    assert not np.array_equal(A[:, 0], B[:, 0])
+    assert abs(np.corrcoef(A[:, 0], B[:, 0])[0, 1]) < 0.15
+
+
+def test_dominant_diagonal_is_exact_row_sum(orc):
+    n = 9
+    G = orc.generate(3, orc.STREAM_A, n, n, dominant=False)
+    D = orc.generate(3, orc.STREAM_A, n, n, dominant=True)
+    off = ~np.eye(n, dtype=bool)
+    assert np.array_equal(D[off], G[off])
+    for i in range(n):
+        s = sum(abs(Fraction(float(v))) for v in G[i, :])   # exact dyadic sum
+        assert D[i, i] == float(s)                           # one correct rounding
+        assert D[i, i] > sum(abs(G[i, j]) for j in range(n) if j != i)
+
+
+def test_batch_sizes_range(orc):
+    s = orc.batch_sizes(5, 4096)
+    assert s.min() >= 32 and s.max() <= 512
+    assert abs(s.mean() - 272) < 10
+    assert len(np.unique(s)) > 400
+
+
+# --- getrf / getrs -------------------------------------------------------------
+
+def _exact_lu(A):
+    """Gaussian elimination with partial pivoting in exact rationals."""
+    n = len(A)
+    M = [[Fraction(float(A[i, j])) for j in range(n)] for i in range(n)]
+    ipiv = []
+    for k in range(n):
+        p = max(range(k, n), key=lambda i: (abs(M[i][k]), -i))
+        ipiv.append(p)
+        M[k], M[p] = M[p], M[k]
+        if M[k][k] != 0:
+            for i in range(k + 1, n):
+                M[i][k] = M[i][k] / M[k][k]
+                for j in range(k + 1, n):
+                    M[i][j] -= M[i][k] * M[k][j]
+    return M, ipiv
+
+
+def _det(M):
+    n = len(M)
+    if n == 1:
+        return M[0][0]
+    return sum((-1) ** j * M[0][j] * _det([row[:j] + row[j + 1:] for row in M[1:]]) for j in range(n))
+
+
+@pytest.mark.parametrize("n,seed", [(1, 1), (2, 2), (3, 3), (4, 4), (5, 5), (6, 6)])
+def test_getrf_matches_exact_rational_elimination(orc, n, seed):
+    A = orc.generate(seed, orc.STREAM_A, n, n)
+    LU, ipiv, info, gap = orc.getrf(A)
+    M, ipiv_exact = _exact_lu(A)
+    assert info == 0
+    assert list(ipiv) == ipiv_exact
+    exact = np.array([[float(v) for v in row] for row in M])
+    assert np.allclose(LU, exact, rtol=0, atol=1e-13 * max(1.0, np.abs(exact).max()))
+
+
+@pytest.mark.parametrize("n,seed", [(2, 1), (3, 2), (4, 3), (5, 4)])
+def test_getrs_matches_cramer(orc, n, seed):
+    A = orc.generate(seed, orc.STREAM_A, n, n)
+    b = orc.generate(seed, orc.STREAM_B, n, 1)[:, 0]
+    LU, ipiv, info, _ = orc.getrf(A)
+    x = orc.getrs(LU, ipiv, b)
+    Mq = [[Fraction(float(A[i, j])) for j in range(n)] for i in range(n)]
+    bq = [Fraction(float(v)) for v in b]
+    d = _det(Mq)
+    xq = []
+    for c in range(n):
+        Mc = [row[:] for row in Mq]
+        for i in range(n):
+            Mc[i][c] = bq[i]
+        xq.append(_det(Mc) / d)
+    xe = np.array([float(v) for v in xq])
+    kappa = np.linalg.cond(A, np.inf)
+    assert np.max(np.abs(x - xe)) / np.max(np.abs(xe)) <= 4 * n * kappa * EPS
+
+
+def test_lu_2x2_by_hand(orc):
+    rows = dict((r.split()[0], r.split()[1:]) for r in _read_golden("lu_2x2_by_hand.txt"))
+    A = np.array([float(Fraction(v)) for v in rows["A"]]).reshape(2, 2)
+    LU, ipiv, info, _ = orc.getrf(A)
+    assert list(ipiv) == [int(v) for v in rows["ipiv"]]
+    assert LU[1, 0] == float(Fraction(rows["L10"][0]))
+    U = [float(Fraction(v)) for v in rows["U"]]
+    assert LU[0, 0] == U[0] and LU[0, 1] == U[1]
+    assert abs(LU[1, 1] - U[2]) <= 2 * EPS
+    b = np.array([float(Fraction(v)) for v in rows["b"]])
+    x = orc.getrs(LU, ipiv, b)
+    xe = np.array([float(Fraction(v)) for v in rows["x"]])
+    assert np.allclose(x, xe, rtol=0, atol=1e-14)
+
+
+@pytest.mark.parametrize("n,seed", [(64, 1), (257, 2), (1024, 3)])
+def test_getrf_pivots_match_lapack(orc, n, seed):
+    sl = pytest.importorskip("scipy.linalg")
+    A = orc.generate(seed, orc.STREAM_A, n, n)
+    LU, ipiv, info, gap = orc.getrf(A)
+    lu, piv = sl.lu_factor(A)
+    assert info == 0
+    if gap > 1e-12:
+        assert np.array_equal(ipiv, piv.astype(np.int32))
+    assert np.max(np.abs(LU - lu)) < 1e-9 * n
+
+
+@pytest.mark.parametrize("n", [100, 512])
+def test_getrf_backward_error_invariant(orc, n):
+    A = orc.generate(n, orc.STREAM_A, n, n)
+    LU, ipiv, info, _ = orc.getrf(A)
+    L = np.tril(LU, -1) + np.eye(n)
+    U = np.triu(LU)
+    rowmap = orc.perm_from_ipiv(ipiv)
+    PA = A[rowmap, :]
+    err = np.abs(PA - L @ U).sum(axis=1).max()
+    assert err / (n * EPS * np.abs(A).sum(axis=1).max()) < 10
+    assert np.abs(np.tril(LU, -1)).max() <= 1.0
+    b = orc.generate(n, orc.STREAM_B, n, 1)[:, 0]
+    x = orc.getrs(LU, ipiv, b)
+    assert orc.scaled_residual(A, x, b) < 16
+
+
+def test_getrf_closed_forms(orc):
+    n = 6
+    LU, ipiv, info, _ = orc.getrf(np.eye(n))
+    assert np.array_equal(LU, np.eye(n)) and list(ipiv) == list(range(n)) and info == 0
+    perm = [3, 0, 5, 1, 4, 2]
+    P = np.zeros((n, n))
+    for i, p in enumerate(perm):
+        P[i, p] = 1.0
+    LU, ipiv, info, _ = orc.getrf(P)
+    rowmap = orc.perm_from_ipiv(ipiv)
+    assert np.array_equal(P[rowmap, :], np.eye(n)) and np.array_equal(LU, np.eye(n))
+    U = np.triu(orc.generate(4, orc.STREAM_A, n, n)) + 4 * np.eye(n)
+    LU, ipiv, info, _ = orc.getrf(U)
+    assert np.array_equal(LU, U) and list(ipiv) == list(range(n))
+    d = np.array([2.0, -4.0, 0.5, 8.0, -1.0, 16.0])
+    b = np.array([1.0, 3.0, -2.0, 5.0, 7.0, -9.0])
+    LU, ipiv, info, _ = orc.getrf(np.diag(d))
+    x = orc.getrs(LU, ipiv, b)
+    assert np.array_equal(x, b / d)
+
+
+def test_getrf_singular_reports_first_zero_pivot(orc):
+    n = 8
+    A = orc.generate(9, orc.STREAM_A, n, n)
+    A[:, 2] = 0.0
+    A[:, 5] = 0.0
+    _, _, info, _ = orc.getrf(A)
+    assert info == 3
+    _, _, info, _ = orc.getrf(np.zeros((3, 3)))
+    assert info == 1
+
+
+@pytest.mark.parametrize("n", [37, 200])
+def test_getrs_transpose_and_multi_rhs(orc, n):
+    A = orc.generate(n, orc.STREAM_A, n, n)
+    B = orc.generate(n, orc.STREAM_B, n, 3)
+    LU, ipiv, _, _ = orc.getrf(A)
+    X = orc.getrs(LU, ipiv, B, trans=0)
+    XT = orc.getrs(LU, ipiv, B, trans=1)
+    assert np.allclose(X, np.linalg.solve(A, B), rtol=0, atol=1e-10)
+    assert np.allclose(XT, np.linalg.solve(A.T, B), rtol=0, atol=1e-10)
+
+
+# --- residual --------------------------------------------------------------------
+
+def test_scaled_residual_closed_form(orc):
+    n = 4
+    A = np.eye(n)
+    b = np.array([1.0, -2.0, 0.5, 0.25])
+    assert orc.scaled_residual(A, b, b) == 0.0
+    delta = 2.0 ** -40
+    x = b.copy()
+    x[0] += delta
+    want = delta / (EPS * (1.0 * np.abs(x).max() + np.abs(b).max()) * n)
+    assert orc.scaled_residual(A, x, b) == pytest.approx(want, rel=1e-15)
+    # ||A||_inf is the maximum absolute row sum
+    A2 = np.array([[1.0, -3.0], [2.0, 0.5]])
+    x2 = np.array([1.0, 1.0])
+    b2 = A2 @ x2 + np.array([0.0, 1e-12])
+    want2 = 1e-12 / (EPS * (4.0 * 1.0 + np.abs(b2).max()) * 2)
+    assert orc.scaled_residual(A2, x2, b2) == pytest.approx(want2, rel=1e-3)
+
+
+@pytest.mark.parametrize("dominant", [False, True])
+def test_scaled_residual_regenerated_matches_stored(orc, dominant):
+    n = 150
+    A = orc.generate(21, orc.STREAM_A, n, n, dominant=dominant)
+    b = orc.generate(21, orc.STREAM_B, n, 1)[:, 0]
+    x = np.linalg.solve(A, b)
+    x[3] += 1e-9
+    assert orc.scaled_residual_gen(21, n, dominant, x, b) == orc.scaled_residual(A, x, b)
+
+
+def test_lu_sample_diff(orc):
+    n = 80
+    A = orc.generate(2, orc.STREAM_A, n, n)
+    LU, ipiv, _, _ = orc.getrf(A)
+    rng = np.random.default_rng(0)
+    si, sj = rng.integers(0, n, 200), rng.integers(0, n, 200)
+    d = orc.lu_sample_diff(2, n, False, LU, ipiv, si, sj)
+    assert np.abs(d).max() < 1e-13
+    LU2 = LU.copy()
+    LU2[10, 20] += 1e-6       # a planted error in the factor must show
+    d2 = orc.lu_sample_diff(2, n, False, LU2, ipiv, np.array([10]), np.array([20]))
+    assert abs(d2[0]) > 1e-7
+
+
+# --- low precision rounding ------------------------------------------------------
+
+def _tie_cases_bf16():
+    base = np.array([1.0, 1.5, -3.25, 1e-30, 7e20, 0.1], dtype=np.float32).view(np.uint32)
+    out = []
+    for b in base:
+        hi = b & 0xFFFF0000
+        for low in (0x8000, 0x7FFF, 0x8001, 0x0001, 0xFFFF):
+            out.append(np.uint32(hi | low))
+        out.append(np.uint32(hi | 0x18000))
+    return np.array(out, dtype=np.uint32).view(np.float32)
+
+
+def test_round_bf16_matches_torch(orc):
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(1)
+    vals = np.concatenate([rng.standard_normal(2000).astype(np.float32) * 10.0 ** rng.integers(-20, 20, 2000),
+                           _tie_cases_bf16()]).astype(np.float32)
+    want = torch.from_numpy(vals).to(torch.bfloat16).float().numpy()
+    got = np.array([orc.round_bf16(v) for v in vals], dtype=np.float32)
+    assert np.array_equal(got, want)
+
+
+def test_round_e4m3_matches_torch(orc):
+    torch = pytest.importorskip("torch")
+    if not hasattr(torch, "float8_e4m3fn"):
+        pytest.skip("no float8 in this torch")
+    rng = np.random.default_rng(2)
+    vals = rng.uniform(-448, 448, 3000).astype(np.float32)
+    small = (rng.standard_normal(2000) * 2.0 ** rng.integers(-12, 4, 2000)).astype(np.float32)
+    grid = np.array([k * 2.0 ** -10 for k in range(-40, 41)], dtype=np.float32)  # subnormal ties
+    vals = np.concatenate([vals, small, grid, np.float32([448.0, -448.0, 0.0, 1.0625, 1.1875])])
+    want = torch.from_numpy(vals).to(torch.float8_e4m3fn).float().numpy()
+    got = np.array([orc.round_e4m3(v) for v in vals], dtype=np.float32)
+    assert np.array_equal(got, want)
+    assert orc.round_e4m3(1000.0) == 448.0 and orc.round_e4m3(-500.0) == -448.0
+
+
+# --- HPL-MxP emulation ---------------------------------------------------------------
+
+def test_mxp_factor_fp32_mode_is_unpivoted_lu(orc):
+    n, nb = 96, 32
+    A = orc.generate(4, orc.STREAM_A, n, n, dominant=True)
+    F, info = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    LU, ipiv, _, _ = orc.getrf(A)
+    assert info == 0 and list(ipiv) == list(range(n))     # dominance: no interchanges
+    rel = np.abs(F - LU).max() / np.abs(LU).max()
+    assert rel < 1e-5
+
+
+def test_mxp_factor_lowprec_error_levels(orc):
+    n, nb = 192, 64
+    A = orc.generate(5, orc.STREAM_A, n, n, dominant=True)
+
+    def err(prec):
+        F, _ = orc.mxp_factor(A, nb, prec)
+        F = F.astype(np.float64)
+        L = np.tril(F, -1) + np.eye(n)
+        U = np.triu(F)
+        return np.abs(A - L @ U).max() / np.abs(A).max()
+
+    e32, e16, e8 = err(orc.PREC_FP32), err(orc.PREC_BF16), err(orc.PREC_FP8)
+    assert e32 < 1e-6
+    assert 1e-6 < e16 < 2.0 ** -8
+    assert e16 < e8 < 2.0 ** -4
+
+
+def test_mxp_factor_diagonal_matrix_exact(orc):
+    d = np.array([3.0, 5.0, 0.25, 8.0, 2.0, 1.0])
+    F, info = orc.mxp_factor(np.diag(d), 4, orc.PREC_BF16)
+    assert np.array_equal(F, np.diag(d).astype(np.float32))
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1])
+def test_mxp_solve_reaches_fp64_solution(orc, refine, prec):
+    n, nb = 256, 64
+    A = orc.generate(6, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(6, orc.STREAM_B, n, 1)[:, 0]
+    out = orc.mxp_solve(A, b, nb, prec=prec, refine=refine)
+    assert out["status"] == 0 and out["sr"] < 16
+    x64, _ = orc.solve(A, b)
+    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 1e-13
+    assert 1 <= out["iters"] <= 20
+
+
+def test_mxp_identity_needs_no_correction(orc):
+    n = 16
+    b = np.array([float(np.float32(v)) for v in np.linspace(-1, 1, n)])
+    out = orc.mxp_solve(np.eye(n), b, 8)
+    assert out["iters"] == 0 and out["sr"] == 0.0 and np.array_equal(out["x"], b)
+
+
+def test_mxp_gmres_beats_classic_ir(orc):
+    n, nb = 256, 64
+    A = orc.generate(8, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(8, orc.STREAM_B, n, 1)[:, 0]
+    ir = orc.mxp_solve(A, b, nb, prec=orc.PREC_FP8, refine=0)
+    gm = orc.mxp_solve(A, b, nb, prec=orc.PREC_FP8, refine=1)
+    assert gm["iters"] <= ir["iters"]
+
+
+def test_mxp_refine_not_converged_status(orc):
+    n = 64
+    A = orc.generate(9, orc.STREAM_A, n, n)          # general matrix: unpivoted LU unstable
+    b = orc.generate(9, orc.STREAM_B, n, 1)[:, 0]
+    F = np.asfortranarray(np.eye(n, dtype=np.float32))  # useless preconditioner
+    out = orc.mxp_refine(A, F, b, refine=0, max_iter=2)
+    assert out["status"] == 4 and out["iters"] == 2
+
+
+# --- adjoint ---------------------------------------------------------------------
+
+def test_adjoint_matches_finite_differences(orc):
+    n, nrhs = 8, 2
+    A = orc.generate(12, orc.STREAM_A, n, n, dominant=True)
+    B = orc.generate(12, orc.STREAM_B, n, nrhs)
+    G = np.random.default_rng(3).standard_normal((n, nrhs))
+    X = np.linalg.solve(A, B)
+    gB, gA = orc.adjoint(A, X, G)
+
+    def f(Am, Bm):
+        return float(np.sum(G * np.linalg.solve(Am, Bm)))
+
+    for (i, j) in [(0, 0), (3, 5), (7, 1)]:
+        h = 1e-6 * max(1.0, abs(A[i, j]))
+        Ap, Am = A.copy(), A.copy()
+        Ap[i, j] += h
+        Am[i, j] -= h
+        fd = (f(Ap, B) - f(Am, B)) / (2 * h)
+        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
+    for (i, c) in [(0, 0), (5, 1)]:
+        h = 1e-6
+        Bp, Bm = B.copy(), B.copy()
+        Bp[i, c] += h
+        Bm[i, c] -= h
+        fd = (f(A, Bp) - f(A, Bm)) / (2 * h)
+        assert abs(fd - gB[i, c]) <= 1e-6 * max(1.0, abs(gB[i, c]))
+
+
+def test_adjoint_matches_torch_autograd(orc):
+    torch = pytest.importorskip("torch")
+    n, nrhs = 24, 3
+    A = orc.generate(13, orc.STREAM_A, n, n)
+    B = orc.generate(13, orc.STREAM_B, n, nrhs)
+    G = np.random.default_rng(4).standard_normal((n, nrhs))
+    At = torch.tensor(A, requires_grad=True)
+    Bt = torch.tensor(B, requires_grad=True)
+    Xt = torch.linalg.solve(At, Bt)
+    (Xt * torch.tensor(G)).sum().backward()
+    gB, gA = orc.adjoint(A, Xt.detach().numpy(), G)
+    assert np.abs(gB - Bt.grad.numpy()).max() <= 1e-10 * np.abs(gB).max()
+    assert np.abs(gA - At.grad.numpy()).max() <= 1e-10 * np.abs(gA).max()
+
+
+def test_adjoint_closed_forms(orc):
+    n, nrhs = 5, 2
+    G = np.arange(10, dtype=np.float64).reshape(n, nrhs)
+    X = np.ones((n, nrhs))
+    gB, gA = orc.adjoint(np.eye(n), X, G)
+    assert np.array_equal(gB, G) and np.array_equal(gA, -G @ X.T)
+    d = np.array([2.0, 4.0, 8.0, 0.5, 0.25])
+    gB, _ = orc.adjoint(np.diag(d), X, G)
+    assert np.allclose(gB, G / d[:, None], rtol=1e-15)
+
+
+def test_flop_count(orc):
+    assert orc.flops(1024) == 2 * 1024 ** 3 / 3 + 2 * 1024 ** 2
