@@ -1,0 +1,331 @@
+#!/usr/bin/env python
+"""Benchmark: HPL FP64 LU solve (n=32768, NB=256, depth-1 look-ahead) on GB300.
+
+One step = one full solve of a fresh seeded system: lu_factor (PFACT, SWAP,
+DTRSM, DGEMM update, look-ahead) + lu_solve, all in the library's CUDA
+kernels through the C ABI. The matrix (8.6 GB) is regenerated on the device
+before each step, outside the timed interval; it is far larger than L2, so no
+L2 flush is needed. value = credited flops (2n^3/3 + 2n^2) / time, summed over
+ranks, divided by the slowest rank's time.
+
+Prints one JSON line (rank 0). --impl reference times the CPU oracle on a
+bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Solve TFLOP/s (2n³/3+2n²): FP64 LU vs MxP+IR at HPL residual<16, % peak"
+FP64_FLOP_PER_CLK_PER_SM = 4.0      # 2 DFMA/clk/SM: nominal 1.25 TF/s / (152 SMs * 2.07 GHz)
+NUM_SMS = 152
+MAX_SM_MHZ = 2070.0
+
+
+def flops(n: int) -> float:
+    return 2.0 * n ** 3 / 3.0 + 2.0 * n ** 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=32768)
+    ap.add_argument("--nb", type=int, default=256)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--cpu-sample-n", type=int, default=6144)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(a):
+    return {"workload": f"hpl_fp64_lu_n{a.n}_nb{a.nb}_lookahead1", "n": a.n, "nb": a.nb, "nrhs": 1,
+            "lookahead": 1, "seed": a.seed, "matrix": "i.i.d. uniform[-0.5,0.5) FP64, SplitMix64 counter generator",
+            "l2": f"inputs larger than L2 ({8.0 * a.n * a.n / 1e9:.1f} GB matrix), no flush",
+            "parallelism": "replicas (one independent solve per GPU)"}
+
+
+# --- distributed plumbing ----------------------------------------------------------
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+
+    def init(self, backend):
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group(backend=backend)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v: float) -> float:
+        if not self.pg:
+            return v
+        import torch
+        dev = "cuda" if torch.cuda.is_available() else "cpu"
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# --- clocks --------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+            self.fh = os.fdopen(fd, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.dev), "-lms", "200"], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for k, v in zip(names[1:], parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(k)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+# --- oracle timing (CPU baseline and the reference arm) ------------------------------
+
+def time_oracle(n: int, seed: int):
+    import oracle
+    A = oracle.generate(seed, oracle.STREAM_A, n, n)
+    b = oracle.generate(seed, oracle.STREAM_B, n, 1)[:, 0]
+    t0 = time.perf_counter()
+    LU, ipiv, info, _ = oracle.getrf(A)
+    x = oracle.getrs(LU, ipiv, b)
+    dt = time.perf_counter() - t0
+    return dt, oracle.num_threads(), oracle.scaled_residual(A, x, b)
+
+
+def run_reference(a, d: Dist):
+    if d.rank != 0:
+        return
+    n = 4096
+    for _ in range(a.warmup):
+        time_oracle(n, a.seed)
+    times = []
+    sr = None
+    cores = 1
+    for _ in range(a.steps):
+        dt, cores, sr = time_oracle(n, a.seed)
+        times.append(dt)
+    total = sum(times)
+    value = flops(n) * len(times) / total / 1e12
+    sample = f"oracle getrf+getrs (unblocked, OpenMP over columns) at n={n} per step"
+    line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(a), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "scaled_residual": sr}
+    print(json.dumps(line), flush=True)
+
+
+# --- our arm -------------------------------------------------------------------------
+
+def run_ours(a, d: Dist):
+    import torch
+
+    import paper_2604_09517_gb300 as hpl
+
+    torch.cuda.set_device(d.local)
+    dev = torch.device("cuda", d.local)
+    hpl.load()
+    n, nb, seed = a.n, a.nb, a.seed
+    A = hpl.colmajor(n, n, device=dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    b0 = torch.empty(n, dtype=torch.float64, device=dev)
+    ipiv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = hpl.Info(dev)
+    opts = hpl.make_opts(nb=nb, lookahead=1)
+    lib = hpl.load()
+    import ctypes
+    ws = hpl.workspace(lib.lu_factor_workspace_size(n, ctypes.byref(opts)), dev)
+    sws = hpl.workspace(lib.lu_solve_workspace_size(n, 1), dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def regenerate():
+        hpl.generate(seed, hpl.STREAM_A, n, n, out=A)
+        hpl.generate(seed, hpl.STREAM_B, n, 1, out=b.view(n, 1))
+        b0.copy_(b)
+
+    def solve():
+        hpl.lu_factor(A, nb=nb, lookahead=1, ipiv=ipiv, ws=ws, info=info)
+        hpl.lu_solve(A, ipiv, b, ws=sws)
+
+    for _ in range(a.warmup):
+        regenerate()
+        solve()
+    torch.cuda.synchronize(dev)
+
+    clocks = ClockSampler(d.local)
+    clocks.start()
+    hpl.set_phase_timing(True)
+    step_ms = []
+    launches = 0
+    for _ in range(a.steps):
+        regenerate()
+        d.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = hpl.launch_count()
+        e0.record(stream)
+        solve()
+        e1.record(stream)
+        launches += hpl.launch_count() - l0
+        torch.cuda.synchronize(dev)
+        d.barrier()
+        step_ms.append(e0.elapsed_time(e1))
+    phases = hpl.phase_times()
+    hpl.set_phase_timing(False)
+    clk = clocks.stop()
+    rec = info.read()
+    sr = float(hpl.scaled_residual(None, b, b0, seed=seed, kind=hpl.GEN_GENERAL))
+
+    total_ms = d.max(sum(step_ms))
+    total_flops = d.sum(flops(n) * len(step_ms))
+    value = total_flops / (total_ms * 1e-3) / 1e12
+
+    # roofline of the dominant kernel: the DGEMM trailing update (DFMA, FP64 ALU bound)
+    upd_ms, upd_flops, upd_cnt = phases["update"]
+    achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    peak = NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
+    phase_report = {k: {"ms_per_step": v[0] / max(len(step_ms), 1), "launch_intervals": v[2]}
+                    for k, v in phases.items() if v[2]}
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        regenerate()
+        A_h = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+        A_h.copy_(A)
+        b_h = b0.cpu().pin_memory()
+        x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
+        torch.cuda.synchronize(dev)
+        e2e_ms = []
+        for _ in range(a.steps):
+            d.barrier()
+            torch.cuda.synchronize(dev)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            A.copy_(A_h, non_blocking=True)
+            b.copy_(b_h, non_blocking=True)
+            solve()
+            x_h.copy_(b, non_blocking=True)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            d.barrier()
+            e2e_ms.append(e0.elapsed_time(e1))
+        e2e_total = d.max(sum(e2e_ms))
+        e2e = {"value": d.sum(flops(n) * len(e2e_ms)) / (e2e_total * 1e-3) / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n,
+               "ms_per_step": e2e_total / len(e2e_ms)}
+        del A_h
+
+    cpu = None
+    if d.rank == 0 and d.world == 1 and not a.no_cpu:
+        dt, cores, _ = time_oracle(a.cpu_sample_n, seed)
+        cpu = {"value": flops(a.cpu_sample_n) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
+               "sample": f"oracle getrf+getrs (unblocked FP64, OpenMP) of one n={a.cpu_sample_n} system, "
+                         f"{dt:.1f} s"}
+
+    if d.rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": d.world, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": total_ms / len(step_ms), "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(a),
+                "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                             "frac": achieved / peak if achieved else None, "traffic": None,
+                             "kernel": "k_dgemm_sub (DFMA trailing update)",
+                             "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
+                "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
+                "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report,
+                "fraction_of_fp64_peak": value / peak}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    d = Dist()
+    if a.impl == "reference":
+        run_reference(a, d)          # rank 0 only; other ranks exit without work
+    else:
+        d.init("nccl")
+        run_ours(a, d)
+    d.close()
+
+
+if __name__ == "__main__":
+    main()

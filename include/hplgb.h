@@ -1,0 +1,171 @@
+/*
+ * hplgb — dense LU solve of HPL and HPL-MxP on one GB300 GPU (sm_103a).
+ *
+ * C ABI. Every pointer argument is a DEVICE pointer owned by the caller unless
+ * stated otherwise; the library never frees caller memory and never calls
+ * cudaMalloc on the compute path (scratch comes from the caller's workspace,
+ * sized by the matching *_workspace_size query). Matrices are column-major
+ * with a leading dimension ld >= rows. Pivot vectors are 0-based int32 with
+ * LAPACK semantics: in order k = 0, 1, ..., row k was interchanged with row
+ * ipiv[k] >= k.
+ *
+ * `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ * Calls are asynchronous on that stream unless a function says otherwise.
+ * The return value reports argument and launch errors at once (nothing is
+ * launched when it is not HPL_OK). Conditions found on the device (a zero
+ * pivot, a timed-out wait, non-convergence) are written to the caller's
+ * hpl_info, which lives in device memory and is valid after the stream
+ * synchronizes.
+ *
+ * Paper: arXiv 2604.09517, "Sustaining Exascale Performance: Lessons from HPL
+ * and HPL-MxP on Aurora". Sec. III-A.1 defines the HPL problem (Ax=b, dense
+ * random FP64 A, LU with partial pivoting then triangular solves, 2/3 N^3 +
+ * O(N^2) flops) and the per-panel phases PFACT, SWAP, DTRSM, DGEMM with
+ * look-ahead. Sec. III-A.2 defines HPL-MxP (factor and trailing update in low
+ * precision without pivoting, residual and corrections in FP64). Sec. II-B
+ * names GMRES-based refinement and a scalable matrix generator.
+ */
+#ifndef HPLGB_H
+#define HPLGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes returned by every call and stored in hpl_info.status. */
+enum {
+    HPL_OK = 0,
+    HPL_ERR_INVALID = 1,        /* bad size, leading dimension, pointer or workspace */
+    HPL_ERR_SINGULAR = 2,       /* exact zero pivot; hpl_info.info = its 1-based index */
+    HPL_ERR_NONFINITE = 3,      /* NaN or Inf met where a finite value is required */
+    HPL_ERR_NOT_CONVERGED = 4,  /* refinement hit max_iter above the tolerance */
+    HPL_ERR_TIMEOUT = 5,        /* a bounded device-side wait gave up */
+    HPL_ERR_NOMEM = 6,          /* workspace too small */
+    HPL_ERR_CUDA = 7            /* a CUDA runtime call failed */
+};
+
+/* Generator kinds (hpl_generate). */
+enum {
+    HPL_GEN_GENERAL = 0,        /* i.i.d. uniform[-0.5, 0.5) */
+    HPL_GEN_DIAG_DOMINANT = 1   /* same, diagonal replaced by the row sum of |a_ij| */
+};
+
+/* Low-precision operand formats of the mixed-precision factorization. */
+enum { HPL_PREC_BF16 = 0, HPL_PREC_FP8_E4M3 = 1 };
+
+/* Refinement methods of the mixed-precision solve. */
+enum { HPL_REFINE_IR = 0, HPL_REFINE_GMRES = 1 };
+
+/* Options. A NULL hpl_opts* means the defaults listed here. Host memory. */
+typedef struct {
+    int64_t nb;          /* panel width NB; 0 = default (256 FP64, 1536 mixed) */
+    int32_t lookahead;   /* 0 = none, 1 = depth-1 look-ahead on a second stream (default 1) */
+    int32_t prec;        /* HPL_PREC_* for the mixed-precision factor (default BF16) */
+    int32_t refine;      /* HPL_REFINE_* (default GMRES) */
+    int32_t max_iter;    /* outer refinement iterations (default 50) */
+    int32_t gmres_m;     /* Arnoldi steps per GMRES cycle (default 30) */
+    int32_t reserved;
+    double tol;          /* scaled-residual target (default 16) */
+    int64_t timeout_ns;  /* limit for any device-side wait (default 20 s) */
+} hpl_opts;
+
+/* Result record, written on the device. Caller-allocated in device memory. */
+typedef struct {
+    int32_t status;          /* HPL_* code of the device-side outcome */
+    int32_t iters;           /* refinement corrections applied (mixed precision) */
+    int64_t info;            /* first exact zero pivot, 1-based; 0 if none */
+    double scaled_residual;  /* last scaled residual computed (mixed precision) */
+    int32_t inner_iters;     /* preconditioner applications inside GMRES */
+    int32_t reserved;
+} hpl_info;
+
+/* Fill the opts struct with the defaults above. Host pointer. */
+void hpl_default_opts(hpl_opts* opts);
+
+/* Name of a status code (static string). */
+const char* hpl_status_string(int status);
+
+/*
+ * hpl_generate — the seeded input generator (Sec. III-A.1: "random entries";
+ * Sec. II-B: HPL-MxP's scalable generator; the exact definition is this
+ * library's): entry (i,j) of the m x ncols matrix is draw number j*m + i of
+ * stream `stream_id`, i.e. SplitMix64 output j*m+i+1 from the state
+ * mix(seed + (stream_id+1)*GAMMA), mapped by its top 53 bits to
+ * uniform[-0.5, 0.5) exactly. With kind = HPL_GEN_DIAG_DOMINANT (m == ncols)
+ * the diagonal of each row becomes the sum of |a_ij| over the row, summed
+ * exactly in integers and rounded once (nearest even).
+ * Stream tags used by this library: A = 0, b/B = 1.
+ * A: device, m x ncols, ld lda >= m. Returns HPL_ERR_INVALID on bad sizes.
+ */
+int hpl_generate(uint64_t seed, uint64_t stream_id, int64_t m, int64_t ncols, int kind,
+                 double* A, int64_t lda, void* stream);
+
+/*
+ * lu_factor — HPL's LU with partial pivoting (Sec. III-A.1, phases PFACT,
+ * SWAP, DTRSM, DGEMM per panel of width NB, look-ahead depth 1 as in the
+ * paper's Table I). In place: A (n x n, lda) is overwritten by L (unit lower,
+ * below the diagonal) and U; ipiv (device, n entries) receives the pivots.
+ * The pivot of each column is the first row attaining the largest magnitude.
+ * A zero pivot sets info->info to its 1-based index, leaves that column
+ * unscaled and sets info->status = HPL_ERR_SINGULAR; the factorization goes on.
+ * ws (device) must hold lu_factor_workspace_size(n, opts) bytes.
+ * With look-ahead the call forks work onto a second, higher-priority stream
+ * and joins it back into `stream` before returning; ordering with respect to
+ * `stream` is as for a single kernel launch.
+ */
+size_t lu_factor_workspace_size(int64_t n, const hpl_opts* opts);
+int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts,
+              void* ws, size_t ws_bytes, hpl_info* info, void* stream);
+
+/*
+ * lu_solve — the triangular solves that follow the factorization
+ * (Sec. III-A.1). trans = 0 solves A X = B: the interchanges are applied to B,
+ * then L (unit lower) forward and U backward substitution. trans = 1 solves
+ * A^T X = B (U^T, then L^T, then the interchanges in reverse order).
+ * B (n x nrhs, ldb) holds b on entry and x on exit. ws must hold
+ * lu_solve_workspace_size(n, nrhs) bytes. A zero on the diagonal of U sets
+ * info->status = HPL_ERR_SINGULAR (the solve still runs; x has Inf/NaN).
+ */
+size_t lu_solve_workspace_size(int64_t n, int64_t nrhs);
+int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const int32_t* ipiv, int trans,
+             double* B, int64_t ldb, void* ws, size_t ws_bytes, hpl_info* info, void* stream);
+
+/*
+ * hpl_scaled_residual — the HPL acceptance quantity (not printed in the paper;
+ * the standard HPL check): ||A x - b||_inf / (eps (||A||_inf ||x||_inf +
+ * ||b||_inf) n), eps = 2^-53, all in FP64. A (n x n, lda) is the ORIGINAL
+ * matrix; with A == NULL it is regenerated from (seed, stream 0, kind) as
+ * hpl_generate defines it. x, b: device vectors of n. out: one device double.
+ * ws must hold hpl_residual_workspace_size(n) bytes.
+ */
+size_t hpl_residual_workspace_size(int64_t n);
+int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, int kind,
+                        const double* x, const double* b, double* out, void* ws, size_t ws_bytes,
+                        void* stream);
+
+/*
+ * Diagnostics.
+ * hplgb_launch_count: kernels launched by the library so far (process-wide).
+ * Phase timers, after the paper's per-panel performance model (Sec. III-A.1,
+ * "Performance Model": each step costs the slowest of DGEMM, PFACT + BCAST and
+ * SWAP; Sec. VI-A, Fig. 4 breaks a run down by phase): while on, lu_factor
+ * brackets each phase with CUDA events on the stream that runs it.
+ * hplgb_phase_times synchronizes those events and returns, per phase
+ * (0 PFACT, 1 SWAP, 2 DTRSM, 3 DGEMM update, 4 other), the summed milliseconds,
+ * the algorithmic work (flops; bytes moved for SWAP) and the number of timed
+ * intervals, then clears the record. ms, work, count: host arrays of 5, any
+ * may be NULL. Returns HPL_ERR_CUDA if an event query fails.
+ * hplgb_last_error: text of the last CUDA error the library met.
+ */
+long long hplgb_launch_count(void);
+void hplgb_set_phase_timing(int on);
+int hplgb_phase_times(double* ms, double* work, long long* count);
+const char* hplgb_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HPLGB_H */

@@ -74,6 +74,7 @@ def _load():
             "orc_raw": (u64, [u64, u64]),
             "orc_uniform": (ctypes.c_double, [u64, u64]),
             "orc_generate": (None, [u64, u64, i64, i64, ctypes.c_int, dp, i64]),
+            "orc_generate_at": (None, [u64, u64, i64, ctypes.c_int, i64, i64p, i64p, dp]),
             "orc_getrf": (i64, [i64, dp, i64, ip, dp]),
             "orc_getrs": (None, [i64, i64, dp, i64, ip, ctypes.c_int, dp, i64]),
             "orc_scaled_residual": (ctypes.c_double, [i64, dp, i64, dp, dp]),
@@ -142,6 +143,15 @@ def generate(seed: int, stream: int, m: int, ncols: int, dominant: bool = False)
     A = np.empty((m, ncols), dtype=np.float64, order="F")
     _load().orc_generate(seed, stream, m, ncols, int(bool(dominant)), _dp(A), max(m, 1))
     return A
+
+
+def generate_at(seed: int, stream: int, m: int, rows, cols, dominant: bool = False) -> np.ndarray:
+    """Entries (rows[t], cols[t]) of the m-row matrix of a stream."""
+    rows = np.ascontiguousarray(rows, dtype=np.int64)
+    cols = np.ascontiguousarray(cols, dtype=np.int64)
+    out = np.empty(rows.shape[0], dtype=np.float64)
+    _load().orc_generate_at(seed, stream, m, int(bool(dominant)), rows.shape[0], _i64p(rows), _i64p(cols), _dp(out))
+    return out
 
 
 def batch_sizes(seed: int, count: int) -> np.ndarray:

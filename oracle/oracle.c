@@ -108,6 +108,21 @@ void orc_generate(uint64_t seed, uint64_t stream, int64_t m, int64_t ncols, int 
     }
 }
 
+/* Sampled entries (rows[t], cols[t]) of the m-row matrix of a stream, for
+ * checks at sizes whose matrix is not kept on the host. With dominant != 0
+ * (square, m x m) a diagonal entry is the exact row sum. */
+static double orc_row_diag_stream(uint64_t key, int64_t n, int64_t i);
+void orc_generate_at(uint64_t seed, uint64_t stream, int64_t m, int dominant, int64_t count,
+                     const int64_t* rows, const int64_t* cols, double* out) {
+    uint64_t key = orc_stream_key(seed, stream);
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t t = 0; t < count; t++) {
+        int64_t i = rows[t], j = cols[t];
+        out[t] = (dominant && i == j) ? orc_row_diag_stream(key, m, i)
+                                      : orc_uniform(key, (uint64_t)(j * m + i));
+    }
+}
+
 /* Entry (i,j) of the generated n x n matrix without storing the matrix. For a
  * dominant matrix the caller supplies the row's diagonal value. */
 static double orc_entry(uint64_t key, int64_t n, int64_t i, int64_t j) {
@@ -119,6 +134,8 @@ static double orc_row_diag(uint64_t key, int64_t n, int64_t i) {
     for (int64_t j = 0; j < n; j++) s += orc_abs_units(key, (uint64_t)(j * n + i));
     return (double)s * 0x1p-53;
 }
+
+static double orc_row_diag_stream(uint64_t key, int64_t n, int64_t i) { return orc_row_diag(key, n, i); }
 
 /* ------------------------------------------------------------------------ */
 /* HPL: LU with partial pivoting (Sec. III-A.1), unblocked, LAPACK dgetf2

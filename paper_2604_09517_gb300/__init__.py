@@ -1,0 +1,244 @@
+"""hplgb: dense LU solve of HPL and HPL-MxP on one GB300 (sm_103a).
+
+Thin ctypes binding over the C ABI in ``include/hplgb.h`` (libhplgb.so, built
+in-tree from ``csrc/``). Every step of the computation runs in the library's
+CUDA kernels; this module only marshals arguments. PyTorch provides device
+memory and the current stream. There is no CPU fallback: if the library is
+missing or no GPU is present, the calls raise.
+
+Matrices are column-major: an m x n matrix is a torch tensor of shape (m, n)
+with strides (1, ld). ``colmajor(m, n)`` allocates one.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import struct
+import threading
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "HplError", "load", "build", "colmajor", "Info", "Opts", "generate", "lu_factor", "lu_solve",
+    "scaled_residual", "STATUS", "GEN_GENERAL", "GEN_DIAG_DOMINANT", "STREAM_A", "STREAM_B",
+]
+
+GEN_GENERAL = 0
+GEN_DIAG_DOMINANT = 1
+PREC_BF16 = 0
+PREC_FP8_E4M3 = 1
+REFINE_IR = 0
+REFINE_GMRES = 1
+STREAM_A = 0
+STREAM_B = 1
+
+STATUS = {0: "HPL_OK", 1: "HPL_ERR_INVALID", 2: "HPL_ERR_SINGULAR", 3: "HPL_ERR_NONFINITE",
+          4: "HPL_ERR_NOT_CONVERGED", 5: "HPL_ERR_TIMEOUT", 6: "HPL_ERR_NOMEM", 7: "HPL_ERR_CUDA"}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class HplError(RuntimeError):
+    def __init__(self, status: int, where: str = ""):
+        self.status = status
+        msg = f"{where}: {STATUS.get(status, status)}"
+        if status == 7 and _lib is not None:
+            msg += " (" + _lib.hplgb_last_error().decode(errors="replace") + ")"
+        super().__init__(msg)
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("nb", ctypes.c_int64), ("lookahead", ctypes.c_int32), ("prec", ctypes.c_int32),
+                ("refine", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64)]
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load():
+    """Load libhplgb.so (building it first if the sources are newer)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not _build.up_to_date():
+            _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError(f"libhplgb.so missing at {path}; run __graft_entry__.build()")
+        lib = ctypes.CDLL(path)
+        i64, u64, vp, i32 = ctypes.c_int64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int
+        sz = ctypes.c_size_t
+        op = ctypes.POINTER(Opts)
+        sig = {
+            "hpl_default_opts": (None, [op]),
+            "hpl_status_string": (ctypes.c_char_p, [i32]),
+            "hplgb_last_error": (ctypes.c_char_p, []),
+            "hpl_generate": (i32, [u64, u64, i64, i64, i32, vp, i64, vp]),
+            "lu_factor_workspace_size": (sz, [i64, op]),
+            "lu_factor": (i32, [i64, vp, i64, vp, op, vp, sz, vp, vp]),
+            "lu_solve_workspace_size": (sz, [i64, i64]),
+            "lu_solve": (i32, [i64, i64, vp, i64, vp, i32, vp, i64, vp, sz, vp, vp]),
+            "hpl_residual_workspace_size": (sz, [i64]),
+            "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
+            "hplgb_launch_count": (ctypes.c_longlong, []),
+            "hplgb_set_phase_timing": (None, [i32]),
+            "hplgb_phase_times": (i32, [vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+        return lib
+
+
+def _check(st: int, where: str):
+    if st != 0:
+        raise HplError(st, where)
+
+
+def _stream(device=None) -> int:
+    return torch.cuda.current_stream(device).cuda_stream
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _ld(t: torch.Tensor) -> int:
+    """Leading dimension of a column-major matrix view (or a vector)."""
+    if t.dim() == 1:
+        assert t.stride(0) == 1
+        return max(t.shape[0], 1)
+    assert t.stride(0) == 1, "matrices must be column-major (stride(0) == 1)"
+    return max(t.stride(1), t.shape[0], 1) if t.shape[1] > 1 else max(t.shape[0], 1)
+
+
+def colmajor(m: int, n: int, dtype=torch.float64, device="cuda", ld: int | None = None) -> torch.Tensor:
+    ld = max(m, 1) if ld is None else ld
+    return torch.empty((n, ld), dtype=dtype, device=device).t()[:m, :]
+
+
+def make_opts(nb: int = 0, lookahead: int = 1, prec: int = PREC_BF16, refine: int = REFINE_GMRES,
+              max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0, timeout_ns: int = 0) -> Opts:
+    o = Opts()
+    load().hpl_default_opts(ctypes.byref(o))
+    o.nb, o.lookahead, o.prec, o.refine = nb, lookahead, prec, refine
+    o.max_iter, o.gmres_m, o.tol = max_iter, gmres_m, tol
+    if timeout_ns:
+        o.timeout_ns = timeout_ns
+    return o
+
+
+class Info:
+    """Device-resident hpl_info record (32 bytes)."""
+
+    def __init__(self, device="cuda"):
+        self.buf = torch.zeros(4, dtype=torch.int64, device=device)
+
+    def ptr(self):
+        return ctypes.c_void_p(self.buf.data_ptr())
+
+    def read(self) -> dict:
+        raw = self.buf.cpu().numpy().tobytes()
+        status, iters, info, sr, inner, _ = struct.unpack("<iiqdii", raw)
+        return dict(status=status, status_name=STATUS.get(status, str(status)), iters=iters, info=info,
+                    scaled_residual=sr, inner_iters=inner)
+
+
+def workspace(nbytes: int, device="cuda") -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def generate(seed: int, stream_id: int, m: int, ncols: int, kind: int = GEN_GENERAL, out: torch.Tensor | None = None,
+             device="cuda") -> torch.Tensor:
+    """Seeded matrix of hpl_generate (column-major m x ncols, FP64)."""
+    lib = load()
+    if out is None:
+        out = colmajor(m, ncols, device=device)
+    _check(lib.hpl_generate(seed, stream_id, m, ncols, kind, _ptr(out), _ld(out), _stream(out.device)),
+           "hpl_generate")
+    return out
+
+
+def lu_factor(A: torch.Tensor, nb: int = 256, lookahead: int = 1, ipiv: torch.Tensor | None = None,
+              ws: torch.Tensor | None = None, info: Info | None = None):
+    """In-place LU with partial pivoting. Returns (ipiv, info)."""
+    lib = load()
+    n = A.shape[0]
+    assert A.shape == (n, n) and A.dtype == torch.float64 and A.is_cuda
+    opts = make_opts(nb=nb, lookahead=lookahead)
+    if ipiv is None:
+        ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
+    need = lib.lu_factor_workspace_size(n, ctypes.byref(opts))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if info is None:
+        info = Info(A.device)
+    _check(lib.lu_factor(n, _ptr(A), _ld(A), _ptr(ipiv), ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(),
+                         _stream(A.device)), "lu_factor")
+    return ipiv[:n], info
+
+
+def lu_solve(LU: torch.Tensor, ipiv: torch.Tensor, B: torch.Tensor, trans: int = 0, ws: torch.Tensor | None = None,
+             info: Info | None = None) -> torch.Tensor:
+    """Solve A X = B (trans=0) or A^T X = B (trans=1) in place on B."""
+    lib = load()
+    n = LU.shape[0]
+    nrhs = 1 if B.dim() == 1 else B.shape[1]
+    need = lib.lu_solve_workspace_size(n, nrhs)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, B.device)
+    _check(lib.lu_solve(n, nrhs, _ptr(LU), _ld(LU), _ptr(ipiv), trans, _ptr(B), _ld(B), _ptr(ws), ws.numel(),
+                        info.ptr() if info is not None else None, _stream(B.device)), "lu_solve")
+    return B
+
+
+def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, seed: int = 0,
+                    kind: int = GEN_GENERAL, ws: torch.Tensor | None = None) -> torch.Tensor:
+    """HPL scaled residual as a 0-dim device tensor (A=None: regenerate A from seed)."""
+    lib = load()
+    n = x.shape[0]
+    out = torch.empty((), dtype=torch.float64, device=x.device)
+    need = lib.hpl_residual_workspace_size(n)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, x.device)
+    _check(lib.hpl_scaled_residual(n, _ptr(A), _ld(A) if A is not None else n, seed, kind, _ptr(x), _ptr(b),
+                                   _ptr(out), _ptr(ws), ws.numel(), _stream(x.device)), "hpl_scaled_residual")
+    return out
+
+
+PHASES = ("pfact", "swap", "trsm", "update", "other")
+
+
+def launch_count() -> int:
+    return int(load().hplgb_launch_count())
+
+
+def set_phase_timing(on: bool) -> None:
+    load().hplgb_set_phase_timing(int(bool(on)))
+
+
+def phase_times() -> dict:
+    """Per-phase {name: (ms, work, intervals)} since timing was switched on."""
+    import numpy as np
+    ms = np.zeros(5)
+    work = np.zeros(5)
+    cnt = np.zeros(5, dtype=np.int64)
+    _check(load().hplgb_phase_times(ms.ctypes.data, work.ctypes.data, cnt.ctypes.data), "hplgb_phase_times")
+    return {name: (float(ms[i]), float(work[i]), int(cnt[i])) for i, name in enumerate(PHASES)}
+
+
+def flops(n: int) -> float:
+    """Operation count credited to one solve: 2n^3/3 + 2n^2."""
+    return 2.0 * n ** 3 / 3.0 + 2.0 * n ** 2

@@ -1,0 +1,101 @@
+// hpl_generate: seeded counter-based matrix generator.
+//
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014) used as a counter-based
+// generator: output c >= 1 of a generator whose state starts at s is
+// mix(s + c * GAMMA). Stream key = output (stream_id + 1) under the seed;
+// entry (i, j) of an m-row matrix = output (j*m + i + 1) under the key, its top
+// 53 bits scaled to [0,1) and shifted by -0.5 (exact). The paper says only
+// that the HPL matrix is random (Sec. III-A.1) and that HPL-MxP has a scalable
+// generator (Sec. II-B); this definition is the library's own.
+#include "common.cuh"
+
+namespace hplgb {
+
+__device__ __forceinline__ uint64_t sm64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+constexpr uint64_t kGamma = 0x9E3779B97F4A7C15ull;
+
+__host__ __device__ __forceinline__ uint64_t sm64_host_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__global__ void k_generate(uint64_t key, int64_t m, int64_t ncols, double* __restrict__ A, int64_t lda) {
+    const int64_t total = m * ncols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = t / m, i = t - j * m;
+        uint64_t h = sm64_mix(key + (uint64_t)(t + 1) * kGamma);
+        A[j * lda + i] = (double)(h >> 11) * 0x1p-53 - 0.5;
+    }
+}
+
+// Round a 128-bit unsigned integer (hi:lo) to the nearest double, ties to
+// even: the top 64 significant bits carry a sticky bit for what is shifted
+// out, then one correctly rounded 64-bit conversion.
+__device__ __forceinline__ double u128_to_double_rn(uint64_t hi, uint64_t lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    int sh = 64 - __clzll((long long)hi);          // bits of hi, 1..64
+    uint64_t top = (sh == 64) ? hi : ((hi << (64 - sh)) | (lo >> sh));
+    uint64_t dropped = (sh == 64) ? lo : (lo & ((1ull << sh) - 1));
+    top |= (dropped != 0);
+    return ldexp(__ull2double_rn(top), sh);
+}
+
+// Diagonal dominance: block of 32 rows (lane = row), 8 warps split the
+// columns; each lane sums |a_ij| / 2^-53 exactly in 128 bits; the warps'
+// partial sums are combined exactly; the diagonal is rounded once.
+__global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __restrict__ A, int64_t lda) {
+    __shared__ uint64_t s_lo[8][32], s_hi[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    uint64_t lo = 0, hi = 0;
+    if (i < n) {
+        for (int64_t j = warp; j < n; j += 8) {
+            double a = A[j * lda + i];
+            uint64_t u = (uint64_t)(fabs(a) * 0x1p53);    // exact: |a| is k * 2^-53, k < 2^52
+            uint64_t nl = lo + u;
+            hi += (nl < lo);
+            lo = nl;
+        }
+    }
+    s_lo[warp][lane] = lo;
+    s_hi[warp][lane] = hi;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        for (int w = 1; w < 8; w++) {
+            uint64_t nl = lo + s_lo[w][lane];
+            hi += s_hi[w][lane] + (nl < lo);
+            lo = nl;
+        }
+        A[i * lda + i] = u128_to_double_rn(hi, lo) * 0x1p-53;
+    }
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" int hpl_generate(uint64_t seed, uint64_t stream_id, int64_t m, int64_t ncols, int kind, double* A,
+                            int64_t lda, void* stream) {
+    if (m < 0 || ncols < 0 || (m > 0 && ncols > 0 && !A) || lda < (m > 1 ? m : 1)) return HPL_ERR_INVALID;
+    if (kind != HPL_GEN_GENERAL && kind != HPL_GEN_DIAG_DOMINANT) return HPL_ERR_INVALID;
+    if (kind == HPL_GEN_DIAG_DOMINANT && m != ncols) return HPL_ERR_INVALID;
+    if (m == 0 || ncols == 0) return HPL_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint64_t key = sm64_host_mix(seed + (stream_id + 1) * kGamma);
+    int64_t total = m * ncols;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 64) blocks = 152 * 64;
+    k_generate<<<(unsigned)blocks, 256, 0, s>>>(key, m, ncols, A, lda);
+    HPL_LAUNCH_CHECK();
+    if (kind == HPL_GEN_DIAG_DOMINANT) {
+        k_dominant_diag<<<(unsigned)((m + 31) / 32), 256, 0, s>>>(m, A, lda);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
+}

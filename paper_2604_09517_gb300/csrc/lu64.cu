@@ -1,0 +1,681 @@
+// lu_factor: HPL's blocked right-looking LU with partial pivoting in FP64.
+//
+// Paper Sec. III-A.1: each step k factors the panel of width NB (PFACT),
+// applies its row interchanges to the rest of the matrix (SWAP), solves for
+// the block row U12 = L11^-1 A12 (DTRSM) and updates the trailing matrix
+// A22 -= L21 U12 (DGEMM); look-ahead overlaps the next panel with the update
+// (depth 1, Table I). On one GPU the broadcast phase disappears.
+//
+// GB300 notes. FP64 runs at ~2 FMA/clk/SM on this part (measured: DFMA
+// 1.196 TFLOP/s, mma.sync f64 1.05 TFLOP/s), so the update is a DFMA kernel
+// and every FP64 phase is bound by the same FP64 pipe; keeping that pipe busy
+// is what look-ahead is for. The panel runs on a second, higher-priority
+// stream, so its CTAs take SMs as soon as update CTAs retire.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+// ---------------------------------------------------------------------------
+// Workspace layout of lu_factor (device memory supplied by the caller).
+struct PanelSync {
+    unsigned int count;
+    unsigned int gen;
+    int abort;
+    int pad;
+};
+
+constexpr int kLeafW = 32;          // widest leaf of the recursive panel
+constexpr int kLeafStride = 33;     // SMEM row stride (doubles) of the leaf
+constexpr int kLeafThreads = 256;
+constexpr int kMaxPanelCtas = 512;
+
+struct Cand {
+    double absval;
+    long long row;
+    double vals[kLeafW];
+};
+
+struct LuWs {
+    PanelSync* sync;
+    Cand* slots;        // [2][kMaxPanelCtas]
+    double* drow;       // [2][kLeafW]
+    int* perm_cnt;      // [2]
+    int* perm_dst;      // [2][2*nb]
+    int* perm_src;      // [2][2*nb]
+};
+
+static size_t lu_ws_layout(int64_t nb, LuWs* w, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return base ? (void*)(base + o) : (void*)nullptr;
+    };
+    void* p0 = take(sizeof(PanelSync));
+    void* p1 = take(sizeof(Cand) * 2 * kMaxPanelCtas);
+    void* p2 = take(sizeof(double) * 2 * kLeafW);
+    void* p3 = take(sizeof(int) * 2);
+    void* p4 = take(sizeof(int) * 2 * 2 * nb);
+    void* p5 = take(sizeof(int) * 2 * 2 * nb);
+    if (w) {
+        w->sync = (PanelSync*)p0;
+        w->slots = (Cand*)p1;
+        w->drow = (double*)p2;
+        w->perm_cnt = (int*)p3;
+        w->perm_dst = (int*)p4;
+        w->perm_src = (int*)p5;
+    }
+    return off;
+}
+
+// ---------------------------------------------------------------------------
+// Grid-wide barrier for the cooperative panel kernel. Bounded: after the
+// deadline it raises `abort`, every CTA sees it and the kernel returns.
+__device__ bool grid_barrier(PanelSync* s, unsigned nblocks, uint64_t deadline) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned* vgen = &s->gen;
+        volatile int* vab = &s->abort;
+        unsigned g = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(&s->count, 1u);
+        if (arrived == nblocks - 1) {
+            atomicExch(&s->count, 0u);
+            __threadfence();
+            atomicAdd(&s->gen, 1u);
+        } else {
+            while (*vgen == g) {
+                if (*vab) break;
+                if (globaltimer_ns() > deadline) {
+                    atomicExch(&s->abort, 1);
+                    break;
+                }
+                __nanosleep(40);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)&s->abort == 0;
+}
+
+// Larger magnitude wins; on equal magnitude the smaller row index wins
+// (first index attaining the maximum, as BLAS idamax).
+__device__ __forceinline__ bool cand_better(double v, long long r, double bv, long long br) {
+    return v > bv || (v == bv && r < br);
+}
+
+// PFACT leaf: factor columns [c0, c0+w) (w <= 32) of rows [c0, n) with
+// partial pivoting. Cooperative launch, P CTAs; CTA b owns rows
+// [c0 + b*rows_per, ...) of the leaf, staged in shared memory (row-major,
+// stride 33). Per column: every CTA finds its local argmax (warp shuffles),
+// publishes it with the candidate row's values (and the owner of the diagonal
+// row publishes that row), one grid barrier, then every CTA picks the same
+// global pivot, swaps, scales by the pivot (true division) and applies the
+// rank-1 update with one warp per row and the multiplier broadcast by shuffle.
+// The interchanges are also applied to the other columns of the enclosing
+// NB-wide panel [pc0, pc0+pw) (the leaf's own columns live in SMEM).
+__global__ void __launch_bounds__(kLeafThreads) k_panel_leaf(
+    int64_t n, double* __restrict__ A, int64_t lda, int64_t c0, int w, int rows_per, int64_t pc0,
+    int64_t pw, int32_t* __restrict__ ipiv, Cand* __restrict__ slots, double* __restrict__ drow,
+    PanelSync* sync, hpl_info* info, int64_t timeout_ns) {
+    extern __shared__ double sm[];
+    __shared__ double s_piv[kLeafW], s_diag[kLeafW];
+    __shared__ double s_wv[kLeafThreads / 32];
+    __shared__ long long s_wr[kLeafThreads / 32];
+    __shared__ long long s_p;
+    __shared__ int s_win;
+
+    const uint64_t deadline = globaltimer_ns() + (uint64_t)timeout_ns;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned P = gridDim.x;
+    const int64_t m = n - c0;
+    const int64_t rbeg = (int64_t)blockIdx.x * rows_per;           // local to c0
+    const int nloc = (int)max((int64_t)0, min((int64_t)rows_per, m - rbeg));
+    const int S = kLeafStride;
+
+    for (int idx = tid; idx < nloc * w; idx += kLeafThreads) {
+        int c = idx / nloc, r = idx - c * nloc;
+        sm[r * S + c] = A[(c0 + c) * lda + c0 + rbeg + r];
+    }
+    // other panel columns handled by this thread for the interchanges
+    const int64_t nother = pw - w;
+    const int64_t gtid = (int64_t)blockIdx.x * kLeafThreads + tid;
+    __syncthreads();
+
+    for (int j = 0; j < w; j++) {
+        const int par = j & 1;
+        const int64_t rowj = c0 + j;                    // global diagonal row
+        // local argmax over owned rows with global index >= rowj
+        double bv = -1.0;
+        long long br = 0x7fffffffffffffffLL;
+        int rstart = (int)max((int64_t)0, (int64_t)j - rbeg);
+        for (int r = rstart + tid; r < nloc; r += kLeafThreads) {
+            double v = fabs(sm[r * S + j]);
+            long long gr = c0 + rbeg + r;
+            if (cand_better(v, gr, bv, br)) { bv = v; br = gr; }
+        }
+        for (int off = 16; off > 0; off >>= 1) {
+            double ov = __shfl_down_sync(0xffffffffu, bv, off);
+            long long orr = __shfl_down_sync(0xffffffffu, br, off);
+            if (cand_better(ov, orr, bv, br)) { bv = ov; br = orr; }
+        }
+        if (lane == 0) { s_wv[warp] = bv; s_wr[warp] = br; }
+        __syncthreads();
+        if (tid == 0) {
+            for (int q = 1; q < kLeafThreads / 32; q++)
+                if (cand_better(s_wv[q], s_wr[q], bv, br)) { bv = s_wv[q]; br = s_wr[q]; }
+            s_p = br;
+            Cand* sl = slots + par * kMaxPanelCtas + blockIdx.x;
+            sl->absval = bv;
+            sl->row = br;
+        }
+        __syncthreads();
+        {
+            Cand* sl = slots + par * kMaxPanelCtas + blockIdx.x;
+            long long mr = s_p;
+            if (tid < w && mr != 0x7fffffffffffffffLL) sl->vals[tid] = sm[(int)(mr - c0 - rbeg) * S + tid];
+            int64_t rd = rowj - c0 - rbeg;               // local index of the diagonal row
+            if (rd >= 0 && rd < nloc && tid < w) drow[par * kLeafW + tid] = sm[rd * S + tid];
+        }
+        __threadfence();
+        if (!grid_barrier(sync, P, deadline)) {
+            if (blockIdx.x == 0 && tid == 0) info->status = HPL_ERR_TIMEOUT;
+            return;
+        }
+        // global pivot: warp 0 scans the P candidates
+        if (warp == 0) {
+            double gv = -1.0;
+            long long gr = 0x7fffffffffffffffLL;
+            int gw = 0;
+            for (unsigned q = lane; q < P; q += 32) {
+                const volatile Cand* sl = slots + par * kMaxPanelCtas + q;
+                double v = sl->absval;
+                long long r = sl->row;
+                if (cand_better(v, r, gv, gr)) { gv = v; gr = r; gw = (int)q; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, gv, off);
+                long long orr = __shfl_down_sync(0xffffffffu, gr, off);
+                int ow = __shfl_down_sync(0xffffffffu, gw, off);
+                if (cand_better(ov, orr, gv, gr)) { gv = ov; gr = orr; gw = ow; }
+            }
+            if (lane == 0) {
+                // no comparable candidate (the column holds only NaN): keep the diagonal row
+                if (gr == 0x7fffffffffffffffLL) { gr = rowj; gw = -1; }
+                s_p = gr;
+                s_win = gw;
+            }
+        }
+        __syncthreads();
+        const long long p = s_p;
+        if (tid < w) {
+            double dv = ((volatile double*)drow)[par * kLeafW + tid];
+            s_diag[tid] = dv;
+            s_piv[tid] = s_win >= 0 ? ((const volatile Cand*)(slots + par * kMaxPanelCtas + s_win))->vals[tid] : dv;
+        }
+        __syncthreads();
+        const double piv = s_piv[j];
+        if (blockIdx.x == 0 && tid == 0) {
+            ipiv[rowj] = (int32_t)p;
+            if (piv == 0.0) atomicCAS((unsigned long long*)&info->info, 0ull, (unsigned long long)(rowj + 1));
+        }
+        // interchange rows rowj and p inside the leaf (SMEM) ...
+        if (p != rowj) {
+            int64_t rp = p - c0 - rbeg, rd = rowj - c0 - rbeg;
+            if (rp >= 0 && rp < nloc && tid < w) sm[rp * S + tid] = s_diag[tid];
+            if (rd >= 0 && rd < nloc && tid < w) sm[rd * S + tid] = s_piv[tid];
+            // ... and in the panel's other columns (global memory)
+            for (int64_t o = gtid; o < nother; o += (int64_t)P * kLeafThreads) {
+                int64_t col = pc0 + (o < c0 - pc0 ? o : o + w);
+                double* cp = A + col * lda;
+                double t = cp[rowj];
+                cp[rowj] = cp[p];
+                cp[p] = t;
+            }
+        }
+        __syncthreads();
+        // scale the column below the diagonal and rank-1 update of the leaf
+        if (piv != 0.0) {
+            const double pl = (lane < w) ? s_piv[lane] : 0.0;
+            int rs = (int)max((int64_t)0, rowj + 1 - c0 - rbeg);
+            for (int r = rs + warp; r < nloc; r += kLeafThreads / 32) {
+                double v = (lane < w) ? sm[r * S + lane] : 0.0;
+                double l = __shfl_sync(0xffffffffu, v, j) / piv;
+                if (lane == j) sm[r * S + lane] = l;
+                else if (lane > j && lane < w) sm[r * S + lane] = fma(-l, pl, v);
+            }
+        }
+        __syncthreads();
+    }
+    for (int idx = tid; idx < nloc * w; idx += kLeafThreads) {
+        int c = idx / nloc, r = idx - c * nloc;
+        A[(c0 + c) * lda + c0 + rbeg + r] = sm[r * S + c];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// SWAP: the sequential interchanges ipiv[k0 .. k0+kb) as a gather. One warp
+// replays them on a list of touched positions and emits (dst, src) pairs with
+// new[dst] = old[src]; the gather kernel then moves whole rows.
+// Block b of the launch handles ipiv[k0_base + b*pb, ... + pb) (clipped at
+// n_end) and writes cnt[b], dst/src + b*2*pb.
+// Entries outside [k, n_total) are not interchanges and are skipped.
+__global__ void k_perm_pairs(const int32_t* __restrict__ ipiv, int64_t k0_base, int pb, int64_t n_end,
+                             int64_t n_total, int* __restrict__ cnt, int* __restrict__ dst, int* __restrict__ src) {
+    extern __shared__ int psm[];
+    const int64_t k0 = k0_base + (int64_t)blockIdx.x * pb;
+    const int kb = (int)min((int64_t)pb, n_end - k0);
+    cnt += blockIdx.x;
+    dst += (int64_t)blockIdx.x * 2 * pb;
+    src += (int64_t)blockIdx.x * 2 * pb;
+    int* pos = psm;               // [2*pb]
+    int* con = psm + 2 * pb;      // [2*pb]
+    const int lane = threadIdx.x;
+    for (int i = lane; i < kb; i += 32) {
+        pos[i] = (int)(k0 + i);
+        con[i] = (int)(k0 + i);
+    }
+    __syncwarp();
+    int L = kb;
+    for (int i = 0; i < kb; i++) {
+        int p = ipiv[k0 + i];
+        if (p <= k0 + i || p >= n_total) continue;
+        int q;
+        if (p < k0 + kb) {
+            q = (int)(p - k0);
+        } else {
+            q = -1;
+            for (int base = kb; base < L && q < 0; base += 32) {
+                int e = base + lane;
+                unsigned b = __ballot_sync(0xffffffffu, e < L && pos[e] == p);
+                if (b) q = base + __ffs(b) - 1;
+            }
+            if (q < 0) {
+                q = L;
+                if (lane == 0) { pos[L] = p; con[L] = p; }
+                L++;
+            }
+        }
+        __syncwarp();
+        if (lane == 0) {
+            int t = con[i];
+            con[i] = con[q];
+            con[q] = t;
+        }
+        __syncwarp();
+    }
+    // compact the pairs that move something
+    int base_out = 0;
+    for (int b = 0; b < L; b += 32) {
+        int e = b + lane;
+        bool mv = e < L && pos[e] != con[e];
+        unsigned bal = __ballot_sync(0xffffffffu, mv);
+        if (mv) {
+            int o = base_out + __popc(bal & ((1u << lane) - 1));
+            dst[o] = pos[e];
+            src[o] = con[e];
+        }
+        base_out += __popc(bal);
+    }
+    if (lane == 0) *cnt = base_out;
+}
+
+// Gather rows for the columns [0, cA) and [cB, n): every CTA takes 8 columns;
+// all reads of a column finish (barrier) before any write.
+constexpr int kSwapCols = 8;
+constexpr int kSwapPairsPerThread = 4;   // 256 threads x 4 >= 2*NB for NB <= 512
+
+__global__ void __launch_bounds__(256) k_laswp_gather(double* __restrict__ A, int64_t lda, int64_t cA, int64_t cB,
+                                                      int64_t n, const int* __restrict__ cnt,
+                                                      const int* __restrict__ dst, const int* __restrict__ src) {
+    const int np = *cnt;
+    if (np == 0) return;
+    const int64_t ncols = cA + (n - cB);
+    const int64_t cbase = (int64_t)blockIdx.x * kSwapCols;
+    double v[kSwapPairsPerThread][kSwapCols];
+#pragma unroll
+    for (int q = 0; q < kSwapPairsPerThread; q++) {
+        int t = threadIdx.x + q * 256;
+#pragma unroll
+        for (int c = 0; c < kSwapCols; c++) {
+            int64_t ci = cbase + c;
+            if (t < np && ci < ncols) {
+                int64_t col = ci < cA ? ci : ci - cA + cB;
+                v[q][c] = A[col * lda + src[t]];
+            }
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kSwapPairsPerThread; q++) {
+        int t = threadIdx.x + q * 256;
+#pragma unroll
+        for (int c = 0; c < kSwapCols; c++) {
+            int64_t ci = cbase + c;
+            if (t < np && ci < ncols) {
+                int64_t col = ci < cA ? ci : ci - cA + cB;
+                A[col * lda + dst[t]] = v[q][c];
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// DTRSM: B <- L^-1 B with L the kk x kk unit lower triangle at A(r0, r0) and
+// B = A(r0 : r0+kk, cb : ce). Each CTA stages 16 columns of B in SMEM and
+// runs forward substitution; 16 thread groups split the rows.
+constexpr int kTrsmCols = 16;
+
+__global__ void __launch_bounds__(256) k_trsm_lunit(double* __restrict__ A, int64_t lda, int64_t r0, int kk,
+                                                    int64_t cb, int64_t ce) {
+    extern __shared__ double xs[];            // [kk][16]
+    const int c = threadIdx.x & 15, g = threadIdx.x >> 4;
+    const int64_t col = cb + (int64_t)blockIdx.x * kTrsmCols + c;
+    const bool live = col < ce;
+    for (int i = g; i < kk; i += 16) xs[i * kTrsmCols + c] = live ? A[col * lda + r0 + i] : 0.0;
+    for (int j = 0; j < kk - 1; j++) {
+        __syncthreads();
+        const double xj = xs[j * kTrsmCols + c];
+        const double* Lj = A + (r0 + j) * lda + r0;     // column j of L
+        for (int i = j + 1 + g; i < kk; i += 16) xs[i * kTrsmCols + c] = fma(-Lj[i], xj, xs[i * kTrsmCols + c]);
+    }
+    __syncthreads();
+    if (live)
+        for (int i = g; i < kk; i += 16) A[col * lda + r0 + i] = xs[i * kTrsmCols + c];
+}
+
+// ---------------------------------------------------------------------------
+// DGEMM: C -= A * B in FP64 with DFMA. 64x64 CTA tile, k-step 16, 256
+// threads with a 4x4 register tile, cp.async double buffering. C is loaded
+// into the accumulators first so every entry sees c - sum(a*b) accumulated in
+// increasing k, as in the unblocked elimination.
+constexpr int kGB = 64, kGK = 16;
+
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
+    unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    int sz = pred ? 8 : 0;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(sa), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
+
+__global__ void __launch_bounds__(256) k_dgemm_sub(int64_t m, int64_t nn, int64_t kk, const double* __restrict__ A,
+                                                   int64_t lda, const double* __restrict__ B, int64_t ldb,
+                                                   double* __restrict__ C, int64_t ldc) {
+    __shared__ __align__(16) double As[2][kGK][kGB + 1];
+    __shared__ __align__(16) double Bs[2][kGK][kGB + 1];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * kGB, col0 = (int64_t)blockIdx.y * kGB;
+
+    auto load_tile = [&](int buf, int64_t k0) {
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int e = tid + 256 * q;
+            int kq = e >> 6, r = e & 63;
+            bool ok = (row0 + r < m) && (k0 + kq < kk);
+            const double* g = ok ? A + (k0 + kq) * lda + row0 + r : A;
+            cp_async8(&As[buf][kq][r], g, ok);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            int e = tid + 256 * q;
+            int c = e >> 4, kq = e & 15;
+            bool ok = (col0 + c < nn) && (k0 + kq < kk);
+            const double* g = ok ? B + (col0 + c) * ldb + k0 + kq : B;
+            cp_async8(&Bs[buf][kq][c], g, ok);
+        }
+        cp_async_commit();
+    };
+
+    double acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
+            acc[i][j] = (r < m && c < nn) ? C[c * ldc + r] : 0.0;
+        }
+
+    const int ntiles = (int)((kk + kGK - 1) / kGK);
+    load_tile(0, 0);
+    for (int t = 0; t < ntiles; t++) {
+        const int buf = t & 1;
+        if (t + 1 < ntiles) {
+            load_tile(buf ^ 1, (int64_t)(t + 1) * kGK);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kq = 0; kq < kGK; kq++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[buf][kq][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[buf][kq][ty + 16 * j];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
+            if (r < m && c < nn) C[c * ldc + r] = acc[i][j];
+        }
+}
+
+__global__ void k_lu_finish(hpl_info* info, const PanelSync* sync) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        if (sync->abort) info->status = HPL_ERR_TIMEOUT;
+        else if (info->info != 0) info->status = HPL_ERR_SINGULAR;
+        else info->status = HPL_OK;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launch helpers.
+
+int launch_dgemm_sub(int64_t m, int64_t nn, int64_t kk, const double* A, int64_t lda, const double* B, int64_t ldb,
+                     double* C, int64_t ldc, cudaStream_t s) {
+    if (m <= 0 || nn <= 0 || kk <= 0) return HPL_OK;
+    dim3 grid((unsigned)((m + kGB - 1) / kGB), (unsigned)((nn + kGB - 1) / kGB));
+    if (grid.y > 65535) return HPL_ERR_INVALID;
+    k_dgemm_sub<<<grid, 256, 0, s>>>(m, nn, kk, A, lda, B, ldb, C, ldc);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+static int launch_trsm(double* A, int64_t lda, int64_t r0, int kk, int64_t cb, int64_t ce, cudaStream_t s) {
+    if (ce <= cb || kk <= 1) return HPL_OK;
+    size_t smem = sizeof(double) * kk * kTrsmCols;
+    unsigned grid = (unsigned)((ce - cb + kTrsmCols - 1) / kTrsmCols);
+    k_trsm_lunit<<<grid, 256, smem, s>>>(A, lda, r0, kk, cb, ce);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+struct PanelPlan {
+    int max_coop;   // co-resident leaf CTAs
+};
+
+static int launch_leaf(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64_t pc0, int64_t pw,
+                       int32_t* ipiv, const LuWs& ws, hpl_info* info, int64_t timeout_ns, const PanelPlan& pp,
+                       cudaStream_t s) {
+    int64_t m = n - c0;
+    int P = (int)std::min<int64_t>((m + 255) / 256, (int64_t)pp.max_coop);
+    if (P < 1) P = 1;
+    int rows_per = (int)((m + P - 1) / P);
+    P = (int)((m + rows_per - 1) / rows_per);
+    size_t smem = sizeof(double) * (size_t)rows_per * kLeafStride;
+    if (smem > 200 * 1024) return HPL_ERR_INVALID;     // matrix too tall for the FP64 panel
+    void* args[] = {&n, &A, &lda, &c0, &w, &rows_per, &pc0, &pw, &ipiv, (void*)&ws.slots, (void*)&ws.drow,
+                    (void*)&ws.sync, &info, &timeout_ns};
+    HPL_CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_panel_leaf, dim3(P), dim3(kLeafThreads), args, smem, s));
+    count_launch();
+    return HPL_OK;
+}
+
+// Recursive PFACT of the panel columns [c0, c0+w) (rows [c0, n)) inside the
+// NB panel [pc0, pc0+pw): left half, TRSM + GEMM on the right half, right half.
+static int panel_rec(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64_t pc0, int64_t pw, int32_t* ipiv,
+                     const LuWs& ws, hpl_info* info, int64_t timeout_ns, const PanelPlan& pp, cudaStream_t s) {
+    if (w <= kLeafW) return launch_leaf(n, A, lda, c0, w, pc0, pw, ipiv, ws, info, timeout_ns, pp, s);
+    int w1 = ((w / 2 + kLeafW - 1) / kLeafW) * kLeafW;
+    if (w1 >= w) w1 = kLeafW;
+    int st = panel_rec(n, A, lda, c0, w1, pc0, pw, ipiv, ws, info, timeout_ns, pp, s);
+    if (st) return st;
+    st = launch_trsm(A, lda, c0, w1, c0 + w1, c0 + w, s);
+    if (st) return st;
+    st = launch_dgemm_sub(n - c0 - w1, w - w1, w1, A + c0 * lda + c0 + w1, lda, A + (c0 + w1) * lda + c0, lda,
+                          A + (c0 + w1) * lda + c0 + w1, lda, s);
+    if (st) return st;
+    return panel_rec(n, A, lda, c0 + w1, w - w1, pc0, pw, ipiv, ws, info, timeout_ns, pp, s);
+}
+
+static int max_coop_leaf_ctas(int num_sms, int64_t n) {
+    // the leaf's dynamic SMEM depends on rows_per; size the bound for the
+    // tallest panel (rows_per <= ceil(n / P)) with one CTA per SM.
+    int per_sm = 0;
+    size_t smem_guess = sizeof(double) * 256 * kLeafStride;
+    cudaFuncSetAttribute((const void*)k_panel_leaf, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k_panel_leaf, kLeafThreads, smem_guess);
+    int64_t need = (n + 255) / 256;
+    int64_t cap = (int64_t)num_sms * std::max(per_sm, 1);
+    if (need > cap) {
+        // fewer CTAs, more rows each; one CTA per SM is always co-resident
+        cap = num_sms;
+    }
+    return (int)std::min<int64_t>(std::min<int64_t>(need, cap), kMaxPanelCtas);
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" size_t lu_factor_workspace_size(int64_t n, const hpl_opts* opts) {
+    (void)n;
+    Opts o = resolve_opts(opts, 256);
+    return lu_ws_layout(o.nb, nullptr, nullptr);
+}
+
+extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts, void* ws,
+                         size_t ws_bytes, hpl_info* info, void* stream) {
+    if (n < 0 || lda < (n > 1 ? n : 1) || !info) return HPL_ERR_INVALID;
+    if (n > 0 && (!A || !ipiv)) return HPL_ERR_INVALID;
+    if (n > 0x7fffffff) return HPL_ERR_INVALID;
+    Opts o = resolve_opts(opts, 256);
+    if (o.nb < 1 || o.nb > 512) return HPL_ERR_INVALID;
+    size_t need = lu_ws_layout(o.nb, nullptr, nullptr);
+    if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
+    cudaStream_t s = (cudaStream_t)stream;
+    HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
+    if (n == 0) return HPL_OK;
+    LuWs w;
+    lu_ws_layout(o.nb, &w, (char*)ws);
+    HPL_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
+
+    DeviceCtx* ctx = nullptr;
+    int st = get_ctx(&ctx);
+    if (st) return st;
+    PanelPlan pp;
+    pp.max_coop = max_coop_leaf_ctas(ctx->num_sms, n);
+    HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_trsm_lunit, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)(sizeof(double) * 512 * kTrsmCols)));
+
+    const int64_t nb = o.nb;
+    const int64_t nsteps = (n + nb - 1) / nb;
+    const bool la = o.lookahead != 0;
+    cudaStream_t ps = la ? ctx->side : s;                // panel stream
+    cudaEvent_t ev_fork = ctx->ev[0], ev_panel = ctx->ev[1], ev_la = ctx->ev[2], ev_join = ctx->ev[3];
+    if (la) {
+        HPL_CUDA_TRY(cudaEventRecord(ev_fork, s));
+        HPL_CUDA_TRY(cudaStreamWaitEvent(ps, ev_fork, 0));
+    }
+    auto panel = [&](int64_t k) -> int {
+        int64_t c0 = k * nb;
+        int kb = (int)std::min(nb, n - c0);
+        const double pm = (double)(n - c0);
+        int slot = phase_begin(ps);
+        int r = panel_rec(n, A, lda, c0, kb, c0, kb, ipiv, w, info, o.timeout_ns, pp, ps);
+        if (r) return r;
+        int par = (int)(k & 1);
+        k_perm_pairs<<<1, 32, sizeof(int) * 4 * kb, ps>>>(ipiv, c0, kb, c0 + kb, n, w.perm_cnt + par,
+                                                           w.perm_dst + par * 2 * nb, w.perm_src + par * 2 * nb);
+        HPL_LAUNCH_CHECK();
+        // getrf of an m x kb panel: m kb^2 - kb^3/3 flops (leading terms)
+        phase_end(slot, ps, PH_PANEL, pm * kb * kb - (double)kb * kb * kb / 3.0);
+        return HPL_OK;
+    };
+
+    st = panel(0);
+    if (st) return st;
+    for (int64_t k = 0; k < nsteps; k++) {
+        const int64_t c0 = k * nb;
+        const int kb = (int)std::min(nb, n - c0);
+        const int64_t c1 = c0 + kb;                      // first trailing column
+        const int par = (int)(k & 1);
+        if (la) {
+            HPL_CUDA_TRY(cudaEventRecord(ev_panel, ps));
+            HPL_CUDA_TRY(cudaStreamWaitEvent(s, ev_panel, 0));
+        }
+        // SWAP on every column outside the panel
+        int64_t ncols_out = c0 + (n - c1);
+        if (ncols_out > 0) {
+            unsigned g = (unsigned)((ncols_out + kSwapCols - 1) / kSwapCols);
+            int slot = phase_begin(s);
+            k_laswp_gather<<<g, 256, 0, s>>>(A, lda, c0, c1, n, w.perm_cnt + par, w.perm_dst + par * 2 * nb,
+                                             w.perm_src + par * 2 * nb);
+            HPL_LAUNCH_CHECK();
+            // at most 2 kb rows move: read + write of each moved element
+            phase_end(slot, s, PH_SWAP, 2.0 * 2.0 * kb * (double)ncols_out * sizeof(double));
+        }
+        if (c1 < n) {
+            // DTRSM on the block row, then DGEMM: look-ahead columns first
+            const int64_t m2 = n - c1;
+            int slot = phase_begin(s);
+            st = launch_trsm(A, lda, c0, kb, c1, n, s);
+            if (st) return st;
+            phase_end(slot, s, PH_TRSM, (double)kb * (kb - 1) * (double)m2);
+            const int64_t la_cols = std::min(nb, n - c1);
+            slot = phase_begin(s);
+            st = launch_dgemm_sub(m2, la_cols, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda, A + c1 * lda + c1,
+                                  lda, s);
+            if (st) return st;
+            phase_end(slot, s, PH_UPDATE, 2.0 * m2 * la_cols * kb);
+            if (la) {
+                HPL_CUDA_TRY(cudaEventRecord(ev_la, s));
+                HPL_CUDA_TRY(cudaStreamWaitEvent(ps, ev_la, 0));
+                st = panel(k + 1);
+                if (st) return st;
+            }
+            if (n - c1 - la_cols > 0) {
+                slot = phase_begin(s);
+                st = launch_dgemm_sub(m2, n - c1 - la_cols, kb, A + c0 * lda + c1, lda, A + (c1 + la_cols) * lda + c0,
+                                      lda, A + (c1 + la_cols) * lda + c1, lda, s);
+                if (st) return st;
+                phase_end(slot, s, PH_UPDATE, 2.0 * m2 * (n - c1 - la_cols) * kb);
+            }
+            if (!la) {
+                st = panel(k + 1);
+                if (st) return st;
+            }
+        }
+    }
+    if (la) {
+        HPL_CUDA_TRY(cudaEventRecord(ev_join, ps));
+        HPL_CUDA_TRY(cudaStreamWaitEvent(s, ev_join, 0));
+    }
+    k_lu_finish<<<1, 32, 0, s>>>(info, w.sync);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}

@@ -1,0 +1,186 @@
+// hpl_scaled_residual: ||Ax - b||_inf / (eps (||A||_inf ||x||_inf + ||b||_inf) n),
+// eps = 2^-53, FP64 (the standard HPL acceptance test; the paper prints no
+// formula). A is read, or regenerated from the seed (hpl_generate's
+// definition) so that very large systems need not keep a copy of A.
+//
+// Pass 1: grid (row blocks of 256, column chunks); each thread owns one row
+// and sums a_ij x_j and |a_ij| over its chunk (deterministic per-chunk
+// partials). Pass 2: per row, the chunks are summed in order, b_i is
+// subtracted and the maxima are combined with an integer atomicMax on the bit
+// patterns of non-negative doubles (order-independent). Pass 3: the quotient.
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+constexpr int kResChunks = 16;
+
+__host__ __device__ __forceinline__ uint64_t res_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double res_u128_to_double(uint64_t hi, uint64_t lo) {
+    if (hi == 0) return __ull2double_rn(lo);
+    int sh = 64 - __clzll((long long)hi);
+    uint64_t top = (sh == 64) ? hi : ((hi << (64 - sh)) | (lo >> sh));
+    uint64_t dropped = (sh == 64) ? lo : (lo & ((1ull << sh) - 1));
+    top |= (dropped != 0);
+    return ldexp(__ull2double_rn(top), sh);
+}
+
+struct ResWs {
+    double* part_r;      // [chunks][n]
+    double* part_a;      // [chunks][n]
+    uint64_t* part_lo;   // [chunks][n] (regenerated dominant matrices)
+    uint64_t* part_hi;   // [chunks][n]
+    unsigned long long* maxima;   // [4]: |r|, row sum, |x|, |b|
+};
+
+static size_t res_ws_layout(int64_t n, ResWs* w, char* base) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return base ? (void*)(base + o) : (void*)nullptr;
+    };
+    void* a = take(sizeof(double) * kResChunks * n);
+    void* b = take(sizeof(double) * kResChunks * n);
+    void* c = take(sizeof(uint64_t) * kResChunks * n);
+    void* d = take(sizeof(uint64_t) * kResChunks * n);
+    void* e = take(sizeof(unsigned long long) * 4);
+    if (w) {
+        w->part_r = (double*)a;
+        w->part_a = (double*)b;
+        w->part_lo = (uint64_t*)c;
+        w->part_hi = (uint64_t*)d;
+        w->maxima = (unsigned long long*)e;
+    }
+    return off;
+}
+
+__global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                     uint64_t key, int dominant, const double* __restrict__ x,
+                                                     ResWs w) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int64_t cw = (n + kResChunks - 1) / kResChunks;
+    const int64_t j0 = chunk * cw, j1 = std::min<int64_t>(n, j0 + cw);
+    if (i >= n) return;
+    double r = 0.0, s = 0.0;
+    uint64_t lo = 0, hi = 0;
+    if (A) {
+        for (int64_t j = j0; j < j1; j++) {
+            double a = A[j * lda + i];
+            r = fma(a, x[j], r);
+            s += fabs(a);
+        }
+    } else {
+        for (int64_t j = j0; j < j1; j++) {
+            uint64_t h = res_mix(key + (uint64_t)(j * n + i + 1) * 0x9E3779B97F4A7C15ull);
+            double a = (double)(h >> 11) * 0x1p-53 - 0.5;
+            if (dominant) {
+                uint64_t m = h >> 11, u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
+                uint64_t nl = lo + u;
+                hi += (nl < lo);
+                lo = nl;
+                if (j == i) continue;     // the diagonal is added once the row sum is known
+            }
+            r = fma(a, x[j], r);
+            s += fabs(a);
+        }
+    }
+    w.part_r[chunk * n + i] = r;
+    w.part_a[chunk * n + i] = s;
+    w.part_lo[chunk * n + i] = lo;
+    w.part_hi[chunk * n + i] = hi;
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double v) {
+    atomicMax(p, (unsigned long long)__double_as_longlong(v));
+}
+
+__global__ void __launch_bounds__(256) k_res_rows(int64_t n, int regen_dominant, const double* __restrict__ x,
+                                                  const double* __restrict__ b, ResWs w) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double mr = 0.0, ma = 0.0, mx = 0.0, mb = 0.0;
+    if (i < n) {
+        double r = 0.0, s = 0.0;
+        uint64_t lo = 0, hi = 0;
+        for (int c = 0; c < kResChunks; c++) {
+            r += w.part_r[c * n + i];
+            s += w.part_a[c * n + i];
+            uint64_t nl = lo + w.part_lo[c * n + i];
+            hi += w.part_hi[c * n + i] + (nl < lo);
+            lo = nl;
+        }
+        if (regen_dominant) {
+            double d = res_u128_to_double(hi, lo) * 0x1p-53;
+            r = fma(d, x[i], r);
+            s += d;
+        }
+        r -= b[i];
+        mr = fabs(r);
+        ma = s;
+        mx = fabs(x[i]);
+        mb = fabs(b[i]);
+    }
+    // NaN compares false everywhere; flag it through the |r| slot as +Inf bits
+    if (mr != mr) mr = __longlong_as_double(0x7ff0000000000000LL);
+    for (int off = 16; off > 0; off >>= 1) {
+        mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
+        ma = fmax(ma, __shfl_down_sync(0xffffffffu, ma, off));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+        mb = fmax(mb, __shfl_down_sync(0xffffffffu, mb, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&w.maxima[0], mr);
+        atomic_max_nonneg(&w.maxima[1], ma);
+        atomic_max_nonneg(&w.maxima[2], mx);
+        atomic_max_nonneg(&w.maxima[3], mb);
+    }
+}
+
+__global__ void k_res_final(int64_t n, const unsigned long long* maxima, double* out) {
+    double mr = __longlong_as_double((long long)maxima[0]);
+    double ma = __longlong_as_double((long long)maxima[1]);
+    double mx = __longlong_as_double((long long)maxima[2]);
+    double mb = __longlong_as_double((long long)maxima[3]);
+    *out = mr / (0x1p-53 * (ma * mx + mb) * (double)n);
+}
+
+size_t residual_ws_bytes(int64_t n) { return res_ws_layout(n > 0 ? n : 1, nullptr, nullptr); }
+
+// Shared by the mixed-precision solver: computes the scaled residual into out.
+int launch_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, int kind, const double* x,
+                           const double* b, double* out, void* ws, cudaStream_t s) {
+    ResWs w;
+    res_ws_layout(n, &w, (char*)ws);
+    HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
+    uint64_t key = res_mix(seed + 1ull * 0x9E3779B97F4A7C15ull);    // stream 0 of the generator
+    dim3 g1((unsigned)((n + 255) / 256), kResChunks);
+    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, key, kind == HPL_GEN_DIAG_DOMINANT, x, w);
+    HPL_LAUNCH_CHECK();
+    k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, !A && kind == HPL_GEN_DIAG_DOMINANT, x, b, w);
+    HPL_LAUNCH_CHECK();
+    k_res_final<<<1, 1, 0, s>>>(n, w.maxima, out);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" size_t hpl_residual_workspace_size(int64_t n) { return residual_ws_bytes(n); }
+
+extern "C" int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, int kind, const double* x,
+                                   const double* b, double* out, void* ws, size_t ws_bytes, void* stream) {
+    if (n <= 0 || !x || !b || !out) return HPL_ERR_INVALID;
+    if (A && lda < n) return HPL_ERR_INVALID;
+    if (kind != HPL_GEN_GENERAL && kind != HPL_GEN_DIAG_DOMINANT) return HPL_ERR_INVALID;
+    if (!ws || ws_bytes < residual_ws_bytes(n)) return HPL_ERR_NOMEM;
+    return launch_scaled_residual(n, A, lda, seed, kind, x, b, out, ws, (cudaStream_t)stream);
+}

@@ -1,0 +1,67 @@
+"""The C-ABI library builds for sm_103a, loads without a GPU and exports every
+function that include/*.h declares (no compute call is made here)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_functions():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        for m in re.finditer(r"\b([A-Za-z_][A-Za-z0-9_]*)\s*\(", text):
+            name = m.group(1)
+            start = text.rfind("\n", 0, m.start()) + 1
+            prefix = text[start:m.start()]
+            if name in ("if", "while", "for", "sizeof", "defined") or "#" in prefix:
+                continue
+            if re.search(r"\b(int|size_t|void|const char\s*\*|double|int64_t|uint64_t)\s*\*?\s*$", prefix):
+                names.add(name)
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2604_09517_gb300 import _build
+    path = _build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_api():
+    names = _declared_functions()
+    for must in ["hpl_generate", "lu_factor", "lu_solve", "hpl_scaled_residual", "lu_factor_workspace_size"]:
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings_without_gpu(lib):
+    lib.hpl_status_string.restype = ctypes.c_char_p
+    assert lib.hpl_status_string(0) == b"HPL_OK"
+    assert lib.hpl_status_string(2) == b"HPL_ERR_SINGULAR"
+    assert lib.hpl_status_string(99) == b"HPL_ERR_UNKNOWN"
+
+
+def test_invalid_arguments_rejected_before_any_launch(lib):
+    """Argument checks run on the host and launch nothing (safe without a GPU)."""
+    lib.hpl_generate.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                                 ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.hpl_generate(1, 0, 10, 10, 0, None, 10, None) == 1          # NULL A
+    assert lib.hpl_generate(1, 0, 10, 10, 0, 8, 5, None) == 1              # lda < m
+    assert lib.hpl_generate(1, 0, 10, 9, 1, 8, 10, None) == 1              # dominant, not square
+    assert lib.hpl_generate(1, 0, 0, 10, 0, None, 1, None) == 0            # empty: nothing to do
+    lib.lu_factor.argtypes = [ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
+    assert lib.lu_factor(-1, 8, 1, 8, None, 8, 1 << 20, 8, None) == 1
+    assert lib.lu_factor(10, 8, 5, 8, None, 8, 1 << 20, 8, None) == 1
+    assert lib.lu_factor(10, 8, 10, 8, None, 8, 16, 8, None) == 6          # workspace too small

@@ -67,6 +67,16 @@ def test_dominant_diagonal_is_exact_row_sum(orc):
         assert D[i, i] > sum(abs(G[i, j]) for j in range(n) if j != i)
 
 
+def test_generate_at_matches_full_matrix(orc):
+    n = 40
+    for dom in (False, True):
+        A = orc.generate(6, orc.STREAM_A, n, n, dominant=dom)
+        rng = np.random.default_rng(1)
+        r, c = rng.integers(0, n, 300), rng.integers(0, n, 300)
+        r[:5] = c[:5]
+        assert np.array_equal(orc.generate_at(6, orc.STREAM_A, n, r, c, dominant=dom), A[r, c])
+
+
 def test_batch_sizes_range(orc):
     s = orc.batch_sizes(5, 4096)
     assert s.min() >= 32 and s.max() <= 512
