@@ -121,6 +121,28 @@ int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* 
               void* ws, size_t ws_bytes, hpl_info* info, void* stream);
 
 /*
+ * lu_factor_noalloc — lu_factor without a workspace argument, for callers
+ * that cannot allocate device memory where they factor (code running under
+ * an allocator it does not own, or with a device-memory budget fixed at
+ * start-up). The paper has no counterpart; this is a convenience of this
+ * library. Same arguments, results and errors as lu_factor, except that the
+ * scratch lu_factor needs comes from one fixed device array inside the
+ * library (lu_factor_noalloc_max_scratch() bytes, 320 KiB, enough for any
+ * NB <= 512), held by every GPU that loads the library until the process
+ * exits. A panel width whose scratch would exceed it returns HPL_ERR_NOMEM
+ * (with a message in hplgb_last_error). The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress) and caches it: make that
+ * first call before any stream capture. The array is shared by all calls on a
+ * device and cleared by each call on its stream; calls whose GPU work
+ * overlaps race on it. It calls no cudaMalloc, cudaFree or other
+ * memory-allocating routine (like lu_factor, its first call on a device also
+ * creates the library's look-ahead stream and events, once).
+ */
+size_t lu_factor_noalloc_max_scratch(void);
+int lu_factor_noalloc(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts,
+                      hpl_info* info, void* stream);
+
+/*
  * lu_solve — the triangular solves that follow the factorization
  * (Sec. III-A.1). trans = 0 solves A X = B: the interchanges are applied to B,
  * then L (unit lower) forward and U backward substitution. trans = 1 solves

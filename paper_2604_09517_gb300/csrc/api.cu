@@ -15,6 +15,12 @@ extern "C" void hplgb_internal_set_error(cudaError_t e, const char* what, const 
              file, line, what);
 }
 
+// Record a plain message as the last error text.
+extern "C" void hplgb_internal_set_message(const char* msg) {
+    std::lock_guard<std::mutex> lk(g_err_mu);
+    snprintf(g_last_error, sizeof(g_last_error), "%s", msg);
+}
+
 // Text of the last CUDA error met by the library (thread-shared, diagnostic only).
 extern "C" const char* hplgb_last_error(void) { return g_last_error; }
 

@@ -22,6 +22,7 @@
     } while (0)
 
 extern "C" void hplgb_internal_set_error(cudaError_t e, const char* what, const char* file, int line);
+extern "C" void hplgb_internal_set_message(const char* msg);
 
 namespace hplgb {
 
