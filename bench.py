@@ -29,6 +29,10 @@ METRIC = "Solve TFLOP/s (2n³/3+2n²): FP64 LU vs MxP+IR at HPL residual<16, % p
 FP64_FLOP_PER_CLK_PER_SM = 4.0      # 2 DFMA/clk/SM: nominal 1.25 TF/s / (152 SMs * 2.07 GHz)
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
+# DRAM bytes (read + write) per flop of the DFMA update kernel, from one ncu
+# capture of an m=7936, n=7680, k=256 launch (959.8 MB for 31.21 GFLOP); the
+# traffic of an update launch scales with its C tile, i.e. with flops at fixed k.
+DGEMM_DRAM_BYTES_PER_FLOP = 959.8e6 / 31.21e9
 
 
 def flops(n: int) -> float:
@@ -260,6 +264,7 @@ def run_ours(a, d: Dist):
     # roofline of the dominant kernel: the DGEMM trailing update (DFMA, FP64 ALU bound)
     upd_ms, upd_flops, upd_cnt = phases["update"]
     achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    traffic = DGEMM_DRAM_BYTES_PER_FLOP * upd_flops / upd_cnt if upd_cnt else None
     peak = NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     phase_report = {k: {"ms_per_step": v[0] / max(len(step_ms), 1), "launch_intervals": v[2]}
                     for k, v in phases.items() if v[2]}
@@ -307,7 +312,8 @@ def run_ours(a, d: Dist):
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": workload_config(a),
                 "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                             "frac": achieved / peak if achieved else None, "traffic": None,
+                             "frac": achieved / peak if achieved else None, "traffic": traffic,
+                             "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None,
                              "kernel": "k_dgemm_sub (DFMA trailing update)",
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,

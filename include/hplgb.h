@@ -169,6 +169,20 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
                         void* stream);
 
 /*
+ * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path
+ * (Sec. III-A.2: the factorization and trailing updates run in low precision;
+ * Table I: BF16 + FP32 + FP64): C = C - A B^T (sub = 1) or C = A B^T (sub = 0),
+ * BF16 operands, FP32 accumulation in tensor memory (tcgen05), FP32 result.
+ * A: M x K, B: N x K, BF16 (raw 16-bit words), K contiguous with row strides
+ * lda, ldb (multiples of 8, base addresses 16-byte aligned). C: FP32
+ * column-major, ldc >= M. err: device int32 the caller zeroes; a bounded
+ * device-side wait that expires stores HPL_ERR_TIMEOUT there. Returns
+ * HPL_ERR_INVALID for bad sizes, strides or alignment.
+ */
+int hplgb_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                    int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream);
+
+/*
  * Diagnostics.
  * hplgb_launch_count: kernels launched by the library so far (process-wide).
  * Phase timers, after the paper's per-panel performance model (Sec. III-A.1,

@@ -90,6 +90,7 @@ def load():
             "lu_solve": (i32, [i64, i64, vp, i64, vp, i32, vp, i64, vp, sz, vp, vp]),
             "hpl_residual_workspace_size": (sz, [i64]),
             "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
+            "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
@@ -216,6 +217,26 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
     _check(lib.hpl_scaled_residual(n, _ptr(A), _ld(A) if A is not None else n, seed, kind, _ptr(x), _ptr(b),
                                    _ptr(out), _ptr(ws), ws.numel(), _stream(x.device)), "hpl_scaled_residual")
     return out
+
+
+def gemm_bf16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sub: bool = True) -> torch.Tensor:
+    """C = C - A B^T (sub) or A B^T on the tcgen05 tensor cores.
+
+    A (M x K) and B (N x K) are bfloat16 with K contiguous; C is FP32 column-major.
+    """
+    lib = load()
+    assert A.dtype == torch.bfloat16 and B.dtype == torch.bfloat16 and C.dtype == torch.float32
+    assert A.stride(1) == 1 and B.stride(1) == 1 and C.stride(0) == 1
+    M, K = A.shape
+    N = B.shape[0]
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    _check(lib.hplgb_gemm_bf16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), _ld(C), int(sub),
+                               _ptr(err), _stream(C.device)), "hplgb_gemm_bf16")
+    torch.cuda.current_stream(C.device).synchronize()
+    e = int(err.item())
+    if e:
+        raise HplError(e, "hplgb_gemm_bf16 (device)")
+    return C
 
 
 PHASES = ("pfact", "swap", "trsm", "update", "other")

@@ -1,0 +1,377 @@
+// BF16 tensor-core GEMM for the mixed-precision factorization (paper
+// Sec. III-A.2: factorization and trailing updates in low precision; the
+// Aurora runs used "BF16-optimized kernels" with FP32 accumulation, Table I).
+//
+//   C (FP32, column-major, ldc) = sub ? C - A * B^T : A * B^T
+//   A: M x K BF16, K contiguous (row stride lda elements)
+//   B: N x K BF16, K contiguous (row stride ldb elements)
+//
+// Blackwell design: a persistent, warp-specialised kernel, one CTA per SM.
+//   warp 0      : TMA producer (cp.async.bulk.tensor, 128B swizzle, 4 stages)
+//   warp 1      : TMEM allocator and single-thread tcgen05.mma issuer
+//   warps 2..5  : epilogue (tcgen05.ld from TMEM, FP32 read-modify-write of C)
+// Tiles are 128 x 256 with a 64-wide K step (one 128-byte swizzle row); the
+// accumulator lives in TMEM, double buffered (2 x 256 columns), so the
+// epilogue of one tile overlaps the MMAs of the next. Tiles are walked in
+// bands of GROUP_M row tiles so the A band stays in L2 while B streams.
+// Every wait is bounded by a %globaltimer deadline; on expiry the CTA raises
+// an error flag, drains what it has in flight, frees TMEM and returns.
+#include <cuda.h>
+
+#include "common.cuh"
+
+namespace hplgb {
+namespace tc {
+
+constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK * 2;
+constexpr int B_BYTES = BN * BK * 2;
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 2 * BN;
+constexpr int THREADS = 192;
+constexpr int GROUP_M = 32;
+constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
+
+// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = BF16
+// (bits 7-9 = 1), B = BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                           ((uint32_t)(BM >> 4) << 24);
+
+struct Params {
+    int M, N, K;
+    float* C;
+    long long ldc;
+    int sub;
+    int* err;
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait. Returns false (and raises the CTA's abort flag and the global
+// error word) when the deadline passes or another role has aborted.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint64_t deadline, volatile int* abort,
+                                          int* err) {
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (globaltimer_ns() > deadline) {
+            *abort = 1;
+            atomicExch(err, HPL_ERR_TIMEOUT);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile stored with the 128-byte
+// swizzle (8 rows x 128 B atoms, 1024-byte aligned): start address >> 4 in
+// bits 0-13, leading byte offset (unused for swizzled K-major; 1) in bits
+// 16-29, stride byte offset 1024 >> 4 in bits 32-45, descriptor version 1 in
+// bits 46-47, layout type 2 (128B swizzle) in bits 61-63.
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+          "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+          "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, int& mt, int& nt) {
+    const int per_group = GROUP_M * nt_count;
+    const int g = t / per_group;
+    const int first = g * GROUP_M;
+    const int gsz = min(mt_count - first, GROUP_M);
+    const int r = t - g * per_group;
+    mt = first + r % gsz;
+    nt = r / gsz;
+}
+
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    unsigned char* tiles = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mt_count = (p.M + BM - 1) / BM, nt_count = (p.N + BN - 1) / BN;
+    const int ntiles = mt_count * nt_count;
+    const int nk = (p.K + BK - 1) / BK;
+    const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&full_bar[s], 1);
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(&tfull_bar[a], 1);
+            mbar_init(&tempty_bar[a], 4);
+        }
+        mbar_init(&drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer ----------------
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
+                int mt, nt;
+                tile_coords(t, mt_count, nt_count, mt, nt);
+                for (int kb = 0; kb < nk; kb++, it++) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&empty_bar[s], ph ^ 1, deadline, &s_abort, p.err)) { ok = false; break; }
+                    unsigned char* sa = tiles + s * STAGE_BYTES;
+                    mbar_expect_tx(&full_bar[s], STAGE_BYTES);
+                    tma_load_2d(sa, &tmA, &full_bar[s], kb * BK, mt * BM);
+                    tma_load_2d(sa + A_BYTES, &tmB, &full_bar[s], kb * BK, nt * BN);
+                }
+            }
+            if (!ok) {
+                // drain: every issued load completes before the CTA can exit
+                const uint32_t first = it > STAGES ? it - STAGES : 0;
+                for (uint32_t j = first; j < it; j++)
+                    mbar_wait(&full_bar[j % STAGES], (j / STAGES) & 1, deadline + 1000000000ull, &s_abort, p.err);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---------------- MMA issuer ----------------
+            uint32_t it = 0, tcount = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x, tcount++) {
+                const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                if (!mbar_wait(&tempty_bar[acc], aph ^ 1, deadline, &s_abort, p.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + acc * BN;
+                for (int kb = 0; kb < nk; kb++, it++) {
+                    const int s = it % STAGES;
+                    const uint32_t ph = (it / STAGES) & 1;
+                    if (!mbar_wait(&full_bar[s], ph, deadline, &s_abort, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tiles + s * STAGE_BYTES);
+                    const uint64_t ad = desc_sw128(sa), bd = desc_sw128(sa + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < BK / 16; kk++)      // 16 BF16 = 32 B per MMA: +2 in the address field
+                        umma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                    umma_commit(&empty_bar[s]);
+                }
+                if (ok) umma_commit(&tfull_bar[acc]);
+            }
+            // all issued MMAs complete before TMEM is released
+            umma_commit(&drain_bar);
+            mbar_wait(&drain_bar, 0, deadline + 1000000000ull, &s_abort, p.err);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..5 ----------------
+        const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
+        const int row_in_tile = quarter * 32 + lane;
+        uint32_t tcount = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tcount++) {
+            int mt, nt;
+            tile_coords(t, mt_count, nt_count, mt, nt);
+            const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
+            tc_fence_after();
+            const int row = mt * BM + row_in_tile;
+            const bool row_ok = row < p.M;
+            for (int c0 = 0; c0 < BN; c0 += 32) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + c0, r);
+                tmem_wait_ld();
+                const int col0 = nt * BN + c0;
+                if (row_ok) {
+                    float* cp = p.C + (long long)col0 * p.ldc + row;
+                    if (p.sub) {
+                        float cv[32];
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            cv[j] = (col0 + j < p.N) ? cp[(long long)j * p.ldc] : 0.0f;
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (col0 + j < p.N) cp[(long long)j * p.ldc] = cv[j] - __uint_as_float(r[j]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; j++)
+                            if (col0 + j < p.N) cp[(long long)j * p.ldc] = __uint_as_float(r[j]);
+                    }
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                     : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Host side: tensor maps through the driver entry point (no libcuda link).
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (EncodeTiledFn)f;
+    }
+    return fn;
+}
+
+// rows x K BF16 matrix, K contiguous, row stride ld elements; box BK x box_rows.
+static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return HPL_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
+}
+
+}  // namespace tc
+
+// C = sub ? C - A B^T : A B^T (see the top of this file). max_ctas <= 0 means
+// one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
+int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
+    using namespace tc;
+    if (M <= 0 || N <= 0) return HPL_OK;
+    if (K <= 0) return HPL_ERR_INVALID;
+    if (M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return HPL_ERR_INVALID;
+    if (lda < K || ldb < K || ldc < M || (lda % 8) || (ldb % 8)) return HPL_ERR_INVALID;
+    if (((uintptr_t)A | (uintptr_t)B) & 15) return HPL_ERR_INVALID;
+    CUtensorMap ma, mb;
+    int st = make_map(&ma, A, M, K, lda, BM);
+    if (st) return st;
+    st = make_map(&mb, B, N, K, ldb, BN);
+    if (st) return st;
+    static bool attr_set = false;
+    if (!attr_set) {
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          DYN_SMEM));
+        attr_set = true;
+    }
+    int dev = 0, sms = kNumSMsGB300;
+    HPL_CUDA_TRY(cudaGetDevice(&dev));
+    HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int64_t ntiles = ((M + BM - 1) / BM) * ((N + BN - 1) / BN);
+    int grid = (int)std::min<int64_t>(ntiles, max_ctas > 0 ? std::min(max_ctas, sms) : sms);
+    Params p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.K = (int)K;
+    p.C = C;
+    p.ldc = ldc;
+    p.sub = sub;
+    p.err = err;
+    p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
+    k_gemm_bf16_tc<<<grid, THREADS, DYN_SMEM, s>>>(ma, mb, p);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" int hplgb_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                               int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream) {
+    if (!err || !C || !A || !B) return HPL_ERR_INVALID;
+    return launch_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
+}

@@ -1,0 +1,46 @@
+"""The tcgen05 BF16 GEMM (C = C - A B^T, FP32 accumulate in TMEM) against a
+plain PyTorch FP64 product of the same BF16 operands, through the C ABI."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(hpl, M, N, K, sub, seed, ld_pad=0):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(seed)
+    lda = ((K + 7) // 8) * 8 + ld_pad
+    Abuf = torch.randn(M, lda, device="cuda", generator=g).to(torch.bfloat16)
+    Bbuf = torch.randn(N, lda, device="cuda", generator=g).to(torch.bfloat16)
+    A, B = Abuf[:, :K], Bbuf[:, :K]
+    C = hpl.colmajor(M, N, dtype=torch.float32)
+    C.copy_(torch.randn(M, N, device="cuda", generator=g))
+    C0 = C.clone()
+    hpl.gemm_bf16(A, B, C, sub=sub)
+    prod = A.double() @ B.double().t()
+    ref = (C0.double() - prod) if sub else prod
+    bound = A.double().abs() @ B.double().abs().t()
+    err = (C.double() - ref).abs()
+    tol = (K * 2.0 ** -23 + 1e-6) * bound + 2.0 ** -23 * C0.double().abs()
+    bad = (err > tol).sum().item()
+    assert bad == 0, f"{bad} entries out of tolerance, max err {err.max().item():.3g}"
+
+
+@pytest.mark.parametrize("M,N,K,sub", [(128, 256, 64, True), (128, 256, 128, False), (1, 1, 8, True),
+                                       (300, 500, 200, True), (257, 513, 72, False), (129, 255, 64, True),
+                                       (1536, 1536, 1536, True), (2048, 4096, 1536, True),
+                                       (4000, 300, 1024, False)])
+def test_gemm_bf16_matches_fp64(hpl, M, N, K, sub):
+    _case(hpl, M, N, K, sub, seed=M + N + K)
+
+
+def test_gemm_bf16_padded_leading_dimension(hpl):
+    _case(hpl, 640, 384, 256, True, seed=3, ld_pad=64)
+
+
+def test_gemm_bf16_rejects_bad_strides(hpl):
+    import torch
+    A = torch.zeros(16, 12, dtype=torch.bfloat16, device="cuda")
+    B = torch.zeros(16, 12, dtype=torch.bfloat16, device="cuda")
+    C = hpl.colmajor(16, 16, dtype=torch.float32)
+    with pytest.raises(hpl.HplError):
+        hpl.gemm_bf16(A, B, C)          # row stride 12 is not a multiple of 8 elements
