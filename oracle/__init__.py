@@ -83,8 +83,8 @@ def _load():
             "orc_lu_sample_diff": (None, [u64, i64, ctypes.c_int, dp, i64, i64p, i64, i64p, i64p, dp]),
             "orc_round_bf16": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_e4m3": (ctypes.c_float, [ctypes.c_float]),
-            "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, fp, i64]),
-            "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, fp, i64, dp, dp, ctypes.c_int, ctypes.c_int,
+            "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, ctypes.c_int, fp, i64, fp]),
+            "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, i64, fp, i64, fp, dp, dp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
             "orc_adjoint": (i64, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64]),
             "orc_batch_sizes": (None, [u64, i64, i64p]),
@@ -239,36 +239,62 @@ def round_e4m3(x: float) -> float:
     return float(_load().orc_round_e4m3(float(x)))
 
 
-def mxp_factor(A, nb: int, prec: int = PREC_BF16):
-    """Blocked unpivoted low-precision LU of FP32(A). Returns (F, info)."""
+NS_ITERS = 3
+
+
+def mxp_factor(A, nb: int, prec: int = PREC_BF16, ns_iters: int = NS_ITERS):
+    """Block LU without pivoting of FP32(A) (see oracle.c). Returns (F, Dinv, info).
+
+    F holds L21 blocks below the diagonal, the block rows A12 above it and the
+    Schur-complemented diagonal blocks D_k on it; Dinv (n x nb) holds D_k^-1
+    in rows k0..k0+kb.
+    """
     F = np.asfortranarray(np.asarray(A, dtype=np.float64).astype(np.float32))
     n = F.shape[0]
-    info = _load().orc_mxp_factor(n, nb, prec, _fp(F), max(n, 1))
-    return F, int(info)
+    Dinv = np.zeros((n, nb), dtype=np.float32, order="F")
+    info = _load().orc_mxp_factor(n, nb, prec, ns_iters, _fp(F), max(n, 1), _fp(Dinv))
+    return F, Dinv, int(info)
 
 
-def mxp_refine(A, F, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0):
-    """Refine with the FP32 factor F. Returns dict(x, status, iters, inner, sr, hist)."""
+def block_lu_parts(F, nb: int):
+    """(L, U) of the block factor as dense FP64 matrices: L block unit lower,
+    U block upper with the D_k on its diagonal."""
+    F = np.asarray(F, dtype=np.float64)
+    n = F.shape[0]
+    L = np.eye(n)
+    U = np.zeros((n, n))
+    for k0 in range(0, n, nb):
+        k1 = min(n, k0 + nb)
+        L[k1:, k0:k1] = F[k1:, k0:k1]
+        U[k0:k1, k0:] = F[k0:k1, k0:]
+    return L, U
+
+
+def mxp_refine(A, F, Dinv, nb: int, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30,
+               tol: float = 16.0):
+    """Refine with the block factor (F, Dinv). Returns dict(x, status, iters, inner, sr, hist)."""
     A = _fortran(A, np.float64)
     F = np.asfortranarray(F, dtype=np.float32)
+    Dinv = np.asfortranarray(Dinv, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = A.shape[0]
     x = np.zeros(n, dtype=np.float64)
     it, inner = ctypes.c_int(0), ctypes.c_int(0)
     sr = ctypes.c_double(0.0)
     hist = np.full(max_iter + 1, np.nan)
-    st = _load().orc_mxp_refine(n, _dp(A), max(n, 1), _fp(F), max(n, 1), _dp(b), _dp(x), int(refine),
-                                int(max_iter), int(gmres_m), float(tol), ctypes.byref(it),
+    st = _load().orc_mxp_refine(n, _dp(A), max(n, 1), nb, _fp(F), max(n, 1), _fp(Dinv), _dp(b), _dp(x),
+                                int(refine), int(max_iter), int(gmres_m), float(tol), ctypes.byref(it),
                                 ctypes.byref(inner), ctypes.byref(sr), _dp(hist))
     return dict(x=x, status=int(st), iters=int(it.value), inner=int(inner.value), sr=float(sr.value),
                 hist=hist[: it.value + 1])
 
 
 def mxp_solve(A, b, nb: int, prec: int = PREC_BF16, refine: int = 1, max_iter: int = 50,
-              gmres_m: int = 30, tol: float = 16.0):
-    F, info = mxp_factor(A, nb, prec)
-    out = mxp_refine(A, F, b, refine, max_iter, gmres_m, tol)
+              gmres_m: int = 30, tol: float = 16.0, ns_iters: int = NS_ITERS):
+    F, Dinv, info = mxp_factor(A, nb, prec, ns_iters)
+    out = mxp_refine(A, F, Dinv, nb, b, refine, max_iter, gmres_m, tol)
     out["F"] = F
+    out["Dinv"] = Dinv
     out["info"] = info
     return out
 

@@ -320,16 +320,24 @@ void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU
  * pivoting, FP64 residual and corrections; Sec. II-B: GMRES-based refinement).
  * Readings, none of which the paper fixes:
  *   - working storage FP32 (FP64 -> FP32 round to nearest);
- *   - per block step of width nb: the diagonal block is factored unpivoted in
- *     FP32; its unit-lower and upper factors are inverted in FP32; the panel
- *     products U12 = inv(L11) A12 and L21 = A21 inv(U11) and the trailing
- *     update A22 -= L21 U12 take their operands rounded to the low precision
- *     and accumulate in FP32, in increasing k;
+ *   - the factorization is the block LU without pivoting (Demmel, Higham &
+ *     Schreiber, "Stability of block LU factorization", Numer. Linear Algebra
+ *     Appl. 2, 1995): A = L U with L block unit lower and U block upper whose
+ *     diagonal blocks D_k are the Schur-complemented diagonal blocks. Per step
+ *     of width nb: D = current diagonal block; Dinv = D^-1 by Newton-Schulz
+ *     (Schulz 1933: X <- X (2I - D X)) from X = diag(D)^-1, ns_iters steps;
+ *     L21 = A21 Dinv; A22 -= L21 A12 (A12 is the block row of U as it stands);
+ *   - products take their operands rounded to the low precision and
+ *     accumulate in FP32 in increasing k. The Newton-Schulz products are kept
+ *     near FP32 accuracy by splitting each operand x into hi = bf16(x) and
+ *     lo = bf16(x - hi) and summing hi*hi, then hi*lo, then lo*hi (three BF16
+ *     products, FP32 accumulation);
  *   - low precision prec = 0: BF16, round to nearest even;
  *     prec = 1: FP8 E4M3 (finite, max 448), round to nearest even, with one
  *     power-of-two scale per 32 consecutive elements along the contraction
  *     index, the smallest one that keeps amax/scale <= 448;
- *     prec = 2: no rounding (FP32 operands), a reference mode.           */
+ *     prec = 2: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
+ *     mode.                                                                  */
 
 /* BF16 round-to-nearest-even of a float: keep 8 significant bits. Written from
  * the format definition (1 sign, 8 exponent, 7 stored fraction bits). */
@@ -418,85 +426,143 @@ static void orc_gemm32(int64_t m, int64_t n, int64_t k, const float* A, int64_t 
         }
 }
 
-/* Blocked unpivoted low-precision LU of the FP32 matrix A (in place). Also
- * returns, if Linv/Uinv are non-NULL (n x nb each, block b at column offset
- * b*nb... stored as nb-wide slices, ld = n), the FP32 inverses of the diagonal
- * factors. Returns info = first zero pivot (1-based) or 0. */
-int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, float* A, int64_t lda) {
+/* C (m x n) += A * B for split operands: A ~ Ah + Al, B ~ Bh + Bl (BF16
+ * parts), accumulating hi*hi, then hi*lo, then lo*hi in FP32 per entry (the
+ * order of one product over a contraction index of length 3k). */
+static void orc_gemm32_split(int64_t m, int64_t n, int64_t k, const float* Ah, const float* Al, int64_t lda,
+                             const float* Bh, const float* Bl, int64_t ldb, float* C, int64_t ldc) {
+#pragma omp parallel for schedule(static)
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = 0; i < m; i++) {
+            float acc = 0.0f;
+            for (int64_t p = 0; p < k; p++) acc += Ah[p * lda + i] * Bh[j * ldb + p];
+            for (int64_t p = 0; p < k; p++) acc += Ah[p * lda + i] * Bl[j * ldb + p];
+            for (int64_t p = 0; p < k; p++) acc += Al[p * lda + i] * Bh[j * ldb + p];
+            C[j * ldc + i] = acc;
+        }
+}
+
+/* hi = bf16(x), lo = bf16(x - hi) for an r x c block (x - hi is exact in FP32). */
+static void orc_split_bf16(const float* X, int64_t r, int64_t c, int64_t ld, float* hi, float* lo) {
+    for (int64_t j = 0; j < c; j++)
+        for (int64_t i = 0; i < r; i++) {
+            float x = X[j * ld + i];
+            float h = orc_round_bf16(x);
+            hi[j * r + i] = h;
+            lo[j * r + i] = orc_round_bf16(x - h);
+        }
+}
+
+/* Newton-Schulz inverse of the kb x kb FP32 block D (ld ldd) into X (ld kb):
+ * X = diag(D)^-1, then ns_iters times R = D X, T = 2I - R, X = X T. With
+ * split != 0 the products use split BF16 operands, else plain FP32. */
+static void orc_newton_schulz(int64_t kb, const float* D, int64_t ldd, int ns_iters, int split, float* X) {
+    size_t sz = sizeof(float) * kb * kb;
+    float *R = (float*)malloc(sz), *Dh = (float*)malloc(sz), *Dl = (float*)malloc(sz);
+    float *Xh = (float*)malloc(sz), *Xl = (float*)malloc(sz), *Th = (float*)malloc(sz), *Tl = (float*)malloc(sz);
+    float* Dc = (float*)malloc(sz);
+    for (int64_t j = 0; j < kb; j++)
+        for (int64_t i = 0; i < kb; i++) {
+            Dc[j * kb + i] = D[j * ldd + i];
+            X[j * kb + i] = (i == j) ? 1.0f / D[j * ldd + j] : 0.0f;
+        }
+    if (split) orc_split_bf16(Dc, kb, kb, kb, Dh, Dl);
+    for (int it = 0; it < ns_iters; it++) {
+        if (split) {
+            orc_split_bf16(X, kb, kb, kb, Xh, Xl);
+            orc_gemm32_split(kb, kb, kb, Dh, Dl, kb, Xh, Xl, kb, R, kb);          /* R = D X */
+        } else {
+            orc_gemm32(kb, kb, kb, Dc, kb, X, kb, R, kb, 0);
+        }
+        for (int64_t j = 0; j < kb; j++)                                         /* T = 2I - R (in R) */
+            for (int64_t i = 0; i < kb; i++) R[j * kb + i] = ((i == j) ? 2.0f : 0.0f) - R[j * kb + i];
+        if (split) {
+            orc_split_bf16(R, kb, kb, kb, Th, Tl);
+            orc_gemm32_split(kb, kb, kb, Xh, Xl, kb, Th, Tl, kb, X, kb);                     /* X = X T */
+        } else {
+            memcpy(Th, X, sz);
+            orc_gemm32(kb, kb, kb, Th, kb, R, kb, X, kb, 0);
+        }
+    }
+    free(R); free(Dh); free(Dl); free(Xh); free(Xl); free(Th); free(Tl); free(Dc);
+}
+
+/* Block LU without pivoting of the FP32 matrix A (n x n, lda), in place:
+ * below the diagonal the blocks L21 of every step, above it the block rows
+ * A12 as they stood at their step, on it the Schur-complemented diagonal
+ * blocks D_k. Dinv (n x nb, ld n) receives D_k^-1 in rows k0..k0+kb.
+ * Returns info = 1-based index of the first exactly zero diagonal entry of a
+ * D_k (Newton-Schulz cannot start there), else 0. */
+int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, int64_t lda, float* Dinv) {
     int64_t info = 0;
-    float* Li = (float*)malloc(sizeof(float) * nb * nb);
-    float* Ui = (float*)malloc(sizeof(float) * nb * nb);
+    float* X = (float*)malloc(sizeof(float) * nb * nb);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
         int64_t kb = n - k0 < nb ? n - k0 : nb;
         float* D = A + k0 * lda + k0;
-        /* 1. unpivoted FP32 getrf of the diagonal block */
-        for (int64_t c = 0; c < kb; c++) {
-            float piv = D[c * lda + c];
-            if (piv == 0.0f) { if (!info) info = k0 + c + 1; continue; }
-            for (int64_t i = c + 1; i < kb; i++) D[c * lda + i] = D[c * lda + i] / piv;
-            for (int64_t j = c + 1; j < kb; j++)
-                for (int64_t i = c + 1; i < kb; i++) D[j * lda + i] -= D[c * lda + i] * D[j * lda + c];
-        }
+        for (int64_t c = 0; c < kb; c++)
+            if (D[c * lda + c] == 0.0f && !info) info = k0 + c + 1;
+        /* 1. D^-1 by Newton-Schulz */
+        orc_newton_schulz(kb, D, lda, ns_iters, prec != 2, X);
+        for (int64_t j = 0; j < kb; j++)
+            for (int64_t i = 0; i < kb; i++) Dinv[j * n + k0 + i] = X[j * kb + i];
         int64_t m = n - k0 - kb;
         if (m == 0) break;
-        /* 2. inverses of the unit-lower and upper factors, column by column */
-        for (int64_t j = 0; j < kb; j++) {
-            for (int64_t i = 0; i < kb; i++) {           /* L x = e_j, forward */
-                float s = (i == j) ? 1.0f : 0.0f;
-                for (int64_t p = 0; p < i; p++) s -= D[p * lda + i] * Li[j * kb + p];
-                Li[j * kb + i] = s;
-            }
-            for (int64_t i = kb - 1; i >= 0; i--) {      /* U x = e_j, backward */
-                float s = (i == j) ? 1.0f : 0.0f;
-                for (int64_t p = i + 1; p < kb; p++) s -= D[p * lda + i] * Ui[j * kb + p];
-                Ui[j * kb + i] = s / D[i * lda + i];
-            }
-        }
-        /* 3. panel products with low-precision operands, FP32 accumulate */
         float* A12 = A + (k0 + kb) * lda + k0;            /* kb x m */
         float* A21 = A + k0 * lda + k0 + kb;              /* m x kb */
         float* A22 = A + (k0 + kb) * lda + k0 + kb;       /* m x m  */
         float* t12 = (float*)malloc(sizeof(float) * kb * m);
         float* t21 = (float*)malloc(sizeof(float) * m * kb);
-        float* Lq = (float*)malloc(sizeof(float) * kb * kb);
-        float* Uq = (float*)malloc(sizeof(float) * kb * kb);
-        memcpy(Lq, Li, sizeof(float) * kb * kb);
-        memcpy(Uq, Ui, sizeof(float) * kb * kb);
-        for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
+        float* Xq = (float*)malloc(sizeof(float) * kb * kb);
+        /* 2. L21 = A21 Dinv with low-precision operands */
+        memcpy(Xq, X, sizeof(float) * kb * kb);
         for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
-        orc_round_operand(prec, Lq, kb, kb, kb, 0);      /* A operand: k along columns */
-        orc_round_operand(prec, t12, kb, m, kb, 1);      /* B operand: k along rows    */
-        orc_round_operand(prec, t21, m, kb, m, 0);
-        orc_round_operand(prec, Uq, kb, kb, kb, 1);
-        orc_gemm32(kb, m, kb, Lq, kb, t12, kb, A12, lda, 0);   /* U12 = inv(L11) A12 */
-        orc_gemm32(m, kb, kb, t21, m, Uq, kb, A21, lda, 0);    /* L21 = A21 inv(U11) */
-        /* 4. trailing update with the rounded panels */
+        orc_round_operand(prec, t21, m, kb, m, 0);       /* A operand: k along columns */
+        orc_round_operand(prec, Xq, kb, kb, kb, 1);      /* B operand: k along rows    */
+        orc_gemm32(m, kb, kb, t21, m, Xq, kb, A21, lda, 0);
+        /* 3. trailing update A22 -= L21 A12 */
         for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
         for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
         orc_round_operand(prec, t21, m, kb, m, 0);
         orc_round_operand(prec, t12, kb, m, kb, 1);
         orc_gemm32(m, m, kb, t21, m, t12, kb, A22, lda, 1);
-        free(t12); free(t21); free(Lq); free(Uq);
+        free(t12); free(t21); free(Xq);
     }
-    free(Li); free(Ui);
+    free(X);
     return info;
 }
 
-/* Preconditioner M^-1 v = U^-1 L^-1 v with the FP32 factor: v rounded to FP32,
- * unit-lower forward and upper backward substitution in FP32, result widened. */
-static void orc_precond(int64_t n, const float* F, int64_t ldf, const double* v, double* out, float* tmp) {
-    for (int64_t i = 0; i < n; i++) tmp[i] = (float)v[i];
-    for (int64_t i = 0; i < n; i++) {
-        float s = tmp[i];
-        for (int64_t j = 0; j < i; j++) s -= F[j * ldf + i] * tmp[j];
-        tmp[i] = s;
+/* Preconditioner M^-1 v with M = L U the block factor, in FP32: y = fl32(v);
+ * forward with the block unit lower L (y_i -= sum_j L_ij y_j over each block
+ * column, in order); backward over the block rows from the last: x_k =
+ * Dinv_k y_k, then y_i -= sum_j U_ij x_j for the rows above. Widened to FP64. */
+static void orc_precond(int64_t n, int64_t nb, const float* F, int64_t ldf, const float* Dinv, const double* v,
+                        double* out, float* y) {
+    float* t = y + n;
+    for (int64_t i = 0; i < n; i++) y[i] = (float)v[i];
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        int64_t kb = n - k0 < nb ? n - k0 : nb;
+        for (int64_t i = k0 + kb; i < n; i++) {
+            float s = 0.0f;
+            for (int64_t j = k0; j < k0 + kb; j++) s += F[j * ldf + i] * y[j];
+            y[i] -= s;
+        }
     }
-    for (int64_t i = n - 1; i >= 0; i--) {
-        float s = tmp[i];
-        for (int64_t j = i + 1; j < n; j++) s -= F[j * ldf + i] * tmp[j];
-        tmp[i] = s / F[i * ldf + i];
+    int64_t last = ((n - 1) / nb) * nb;
+    for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+        int64_t kb = n - k0 < nb ? n - k0 : nb;
+        for (int64_t i = 0; i < kb; i++) {
+            float s = 0.0f;
+            for (int64_t j = 0; j < kb; j++) s += Dinv[j * n + k0 + i] * y[k0 + j];
+            t[i] = s;
+        }
+        for (int64_t i = 0; i < kb; i++) y[k0 + i] = t[i];
+        for (int64_t i = 0; i < k0; i++) {
+            float s = 0.0f;
+            for (int64_t j = k0; j < k0 + kb; j++) s += F[j * ldf + i] * y[j];
+            y[i] -= s;
+        }
     }
-    for (int64_t i = 0; i < n; i++) out[i] = (double)tmp[i];
+    for (int64_t i = 0; i < n; i++) out[i] = (double)y[i];
 }
 
 static void orc_matvec(int64_t n, const double* A, int64_t lda, const double* x, double* y) {
@@ -514,7 +580,7 @@ static double orc_dot(int64_t n, const double* a, const double* b) {
     return s;
 }
 
-/* Refinement to FP64 accuracy with the low-precision factor F (Sec. III-A.2,
+/* Refinement to FP64 accuracy with the low-precision block factor (F, Dinv) (Sec. III-A.2,
  * Sec. II-B). x0 = M^-1 b. Each outer iteration computes r = b - A x in FP64
  * and the scaled residual; it stops once that is below tol. Otherwise the
  * correction d solves A d = r either by one preconditioner application
@@ -527,7 +593,8 @@ static double orc_dot(int64_t n, const double* a, const double* b) {
  * iters = corrections applied, inner = preconditioner applications inside
  * GMRES (equal to iters for refine = 0). hist (optional, max_iter+1) receives
  * the scaled residual before each correction. */
-int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int64_t ldf,
+int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const float* F, int64_t ldf,
+                   const float* Dinv,
                    const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
                    int* iters, int* inner, double* final_sr, double* hist) {
     double eps = 0x1p-53;
@@ -538,7 +605,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int6
         if (s > anorm) anorm = s;
     }
     double bnorm = orc_norm_inf_vec(n, b);
-    float* tmp = (float*)malloc(sizeof(float) * n);
+    float* tmp = (float*)malloc(sizeof(float) * 2 * n);
     double* r = (double*)malloc(sizeof(double) * n);
     double* d = (double*)malloc(sizeof(double) * n);
     int m = gmres_m > 0 ? gmres_m : 1;
@@ -549,7 +616,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int6
     double* sn = (double*)malloc(sizeof(double) * m);
     double* g = (double*)malloc(sizeof(double) * (m + 1));
     double* y = (double*)malloc(sizeof(double) * m);
-    orc_precond(n, F, ldf, b, x, tmp);
+    orc_precond(n, nb, F, ldf, Dinv, b, x, tmp);
     int it = 0, inn = 0, status = 4;
     double sr = INFINITY;
     for (;;) {
@@ -560,7 +627,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int6
         if (sr < tol) { status = 0; break; }
         if (it >= max_iter) break;
         if (refine == 0) {
-            orc_precond(n, F, ldf, r, d, tmp);
+            orc_precond(n, nb, F, ldf, Dinv, r, d, tmp);
             inn++;
         } else {
             double beta = sqrt(orc_dot(n, r, r));
@@ -572,7 +639,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, const float* F, int6
                 double* vj = V + (int64_t)j * n;
                 double* zj = Z + (int64_t)j * n;
                 double* w = V + (int64_t)(j + 1) * n;
-                orc_precond(n, F, ldf, vj, zj, tmp);
+                orc_precond(n, nb, F, ldf, Dinv, vj, zj, tmp);
                 inn++;
                 orc_matvec(n, A, lda, zj, w);
                 for (int i = 0; i <= j; i++) {

@@ -311,14 +311,39 @@ def test_round_e4m3_matches_torch(orc):
 
 # --- HPL-MxP emulation ---------------------------------------------------------------
 
-def test_mxp_factor_fp32_mode_is_unpivoted_lu(orc):
+def test_mxp_factor_fp32_mode_is_block_lu(orc):
+    """FP32 reference mode: L U reproduces A, and every D_k equals L_kk U_kk of
+    the scalar unpivoted LU (computed independently by getrf, which makes no
+    interchange on a diagonally dominant matrix)."""
     n, nb = 96, 32
     A = orc.generate(4, orc.STREAM_A, n, n, dominant=True)
-    F, info = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    F, Dinv, info = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    assert info == 0
+    L, U = orc.block_lu_parts(F, nb)
+    assert np.abs(A - L @ U).max() / np.abs(A).max() < 1e-6
     LU, ipiv, _, _ = orc.getrf(A)
-    assert info == 0 and list(ipiv) == list(range(n))     # dominance: no interchanges
-    rel = np.abs(F - LU).max() / np.abs(LU).max()
-    assert rel < 1e-5
+    assert list(ipiv) == list(range(n))
+    Ls, Us = np.tril(LU, -1) + np.eye(n), np.triu(LU)
+    for k0 in range(0, n, nb):
+        s = slice(k0, k0 + nb)
+        Dk = Ls[s, s] @ Us[s, s]
+        assert np.abs(F[s, s] - Dk).max() / np.abs(Dk).max() < 1e-6
+        assert np.abs(Dinv[s, :] @ Dk - np.eye(nb)).max() < 1e-5
+
+
+def test_newton_schulz_inverse_accuracy(orc):
+    n, nb = 512, 256
+    A = orc.generate(14, orc.STREAM_A, n, n, dominant=True)
+    for prec, tol in ((orc.PREC_BF16, 2e-5), (orc.PREC_FP8, 2e-5), (orc.PREC_FP32, 5e-6)):
+        F, Dinv, _ = orc.mxp_factor(A, nb, prec)
+        for k0 in range(0, n, nb):
+            s = slice(k0, k0 + nb)
+            resid = np.abs(F[s, s].astype(np.float64) @ Dinv[s, :].astype(np.float64) - np.eye(nb)).max()
+            assert resid < tol, (prec, k0, resid)
+    # fewer iterations give a worse inverse (the iteration is really applied)
+    F1, D1, _ = orc.mxp_factor(A, nb, orc.PREC_BF16, ns_iters=1)
+    r1 = np.abs(F1[:nb, :nb].astype(np.float64) @ D1[:nb, :].astype(np.float64) - np.eye(nb)).max()
+    assert r1 > 1e-5
 
 
 def test_mxp_factor_lowprec_error_levels(orc):
@@ -326,22 +351,22 @@ def test_mxp_factor_lowprec_error_levels(orc):
     A = orc.generate(5, orc.STREAM_A, n, n, dominant=True)
 
     def err(prec):
-        F, _ = orc.mxp_factor(A, nb, prec)
-        F = F.astype(np.float64)
-        L = np.tril(F, -1) + np.eye(n)
-        U = np.triu(F)
-        return np.abs(A - L @ U).max() / np.abs(A).max()
+        F, _, _ = orc.mxp_factor(A, nb, prec)
+        L, U = orc.block_lu_parts(F, nb)
+        return np.abs(A - L @ U).max() / np.abs(A[~np.eye(n, dtype=bool)]).max()
 
     e32, e16, e8 = err(orc.PREC_FP32), err(orc.PREC_BF16), err(orc.PREC_FP8)
-    assert e32 < 1e-6
-    assert 1e-6 < e16 < 2.0 ** -8
-    assert e16 < e8 < 2.0 ** -4
+    assert e32 < 1e-4
+    assert e32 < e16 < 2.0 ** -6
+    assert e16 < e8 < 2.0 ** -2
 
 
 def test_mxp_factor_diagonal_matrix_exact(orc):
-    d = np.array([3.0, 5.0, 0.25, 8.0, 2.0, 1.0])
-    F, info = orc.mxp_factor(np.diag(d), 4, orc.PREC_BF16)
+    d = np.array([2.0, 4.0, 0.25, 8.0, 0.5, 1.0])
+    F, Dinv, info = orc.mxp_factor(np.diag(d), 4, orc.PREC_BF16)
     assert np.array_equal(F, np.diag(d).astype(np.float32))
+    assert np.array_equal(Dinv[:4, :4], np.diag(1 / d[:4]).astype(np.float32))
+    assert np.array_equal(Dinv[4:, :2], np.diag(1 / d[4:]).astype(np.float32))
 
 
 @pytest.mark.parametrize("refine", [0, 1])
@@ -353,8 +378,23 @@ def test_mxp_solve_reaches_fp64_solution(orc, refine, prec):
     out = orc.mxp_solve(A, b, nb, prec=prec, refine=refine)
     assert out["status"] == 0 and out["sr"] < 16
     x64, _ = orc.solve(A, b)
-    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 1e-13
+    # a scaled residual below 16 bounds the forward error by ~ kappa * 16 * n * eps
+    bound = 2 * 16 * n * EPS * np.linalg.cond(A, np.inf)
+    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < bound
     assert 1 <= out["iters"] <= 20
+
+
+def test_mxp_preconditioner_is_block_lu_inverse(orc):
+    """With the FP32 factor, one preconditioner application solves L U x = b
+    (checked against numpy's solve of the assembled L U)."""
+    n, nb = 128, 32
+    A = orc.generate(15, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(15, orc.STREAM_B, n, 1)[:, 0].astype(np.float32).astype(np.float64)
+    F, Dinv, _ = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    out = orc.mxp_refine(A, F, Dinv, nb, b, refine=0, max_iter=0)
+    L, U = orc.block_lu_parts(F, nb)
+    x_ref = np.linalg.solve(L @ U, b)
+    assert np.abs(out["x"] - x_ref).max() / np.abs(x_ref).max() < 1e-5
 
 
 def test_mxp_identity_needs_no_correction(orc):
@@ -364,7 +404,7 @@ def test_mxp_identity_needs_no_correction(orc):
     assert out["iters"] == 0 and out["sr"] == 0.0 and np.array_equal(out["x"], b)
 
 
-def test_mxp_gmres_beats_classic_ir(orc):
+def test_mxp_gmres_not_worse_than_classic_ir(orc):
     n, nb = 256, 64
     A = orc.generate(8, orc.STREAM_A, n, n, dominant=True)
     b = orc.generate(8, orc.STREAM_B, n, 1)[:, 0]
@@ -375,10 +415,12 @@ def test_mxp_gmres_beats_classic_ir(orc):
 
 def test_mxp_refine_not_converged_status(orc):
     n = 64
-    A = orc.generate(9, orc.STREAM_A, n, n)          # general matrix: unpivoted LU unstable
+    A = orc.generate(9, orc.STREAM_A, n, n)          # general matrix, useless preconditioner
     b = orc.generate(9, orc.STREAM_B, n, 1)[:, 0]
-    F = np.asfortranarray(np.eye(n, dtype=np.float32))  # useless preconditioner
-    out = orc.mxp_refine(A, F, b, refine=0, max_iter=2)
+    F = np.asfortranarray(np.eye(n, dtype=np.float32))
+    Dinv = np.asfortranarray(np.eye(n, 32, dtype=np.float32))
+    Dinv[32:, :] = np.eye(32, dtype=np.float32)
+    out = orc.mxp_refine(A, F, Dinv, 32, b, refine=0, max_iter=2)
     assert out["status"] == 4 and out["iters"] == 2
 
 
