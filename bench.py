@@ -1,5 +1,6 @@
 #!/usr/bin/env python
-"""Benchmark: HPL FP64 LU solve (n=32768, NB=256, depth-1 look-ahead) on GB300.
+"""Benchmark: HPL FP64 LU solve (n=32768, NB=256, depth-1 look-ahead) on GB300,
+with the HPL-MxP mixed-precision solve (n=98304, NB=1536) reported beside it.
 
 One step = one full solve of a fresh seeded system: lu_factor (PFACT, SWAP,
 DTRSM, DGEMM update, look-ahead) + lu_solve, all in the library's CUDA
@@ -7,6 +8,10 @@ kernels through the C ABI. The matrix (8.6 GB) is regenerated on the device
 before each step, outside the timed interval; it is far larger than L2, so no
 L2 flush is needed. value = credited flops (2n^3/3 + 2n^2) / time, summed over
 ranks, divided by the slowest rank's time.
+
+The mixed-precision solve (BF16 block-LU on the tcgen05 tensor cores + FP64
+GMRES refinement) is timed the same way and reported under "mxp", with its
+speedup over the FP64 LU's rate.
 
 Prints one JSON line (rank 0). --impl reference times the CPU oracle on a
 bounded sample of the same workload instead.
@@ -51,6 +56,9 @@ def parse():
     ap.add_argument("--cpu-sample-n", type=int, default=6144)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-mxp", action="store_true", help="skip the mixed-precision solve")
+    ap.add_argument("--mxp-n", type=int, default=98304)
+    ap.add_argument("--mxp-nb", type=int, default=1536)
     return ap.parse_args()
 
 
@@ -197,6 +205,77 @@ def run_reference(a, d: Dist):
 
 # --- our arm -------------------------------------------------------------------------
 
+def measured_peaks():
+    """Pool-measured peaks (copy bandwidth, cuBLAS BF16) or the fallback figures."""
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained", p["bf16_tflops"]), "source": "measured"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+def run_mxp(a, d: Dist, dev, fp64_value):
+    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 1536):
+    BF16 block-LU factor on the tcgen05 tensor cores + FP64 GMRES refinement."""
+    import torch
+
+    import paper_2604_09517_gb300 as hpl
+
+    n, nb, seed = a.mxp_n, a.mxp_nb, a.seed
+    A = hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
+    b = hpl.generate(seed, hpl.STREAM_B, n, 1, device=dev)[:, 0].contiguous()
+    X = hpl.colmajor(n, 1, device=dev)
+    info = hpl.Info(dev)
+    ws = None
+    for _ in range(a.warmup):
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info)
+    stream = torch.cuda.current_stream(dev)
+    torch.cuda.synchronize(dev)
+    hpl.set_phase_timing(True)
+    step_ms, launches = [], 0
+    for _ in range(a.steps):
+        d.barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        l0 = hpl.launch_count()
+        e0.record(stream)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info)
+        e1.record(stream)
+        launches += hpl.launch_count() - l0
+        torch.cuda.synchronize(dev)
+        d.barrier()
+        step_ms.append(e0.elapsed_time(e1))
+    phases = hpl.phase_times()
+    hpl.set_phase_timing(False)
+    rec = info.read()
+    total_ms = d.max(sum(step_ms))
+    value = d.sum(flops(n) * len(step_ms)) / (total_ms * 1e-3) / 1e12
+    peaks = measured_peaks()
+    upd_ms, upd_flops, upd_cnt = phases["update"]
+    achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
+    peak = peaks["bf16_tflops_sustained"]
+    del A, X, ws
+    torch.cuda.empty_cache()
+    return {"workload": f"hpl_mxp_bf16_n{n}_nb{nb}_gmres", "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
+            "ms_per_step": total_ms / len(step_ms), "steps": a.steps, "warmup": a.warmup,
+            "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
+            "preconditioner_applications": rec["inner_iters"],
+            "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,
+            "fp64_lu_time_at_this_n_s": flops(n) / (fp64_value * 1e12) if fp64_value else None,
+            "fraction_of_bf16_peak": value / peak, "gpu_launches": int(launches),
+            "matrix": "uniform[-0.5,0.5) FP64, diagonal = row sum of |a_ij| (diagonally dominant)",
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "kernel": "k_gemm_bf16_tc (tcgen05 trailing update A22 -= L21 A12, FP32 C)",
+                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})",
+                         "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
+            "phases": {k: {"ms_per_step": v[0] / len(step_ms), "intervals": v[2]} for k, v in phases.items() if v[2]}}
+
+
 def run_ours(a, d: Dist):
     import torch
 
@@ -306,6 +385,10 @@ def run_ours(a, d: Dist):
                "sample": f"oracle getrf+getrs (unblocked FP64, OpenMP) of one n={a.cpu_sample_n} system, "
                          f"{dt:.1f} s"}
 
+    del A, b, b0, ipiv, ws, sws
+    torch.cuda.empty_cache()
+    mxp = None if a.no_mxp else run_mxp(a, d, dev, value)
+
     if d.rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": d.world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": total_ms / len(step_ms), "higher_is_better": True,
@@ -318,7 +401,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report,
-                "fraction_of_fp64_peak": value / peak}
+                "fraction_of_fp64_peak": value / peak, "mxp": mxp}
         print(json.dumps(line), flush=True)
 
 

@@ -169,6 +169,36 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
                         void* stream);
 
 /*
+ * mxp_solve — the HPL-MxP solve (Sec. III-A.2: factorization and trailing
+ * updates in low precision without pivoting, residual and corrections in
+ * FP64; Sec. II-B: non-stationary refinement based on GMRES). A (n x n, lda,
+ * FP64, read only) should be diagonally dominant (the HPL-MxP matrix class,
+ * hpl_generate with HPL_GEN_DIAG_DOMINANT). The factorization is the block LU
+ * without pivoting of an FP32 copy of A with panel width opts->nb (default
+ * 1536): per step, the inverse of the diagonal block by Newton-Schulz
+ * iterations with split-BF16 tensor-core products, then L21 = A21 D^-1 and
+ * A22 -= L21 A12 with BF16 operands and FP32 accumulation. Each of the nrhs
+ * columns of B (ldb) is then solved into X (ldx) by FP64 refinement (opts->
+ * refine: classic iterative refinement or GMRES(opts->gmres_m) with the
+ * factor as right preconditioner) until the HPL scaled residual is below
+ * opts->tol (default 16) or opts->max_iter corrections were made.
+ * On return info (device) holds the status (HPL_OK, HPL_ERR_NOT_CONVERGED with
+ * the best x so far, HPL_ERR_NONFINITE), the largest correction count and
+ * scaled residual over the right-hand sides, and the preconditioner
+ * applications. The call blocks the host until the solve is done (the
+ * refinement reads one scalar per step). ws (device, mxp_workspace_size
+ * bytes) keeps the factor afterwards: FP32 F (n x n, ld n) at byte offset 0
+ * (L21 blocks below the diagonal, U blocks above, D_k on it) and FP32
+ * D_k^-1 (n x nb, ld n, block k in rows k*nb..) at offset
+ * align256(4 n^2). Only opts->prec = HPL_PREC_BF16 is accepted; A == NULL
+ * returns HPL_ERR_INVALID; seed is reserved.
+ */
+size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts);
+int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B, int64_t ldb,
+              double* X, int64_t ldx, const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* info,
+              void* stream);
+
+/*
  * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path
  * (Sec. III-A.2: the factorization and trailing updates run in low precision;
  * Table I: BF16 + FP32 + FP64): C = C - A B^T (sub = 1) or C = A B^T (sub = 0),

@@ -91,6 +91,8 @@ def load():
             "hpl_residual_workspace_size": (sz, [i64]),
             "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
             "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
+            "mxp_workspace_size": (sz, [i64, i64, op]),
+            "mxp_solve": (i32, [i64, i64, vp, i64, u64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
@@ -217,6 +219,43 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
     _check(lib.hpl_scaled_residual(n, _ptr(A), _ld(A) if A is not None else n, seed, kind, _ptr(x), _ptr(b),
                                    _ptr(out), _ptr(ws), ws.numel(), _stream(x.device)), "hpl_scaled_residual")
     return out
+
+
+def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = REFINE_GMRES, max_iter: int = 50,
+              gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
+              info: Info | None = None):
+    """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
+
+    Returns (X, info, ws); ws holds the block factor afterwards (see mxp_factor_views).
+    """
+    lib = load()
+    n = A.shape[0]
+    vec = B.dim() == 1
+    Bm = B.view(n, 1) if vec else B
+    nrhs = Bm.shape[1]
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol)
+    if X is None:
+        X = colmajor(n, nrhs, device=A.device)
+    Xm = X.view(n, 1) if X.dim() == 1 else X
+    need = lib.mxp_workspace_size(n, nrhs, ctypes.byref(opts))
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, A.device)
+    if info is None:
+        info = Info(A.device)
+    _check(lib.mxp_solve(n, nrhs, _ptr(A), _ld(A), 0, _ptr(Bm), _ld(Bm) if nrhs > 1 else n, _ptr(Xm),
+                         _ld(Xm) if nrhs > 1 else n, ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(),
+                         _stream(A.device)), "mxp_solve")
+    return X, info, ws
+
+
+def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 1536):
+    """(F, Dinv) views of the block factor that mxp_solve leaves in its workspace."""
+    nb = min(nb, n)
+    f_bytes = 4 * n * n
+    d_off = (f_bytes + 255) // 256 * 256
+    F = ws[:f_bytes].view(torch.float32).view(n, n).t()
+    Dinv = ws[d_off:d_off + 4 * n * nb].view(torch.float32).view(nb, n).t()
+    return F, Dinv
 
 
 def gemm_bf16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sub: bool = True) -> torch.Tensor:

@@ -1,0 +1,582 @@
+// mxp_solve: the HPL-MxP solve (paper Sec. III-A.2; Sec. II-B for GMRES-based
+// refinement) on one GB300.
+//
+// Factorization: block LU without pivoting (Demmel, Higham & Schreiber 1995)
+// of an FP32 working copy F of A, panel width NB. Per step k:
+//   D   = diagonal block of F (kb x kb, the Schur complement so far)
+//   D^-1 by Newton-Schulz, X <- X (2I - D X) from X = diag(D)^-1, with each
+//        product on the tcgen05 tensor cores in split BF16 (operands hi + lo,
+//        products hi*hi + hi*lo + lo*hi over a contraction of length 3kb)
+//   L21 = A21 D^-1         (BF16 operands, FP32 accumulate, written into F)
+//   A22 = A22 - L21 A12    (BF16 operands, FP32 accumulate in TMEM, FP32 C)
+// Every O(n^2 NB) and O(n^3) product runs on the tensor cores; the FP32 work
+// outside them is elementwise.
+// Refinement (FP64): x0 = M^-1 b with M = L U applied in FP32 by block
+// forward / backward substitution (GEMV kernels over the factor's panels and
+// the stored D_k^-1); then r = b - A x in FP64 with the scaled residual; stop
+// below tol; correction by classic iterative refinement (d = M^-1 r) or by
+// GMRES right-preconditioned with M^-1 (modified Gram-Schmidt and Givens
+// rotations in FP64; the Hessenberg least-squares problem is solved on the
+// host), x += d. The host reads one scalar per GMRES step and per outer
+// iteration, so mxp_solve returns only when the solve is done.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hplgb {
+
+int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s);
+size_t residual_ws_bytes(int64_t n);
+int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
+                        double* sr, void* ws, cudaStream_t s);
+
+constexpr int kNsIters = 3;
+constexpr int kDotBlocks = 304;
+
+static inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
+
+// ---------------------------------------------------------------------------
+// Operand conversion. X is FP32 column-major (rows x cols, ldx). The BF16
+// operand has K contiguous with row stride ldo and starts at column seg_off:
+//   trans = 1: operand row r (< rows) holds X(r, 0..cols): the M x K operand
+//              of X itself (K = cols);
+//   trans = 0: operand row c (< cols) holds X(0..rows, c): the N x K operand
+//              for a product with X on the right (K = rows).
+// part 0 = round to nearest even, 1 = hi = bf16(x), 2 = lo = bf16(x - hi).
+// K positions in [K extent, kpad) are written as zeros.
+__device__ __forceinline__ float bf16_part(float x, int part) {
+    float h = __bfloat162float(__float2bfloat16_rn(x));
+    return part == 2 ? __bfloat162float(__float2bfloat16_rn(x - h)) : h;
+}
+
+__global__ void __launch_bounds__(256) k_to_bf16_t(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                   int64_t cols, int part, __nv_bfloat16* __restrict__ out,
+                                                   int64_t ldo, int64_t seg_off, int64_t kpad) {
+    __shared__ float tile[32][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        int64_t c = c0 + i, r = r0 + tx;
+        tile[i][tx] = (c < cols && r < rows) ? X[c * ldx + r] : 0.0f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        int64_t r = r0 + i, c = c0 + tx;
+        if (r < rows && c < kpad) out[r * ldo + seg_off + c] = __float2bfloat16_rn(bf16_part(tile[tx][i], part));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_to_bf16_n(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                   int64_t cols, int part, __nv_bfloat16* __restrict__ out,
+                                                   int64_t ldo, int64_t seg_off, int64_t kpad) {
+    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;   // K index
+    const int64_t c = blockIdx.y;                                  // operand row
+    if (r >= kpad || c >= cols) return;
+    float v = r < rows ? X[c * ldx + r] : 0.0f;
+    out[c * ldo + seg_off + r] = __float2bfloat16_rn(bf16_part(v, part));
+}
+
+static int to_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, int part, uint16_t* out,
+                   int64_t ldo, int64_t seg_off, int64_t kpad, cudaStream_t s) {
+    if (trans) {
+        dim3 g((unsigned)((kpad + 31) / 32), (unsigned)((rows + 31) / 32));
+        k_to_bf16_t<<<g, dim3(32, 8), 0, s>>>(X, ldx, rows, cols, part, (__nv_bfloat16*)out, ldo, seg_off, kpad);
+    } else {
+        if (cols > 65535) {
+            // split the operand rows over several launches (grid.y limit)
+            for (int64_t c0 = 0; c0 < cols; c0 += 65535) {
+                int64_t cc = std::min<int64_t>(65535, cols - c0);
+                dim3 g((unsigned)((kpad + 255) / 256), (unsigned)cc);
+                k_to_bf16_n<<<g, 256, 0, s>>>(X + c0 * ldx, ldx, rows, cc, part, (__nv_bfloat16*)(out + c0 * ldo),
+                                              ldo, seg_off, kpad);
+                HPL_LAUNCH_CHECK();
+            }
+            return HPL_OK;
+        }
+        dim3 g((unsigned)((kpad + 255) / 256), (unsigned)cols);
+        k_to_bf16_n<<<g, 256, 0, s>>>(X, ldx, rows, cols, part, (__nv_bfloat16*)out, ldo, seg_off, kpad);
+    }
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Small dense kernels.
+__global__ void k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda, float* __restrict__ F,
+                                 int64_t ldf) {
+    const int64_t total = n * n;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = t / n, i = t - j * n;
+        F[j * ldf + i] = (float)A[j * lda + i];
+    }
+}
+
+__global__ void k_ns_init(const float* __restrict__ D, int64_t ldd, int kb, float* __restrict__ X) {
+    const int64_t total = (int64_t)kb * kb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = t / kb, i = t - j * kb;
+        X[t] = (i == j) ? 1.0f / D[j * ldd + j] : 0.0f;
+    }
+}
+
+__global__ void k_two_minus_eye(float* __restrict__ R, int kb) {
+    const int64_t total = (int64_t)kb * kb;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = t / kb, i = t - j * kb;
+        R[t] = ((i == j) ? 2.0f : 0.0f) - R[t];
+    }
+}
+
+__global__ void k_copy_block32(const float* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                               float* __restrict__ dst, int64_t ldd) {
+    const int64_t total = rows * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = t / rows, i = t - j * rows;
+        dst[j * ldd + i] = src[j * lds + i];
+    }
+}
+
+__global__ void k_zero_diag_flag(const float* __restrict__ D, int64_t ldd, int kb, int64_t k0, hpl_info* info) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kb; i += gridDim.x * blockDim.x)
+        if (D[(int64_t)i * ldd + i] == 0.0f)
+            atomicCAS((unsigned long long*)&info->info, 0ull, (unsigned long long)(k0 + i + 1));
+}
+
+// y (= or -=) P x, P FP32 column-major rows x cols. 32 rows per CTA (lane =
+// row), the 8 warps split the columns, partial sums combined in a fixed order.
+__global__ void __launch_bounds__(256) k_gemv32(int64_t rows, int64_t cols, const float* __restrict__ P, int64_t ldp,
+                                                const float* __restrict__ x, float* __restrict__ y, int sub) {
+    __shared__ float part[8][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
+    float acc = 0.0f;
+    if (r < rows) {
+#pragma unroll 4
+        for (int64_t c = warp; c < cols; c += 8) acc = fmaf(P[c * ldp + r], __ldg(x + c), acc);
+    }
+    part[warp][lane] = acc;
+    __syncthreads();
+    if (warp == 0 && r < rows) {
+        float s = 0.0f;
+        for (int w = 0; w < 8; w++) s += part[w][lane];
+        y[r] = sub ? y[r] - s : s;
+    }
+}
+
+__global__ void k_f64_to_f32(int64_t n, const double* __restrict__ v, float* __restrict__ y) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = (float)v[i];
+}
+__global__ void k_f32_to_f64(int64_t n, const float* __restrict__ y, double* __restrict__ v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        v[i] = (double)y[i];
+}
+__global__ void k_copy32(int64_t n, const float* __restrict__ a, float* __restrict__ b) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = a[i];
+}
+
+// --- FP64 vector kernels of the refinement (deterministic reductions) ---
+__global__ void __launch_bounds__(256) k_dot_partial(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, double* __restrict__ part) {
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x; i < n; i += (int64_t)gridDim.x * 256) s = fma(a[i], b[i], s);
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = sm[0];
+}
+__global__ void __launch_bounds__(256) k_dot_final(int nparts, const double* __restrict__ part, double* out,
+                                                   int take_sqrt) {
+    __shared__ double sm[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < nparts; i += 256) s += part[i];
+    sm[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sm[threadIdx.x] += sm[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = take_sqrt ? sqrt(sm[0]) : sm[0];
+}
+// y += sign * (*alpha) * x
+__global__ void k_axpy_dev(int64_t n, const double* __restrict__ alpha, double sign, const double* __restrict__ x,
+                           double* __restrict__ y) {
+    const double a = sign * *alpha;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = fma(a, x[i], y[i]);
+}
+// y = x / (*s) (0 when *s == 0)
+__global__ void k_scale_inv_dev(int64_t n, const double* __restrict__ sc, const double* __restrict__ x,
+                                double* __restrict__ y) {
+    const double d = *sc;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] = d != 0.0 ? x[i] / d : 0.0;
+}
+__global__ void k_add64(int64_t n, const double* __restrict__ d, double* __restrict__ x) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        x[i] += d[i];
+}
+// d = sum_t y[t] * Z[:, t]
+__global__ void k_combine(int64_t n, int k, const double* __restrict__ Z, int64_t ldz, const double* __restrict__ y,
+                          double* __restrict__ d) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int t = 0; t < k; t++) s = fma(y[t], Z[t * ldz + i], s);
+        d[i] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Workspace.
+struct MxpWs {
+    float* F;          // n x n working matrix / factor (ld = n)
+    float* Dinv;       // n x nb, D_k^-1 in rows k0..k0+kb (ld = n)
+    uint16_t* opA;     // BF16 operand (n x nb8)
+    uint16_t* opB;     // BF16 operand (n x nb8)
+    uint16_t* nsD;     // split D as A operand (nb x 3 nb8)
+    uint16_t* nsX;     // split X as A operand
+    uint16_t* nsB;     // split X or T as B operand
+    float* R;          // nb x nb
+    float* X;          // nb x nb
+    void* resws;       // residual partial sums
+    double* r;         // n
+    double* d;         // n
+    double* V;         // n x (m+1)
+    double* Z;         // n x m
+    double* h;         // (m+1) x m Hessenberg on the device
+    double* y;         // m coefficients
+    double* part;      // dot partials
+    double* scal;      // 4 device scalars (sr, beta, ...)
+    float* y32;        // 2n FP32 scratch
+    int* err;          // device error word of the GEMM kernels
+};
+
+static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) {
+    const int64_t nb8 = round8(nb);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        size_t o = off;
+        off = align_up(off + bytes, 256);
+        return base ? (void*)(base + o) : (void*)nullptr;
+    };
+    MxpWs t;
+    t.F = (float*)take(sizeof(float) * n * n);
+    t.Dinv = (float*)take(sizeof(float) * n * nb);
+    t.opA = (uint16_t*)take(2 * n * nb8);
+    t.opB = (uint16_t*)take(2 * n * nb8);
+    t.nsD = (uint16_t*)take(2 * nb * 3 * nb8);
+    t.nsX = (uint16_t*)take(2 * nb * 3 * nb8);
+    t.nsB = (uint16_t*)take(2 * nb * 3 * nb8);
+    t.R = (float*)take(sizeof(float) * nb * nb);
+    t.X = (float*)take(sizeof(float) * nb * nb);
+    t.resws = take(residual_ws_bytes(n));
+    t.r = (double*)take(sizeof(double) * n);
+    t.d = (double*)take(sizeof(double) * n);
+    t.V = (double*)take(sizeof(double) * n * (m + 1));
+    t.Z = (double*)take(sizeof(double) * n * m);
+    t.h = (double*)take(sizeof(double) * (m + 1) * m);
+    t.y = (double*)take(sizeof(double) * (m + 1));
+    t.part = (double*)take(sizeof(double) * kDotBlocks);
+    t.scal = (double*)take(sizeof(double) * 8);
+    t.y32 = (float*)take(sizeof(float) * 2 * n);
+    t.err = (int*)take(sizeof(int) * 4);
+    if (w) *w = t;
+    return off;
+}
+
+static unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
+
+struct Mxp {
+    int64_t n, nb;
+    int m;
+    Opts o;
+    MxpWs w;
+    cudaStream_t s;
+    const double* A;
+    int64_t lda;
+
+    int dot(const double* a, const double* b, double* out, int take_sqrt) {
+        k_dot_partial<<<kDotBlocks, 256, 0, s>>>(n, a, b, w.part);
+        HPL_LAUNCH_CHECK();
+        k_dot_final<<<1, 256, 0, s>>>(kDotBlocks, w.part, out, take_sqrt);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
+
+    // ---- factorization ----
+    int factor(hpl_info* info) {
+        const int64_t ldf = n;
+        HPL_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, s));
+        k_f64_to_f32_mat<<<grid_for(n * n), 256, 0, s>>>(n, A, lda, w.F, ldf);
+        HPL_LAUNCH_CHECK();
+        for (int64_t k0 = 0; k0 < n; k0 += nb) {
+            const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
+            float* D = w.F + k0 * ldf + k0;
+            int slot = phase_begin(s);
+            k_zero_diag_flag<<<1, 256, 0, s>>>(D, ldf, (int)kb, k0, info);
+            HPL_LAUNCH_CHECK();
+            k_ns_init<<<grid_for(kb * kb), 256, 0, s>>>(D, ldf, (int)kb, w.X);
+            HPL_LAUNCH_CHECK();
+            int st;
+            // split D as the A operand: [hi | hi | lo]
+            if ((st = to_bf16(D, ldf, kb, kb, 1, 1, w.nsD, K3, 0, kb8, s))) return st;
+            if ((st = to_bf16(D, ldf, kb, kb, 1, 1, w.nsD, K3, kb8, kb8, s))) return st;
+            if ((st = to_bf16(D, ldf, kb, kb, 1, 2, w.nsD, K3, 2 * kb8, kb8, s))) return st;
+            for (int it = 0; it < kNsIters; it++) {
+                // R = D X: B operand from X, [hi | lo | hi]
+                if ((st = to_bf16(w.X, kb, kb, kb, 0, 1, w.nsB, K3, 0, kb8, s))) return st;
+                if ((st = to_bf16(w.X, kb, kb, kb, 0, 2, w.nsB, K3, kb8, kb8, s))) return st;
+                if ((st = to_bf16(w.X, kb, kb, kb, 0, 1, w.nsB, K3, 2 * kb8, kb8, s))) return st;
+                if ((st = launch_gemm_bf16(kb, kb, K3, w.nsD, K3, w.nsB, K3, w.R, kb, 0, w.err, o.timeout_ns, 0, s)))
+                    return st;
+                k_two_minus_eye<<<grid_for(kb * kb), 256, 0, s>>>(w.R, (int)kb);
+                HPL_LAUNCH_CHECK();
+                // X = X T: A operand from X [hi | hi | lo], B operand from T [hi | lo | hi]
+                if ((st = to_bf16(w.X, kb, kb, kb, 1, 1, w.nsX, K3, 0, kb8, s))) return st;
+                if ((st = to_bf16(w.X, kb, kb, kb, 1, 1, w.nsX, K3, kb8, kb8, s))) return st;
+                if ((st = to_bf16(w.X, kb, kb, kb, 1, 2, w.nsX, K3, 2 * kb8, kb8, s))) return st;
+                if ((st = to_bf16(w.R, kb, kb, kb, 0, 1, w.nsB, K3, 0, kb8, s))) return st;
+                if ((st = to_bf16(w.R, kb, kb, kb, 0, 2, w.nsB, K3, kb8, kb8, s))) return st;
+                if ((st = to_bf16(w.R, kb, kb, kb, 0, 1, w.nsB, K3, 2 * kb8, kb8, s))) return st;
+                if ((st = launch_gemm_bf16(kb, kb, K3, w.nsX, K3, w.nsB, K3, w.X, kb, 0, w.err, o.timeout_ns, 0, s)))
+                    return st;
+            }
+            k_copy_block32<<<grid_for(kb * kb), 256, 0, s>>>(w.X, kb, kb, kb, w.Dinv + k0, n);
+            HPL_LAUNCH_CHECK();
+            if (m2 > 0) {
+                float* A21 = w.F + k0 * ldf + k0 + kb;
+                float* A12 = w.F + (k0 + kb) * ldf + k0;
+                float* A22 = w.F + (k0 + kb) * ldf + k0 + kb;
+                // L21 = A21 D^-1
+                if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
+                if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                if ((st = launch_gemm_bf16(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0, w.err, o.timeout_ns, 0, s)))
+                    return st;
+                phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
+                // A22 -= L21 A12
+                slot = phase_begin(s);
+                if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
+                if ((st = to_bf16(A12, ldf, kb, m2, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                if ((st = launch_gemm_bf16(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1, w.err, o.timeout_ns, 0, s)))
+                    return st;
+                phase_end(slot, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
+            } else {
+                phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb);
+            }
+        }
+        return HPL_OK;
+    }
+
+    // ---- preconditioner: out = M^-1 v (FP64 in and out, FP32 inside) ----
+    int precond(const double* v, double* out) {
+        const int64_t ldf = n;
+        float* y = w.y32;
+        float* t = w.y32 + n;
+        int slot = phase_begin(s);
+        k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, v, y);
+        HPL_LAUNCH_CHECK();
+        for (int64_t k0 = 0; k0 < n; k0 += nb) {
+            const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+            if (m2 > 0) {
+                k_gemv32<<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0,
+                                                                   y + k0 + kb, 1);
+                HPL_LAUNCH_CHECK();
+            }
+        }
+        const int64_t last = ((n - 1) / nb) * nb;
+        for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+            const int64_t kb = std::min(nb, n - k0);
+            k_gemv32<<<(unsigned)((kb + 31) / 32), 256, 0, s>>>(kb, kb, w.Dinv + k0, n, y + k0, t, 0);
+            HPL_LAUNCH_CHECK();
+            k_copy32<<<grid_for(kb), 256, 0, s>>>(kb, t, y + k0);
+            HPL_LAUNCH_CHECK();
+            if (k0 > 0) {
+                k_gemv32<<<(unsigned)((k0 + 31) / 32), 256, 0, s>>>(k0, kb, w.F + k0 * ldf, ldf, y + k0, y, 1);
+                HPL_LAUNCH_CHECK();
+            }
+        }
+        k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, y, out);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_OTHER, 4.0 * n * n + 4.0 * n * nb);
+        return HPL_OK;
+    }
+
+    int read_scalar(const double* dev, double* host) {
+        HPL_CUDA_TRY(cudaMemcpyAsync(host, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+        HPL_CUDA_TRY(cudaStreamSynchronize(s));
+        return HPL_OK;
+    }
+
+    int check_err(int* status) {
+        int e = 0;
+        HPL_CUDA_TRY(cudaMemcpyAsync(&e, w.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        HPL_CUDA_TRY(cudaStreamSynchronize(s));
+        if (e) *status = e;
+        return HPL_OK;
+    }
+
+    // GMRES correction: d solves A d = r approximately (right preconditioning).
+    int gmres(const double* r, double* d, int* inner) {
+        const int64_t ldv = n;
+        double beta = 0.0;
+        int st;
+        if ((st = dot(r, r, w.scal + 1, 1))) return st;
+        if ((st = read_scalar(w.scal + 1, &beta))) return st;
+        if (!(beta > 0.0) || !std::isfinite(beta)) {
+            HPL_CUDA_TRY(cudaMemsetAsync(d, 0, sizeof(double) * n, s));
+            return HPL_OK;
+        }
+        k_scale_inv_dev<<<grid_for(n), 256, 0, s>>>(n, w.scal + 1, r, w.V);
+        HPL_LAUNCH_CHECK();
+        std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0), y(m), col(m + 1);
+        g[0] = beta;
+        int kk = 0;
+        for (int j = 0; j < m; j++) {
+            double* vj = w.V + (int64_t)j * ldv;
+            double* zj = w.Z + (int64_t)j * ldv;
+            double* wv = w.V + (int64_t)(j + 1) * ldv;
+            if ((st = precond(vj, zj))) return st;
+            (*inner)++;
+            if ((st = launch_residual_vec(n, A, lda, zj, nullptr, wv, nullptr, w.resws, s))) return st;
+            for (int i = 0; i <= j; i++) {
+                double* hij = w.h + (int64_t)j * (m + 1) + i;
+                if ((st = dot(wv, w.V + (int64_t)i * ldv, hij, 0))) return st;
+                k_axpy_dev<<<grid_for(n), 256, 0, s>>>(n, hij, -1.0, w.V + (int64_t)i * ldv, wv);
+                HPL_LAUNCH_CHECK();
+            }
+            double* hn = w.h + (int64_t)j * (m + 1) + j + 1;
+            if ((st = dot(wv, wv, hn, 1))) return st;
+            k_scale_inv_dev<<<grid_for(n), 256, 0, s>>>(n, hn, wv, wv);
+            HPL_LAUNCH_CHECK();
+            HPL_CUDA_TRY(cudaMemcpyAsync(col.data(), w.h + (int64_t)j * (m + 1), sizeof(double) * (j + 2),
+                                         cudaMemcpyDeviceToHost, s));
+            HPL_CUDA_TRY(cudaStreamSynchronize(s));
+            for (int i = 0; i < j; i++) {                    // previous rotations
+                double a = col[i], c = col[i + 1];
+                col[i] = cs[i] * a + sn[i] * c;
+                col[i + 1] = -sn[i] * a + cs[i] * c;
+            }
+            double a = col[j], c = col[j + 1];
+            double rho = std::hypot(a, c);
+            cs[j] = rho != 0.0 ? a / rho : 1.0;
+            sn[j] = rho != 0.0 ? c / rho : 0.0;
+            col[j] = rho;
+            col[j + 1] = 0.0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            for (int i = 0; i <= j; i++) H[(size_t)j * (m + 1) + i] = col[i];
+            kk = j + 1;
+            if (std::fabs(g[j + 1]) <= 1e-10 * beta || rho == 0.0) break;
+        }
+        for (int i = kk - 1; i >= 0; i--) {
+            double sacc = g[i];
+            for (int q = i + 1; q < kk; q++) sacc -= H[(size_t)q * (m + 1) + i] * y[q];
+            y[i] = sacc / H[(size_t)i * (m + 1) + i];
+        }
+        HPL_CUDA_TRY(cudaMemcpyAsync(w.y, y.data(), sizeof(double) * kk, cudaMemcpyHostToDevice, s));
+        k_combine<<<grid_for(n), 256, 0, s>>>(n, kk, w.Z, ldv, w.y, d);
+        HPL_LAUNCH_CHECK();
+        HPL_CUDA_TRY(cudaStreamSynchronize(s));    // y lives on the host stack
+        return HPL_OK;
+    }
+
+    // Refine one right-hand side. Returns the HPL_* outcome.
+    int refine(const double* b, double* x, int* iters, int* inner, double* sr_out, int* status) {
+        int st;
+        if ((st = precond(b, x))) return st;
+        int it = 0;
+        double sr = INFINITY;
+        *status = HPL_ERR_NOT_CONVERGED;
+        for (;;) {
+            if ((st = launch_residual_vec(n, A, lda, x, b, w.r, w.scal, w.resws, s))) return st;
+            if ((st = read_scalar(w.scal, &sr))) return st;
+            if (!std::isfinite(sr)) { *status = HPL_ERR_NONFINITE; break; }
+            if (sr < o.tol) { *status = HPL_OK; break; }
+            if (it >= o.max_iter) break;
+            if (o.refine == HPL_REFINE_IR) {
+                if ((st = precond(w.r, w.d))) return st;
+                (*inner)++;
+            } else {
+                if ((st = gmres(w.r, w.d, inner))) return st;
+            }
+            k_add64<<<grid_for(n), 256, 0, s>>>(n, w.d, x);
+            HPL_LAUNCH_CHECK();
+            it++;
+        }
+        *iters = it;
+        *sr_out = sr;
+        return check_err(status);
+    }
+};
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts) {
+    (void)nrhs;
+    Opts o = resolve_opts(opts, 1536);
+    int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
+    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr);
+}
+
+extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
+                         int64_t ldb, double* X, int64_t ldx, const hpl_opts* opts, void* ws, size_t ws_bytes,
+                         hpl_info* info, void* stream) {
+    (void)seed;
+    if (n <= 0 || nrhs < 0 || !A || lda < n || !info) return HPL_ERR_INVALID;
+    if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
+    if (n > 0x7fffffff) return HPL_ERR_INVALID;
+    Opts o = resolve_opts(opts, 1536);
+    if (o.nb < 8 || o.prec != HPL_PREC_BF16) return HPL_ERR_INVALID;
+    if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
+    Mxp mx;
+    mx.n = n;
+    mx.nb = std::min<int64_t>(o.nb, n);
+    mx.m = o.gmres_m;
+    mx.o = o;
+    mx.s = (cudaStream_t)stream;
+    mx.A = A;
+    mx.lda = lda;
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
+    if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
+    cudaStream_t s = mx.s;
+    HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
+    int st = mx.factor(info);
+    if (st) return st;
+    hpl_info h;
+    memset(&h, 0, sizeof(h));
+    h.status = HPL_OK;
+    HPL_CUDA_TRY(cudaMemcpyAsync(&h.info, &info->info, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    HPL_CUDA_TRY(cudaStreamSynchronize(s));
+    int worst = HPL_OK;
+    double worst_sr = 0.0;
+    int max_it = 0, inner = 0;
+    for (int64_t c = 0; c < nrhs; c++) {
+        int it = 0, status = HPL_OK;
+        double sr = 0.0;
+        if ((st = mx.refine(B + c * ldb, X + c * ldx, &it, &inner, &sr, &status))) return st;
+        if (status != HPL_OK && worst == HPL_OK) worst = status;
+        max_it = std::max(max_it, it);
+        worst_sr = std::max(worst_sr, sr);
+    }
+    h.status = worst;
+    if (h.info != 0 && worst == HPL_OK) h.status = HPL_ERR_SINGULAR;
+    h.iters = max_it;
+    h.inner_iters = inner;
+    h.scaled_residual = worst_sr;
+    HPL_CUDA_TRY(cudaMemcpyAsync(info, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    HPL_CUDA_TRY(cudaStreamSynchronize(s));
+    return HPL_OK;
+}

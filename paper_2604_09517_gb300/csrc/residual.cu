@@ -72,6 +72,7 @@ __global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __
     double r = 0.0, s = 0.0;
     uint64_t lo = 0, hi = 0;
     if (A) {
+#pragma unroll 8
         for (int64_t j = j0; j < j1; j++) {
             double a = A[j * lda + i];
             r = fma(a, x[j], r);
@@ -151,7 +152,40 @@ __global__ void k_res_final(int64_t n, const unsigned long long* maxima, double*
     *out = mr / (0x1p-53 * (ma * mx + mb) * (double)n);
 }
 
+// Residual vector and matrix-vector product for the refinement loop: after
+// k_res_partial, r_i = b_i - sum of the row's partials (b != NULL) or
+// r_i = sum of the partials (b == NULL, i.e. r = A x).
+__global__ void __launch_bounds__(256) k_res_vec(int64_t n, const double* __restrict__ b, ResWs w,
+                                                 double* __restrict__ r) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    double s = 0.0;
+    for (int c = 0; c < kResChunks; c++) s += w.part_r[c * n + i];
+    r[i] = b ? b[i] - s : s;
+}
+
 size_t residual_ws_bytes(int64_t n) { return res_ws_layout(n > 0 ? n : 1, nullptr, nullptr); }
+
+// r = b - A x (b != NULL) or r = A x (b == NULL), A stored column-major (FP64).
+// With sr != NULL (and b != NULL) also the scaled residual of x.
+int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
+                        double* sr, void* ws, cudaStream_t s) {
+    ResWs w;
+    res_ws_layout(n, &w, (char*)ws);
+    dim3 g1((unsigned)((n + 255) / 256), kResChunks);
+    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, 0, 0, x, w);
+    HPL_LAUNCH_CHECK();
+    k_res_vec<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, w, r);
+    HPL_LAUNCH_CHECK();
+    if (sr && b) {
+        HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
+        k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, 0, x, b, w);
+        HPL_LAUNCH_CHECK();
+        k_res_final<<<1, 1, 0, s>>>(n, w.maxima, sr);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
+}
 
 // Shared by the mixed-precision solver: computes the scaled residual into out.
 int launch_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, int kind, const double* x,
