@@ -199,6 +199,51 @@ int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t se
               void* stream);
 
 /*
+ * lu_solve_backward — the adjoint of X = A^-1 B (not in the paper; the
+ * differentiable form of the mixed-precision solve): grad_B = A^-T G and, if
+ * gradA != NULL, grad_A = -grad_B X^T. ws must be the workspace of an
+ * mxp_solve of the same A with the same n and opts: its saved block factor is
+ * reused (transposed: M^-T = L^-T U^-T as preconditioner) and each column of
+ * G (n x nrhs, ldg) is refined in FP64 against A^T to the scaled-residual
+ * tolerance, into gradB (ldgb). X (ldx) is the forward solution; gradA
+ * (n x n, ldga) is written, not accumulated. info as for mxp_solve (residuals
+ * of the transposed system). Blocks the host like mxp_solve.
+ */
+int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
+                      const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA, int64_t ldga,
+                      const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* info, void* stream);
+
+/*
+ * Batched solve — many independent small systems (32 <= n <= 512) in one
+ * persistent launch, each system solved by one CTA taken from an atomic work
+ * queue ordered longest first. kind[s] = 0: HPL's FP64 LU with partial
+ * pivoting (Sec. III-A.1) then the triangular solves, pivots into ipiv[s];
+ * kind[s] = 1: a diagonally dominant system solved the HPL-MxP way
+ * (Sec. III-A.2): the BF16 block-LU factor of mxp_solve (panel width 32,
+ * BF16-rounded operands, FP32 accumulation) then FP64 iterative refinement to
+ * opts->tol within opts->max_iter corrections. A[s] (device, n[s] x n[s],
+ * lda[s]; overwritten by L\U for kind 0, read only for kind 1) and B[s]
+ * (device, n[s]: b in, x out) are per-system pointers given in HOST arrays, as
+ * are n, lda, ipiv and kind. infos: device array of count hpl_info, one per
+ * system in the caller's order.
+ * solve_batched_plan writes the work table into ws (synchronous host-to-device
+ * copy; ws must hold solve_batched_workspace_size bytes) and launches nothing.
+ * solve_batched_run (re)launches the planned work on `stream`: a queue reset
+ * and one kernel, no host synchronisation, so it can be captured into a CUDA
+ * graph and replayed; max_ctas <= 0 means one CTA per SM. solve_batched is
+ * plan + run. hpl_batch_sizes draws the sizes of the batched workload,
+ * n_s = 32 + (draw s of generator stream 2 mod 481), into a host array.
+ */
+int hpl_batch_sizes(uint64_t seed, int64_t count, int64_t* n_out);
+size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind);
+int solve_batched_plan(int64_t count, const int64_t* n, double* const* A, const int64_t* lda, double* const* B,
+                       int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts, void* ws, size_t ws_bytes);
+int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* stream);
+int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64_t* lda, double* const* B,
+                  int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts, void* ws, size_t ws_bytes,
+                  hpl_info* infos, void* stream);
+
+/*
  * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path
  * (Sec. III-A.2: the factorization and trailing updates run in low precision;
  * Table I: BF16 + FP32 + FP64): C = C - A B^T (sub = 1) or C = A B^T (sub = 0),

@@ -92,6 +92,11 @@ def load():
             "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
             "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
             "mxp_workspace_size": (sz, [i64, i64, op]),
+            "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
+            "hpl_batch_sizes": (i32, [u64, i64, vp]),
+            "solve_batched_workspace_size": (sz, [i64, vp, vp]),
+            "solve_batched_plan": (i32, [i64, vp, vp, vp, vp, vp, vp, op, vp, sz]),
+            "solve_batched_run": (i32, [vp, vp, i32, vp]),
             "mxp_solve": (i32, [i64, i64, vp, i64, u64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
@@ -231,7 +236,11 @@ def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = RE
     lib = load()
     n = A.shape[0]
     vec = B.dim() == 1
-    Bm = B.view(n, 1) if vec else B
+    Bm = B.reshape(n, 1) if vec else B
+    if Bm.stride(0) != 1:
+        Bc = colmajor(n, Bm.shape[1], device=A.device)
+        Bc.copy_(Bm)
+        Bm = Bc
     nrhs = Bm.shape[1]
     opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol)
     if X is None:
@@ -246,6 +255,145 @@ def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = RE
                          _ld(Xm) if nrhs > 1 else n, ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(),
                          _stream(A.device)), "mxp_solve")
     return X, info, ws
+
+
+def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: torch.Tensor, nb: int = 1536,
+                      want_grad_a: bool = True, refine: int = REFINE_GMRES, max_iter: int = 50, gmres_m: int = 30,
+                      tol: float = 16.0):
+    """Adjoint of X = A^-1 B from the factor mxp_solve left in ws: (grad_B, grad_A, info)."""
+    lib = load()
+    n = A.shape[0]
+    Gm = G.reshape(n, -1) if G.dim() == 1 else G
+    Xm = X.reshape(n, -1) if X.dim() == 1 else X
+    nrhs = Gm.shape[1]
+    Gc = colmajor(n, nrhs, device=A.device)
+    Gc.copy_(Gm)
+    Xc = colmajor(n, nrhs, device=A.device)
+    Xc.copy_(Xm)
+    gB = colmajor(n, nrhs, device=A.device)
+    gA = colmajor(n, n, device=A.device) if want_grad_a else None
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol)
+    info = Info(A.device)
+    _check(lib.lu_solve_backward(n, nrhs, _ptr(A), _ld(A), _ptr(Xc), n, _ptr(Gc), n, _ptr(gB), n, _ptr(gA), n,
+                                 ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(), _stream(A.device)),
+           "lu_solve_backward")
+    return gB, gA, info
+
+
+class SolveFn(torch.autograd.Function):
+    """X = A^-1 B with the mixed-precision forward (BF16 block LU + FP64
+    refinement) and the hand-written adjoint backward on the saved factor.
+    A must be FP64, square, column-major and diagonally dominant."""
+
+    @staticmethod
+    def forward(ctx, A, B, nb=1536):
+        Ac = A if A.stride(0) == 1 else A.t().contiguous().t()
+        Bm = B.reshape(B.shape[0], -1) if B.dim() == 1 else B
+        Bc = colmajor(Bm.shape[0], Bm.shape[1], device=A.device)
+        Bc.copy_(Bm)
+        X, info, ws = mxp_solve(Ac.detach(), Bc, nb=nb)
+        rec = info.read()
+        if rec["status"] != 0:
+            raise HplError(rec["status"], "SolveFn.forward")
+        ctx.save_for_backward(Ac.detach(), X)
+        ctx.ws, ctx.nb, ctx.vec = ws, nb, B.dim() == 1
+        out = X.clone()
+        return out[:, 0] if ctx.vec else out
+
+    @staticmethod
+    def backward(ctx, G):
+        A, X = ctx.saved_tensors
+        gB, gA, info = lu_solve_backward(A, X, G, ctx.ws, nb=ctx.nb, want_grad_a=ctx.needs_input_grad[0])
+        rec = info.read()
+        if rec["status"] != 0:
+            raise HplError(rec["status"], "SolveFn.backward")
+        if ctx.vec:
+            gB = gB[:, 0]
+        return gA, gB, None
+
+
+def solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536) -> torch.Tensor:
+    """Differentiable mixed-precision solve X = A^-1 B (see SolveFn)."""
+    return SolveFn.apply(A, B, nb)
+
+
+def batch_sizes(seed: int, count: int):
+    """Sizes of the batched workload (generator stream 2), as a numpy int64 array."""
+    import numpy as np
+    out = np.empty(count, dtype=np.int64)
+    _check(load().hpl_batch_sizes(seed, count, out.ctypes.data), "hpl_batch_sizes")
+    return out
+
+
+class Batch:
+    """Device buffers and the plan of a batched solve.
+
+    System s has size n[s] and kind[s] (0: general, pivoted FP64; 1: diagonally
+    dominant, BF16 factor + FP64 refinement); its matrix (column-major, ld n[s])
+    and right-hand side live in two flat FP64 buffers at offsets a_off[s] and
+    b_off[s]; generate() fills them from generator streams 16+2s and 17+2s.
+    """
+
+    def __init__(self, n, kind, device="cuda"):
+        import numpy as np
+        self.n = np.ascontiguousarray(n, dtype=np.int64)
+        self.kind = np.ascontiguousarray(kind, dtype=np.uint8)
+        self.count = len(self.n)
+        self.device = device
+        sq = self.n * self.n
+        self.a_off = np.concatenate([[0], np.cumsum(sq)[:-1]]).astype(np.int64)
+        self.b_off = np.concatenate([[0], np.cumsum(self.n)[:-1]]).astype(np.int64)
+        self.A = torch.empty(int(sq.sum()), dtype=torch.float64, device=device)
+        self.B = torch.empty(int(self.n.sum()), dtype=torch.float64, device=device)
+        self.ipiv = torch.zeros(int(self.n.sum()), dtype=torch.int32, device=device)
+        self.infos = torch.zeros(self.count * 4, dtype=torch.int64, device=device)
+        ea, eb, ei = self.A.element_size(), self.B.element_size(), self.ipiv.element_size()
+        self.pA = (ctypes.c_void_p * self.count)(*[self.A.data_ptr() + int(o) * ea for o in self.a_off])
+        self.pB = (ctypes.c_void_p * self.count)(*[self.B.data_ptr() + int(o) * eb for o in self.b_off])
+        self.pP = (ctypes.c_void_p * self.count)(*[self.ipiv.data_ptr() + int(o) * ei for o in self.b_off])
+        self.lda = np.ascontiguousarray(self.n, dtype=np.int64)
+        self.ws = None
+
+    def matrix(self, s):
+        n, o = int(self.n[s]), int(self.a_off[s])
+        return self.A[o:o + n * n].view(n, n).t()
+
+    def rhs(self, s):
+        n, o = int(self.n[s]), int(self.b_off[s])
+        return self.B[o:o + n]
+
+    def pivots(self, s):
+        n, o = int(self.n[s]), int(self.b_off[s])
+        return self.ipiv[o:o + n]
+
+    def generate(self, seed: int):
+        for s in range(self.count):
+            n = int(self.n[s])
+            generate(seed, 16 + 2 * s, n, n, int(self.kind[s]), out=self.matrix(s), device=self.device)
+            generate(seed, 17 + 2 * s, n, 1, GEN_GENERAL, out=self.rhs(s).view(n, 1), device=self.device)
+
+    def plan(self, max_iter: int = 50, tol: float = 16.0):
+        lib = load()
+        need = lib.solve_batched_workspace_size(self.count, self.n.ctypes.data, self.kind.ctypes.data)
+        if self.ws is None or self.ws.numel() < need:
+            self.ws = workspace(need, self.device)
+        opts = make_opts(max_iter=max_iter, tol=tol)
+        torch.cuda.synchronize(self.device)
+        _check(lib.solve_batched_plan(self.count, self.n.ctypes.data, self.pA, self.lda.ctypes.data, self.pB,
+                                      self.pP, self.kind.ctypes.data, ctypes.byref(opts), _ptr(self.ws),
+                                      self.ws.numel()), "solve_batched_plan")
+
+    def run(self, max_ctas: int = 0):
+        _check(load().solve_batched_run(_ptr(self.ws), _ptr(self.infos), max_ctas, _stream(self.device)),
+               "solve_batched_run")
+
+    def info(self, s=None):
+        raw = self.infos.cpu().numpy()
+        recs = []
+        for q in range(self.count) if s is None else [s]:
+            st, it, inf, sr, inner, _ = struct.unpack("<iiqdii", raw[4 * q:4 * q + 4].tobytes())
+            recs.append(dict(status=st, iters=it, info=inf, scaled_residual=sr, inner_iters=inner))
+        return recs if s is None else recs[0]
 
 
 def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 1536):

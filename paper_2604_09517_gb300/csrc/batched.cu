@@ -1,0 +1,592 @@
+// solve_batched: many independent small systems in one persistent launch.
+//
+// Each CTA takes the next system from an atomic work queue (the plan orders
+// the systems by decreasing estimated cost, longest first) and solves it
+// alone, its matrix in global memory (L2-resident) with one panel of NB
+// columns staged in shared memory:
+//   kind 0 (general): HPL's LU with partial pivoting in FP64 (Sec. III-A.1):
+//     blocked right-looking, panel factored in SMEM (block argmax with the
+//     first-index tie rule, row swaps, true division, rank-1), interchanges
+//     applied to the other columns, TRSM of the block row, DFMA update of the
+//     trailing matrix in 64 x 64 register-tiled blocks; then P b, forward and
+//     backward substitution.
+//   kind 1 (diagonally dominant): the HPL-MxP reading (Sec. III-A.2) used by
+//     mxp_solve, per system: block LU without pivoting of an FP32 copy with
+//     panel width NB, D^-1 by Newton-Schulz with split-BF16 products,
+//     L21 = A21 D^-1 and A22 -= L21 A12 with BF16-rounded operands and FP32
+//     accumulation (here on the CUDA cores: a product of two BF16 values is
+//     exact in FP32, as in the tensor cores), then FP64 iterative refinement
+//     (r = b - A x in FP64, x += M^-1 r) to the scaled-residual tolerance.
+// The run launch (queue reset + kernel) holds no host synchronisation, so it
+// can be captured in a CUDA graph and replayed.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hplgb {
+namespace bt {
+
+constexpr int NB = 32;             // panel width
+constexpr int NMAX = 512;          // largest system handled
+constexpr int THREADS = 256;
+constexpr int PS = NB + 1;         // SMEM panel row stride (doubles)
+
+struct Sys {
+    long long n, lda;
+    double* A;        // FP64 matrix (kind 0: factored in place; kind 1: read only)
+    double* b;        // right-hand side in, solution out
+    int32_t* ipiv;    // kind 0
+    float* W;         // kind 1: FP32 block factor (n x n, ld n)
+    float* Dinv;      // kind 1: D_k^-1 (n x NB, ld n)
+    double* r;        // kind 1: FP64 residual / correction scratch (2n)
+    float* y32;       // kind 1: FP32 scratch (2n)
+    int kind;
+    int pad;
+};
+
+struct Header {
+    unsigned int counter;
+    int count;
+    int max_iter;
+    int pad;
+    double tol;
+};
+
+// ---- block-wide reductions -------------------------------------------------
+__device__ __forceinline__ double block_sum(double v, double* red) {
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; w++) s += red[w];
+    return s;
+}
+
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    for (int w = 0; w < THREADS / 32; w++) s = fmax(s, red[w]);
+    return s;
+}
+
+// ---- kind 0: FP64 LU with partial pivoting -----------------------------------
+
+// Update C (rows r0.., cols c0..; m x nn) -= L (m x kb, in the SMEM panel at
+// panel row offset prow) * U (kb x nn, global rows k0.., cols c0..).
+__device__ void upd64(double* A, long long lda, const double* P, int prow, int m, int nn, int kb, long long r0,
+                      long long c0, long long k0, double* Us) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int tj = 0; tj < nn; tj += 64) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < NB * 64; e += THREADS) {
+            int kq = e / 64, c = e % 64;
+            Us[kq * 65 + c] = (kq < kb && tj + c < nn) ? A[(c0 + tj + c) * lda + k0 + kq] : 0.0;
+        }
+        __syncthreads();
+        for (int ti = 0; ti < m; ti += 64) {
+            double acc[4][4];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    int r = ti + tx + 16 * i, c = tj + ty + 16 * j;
+                    acc[i][j] = (r < m && c < nn) ? A[(c0 + c) * lda + r0 + r] : 0.0;
+                }
+            for (int kq = 0; kq < kb; kq++) {
+                double a[4], bb[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    int r = ti + tx + 16 * i;
+                    a[i] = r < m ? P[(prow + r) * PS + kq] : 0.0;
+                }
+#pragma unroll
+                for (int j = 0; j < 4; j++) bb[j] = Us[kq * 65 + ty + 16 * j];
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) acc[i][j] = fma(-a[i], bb[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    int r = ti + tx + 16 * i, c = tj + ty + 16 * j;
+                    if (r < m && c < nn) A[(c0 + c) * lda + r0 + r] = acc[i][j];
+                }
+        }
+    }
+}
+
+__device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long* redi, hpl_info* info) {
+    const int n = (int)S.n;
+    const long long lda = S.lda;
+    double* A = S.A;
+    int first_zero = 0;
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int kb = min(NB, n - k0), pm = n - k0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < pm * kb; e += THREADS) {
+            int c = e / pm, r = e % pm;
+            P[r * PS + c] = A[(long long)(k0 + c) * lda + k0 + r];
+        }
+        __syncthreads();
+        for (int j = 0; j < kb; j++) {
+            // argmax of |P(j.., j)|, first index on ties
+            double bv = -1.0;
+            long long br = 0x7fffffffffffffffLL;
+            for (int r = j + threadIdx.x; r < pm; r += THREADS) {
+                double v = fabs(P[r * PS + j]);
+                if (v > bv || (v == bv && r < br)) { bv = v; br = r; }
+            }
+            for (int off = 16; off > 0; off >>= 1) {
+                double ov = __shfl_down_sync(0xffffffffu, bv, off);
+                long long orr = __shfl_down_sync(0xffffffffu, br, off);
+                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
+            }
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+            __syncthreads();
+            if (lane == 0) { red[warp] = bv; redi[warp] = br; }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 1; w < THREADS / 32; w++)
+                    if (red[w] > bv || (red[w] == bv && redi[w] < br)) { bv = red[w]; br = redi[w]; }
+                if (br == 0x7fffffffffffffffLL) br = j;          // only NaN: keep the diagonal row
+                redi[THREADS / 32] = br;
+            }
+            __syncthreads();
+            const int p = (int)redi[THREADS / 32];
+            if (threadIdx.x == 0) S.ipiv[k0 + j] = k0 + p;
+            if (p != j)
+                for (int c = threadIdx.x; c < kb; c += THREADS) {
+                    double t = P[j * PS + c];
+                    P[j * PS + c] = P[p * PS + c];
+                    P[p * PS + c] = t;
+                }
+            __syncthreads();
+            const double piv = P[j * PS + j];
+            if (piv == 0.0) {
+                if (!first_zero) first_zero = k0 + j + 1;
+                continue;
+            }
+            for (int r = j + 1 + threadIdx.x; r < pm; r += THREADS) {
+                double l = P[r * PS + j] / piv;
+                P[r * PS + j] = l;
+                for (int c = j + 1; c < kb; c++) P[r * PS + c] = fma(-l, P[j * PS + c], P[r * PS + c]);
+            }
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < pm * kb; e += THREADS) {
+            int c = e / pm, r = e % pm;
+            A[(long long)(k0 + c) * lda + k0 + r] = P[r * PS + c];
+        }
+        __syncthreads();
+        // interchanges on the other columns, in order, one thread per column
+        for (int c = threadIdx.x; c < n; c += THREADS) {
+            if (c >= k0 && c < k0 + kb) continue;
+            double* col = A + (long long)c * lda;
+            for (int j = 0; j < kb; j++) {
+                int p = S.ipiv[k0 + j];
+                if (p != k0 + j) {
+                    double t = col[k0 + j];
+                    col[k0 + j] = col[p];
+                    col[p] = t;
+                }
+            }
+        }
+        __syncthreads();
+        const int c1 = k0 + kb, m = n - c1;
+        if (m > 0) {
+            // U12 = L11^-1 A12, one thread per column
+            for (int c = c1 + threadIdx.x; c < n; c += THREADS) {
+                double* col = A + (long long)c * lda + k0;
+                for (int i = 1; i < kb; i++) {
+                    double s = col[i];
+                    for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], col[q], s);
+                    col[i] = s;
+                }
+            }
+            __syncthreads();
+            upd64(A, lda, P, kb, m, m, kb, c1, c1, k0, Us);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && first_zero) info->info = first_zero;
+    // solve: P b, L forward, U backward (column-oriented, one sync per column)
+    double* b = S.b;
+    if (threadIdx.x == 0)
+        for (int k = 0; k < n; k++) {
+            int p = S.ipiv[k];
+            if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+        }
+    __syncthreads();
+    for (int j = 0; j < n; j++) {
+        const double xj = b[j];
+        for (int i = j + 1 + threadIdx.x; i < n; i += THREADS) b[i] = fma(-A[(long long)j * lda + i], xj, b[i]);
+        __syncthreads();
+    }
+    for (int j = n - 1; j >= 0; j--) {
+        if (threadIdx.x == 0) b[j] = b[j] / A[(long long)j * lda + j];
+        __syncthreads();
+        const double xj = b[j];
+        for (int i = threadIdx.x; i < j; i += THREADS) b[i] = fma(-A[(long long)j * lda + i], xj, b[i]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) info->status = first_zero ? HPL_ERR_SINGULAR : HPL_OK;
+}
+
+// ---- kind 1: BF16 block LU + FP64 refinement ----------------------------------
+
+__device__ __forceinline__ float bfr(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// C (m x nn, FP32, ldc) (= or -=) rnd(A) (m x kb, lda) * rnd(B) (kb x nn, ldb),
+// FP32 accumulation; operands rounded to BF16 (split = 0) or split into
+// hi + lo with hi*hi, hi*lo, lo*hi accumulated in that order (split = 1).
+__device__ void gemm32(int m, int nn, int kb, const float* A, long long lda, const float* B, long long ldb, float* C,
+                       long long ldc, int sub, int split) {
+    for (int e = threadIdx.x; e < m * nn; e += THREADS) {
+        int j = e / m, i = e % m;
+        float acc = 0.0f;
+        if (!split) {
+            for (int q = 0; q < kb; q++) acc = fmaf(bfr(A[(long long)q * lda + i]), bfr(B[(long long)j * ldb + q]), acc);
+        } else {
+            for (int q = 0; q < kb; q++) acc = fmaf(bfr(A[(long long)q * lda + i]), bfr(B[(long long)j * ldb + q]), acc);
+            for (int q = 0; q < kb; q++) {
+                float bv = B[(long long)j * ldb + q];
+                acc = fmaf(bfr(A[(long long)q * lda + i]), bfr(bv - bfr(bv)), acc);
+            }
+            for (int q = 0; q < kb; q++) {
+                float av = A[(long long)q * lda + i];
+                acc = fmaf(bfr(av - bfr(av)), bfr(B[(long long)j * ldb + q]), acc);
+            }
+        }
+        C[(long long)j * ldc + i] = sub ? C[(long long)j * ldc + i] - acc : acc;
+    }
+}
+
+// Block LU without pivoting of W (FP32 copy of A); D^-1 in Dinv. X, R: SMEM
+// NB x NB FP32 scratch.
+__device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* info) {
+    const int n = (int)S.n;
+    float* W = S.W;
+    for (int e = threadIdx.x; e < n * n; e += THREADS) {
+        int j = e / n, i = e % n;
+        W[(long long)j * n + i] = (float)S.A[(long long)j * S.lda + i];
+    }
+    __syncthreads();
+    int first_zero = 0;
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int kb = min(NB, n - k0), m = n - k0 - kb;
+        float* D = W + (long long)k0 * n + k0;
+        for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
+            int j = e / kb, i = e % kb;
+            X[j * NB + i] = (i == j) ? 1.0f / D[(long long)j * n + j] : 0.0f;
+        }
+        if (threadIdx.x == 0)
+            for (int i = 0; i < kb; i++)
+                if (D[(long long)i * n + i] == 0.0f && !first_zero) first_zero = k0 + i + 1;
+        __syncthreads();
+        for (int it = 0; it < 3; it++) {
+            gemm32(kb, kb, kb, D, n, X, NB, R, NB, 0, 1);               // R = D X
+            __syncthreads();
+            for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
+                int j = e / kb, i = e % kb;
+                R[j * NB + i] = ((i == j) ? 2.0f : 0.0f) - R[j * NB + i];
+            }
+            __syncthreads();
+            gemm32(kb, kb, kb, X, NB, R, NB, T, NB, 0, 1);              // T = X (2I - R)
+            __syncthreads();
+            for (int e = threadIdx.x; e < kb * kb; e += THREADS) X[(e / kb) * NB + e % kb] = T[(e / kb) * NB + e % kb];
+            __syncthreads();
+        }
+        for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
+            int j = e / kb, i = e % kb;
+            S.Dinv[(long long)j * n + k0 + i] = X[j * NB + i];
+        }
+        if (m > 0) {
+            float* A21 = W + (long long)k0 * n + k0 + kb;
+            float* A12 = W + (long long)(k0 + kb) * n + k0;
+            float* A22 = W + (long long)(k0 + kb) * n + k0 + kb;
+            // L21 = A21 D^-1: read all of A21's rows before overwriting them
+            for (int r0 = 0; r0 < m; r0 += NB) {
+                const int rm = min(NB, m - r0);
+                gemm32(rm, kb, kb, A21 + r0, n, X, NB, T, NB, 0, 0);
+                __syncthreads();
+                for (int e = threadIdx.x; e < rm * kb; e += THREADS) {
+                    int j = e / rm, i = e % rm;
+                    A21[(long long)j * n + r0 + i] = T[j * NB + i];
+                }
+                __syncthreads();
+            }
+            gemm32(m, m, kb, A21, n, A12, n, A22, n, 1, 0);              // A22 -= L21 A12
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0 && first_zero) info->info = first_zero;
+    __syncthreads();
+}
+
+// out = M^-1 v (FP64 in and out), M the block factor, FP32 inside.
+__device__ void precond32(const Sys& S, const double* v, double* out) {
+    const int n = (int)S.n;
+    float* y = S.y32;
+    float* t = S.y32 + n;
+    for (int i = threadIdx.x; i < n; i += THREADS) y[i] = (float)v[i];
+    __syncthreads();
+    for (int k0 = 0; k0 < n; k0 += NB) {
+        const int kb = min(NB, n - k0);
+        for (int i = k0 + kb + threadIdx.x; i < n; i += THREADS) {
+            float s = 0.0f;
+            for (int j = k0; j < k0 + kb; j++) s = fmaf(S.W[(long long)j * n + i], y[j], s);
+            y[i] -= s;
+        }
+        __syncthreads();
+    }
+    const int last = ((n - 1) / NB) * NB;
+    for (int k0 = last; k0 >= 0; k0 -= NB) {
+        const int kb = min(NB, n - k0);
+        for (int i = threadIdx.x; i < kb; i += THREADS) {
+            float s = 0.0f;
+            for (int j = 0; j < kb; j++) s = fmaf(S.Dinv[(long long)j * n + k0 + i], y[k0 + j], s);
+            t[i] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kb; i += THREADS) y[k0 + i] = t[i];
+        __syncthreads();
+        for (int i = threadIdx.x; i < k0; i += THREADS) {
+            float s = 0.0f;
+            for (int j = k0; j < k0 + kb; j++) s = fmaf(S.W[(long long)j * n + i], y[j], s);
+            y[i] -= s;
+        }
+        __syncthreads();
+    }
+    for (int i = threadIdx.x; i < n; i += THREADS) out[i] = (double)y[i];
+    __syncthreads();
+}
+
+// r = b - A x (FP64), returns the HPL scaled residual.
+__device__ double resid64(const Sys& S, const double* x, const double* b, double* r, double* red) {
+    const int n = (int)S.n;
+    double rmax = 0.0, amax = 0.0, xmax = 0.0, bmax = 0.0;
+    for (int i = threadIdx.x; i < n; i += THREADS) {
+        double s = 0.0, a = 0.0;
+        for (int j = 0; j < n; j++) {
+            double v = S.A[(long long)j * S.lda + i];
+            s = fma(v, x[j], s);
+            a += fabs(v);
+        }
+        r[i] = b[i] - s;
+        rmax = fmax(rmax, fabs(r[i]) != fabs(r[i]) ? INFINITY : fabs(r[i]));
+        amax = fmax(amax, a);
+        xmax = fmax(xmax, fabs(x[i]));
+        bmax = fmax(bmax, fabs(b[i]));
+    }
+    rmax = block_max(rmax, red);
+    amax = block_max(amax, red);
+    xmax = block_max(xmax, red);
+    bmax = block_max(bmax, red);
+    return rmax / (0x1p-53 * (amax * xmax + bmax) * (double)n);
+}
+
+__device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float* T, double* red, hpl_info* info) {
+    const int n = (int)S.n;
+    blocklu32(S, X, R, T, info);
+    double* bx = S.b;             // b in, x out
+    double* r = S.r;
+    double* b0 = S.r + n;         // keep b
+    for (int i = threadIdx.x; i < n; i += THREADS) b0[i] = bx[i];
+    __syncthreads();
+    precond32(S, b0, bx);
+    int it = 0;
+    double sr = INFINITY;
+    int status = HPL_ERR_NOT_CONVERGED;
+    for (;;) {
+        sr = resid64(S, bx, b0, r, red);
+        if (!(sr == sr) || sr == INFINITY) { status = HPL_ERR_NONFINITE; break; }
+        if (sr < H->tol) { status = HPL_OK; break; }
+        if (it >= H->max_iter) break;
+        precond32(S, r, r);
+        for (int i = threadIdx.x; i < n; i += THREADS) bx[i] += r[i];
+        __syncthreads();
+        it++;
+    }
+    if (threadIdx.x == 0) {
+        info->status = status;
+        info->iters = it;
+        info->inner_iters = it;
+        info->scaled_residual = sr;
+    }
+}
+
+constexpr size_t SMEM = sizeof(double) * (NMAX * PS + NB * 65) + sizeof(float) * 3 * NB * NB;
+
+}  // namespace bt
+
+// Workspace: header, system table, then per dominant system W (n x n FP32),
+// Dinv (n x NB FP32), r (2n FP64), y32 (2n FP32).
+static size_t batched_ws_layout(int64_t count, const int64_t* n, const uint8_t* kind, std::vector<size_t>* offs) {
+    size_t off = align_up(sizeof(bt::Header), 256);
+    off = align_up(off + sizeof(bt::Sys) * (size_t)count, 256);
+    if (offs) offs->assign((size_t)count, 0);
+    for (int64_t s = 0; s < count; s++) {
+        if (kind[s] != 1) continue;
+        if (offs) (*offs)[s] = off;
+        int64_t m = n[s];
+        off = align_up(off + sizeof(float) * m * m, 256);
+        off = align_up(off + sizeof(float) * m * bt::NB, 256);
+        off = align_up(off + sizeof(double) * 2 * m, 256);
+        off = align_up(off + sizeof(float) * 2 * m, 256);
+    }
+    return off;
+}
+
+}  // namespace hplgb
+
+using namespace hplgb;
+
+extern "C" size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind) {
+    if (count <= 0 || !n || !kind) return 256;
+    return batched_ws_layout(count, n, kind, nullptr);
+}
+
+extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const* A, const int64_t* lda,
+                                  double* const* B, int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts,
+                                  void* ws, size_t ws_bytes) {
+    if (count <= 0 || count > 0x7fffffff || !n || !A || !lda || !B || !kind || !ws) return HPL_ERR_INVALID;
+    for (int64_t s = 0; s < count; s++) {
+        if (n[s] < 1 || n[s] > bt::NMAX || lda[s] < n[s] || !A[s] || !B[s] || kind[s] > 1) return HPL_ERR_INVALID;
+        if (kind[s] == 0 && (!ipiv || !ipiv[s])) return HPL_ERR_INVALID;
+    }
+    std::vector<size_t> offs;
+    size_t need = batched_ws_layout(count, n, kind, &offs);
+    if (ws_bytes < need) return HPL_ERR_NOMEM;
+    Opts o = resolve_opts(opts, bt::NB);
+    // longest first: FP64 work costs ~64x FP32 work on this part
+    std::vector<double> cost((size_t)count);
+    for (int64_t s = 0; s < count; s++) {
+        double m = (double)n[s];
+        cost[s] = kind[s] == 0 ? 64.0 * m * m * m / 3.0 : m * m * m / 3.0 + 3.0 * 64.0 * m * m;
+    }
+    std::vector<int64_t> order((size_t)count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::vector<bt::Sys> table((size_t)count);
+    char* base = (char*)ws;
+    for (int64_t q = 0; q < count; q++) {
+        int64_t s = order[q];
+        bt::Sys& S = table[q];
+        memset(&S, 0, sizeof(S));
+        S.n = n[s];
+        S.lda = lda[s];
+        S.A = A[s];
+        S.b = B[s];
+        S.ipiv = kind[s] == 0 ? ipiv[s] : nullptr;
+        S.kind = kind[s];
+        S.pad = (int)s;                     // original index: infos are written in the caller's order
+        if (kind[s] == 1) {
+            int64_t m = n[s];
+            size_t off = offs[s];
+            S.W = (float*)(base + off);
+            off = align_up(off + sizeof(float) * m * m, 256);
+            S.Dinv = (float*)(base + off);
+            off = align_up(off + sizeof(float) * m * bt::NB, 256);
+            S.r = (double*)(base + off);
+            off = align_up(off + sizeof(double) * 2 * m, 256);
+            S.y32 = (float*)(base + off);
+        }
+    }
+    bt::Header h;
+    memset(&h, 0, sizeof(h));
+    h.count = (int)count;
+    h.max_iter = o.max_iter;
+    h.tol = o.tol;
+    HPL_CUDA_TRY(cudaMemcpy(base, &h, sizeof(h), cudaMemcpyHostToDevice));
+    HPL_CUDA_TRY(cudaMemcpy(base + align_up(sizeof(bt::Header), 256), table.data(), sizeof(bt::Sys) * count,
+                            cudaMemcpyHostToDevice));
+    return HPL_OK;
+}
+
+namespace hplgb {
+namespace bt {
+// Table entries carry the caller's index in `pad`; the kernel writes infos there.
+__global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restrict__ table, Header* H,
+                                                            hpl_info* infos);
+}  // namespace bt
+}  // namespace hplgb
+
+extern "C" int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* stream) {
+    if (!ws || !infos) return HPL_ERR_INVALID;
+    cudaStream_t s = (cudaStream_t)stream;
+    char* base = (char*)ws;
+    bt::Header* H = (bt::Header*)base;
+    const bt::Sys* table = (const bt::Sys*)(base + align_up(sizeof(bt::Header), 256));
+    static bool attr = false;
+    if (!attr) {
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt::SMEM));
+        attr = true;
+    }
+    int dev = 0, sms = kNumSMsGB300;
+    HPL_CUDA_TRY(cudaGetDevice(&dev));
+    HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int grid = max_ctas > 0 ? std::min(max_ctas, sms) : sms;
+    HPL_CUDA_TRY(cudaMemsetAsync(&H->counter, 0, sizeof(unsigned int), s));
+    bt::k_batched_run<<<grid, bt::THREADS, bt::SMEM, s>>>(table, H, infos);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+extern "C" int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64_t* lda,
+                             double* const* B, int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts,
+                             void* ws, size_t ws_bytes, hpl_info* infos, void* stream) {
+    int st = solve_batched_plan(count, n, A, lda, B, ipiv, kind, opts, ws, ws_bytes);
+    if (st) return st;
+    return solve_batched_run(ws, infos, 0, stream);
+}
+
+namespace hplgb {
+namespace bt {
+__global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restrict__ table, Header* H,
+                                                            hpl_info* infos) {
+    extern __shared__ double bsm[];
+    __shared__ double red[THREADS / 32 + 1];
+    __shared__ long long redi[THREADS / 32 + 1];
+    __shared__ int s_idx;
+    double* P = bsm;
+    double* Us = bsm + NMAX * PS;
+    float* X = (float*)(Us + NB * 65);
+    float* R = X + NB * NB;
+    float* T = R + NB * NB;
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&H->counter, 1u);
+        __syncthreads();
+        const int idx = s_idx;
+        __syncthreads();
+        if (idx >= H->count) break;
+        const Sys S = table[idx];
+        hpl_info* info = infos + S.pad;
+        if (threadIdx.x == 0) {
+            info->status = 0;
+            info->iters = 0;
+            info->info = 0;
+            info->scaled_residual = 0.0;
+            info->inner_iters = 0;
+        }
+        __syncthreads();
+        if (S.kind == 0) lu64(S, P, Us, red, redi, info);
+        else mxp_one(S, H, X, R, T, red, info);
+        __syncthreads();
+    }
+}
+}  // namespace bt
+}  // namespace hplgb

@@ -80,6 +80,15 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 
 using namespace hplgb;
 
+// Sizes of the batched workload: n_s = 32 + (draw s of stream 2 mod 481),
+// uniform on [32, 512] up to a modulo bias below 1e-16. Host memory out.
+extern "C" int hpl_batch_sizes(uint64_t seed, int64_t count, int64_t* n_out) {
+    if (count < 0 || (count > 0 && !n_out)) return HPL_ERR_INVALID;
+    const uint64_t key = sm64_host_mix(seed + 3 * kGamma);
+    for (int64_t s = 0; s < count; s++) n_out[s] = 32 + (int64_t)(sm64_host_mix(key + (uint64_t)(s + 1) * kGamma) % 481);
+    return HPL_OK;
+}
+
 extern "C" int hpl_generate(uint64_t seed, uint64_t stream_id, int64_t m, int64_t ncols, int kind, double* A,
                             int64_t lda, void* stream) {
     if (m < 0 || ncols < 0 || (m > 0 && ncols > 0 && !A) || lda < (m > 1 ? m : 1)) return HPL_ERR_INVALID;

@@ -34,6 +34,8 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
 size_t residual_ws_bytes(int64_t n);
 int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
                         double* sr, void* ws, cudaStream_t s);
+int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
+                          double* sr, void* ws, cudaStream_t s);
 
 constexpr int kNsIters = 3;
 constexpr int kDotBlocks = 304;
@@ -166,6 +168,62 @@ __global__ void __launch_bounds__(256) k_gemv32(int64_t rows, int64_t cols, cons
         for (int w = 0; w < 8; w++) s += part[w][lane];
         y[r] = sub ? y[r] - s : s;
     }
+}
+
+// y (= or -=) P^T x: one warp per column c of P (rows x cols, FP32 column-
+// major), lanes over the rows, shuffle reduction.
+__global__ void __launch_bounds__(256) k_gemvT32(int64_t rows, int64_t cols, const float* __restrict__ P,
+                                                 int64_t ldp, const float* __restrict__ x, float* __restrict__ y,
+                                                 int sub) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= cols) return;
+    const float* col = P + c * ldp;
+    float acc = 0.0f;
+#pragma unroll 4
+    for (int64_t r = lane; r < rows; r += 32) acc = fmaf(col[r], x[r], acc);
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+    if (lane == 0) y[c] = sub ? y[c] - acc : acc;
+}
+
+// grad_A = -G X^T for G, X n x k (FP64, column-major): 64 x 64 output tiles,
+// k staged 16 at a time in shared memory, 4 x 4 DFMA register tiles.
+__global__ void __launch_bounds__(256) k_outer_neg(int64_t n, int64_t k, const double* __restrict__ G, int64_t ldg,
+                                                   const double* __restrict__ X, int64_t ldx, double* __restrict__ C,
+                                                   int64_t ldc) {
+    __shared__ double Gs[16][65], Xs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * 64, col0 = (int64_t)blockIdx.y * 64;
+    double acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < k; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kq = e >> 6, r = e & 63;
+            bool okk = k0 + kq < k;
+            Gs[kq][r] = (okk && row0 + r < n) ? G[(k0 + kq) * ldg + row0 + r] : 0.0;
+            Xs[kq][r] = (okk && col0 + r < n) ? X[(k0 + kq) * ldx + col0 + r] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kq = 0; kq < 16; kq++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = Gs[kq][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Xs[kq][ty + 16 * j];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
+            if (r < n && c < n) C[c * ldc + r] = -acc[i][j];
+        }
 }
 
 __global__ void k_f64_to_f32(int64_t n, const double* __restrict__ v, float* __restrict__ y) {
@@ -304,6 +362,13 @@ struct Mxp {
     cudaStream_t s;
     const double* A;
     int64_t lda;
+    bool trans = false;     // solve A^T x = b with the same factor (the adjoint)
+
+    // r = b - op(A) x (b != NULL, scaled residual into sr if given) or r = op(A) x
+    int resid(const double* x, const double* b, double* r, double* sr) {
+        return trans ? launch_residual_vec_t(n, A, lda, x, b, r, sr, w.resws, s)
+                     : launch_residual_vec(n, A, lda, x, b, r, sr, w.resws, s);
+    }
 
     int dot(const double* a, const double* b, double* out, int take_sqrt) {
         k_dot_partial<<<kDotBlocks, 256, 0, s>>>(n, a, b, w.part);
@@ -377,8 +442,47 @@ struct Mxp {
         return HPL_OK;
     }
 
+    // ---- transposed preconditioner: out = M^-T v, M^T = U^T L^T ----
+    // U^T is block lower with diagonal blocks D_k^T: forward, z_k = D_k^-T y_k,
+    // then the later entries lose (U row panel of block k)^T z_k. L^T is block
+    // unit upper: backward, y_k -= (L column panel below block k)^T y_below.
+    int precondT(const double* v, double* out) {
+        const int64_t ldf = n;
+        float* y = w.y32;
+        float* t = w.y32 + n;
+        int slot = phase_begin(s);
+        k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, v, y);
+        HPL_LAUNCH_CHECK();
+        for (int64_t k0 = 0; k0 < n; k0 += nb) {
+            const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+            k_gemvT32<<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(kb, kb, w.Dinv + k0, n, y + k0, t, 0);
+            HPL_LAUNCH_CHECK();
+            k_copy32<<<grid_for(kb), 256, 0, s>>>(kb, t, y + k0);
+            HPL_LAUNCH_CHECK();
+            if (m2 > 0) {
+                k_gemvT32<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(kb, m2, w.F + (k0 + kb) * ldf + k0, ldf, y + k0,
+                                                                  y + k0 + kb, 1);
+                HPL_LAUNCH_CHECK();
+            }
+        }
+        const int64_t last = ((n - 1) / nb) * nb;
+        for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+            const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+            if (m2 > 0) {
+                k_gemvT32<<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0 + kb,
+                                                                  y + k0, 1);
+                HPL_LAUNCH_CHECK();
+            }
+        }
+        k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, y, out);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_OTHER, 4.0 * n * n + 4.0 * n * nb);
+        return HPL_OK;
+    }
+
     // ---- preconditioner: out = M^-1 v (FP64 in and out, FP32 inside) ----
     int precond(const double* v, double* out) {
+        if (trans) return precondT(v, out);
         const int64_t ldf = n;
         float* y = w.y32;
         float* t = w.y32 + n;
@@ -447,7 +551,7 @@ struct Mxp {
             double* wv = w.V + (int64_t)(j + 1) * ldv;
             if ((st = precond(vj, zj))) return st;
             (*inner)++;
-            if ((st = launch_residual_vec(n, A, lda, zj, nullptr, wv, nullptr, w.resws, s))) return st;
+            if ((st = resid(zj, nullptr, wv, nullptr))) return st;
             for (int i = 0; i <= j; i++) {
                 double* hij = w.h + (int64_t)j * (m + 1) + i;
                 if ((st = dot(wv, w.V + (int64_t)i * ldv, hij, 0))) return st;
@@ -498,7 +602,7 @@ struct Mxp {
         double sr = INFINITY;
         *status = HPL_ERR_NOT_CONVERGED;
         for (;;) {
-            if ((st = launch_residual_vec(n, A, lda, x, b, w.r, w.scal, w.resws, s))) return st;
+            if ((st = resid(x, b, w.r, w.scal))) return st;
             if ((st = read_scalar(w.scal, &sr))) return st;
             if (!std::isfinite(sr)) { *status = HPL_ERR_NONFINITE; break; }
             if (sr < o.tol) { *status = HPL_OK; break; }
@@ -573,6 +677,65 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     }
     h.status = worst;
     if (h.info != 0 && worst == HPL_OK) h.status = HPL_ERR_SINGULAR;
+    h.iters = max_it;
+    h.inner_iters = inner;
+    h.scaled_residual = worst_sr;
+    HPL_CUDA_TRY(cudaMemcpyAsync(info, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    HPL_CUDA_TRY(cudaStreamSynchronize(s));
+    return HPL_OK;
+}
+
+// Adjoint of X = A^-1 B: grad_B = A^-T G by the same refinement with the
+// transposed system (M^-T from the saved block factor as preconditioner, FP64
+// residuals with A^T), then grad_A = -grad_B X^T (FP64 outer product).
+extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
+                                 const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA,
+                                 int64_t ldga, const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* info,
+                                 void* stream) {
+    if (n <= 0 || nrhs < 0 || !A || lda < n || !info || !ws) return HPL_ERR_INVALID;
+    if (nrhs > 0 && (!G || !gradB || ldg < n || ldgb < n)) return HPL_ERR_INVALID;
+    if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
+    if (n > 0x7fffffff) return HPL_ERR_INVALID;
+    Opts o = resolve_opts(opts, 1536);
+    if (o.nb < 8 || o.prec != HPL_PREC_BF16) return HPL_ERR_INVALID;
+    Mxp mx;
+    mx.n = n;
+    mx.nb = std::min<int64_t>(o.nb, n);
+    mx.m = o.gmres_m;
+    mx.o = o;
+    mx.s = (cudaStream_t)stream;
+    mx.A = A;
+    mx.lda = lda;
+    mx.trans = true;
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
+    if (ws_bytes < need) return HPL_ERR_NOMEM;
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
+    cudaStream_t s = mx.s;
+    HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
+    HPL_CUDA_TRY(cudaMemsetAsync(mx.w.err, 0, sizeof(int) * 4, s));
+    int st, worst = HPL_OK, max_it = 0, inner = 0;
+    double worst_sr = 0.0;
+    for (int64_t c = 0; c < nrhs; c++) {
+        int it = 0, status = HPL_OK;
+        double sr = 0.0;
+        if ((st = mx.refine(G + c * ldg, gradB + c * ldgb, &it, &inner, &sr, &status))) return st;
+        if (status != HPL_OK && worst == HPL_OK) worst = status;
+        max_it = std::max(max_it, it);
+        worst_sr = std::max(worst_sr, sr);
+    }
+    if (gradA && nrhs > 0) {
+        dim3 g((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));
+        if (g.y > 65535) return HPL_ERR_INVALID;
+        int slot = phase_begin(s);
+        k_outer_neg<<<g, 256, 0, s>>>(n, nrhs, gradB, ldgb, X, ldx, gradA, ldga);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_OTHER, 2.0 * n * n * nrhs);
+    } else if (gradA) {
+        for (int64_t j = 0; j < n; j++) HPL_CUDA_TRY(cudaMemsetAsync(gradA + j * ldga, 0, sizeof(double) * n, s));
+    }
+    hpl_info h;
+    memset(&h, 0, sizeof(h));
+    h.status = worst;
     h.iters = max_it;
     h.inner_iters = inner;
     h.scaled_residual = worst_sr;

@@ -164,6 +164,77 @@ __global__ void __launch_bounds__(256) k_res_vec(int64_t n, const double* __rest
     r[i] = b ? b[i] - s : s;
 }
 
+// Transposed residual for the adjoint solve: one warp per column j of A,
+// r_j = b_j - sum_i a_ij x_i (b != NULL) or r_j = sum_i a_ij x_i (b == NULL),
+// and the column sums of |a_ij| (the row sums of A^T) into part_a[0..n).
+__global__ void __launch_bounds__(256) k_res_cols_t(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ x, const double* __restrict__ b,
+                                                    double* __restrict__ r, double* __restrict__ csum) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const double* col = A + j * lda;
+    double s = 0.0, a = 0.0;
+#pragma unroll 4
+    for (int64_t i = lane; i < n; i += 32) {
+        double v = col[i];
+        s = fma(v, x[i], s);
+        a += fabs(v);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        s += __shfl_down_sync(0xffffffffu, s, off);
+        a += __shfl_down_sync(0xffffffffu, a, off);
+    }
+    if (lane == 0) {
+        r[j] = b ? b[j] - s : s;
+        csum[j] = a;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_res_max_t(int64_t n, const double* __restrict__ r,
+                                                   const double* __restrict__ csum, const double* __restrict__ x,
+                                                   const double* __restrict__ b, unsigned long long* maxima) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double mr = 0.0, ma = 0.0, mx = 0.0, mb = 0.0;
+    if (i < n) {
+        mr = fabs(r[i]);
+        ma = csum[i];
+        mx = fabs(x[i]);
+        mb = fabs(b[i]);
+    }
+    if (mr != mr) mr = __longlong_as_double(0x7ff0000000000000LL);
+    for (int off = 16; off > 0; off >>= 1) {
+        mr = fmax(mr, __shfl_down_sync(0xffffffffu, mr, off));
+        ma = fmax(ma, __shfl_down_sync(0xffffffffu, ma, off));
+        mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, off));
+        mb = fmax(mb, __shfl_down_sync(0xffffffffu, mb, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(&maxima[0], mr);
+        atomic_max_nonneg(&maxima[1], ma);
+        atomic_max_nonneg(&maxima[2], mx);
+        atomic_max_nonneg(&maxima[3], mb);
+    }
+}
+
+// r = b - A^T x (or A^T x when b == NULL), with the scaled residual of the
+// transposed system (||A^T||_inf = max column sum of |A|) into sr if given.
+int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
+                          double* sr, void* ws, cudaStream_t s) {
+    ResWs w;
+    res_ws_layout(n, &w, (char*)ws);
+    k_res_cols_t<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(n, A, lda, x, b, r, w.part_a);
+    HPL_LAUNCH_CHECK();
+    if (sr && b) {
+        HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
+        k_res_max_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, r, w.part_a, x, b, w.maxima);
+        HPL_LAUNCH_CHECK();
+        k_res_final<<<1, 1, 0, s>>>(n, w.maxima, sr);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
+}
+
 size_t residual_ws_bytes(int64_t n) { return res_ws_layout(n > 0 ? n : 1, nullptr, nullptr); }
 
 // r = b - A x (b != NULL) or r = A x (b == NULL), A stored column-major (FP64).

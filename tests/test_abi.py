@@ -65,3 +65,12 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.lu_factor(-1, 8, 1, 8, None, 8, 1 << 20, 8, None) == 1
     assert lib.lu_factor(10, 8, 5, 8, None, 8, 1 << 20, 8, None) == 1
     assert lib.lu_factor(10, 8, 10, 8, None, 8, 16, 8, None) == 6          # workspace too small
+
+
+def test_batch_sizes_host_function_matches_oracle(lib, orc):
+    """hpl_batch_sizes is host code (no GPU needed): same draws as the oracle."""
+    import numpy as np
+    out = np.empty(4096, dtype=np.int64)
+    lib.hpl_batch_sizes.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
+    assert lib.hpl_batch_sizes(1, 4096, out.ctypes.data) == 0
+    assert np.array_equal(out, orc.batch_sizes(1, 4096))
