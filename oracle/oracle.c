@@ -334,8 +334,10 @@ void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU
  *     products, FP32 accumulation);
  *   - low precision prec = 0: BF16, round to nearest even;
  *     prec = 1: FP8 E4M3 (finite, max 448), round to nearest even, with one
- *     power-of-two scale per 32 consecutive elements along the contraction
- *     index, the smallest one that keeps amax/scale <= 448;
+ *     power-of-two scale per operand row (A operand) or column (B operand)
+ *     over the whole contraction index, the smallest one that keeps
+ *     amax/scale <= 448; FP8 applies to the trailing update, the panel
+ *     product L21 = A21 D^-1 keeps BF16 operands;
  *     prec = 2: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
  *     mode.                                                                  */
 
@@ -389,27 +391,24 @@ static void orc_round_operand(int prec, float* X, int64_t r, int64_t c, int64_t 
             for (int64_t i = 0; i < r; i++) X[j * ld + i] = orc_round_bf16(X[j * ld + i]);
         return;
     }
-    /* FP8 with a scale per 32 contraction elements. */
+    /* FP8 with one scale per operand row (A) or column (B), i.e. per 1 x K
+     * tile along the whole contraction index. */
     if (kdim_is_rows) {
-        for (int64_t j = 0; j < c; j++)
-            for (int64_t i0 = 0; i0 < r; i0 += 32) {
-                int64_t i1 = i0 + 32 < r ? i0 + 32 : r;
-                double amax = 0.0;
-                for (int64_t i = i0; i < i1; i++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
-                int e = orc_e4m3_block_exp(amax);
-                for (int64_t i = i0; i < i1; i++)
-                    X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
-            }
+        for (int64_t j = 0; j < c; j++) {
+            double amax = 0.0;
+            for (int64_t i = 0; i < r; i++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
+            int e = orc_e4m3_block_exp(amax);
+            for (int64_t i = 0; i < r; i++)
+                X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+        }
     } else {
-        for (int64_t i = 0; i < r; i++)
-            for (int64_t j0 = 0; j0 < c; j0 += 32) {
-                int64_t j1 = j0 + 32 < c ? j0 + 32 : c;
-                double amax = 0.0;
-                for (int64_t j = j0; j < j1; j++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
-                int e = orc_e4m3_block_exp(amax);
-                for (int64_t j = j0; j < j1; j++)
-                    X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
-            }
+        for (int64_t i = 0; i < r; i++) {
+            double amax = 0.0;
+            for (int64_t j = 0; j < c; j++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
+            int e = orc_e4m3_block_exp(amax);
+            for (int64_t j = 0; j < c; j++)
+                X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+        }
     }
 }
 
@@ -516,8 +515,9 @@ int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, 
         /* 2. L21 = A21 Dinv with low-precision operands */
         memcpy(Xq, X, sizeof(float) * kb * kb);
         for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
-        orc_round_operand(prec, t21, m, kb, m, 0);       /* A operand: k along columns */
-        orc_round_operand(prec, Xq, kb, kb, kb, 1);      /* B operand: k along rows    */
+        const int pprec = prec == 2 ? 2 : 0;             /* the panel product stays BF16 */
+        orc_round_operand(pprec, t21, m, kb, m, 0);      /* A operand: k along columns */
+        orc_round_operand(pprec, Xq, kb, kb, kb, 1);     /* B operand: k along rows    */
         orc_gemm32(m, kb, kb, t21, m, Xq, kb, A21, lda, 0);
         /* 3. trailing update A22 -= L21 A12 */
         for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
