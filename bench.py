@@ -59,6 +59,7 @@ def parse():
     ap.add_argument("--no-mxp", action="store_true", help="skip the mixed-precision solve")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched solve")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable solve")
+    ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--mxp-n", type=int, default=98304)
     ap.add_argument("--mxp-nb", type=int, default=1536)
     return ap.parse_args()
@@ -229,7 +230,7 @@ def run_batched(a, d: Dist, dev):
 
     import paper_2604_09517_gb300 as hpl
 
-    count = 4096
+    count = a.batched_count
     n = hpl.batch_sizes(a.seed, count)
     kind = np.array([0 if s < count // 2 else 1 for s in range(count)], dtype=np.uint8)
     bt = hpl.Batch(n, kind, device=dev)
@@ -267,7 +268,7 @@ def run_batched(a, d: Dist, dev):
     total_ms = d.max(sum(step_ms))
     value = d.sum(work * len(step_ms)) / (total_ms * 1e-3) / 1e12
     fp64_work = float(sum(flops(int(m)) for m, k in zip(n, kind) if k == 0))
-    return {"workload": "batched_4096_n32to512_half_fp64_half_bf16ir", "systems": count, "value": value,
+    return {"workload": f"batched_{count}_n32to512_half_fp64_half_bf16ir", "systems": count, "value": value,
             "unit": "TFLOP/s", "ms_per_step": total_ms / len(step_ms), "solved_ok": ok,
             "flops_per_step": work, "fp64_share_of_flops": fp64_work / work, "cuda_graph": True,
             "gpu_launches_per_step": 1,
@@ -309,9 +310,10 @@ def run_adjoint(a, d: Dist, dev):
             "grad_a_outer_product_gflop": 2.0 * n * n * nrhs / 1e9}
 
 
-def run_mxp(a, d: Dist, dev, fp64_value):
+def run_mxp(a, d: Dist, dev, fp64_value, prec=0):
     """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 1536):
-    BF16 block-LU factor on the tcgen05 tensor cores + FP64 GMRES refinement."""
+    block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
+    prec = 1) + FP64 GMRES refinement."""
     import torch
 
     import paper_2604_09517_gb300 as hpl
@@ -323,7 +325,7 @@ def run_mxp(a, d: Dist, dev, fp64_value):
     info = hpl.Info(dev)
     ws = None
     for _ in range(a.warmup):
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
     hpl.set_phase_timing(True)
@@ -335,7 +337,7 @@ def run_mxp(a, d: Dist, dev, fp64_value):
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = hpl.launch_count()
         e0.record(stream)
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec)
         e1.record(stream)
         launches += hpl.launch_count() - l0
         torch.cuda.synchronize(dev)
@@ -349,21 +351,23 @@ def run_mxp(a, d: Dist, dev, fp64_value):
     peaks = measured_peaks()
     upd_ms, upd_flops, upd_cnt = phases["update"]
     achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
-    peak = peaks["bf16_tflops_sustained"]
+    # FP8 dense peak: the measured BF16 peak times the nominal FP8/BF16 ratio (4.5 / 2.25)
+    peak = peaks["bf16_tflops_sustained"] * (2.0 if prec else 1.0)
     del A, X, ws
     torch.cuda.empty_cache()
-    return {"workload": f"hpl_mxp_bf16_n{n}_nb{nb}_gmres", "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
+    tag = "fp8e4m3" if prec else "bf16"
+    return {"workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres", "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
             "ms_per_step": total_ms / len(step_ms), "steps": a.steps, "warmup": a.warmup,
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
             "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,
             "fp64_lu_time_at_this_n_s": flops(n) / (fp64_value * 1e12) if fp64_value else None,
-            "fraction_of_bf16_peak": value / peak, "gpu_launches": int(launches),
+            f"fraction_of_{tag}_peak": value / peak, "gpu_launches": int(launches),
             "matrix": "uniform[-0.5,0.5) FP64, diagonal = row sum of |a_ij| (diagonally dominant)",
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
-                         "kernel": "k_gemm_bf16_tc (tcgen05 trailing update A22 -= L21 A12, FP32 C)",
-                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})",
+                         "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
+                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec else ""),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
             "phases": {k: {"ms_per_step": v[0] / len(step_ms), "intervals": v[2]} for k, v in phases.items() if v[2]}}
 
@@ -480,6 +484,7 @@ def run_ours(a, d: Dist):
     del A, b, b0, ipiv, ws, sws
     torch.cuda.empty_cache()
     mxp = None if a.no_mxp else run_mxp(a, d, dev, value)
+    mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1)
     batched = None if a.no_batched else run_batched(a, d, dev)
     adjoint = None if a.no_adjoint else run_adjoint(a, d, dev)
 
@@ -495,7 +500,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report,
-                "fraction_of_fp64_peak": value / peak, "mxp": mxp, "batched": batched, "adjoint": adjoint}
+                "fraction_of_fp64_peak": value / peak, "mxp": mxp, "mxp_fp8": mxp_fp8, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 

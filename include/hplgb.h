@@ -190,8 +190,11 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * bytes) keeps the factor afterwards: FP32 F (n x n, ld n) at byte offset 0
  * (L21 blocks below the diagonal, U blocks above, D_k on it) and FP32
  * D_k^-1 (n x nb, ld n, block k in rows k*nb..) at offset
- * align256(4 n^2). Only opts->prec = HPL_PREC_BF16 is accepted; A == NULL
- * returns HPL_ERR_INVALID; seed is reserved.
+ * align256(4 n^2). opts->prec = HPL_PREC_FP8_E4M3 runs the trailing update
+ * with FP8 E4M3 operands instead (one power-of-two scale per row of L21 and
+ * per column of A12 over the panel width, applied in the GEMM epilogue; the
+ * panel product L21 = A21 D^-1 keeps BF16). A == NULL returns
+ * HPL_ERR_INVALID; seed is reserved.
  */
 size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts);
 int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B, int64_t ldb,
@@ -256,6 +259,17 @@ int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64
  */
 int hplgb_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
                     int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream);
+
+/*
+ * hplgb_gemm_fp8 — the FP8 variant of the update product (configs only; the
+ * paper names FP32, FP16 and BF16): C = C - (A B^T) .* (sa sb^T) (sub = 1) or
+ * C = (A B^T) .* (sa sb^T), A: M x K and B: N x K FP8 E4M3 bytes, K contiguous,
+ * row strides lda, ldb multiples of 16 bytes, 16-byte aligned bases; sa (M)
+ * and sb (N) device FP32 scales (NULL = 1); FP32 accumulation in tensor
+ * memory (tcgen05 kind::f8f6f4). C, err as hplgb_gemm_bf16.
+ */
+int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
+                   const float* sa, const float* sb, float* C, int64_t ldc, int sub, int32_t* err, void* stream);
 
 /*
  * Diagnostics.

@@ -91,6 +91,7 @@ def load():
             "hpl_residual_workspace_size": (sz, [i64]),
             "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
             "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
+            "hplgb_gemm_fp8": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, vp, vp, i64, i32, vp, vp]),
             "mxp_workspace_size": (sz, [i64, i64, op]),
             "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hpl_batch_sizes": (i32, [u64, i64, vp]),
@@ -228,7 +229,7 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
 
 def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-              info: Info | None = None):
+              info: Info | None = None, prec: int = PREC_BF16):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
 
     Returns (X, info, ws); ws holds the block factor afterwards (see mxp_factor_views).
@@ -242,7 +243,7 @@ def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = RE
         Bc.copy_(Bm)
         Bm = Bc
     nrhs = Bm.shape[1]
-    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol)
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec)
     if X is None:
         X = colmajor(n, nrhs, device=A.device)
     Xm = X.view(n, 1) if X.dim() == 1 else X
@@ -423,6 +424,23 @@ def gemm_bf16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sub: bool = Tru
     e = int(err.item())
     if e:
         raise HplError(e, "hplgb_gemm_bf16 (device)")
+    return C
+
+
+def gemm_fp8(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None, sub: bool = True) -> torch.Tensor:
+    """C = C - (A B^T) * sa sb^T (sub) or the product, A and B float8_e4m3fn with K contiguous."""
+    lib = load()
+    assert A.dtype == torch.float8_e4m3fn and B.dtype == torch.float8_e4m3fn and C.dtype == torch.float32
+    assert A.stride(1) == 1 and B.stride(1) == 1 and C.stride(0) == 1
+    M, K = A.shape
+    N = B.shape[0]
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    _check(lib.hplgb_gemm_fp8(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(sa), _ptr(sb), _ptr(C),
+                              _ld(C), int(sub), _ptr(err), _stream(C.device)), "hplgb_gemm_fp8")
+    torch.cuda.current_stream(C.device).synchronize()
+    e = int(err.item())
+    if e:
+        raise HplError(e, "hplgb_gemm_fp8 (device)")
     return C
 
 

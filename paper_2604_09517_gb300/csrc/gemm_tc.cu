@@ -9,7 +9,7 @@
 // Blackwell design: a persistent, warp-specialised kernel, one CTA per SM.
 //   warp 0      : TMA producer (cp.async.bulk.tensor, 128B swizzle, 4 stages)
 //   warp 1      : TMEM allocator and single-thread tcgen05.mma issuer
-//   warps 2..5  : epilogue (tcgen05.ld from TMEM, FP32 read-modify-write of C)
+//   warps 2..9  : epilogue (tcgen05.ld from TMEM, FP32 read-modify-write of C)
 // Tiles are 128 x 256 with a 64-wide K step (one 128-byte swizzle row); the
 // accumulator lives in TMEM, double buffered (2 x 256 columns), so the
 // epilogue of one tile overlaps the MMAs of the next. Tiles are walked in
@@ -23,21 +23,36 @@
 namespace hplgb {
 namespace tc {
 
-constexpr int BM = 128, BN = 256, BK = 64;
+constexpr int BM = 128, BN = 256;
+constexpr int BKB = 128;                 // K bytes per stage: one 128-byte swizzle row
 constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK * 2;
-constexpr int B_BYTES = BN * BK * 2;
+constexpr int A_BYTES = BM * BKB;
+constexpr int B_BYTES = BN * BKB;
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 2 * BN;
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;
 constexpr int GROUP_M = 32;
 constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
 
-// Instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A = BF16
-// (bits 7-9 = 1), B = BF16 (bits 10-12 = 1), both K-major (bits 15, 16 = 0),
-// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                           ((uint32_t)(BM >> 4) << 24);
+// Operand kinds: 0 = BF16 (kind::f16, 2 bytes, 64 K per stage), 1 = FP8 E4M3
+// (kind::f8f6f4, 1 byte, 128 K per stage). Either way one MMA consumes 32
+// bytes of K (16 BF16 or 32 E4M3 values).
+// Instruction descriptor: D = F32 (bits 4-5 = 1); A and B formats in bits
+// 7-9 and 10-12 (BF16 = 1 for kind::f16; E4M3 = 0 for kind::f8f6f4); both
+// K-major (bits 15, 16 = 0); N >> 3 at bits 17-22; M >> 4 at bits 24-28.
+template <int KIND>
+struct Kind;
+template <>
+struct Kind<0> {
+    static constexpr int ELEM = 2;
+    static constexpr uint32_t IDESC =
+        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
+template <>
+struct Kind<1> {
+    static constexpr int ELEM = 1;
+    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+};
 
 struct Params {
     int M, N, K;
@@ -46,6 +61,8 @@ struct Params {
     int sub;
     int* err;
     long long timeout_ns;
+    const float* sa;       // optional per-row scale of the product (M)
+    const float* sb;       // optional per-column scale of the product (N)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -109,13 +126,23 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-        "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
-        : "memory");
+template <int KIND>
+__device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    if constexpr (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(Kind<0>::IDESC), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(Kind<1>::IDESC), "r"(accumulate)
+            : "memory");
+    }
 }
 
 __device__ __forceinline__ void umma_commit(uint64_t* bar) {
@@ -149,8 +176,10 @@ __device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, i
     nt = r / gsz;
 }
 
+template <int KIND>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_bf16_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    constexpr int BK = BKB / Kind<KIND>::ELEM;     // K elements per stage
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
     __shared__ uint32_t s_tmem;
@@ -171,7 +200,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         for (int a = 0; a < 2; a++) {
             mbar_init(&tfull_bar[a], 1);
-            mbar_init(&tempty_bar[a], 4);
+            mbar_init(&tempty_bar[a], 8);
         }
         mbar_init(&drain_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -232,8 +261,8 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint32_t sa = smem_u32(tiles + s * STAGE_BYTES);
                     const uint64_t ad = desc_sw128(sa), bd = desc_sw128(sa + A_BYTES);
 #pragma unroll
-                    for (int kk = 0; kk < BK / 16; kk++)      // 16 BF16 = 32 B per MMA: +2 in the address field
-                        umma_bf16(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                    for (int kk = 0; kk < BKB / 32; kk++)     // 32 bytes of K per MMA: +2 in the address field
+                        umma<KIND>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
                     umma_commit(&empty_bar[s]);
                 }
                 if (ok) umma_commit(&tfull_bar[acc]);
@@ -243,9 +272,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             mbar_wait(&drain_bar, 0, deadline + 1000000000ull, &s_abort, p.err);
         }
     } else {
-        // ---------------- epilogue: warps 2..5 ----------------
-        const int quarter = warp & 3;                   // TMEM lane quarter this warp may access
+        // ---------------- epilogue: warps 2..9 ----------------
+        // warp w reads TMEM lane quarter (w & 3) and the column half (w - 2) / 4
+        // of the tile; the C values of the next 32-column chunk are loaded
+        // before the current chunk is stored, so loads stay in flight.
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
+        constexpr int CHUNKS = BN / 2 / 32;
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tcount++) {
             int mt, nt;
@@ -255,26 +289,42 @@ __global__ void __launch_bounds__(THREADS, 1)
             tc_fence_after();
             const int row = mt * BM + row_in_tile;
             const bool row_ok = row < p.M;
-            for (int c0 = 0; c0 < BN; c0 += 32) {
+            const int cbase = nt * BN + half * (BN / 2);
+            float* cp = p.C + (long long)cbase * p.ldc + row;
+            const int ncol = min(BN / 2, p.N - cbase);      // valid columns of this half (may be <= 0)
+            float cv[32];
+            if (p.sub) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? cp[(long long)j * p.ldc] : 0.0f;
+            }
+#pragma unroll 1
+            for (int c = 0; c < CHUNKS; c++) {
                 uint32_t r[32];
-                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + c0, r);
-                tmem_wait_ld();
-                const int col0 = nt * BN + c0;
-                if (row_ok) {
-                    float* cp = p.C + (long long)col0 * p.ldc + row;
-                    if (p.sub) {
-                        float cv[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + half * (BN / 2) + c * 32, r);
+                float nv[32];
+                if (p.sub && c + 1 < CHUNKS) {
 #pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            cv[j] = (col0 + j < p.N) ? cp[(long long)j * p.ldc] : 0.0f;
-#pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (col0 + j < p.N) cp[(long long)j * p.ldc] = cv[j] - __uint_as_float(r[j]);
-                    } else {
-#pragma unroll
-                        for (int j = 0; j < 32; j++)
-                            if (col0 + j < p.N) cp[(long long)j * p.ldc] = __uint_as_float(r[j]);
+                    for (int j = 0; j < 32; j++) {
+                        const int jj = (c + 1) * 32 + j;
+                        nv[j] = (row_ok && jj < ncol) ? cp[(long long)jj * p.ldc] : 0.0f;
                     }
+                }
+                tmem_wait_ld();
+                if (row_ok) {
+                    const float rs = p.sa ? p.sa[row] : 1.0f;
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int jj = c * 32 + j;
+                        if (jj < ncol) {
+                            float v = __uint_as_float(r[j]) * rs;
+                            if (p.sb) v *= p.sb[cbase + jj];
+                            cp[(long long)jj * p.ldc] = p.sub ? cv[j] - v : v;
+                        }
+                    }
+                }
+                if (p.sub && c + 1 < CHUNKS) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) cv[j] = nv[j];
                 }
             }
             tc_fence_before();
@@ -310,40 +360,40 @@ static EncodeTiledFn get_encode() {
     return fn;
 }
 
-// rows x K BF16 matrix, K contiguous, row stride ld elements; box BK x box_rows.
-static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows) {
+// rows x K matrix of `elem`-byte values, K contiguous, row stride ld
+// elements; box of one 128-byte swizzle row (128 / elem values) x box_rows.
+static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, int64_t ld, int box_rows, int elem) {
     EncodeTiledFn enc = get_encode();
     if (!enc) return HPL_ERR_CUDA;
     cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
-    cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * elem};
+    cuuint32_t box[2] = {(cuuint32_t)(BKB / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
-                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult r = enc(m, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+                     const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
 }
 
-}  // namespace tc
-
-// C = sub ? C - A B^T : A B^T (see the top of this file). max_ctas <= 0 means
-// one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
-int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
-                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
-    using namespace tc;
+template <int KIND>
+static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                       int max_ctas, cudaStream_t s) {
+    constexpr int elem = Kind<KIND>::ELEM;
     if (M <= 0 || N <= 0) return HPL_OK;
     if (K <= 0) return HPL_ERR_INVALID;
     if (M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return HPL_ERR_INVALID;
-    if (lda < K || ldb < K || ldc < M || (lda % 8) || (ldb % 8)) return HPL_ERR_INVALID;
+    // TMA: 16-byte aligned base addresses and row strides
+    if (lda < K || ldb < K || ldc < M || (lda * elem) % 16 || (ldb * elem) % 16) return HPL_ERR_INVALID;
     if (((uintptr_t)A | (uintptr_t)B) & 15) return HPL_ERR_INVALID;
     CUtensorMap ma, mb;
-    int st = make_map(&ma, A, M, K, lda, BM);
+    int st = make_map(&ma, A, M, K, lda, BM, elem);
     if (st) return st;
-    st = make_map(&mb, B, N, K, ldb, BN);
+    st = make_map(&mb, B, N, K, ldb, BN, elem);
     if (st) return st;
     static bool attr_set = false;
     if (!attr_set) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           DYN_SMEM));
         attr_set = true;
     }
@@ -361,9 +411,28 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
     p.sub = sub;
     p.err = err;
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
-    k_gemm_bf16_tc<<<grid, THREADS, DYN_SMEM, s>>>(ma, mb, p);
+    p.sa = sa;
+    p.sb = sb;
+    k_gemm_tc<KIND><<<grid, THREADS, DYN_SMEM, s>>>(ma, mb, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
+}
+
+}  // namespace tc
+
+// C = sub ? C - A B^T : A B^T (see the top of this file). max_ctas <= 0 means
+// one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
+int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
+    return tc::launch_kind<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas, s);
+}
+
+// FP8 E4M3 operands (bytes, K contiguous); the product of row i and column j
+// is multiplied by sa[i] * sb[j] before it is stored or subtracted.
+int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
+                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                    int max_ctas, cudaStream_t s) {
+    return tc::launch_kind<1>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
 }
 
 }  // namespace hplgb
@@ -374,4 +443,11 @@ extern "C" int hplgb_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* 
                                int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream) {
     if (!err || !C || !A || !B) return HPL_ERR_INVALID;
     return launch_gemm_bf16(M, N, K, A, lda, B, ldb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
+}
+
+extern "C" int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B,
+                              int64_t ldb, const float* sa, const float* sb, float* C, int64_t ldc, int sub,
+                              int32_t* err, void* stream) {
+    if (!err || !C || !A || !B) return HPL_ERR_INVALID;
+    return launch_gemm_fp8(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
 }

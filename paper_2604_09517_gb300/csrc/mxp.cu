@@ -20,6 +20,7 @@
 // host), x += d. The host reads one scalar per GMRES step and per outer
 // iteration, so mxp_solve returns only when the solve is done.
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 
 #include <algorithm>
 #include <cmath>
@@ -31,6 +32,9 @@ namespace hplgb {
 
 int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                      float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s);
+int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
+                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                    int max_ctas, cudaStream_t s);
 size_t residual_ws_bytes(int64_t n);
 int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
                         double* sr, void* ws, cudaStream_t s);
@@ -105,6 +109,79 @@ static int to_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols, int 
     }
     HPL_LAUNCH_CHECK();
     return HPL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// FP8 E4M3 operands of the trailing update, one power-of-two scale per operand
+// row (A) or column (B) over the whole contraction index: the smallest e with
+// amax * 2^-e <= 448 (amax = f 2^E with 0.5 <= f < 1: e = E - 9 when
+// f <= 448/512, else E - 8); values x * 2^-e rounded to nearest even with
+// saturation; the scale 2^e is returned for the GEMM epilogue.
+__device__ __forceinline__ int e4m3_scale_exp(float amax) {
+    if (!(amax > 0.0f) || !isfinite(amax)) return 0;
+    int E;
+    float f = frexpf(amax, &E);
+    return f <= 0.875f ? E - 9 : E - 8;
+}
+
+__device__ __forceinline__ unsigned char to_e4m3(float x) {
+    return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+
+// A operand: X (rows x cols, column-major) -> out row r = X(r, :) (K = cols),
+// sa[r] = 2^e. 32 rows per CTA, the 8 warps split the columns.
+__global__ void __launch_bounds__(256) k_quant_rows_e4m3(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                         int64_t cols, unsigned char* __restrict__ out, int64_t ldo,
+                                                         int64_t kpad, float* __restrict__ sa) {
+    __shared__ float part[8][33];
+    __shared__ float inv[32];
+    __shared__ float tile[32][33];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r0 = (int64_t)blockIdx.x * 32;
+    const int64_t r = r0 + lane;
+    float amax = 0.0f;
+    if (r < rows)
+        for (int64_t c = warp; c < cols; c += 8) amax = fmaxf(amax, fabsf(X[c * ldx + r]));
+    part[warp][lane] = amax;
+    __syncthreads();
+    if (warp == 0) {
+        float m = 0.0f;
+        for (int w = 0; w < 8; w++) m = fmaxf(m, part[w][lane]);
+        const int e = e4m3_scale_exp(m);
+        inv[lane] = ldexpf(1.0f, -e);
+        if (r < rows) sa[r] = ldexpf(1.0f, e);
+    }
+    __syncthreads();
+    for (int64_t c0 = 0; c0 < kpad; c0 += 32) {
+        for (int i = warp; i < 32; i += 8) {
+            const int64_t c = c0 + i;
+            tile[lane][i] = (r < rows && c < cols) ? X[c * ldx + r] : 0.0f;
+        }
+        __syncthreads();
+        for (int i = warp; i < 32; i += 8) {
+            const int64_t rr = r0 + i, c = c0 + lane;
+            if (rr < rows && c < kpad) out[rr * ldo + c] = to_e4m3(tile[i][lane] * inv[i]);
+        }
+        __syncthreads();
+    }
+}
+
+// B operand: X (K rows x cols, column-major) -> out row c = X(:, c), sb[c] = 2^e.
+// One warp per column.
+__global__ void __launch_bounds__(256) k_quant_cols_e4m3(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                         int64_t cols, unsigned char* __restrict__ out, int64_t ldo,
+                                                         int64_t kpad, float* __restrict__ sb) {
+    const int lane = threadIdx.x & 31;
+    const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (c >= cols) return;
+    const float* col = X + c * ldx;
+    float amax = 0.0f;
+    for (int64_t r = lane; r < rows; r += 32) amax = fmaxf(amax, fabsf(col[r]));
+    for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+    const int e = e4m3_scale_exp(amax);
+    const float inv = ldexpf(1.0f, -e);
+    if (lane == 0) sb[c] = ldexpf(1.0f, e);
+    for (int64_t r = lane; r < kpad; r += 32) out[c * ldo + r] = to_e4m3(r < rows ? col[r] * inv : 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -317,6 +394,8 @@ struct MxpWs {
     double* scal;      // 4 device scalars (sr, beta, ...)
     float* y32;        // 2n FP32 scratch
     int* err;          // device error word of the GEMM kernels
+    float* sa;         // n: FP8 row scales of the update's A operand
+    float* sb;         // n: FP8 column scales of the update's B operand
 };
 
 static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) {
@@ -348,6 +427,8 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) 
     t.scal = (double*)take(sizeof(double) * 8);
     t.y32 = (float*)take(sizeof(float) * 2 * n);
     t.err = (int*)take(sizeof(int) * 4);
+    t.sa = (float*)take(sizeof(float) * n);
+    t.sb = (float*)take(sizeof(float) * n);
     if (w) *w = t;
     return off;
 }
@@ -430,10 +511,24 @@ struct Mxp {
                 phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
                 // A22 -= L21 A12
                 slot = phase_begin(s);
-                if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
-                if ((st = to_bf16(A12, ldf, kb, m2, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
-                if ((st = launch_gemm_bf16(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1, w.err, o.timeout_ns, 0, s)))
-                    return st;
+                if (o.prec == HPL_PREC_FP8_E4M3) {
+                    const int64_t kb16 = (kb + 15) / 16 * 16;
+                    uint8_t* qa = (uint8_t*)w.opA;
+                    uint8_t* qb = (uint8_t*)w.opB;
+                    k_quant_rows_e4m3<<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa);
+                    HPL_LAUNCH_CHECK();
+                    k_quant_cols_e4m3<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb);
+                    HPL_LAUNCH_CHECK();
+                    if ((st = launch_gemm_fp8(m2, m2, kb, qa, kb16, qb, kb16, w.sa, w.sb, A22, ldf, 1, w.err,
+                                              o.timeout_ns, 0, s)))
+                        return st;
+                } else {
+                    if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
+                    if ((st = to_bf16(A12, ldf, kb, m2, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                    if ((st = launch_gemm_bf16(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1, w.err, o.timeout_ns, 0,
+                                               s)))
+                        return st;
+                }
                 phase_end(slot, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
             } else {
                 phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb);
@@ -642,7 +737,7 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, 1536);
-    if (o.nb < 8 || o.prec != HPL_PREC_BF16) return HPL_ERR_INVALID;
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
     if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
     Mxp mx;
     mx.n = n;
@@ -697,7 +792,7 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, 1536);
-    if (o.nb < 8 || o.prec != HPL_PREC_BF16) return HPL_ERR_INVALID;
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
     Mxp mx;
     mx.n = n;
     mx.nb = std::min<int64_t>(o.nb, n);

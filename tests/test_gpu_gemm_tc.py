@@ -44,3 +44,29 @@ def test_gemm_bf16_rejects_bad_strides(hpl):
     C = hpl.colmajor(16, 16, dtype=torch.float32)
     with pytest.raises(hpl.HplError):
         hpl.gemm_bf16(A, B, C)          # row stride 12 is not a multiple of 8 elements
+
+
+@pytest.mark.parametrize("M,N,K,sub,scaled", [(128, 256, 128, True, False), (300, 500, 208, True, True),
+                                              (1536, 2048, 1536, True, True), (257, 129, 64, False, True)])
+def test_gemm_fp8_matches_fp64(hpl, M, N, K, sub, scaled):
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M + N + K)
+    ld = (K + 15) // 16 * 16
+    A = (torch.randn(M, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+    B = (torch.randn(N, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+    sa = torch.pow(2.0, torch.randint(-4, 4, (M,), device="cuda", generator=g).float()) if scaled else None
+    sb = torch.pow(2.0, torch.randint(-4, 4, (N,), device="cuda", generator=g).float()) if scaled else None
+    C = hpl.colmajor(M, N, dtype=torch.float32)
+    C.copy_(torch.randn(M, N, device="cuda", generator=g))
+    C0 = C.clone()
+    hpl.gemm_fp8(A, B, C, sa, sb, sub=sub)
+    Ad, Bd = A.double(), B.double()
+    if scaled:
+        Ad = Ad * sa.double()[:, None]
+        Bd = Bd * sb.double()[:, None]
+    prod = Ad @ Bd.t()
+    ref = C0.double() - prod if sub else prod
+    bound = Ad.abs() @ Bd.abs().t()
+    err = (C.double() - ref).abs()
+    tol = (K * 2.0 ** -23 + 1e-6) * bound + 2.0 ** -23 * C0.double().abs()
+    assert (err > tol).sum().item() == 0, err.max().item()

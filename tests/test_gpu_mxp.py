@@ -92,7 +92,7 @@ def test_mxp_rejects_invalid(hpl):
     import ctypes
     import torch
     lib = hpl.load()
-    opts = hpl.make_opts(nb=64, prec=hpl.PREC_FP8_E4M3)
+    opts = hpl.make_opts(nb=64, prec=7)                # no such precision: refused before any launch
     assert lib.mxp_solve(64, 1, 8, 64, 0, 8, 64, 8, 64, ctypes.byref(opts), 8, 1 << 30, 8, None) == 1
     opts = hpl.make_opts(nb=64)
     assert lib.mxp_solve(64, 1, None, 64, 0, 8, 64, 8, 64, ctypes.byref(opts), 8, 1 << 30, 8, None) == 1
@@ -115,3 +115,29 @@ def test_mxp_full_size_n98304(hpl, orc):
     del ws, A
     torch.cuda.empty_cache()
     assert orc.scaled_residual_gen(seed, n, True, _np(x)[:, 0], _np(b)) < 16
+
+
+@pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256)])
+def test_mxp_fp8_variant(hpl, orc, n, nb):
+    """FP8 E4M3 trailing update: factor blocks vs the oracle's FP8 emulation,
+    FP64 solution, and iteration counts (reported; within 2 of the oracle)."""
+    import torch
+    A, b = _system(hpl, n, 12)
+    A0, b0 = _np(A).copy(order="F"), _np(b).copy()
+    x, info, ws = hpl.mxp_solve(A, b, nb=nb, prec=hpl.PREC_FP8_E4M3)
+    torch.cuda.synchronize()
+    rec = info.read()
+    assert rec["status"] == 0, rec
+    xg = _np(x)[:, 0]
+    assert orc.scaled_residual(A0, xg, b0) < 16
+    x64, _ = orc.solve(A0, b0)
+    assert np.abs(xg - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A0, np.inf)
+    F, _ = hpl.mxp_factor_views(ws, n, nb)
+    Fo, _, _ = orc.mxp_factor(A0, nb, orc.PREC_FP8)
+    Fg = _np(F).astype(np.float64)
+    off = ~np.eye(n, dtype=bool)
+    # updated entries: FP8 rounding decisions may differ on nearly equal inputs
+    assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -3 * np.abs(Fo[off]).max()
+    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 1e-4 * np.abs(np.diag(Fo)).max()
+    emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_FP8, refine=1)
+    assert abs(rec["iters"] - emu["iters"]) <= 2
