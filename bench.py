@@ -1,6 +1,6 @@
 #!/usr/bin/env python
 """Benchmark: HPL FP64 LU solve (n=32768, NB=256, depth-1 look-ahead) on GB300,
-with the HPL-MxP mixed-precision solve (n=98304, NB=1536) reported beside it.
+with the HPL-MxP mixed-precision solve (n=98304, NB=3072) reported beside it.
 
 One step = one full solve of a fresh seeded system: lu_factor (PFACT, SWAP,
 DTRSM, DGEMM update, look-ahead) + lu_solve, all in the library's CUDA
@@ -61,7 +61,7 @@ def parse():
     ap.add_argument("--no-adjoint", action="store_true", help="skip the differentiable solve")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--mxp-n", type=int, default=98304)
-    ap.add_argument("--mxp-nb", type=int, default=1536)
+    ap.add_argument("--mxp-nb", type=int, default=3072)
     return ap.parse_args()
 
 
@@ -284,7 +284,7 @@ def run_adjoint(a, d: Dist, dev):
 
     import paper_2604_09517_gb300 as hpl
 
-    n, nrhs, nb = 4096, 64, 1536
+    n, nrhs, nb = 4096, 64, 2048
     A = hpl.generate(a.seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
     B = hpl.generate(a.seed, hpl.STREAM_B, n, nrhs, device=dev)
     G = torch.from_numpy(np.random.default_rng(a.seed).standard_normal((n, nrhs))).to(dev)
@@ -311,7 +311,7 @@ def run_adjoint(a, d: Dist, dev):
 
 
 def run_mxp(a, d: Dist, dev, fp64_value, prec=0):
-    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 1536):
+    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
     block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
     prec = 1) + FP64 GMRES refinement."""
     import torch

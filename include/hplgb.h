@@ -61,7 +61,7 @@ enum { HPL_REFINE_IR = 0, HPL_REFINE_GMRES = 1 };
 
 /* Options. A NULL hpl_opts* means the defaults listed here. Host memory. */
 typedef struct {
-    int64_t nb;          /* panel width NB; 0 = default (256 FP64, 1536 mixed) */
+    int64_t nb;          /* panel width NB; 0 = default (256 FP64, 3072 mixed, 32 batched) */
     int32_t lookahead;   /* 0 = none, 1 = depth-1 look-ahead on a second stream (default 1) */
     int32_t prec;        /* HPL_PREC_* for the mixed-precision factor (default BF16) */
     int32_t refine;      /* HPL_REFINE_* (default GMRES) */
@@ -175,7 +175,7 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * FP64, read only) should be diagonally dominant (the HPL-MxP matrix class,
  * hpl_generate with HPL_GEN_DIAG_DOMINANT). The factorization is the block LU
  * without pivoting of an FP32 copy of A with panel width opts->nb (default
- * 1536): per step, the inverse of the diagonal block by Newton-Schulz
+ * 3072): per step, the inverse of the diagonal block by Newton-Schulz
  * iterations with split-BF16 tensor-core products, then L21 = A21 D^-1 and
  * A22 -= L21 A12 with BF16 operands and FP32 accumulation. Each of the nrhs
  * columns of B (ldb) is then solved into X (ldx) by FP64 refinement (opts->
@@ -279,10 +279,13 @@ int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t ld
  * SWAP; Sec. VI-A, Fig. 4 breaks a run down by phase): while on, lu_factor
  * brackets each phase with CUDA events on the stream that runs it.
  * hplgb_phase_times synchronizes those events and returns, per phase
- * (0 PFACT, 1 SWAP, 2 DTRSM, 3 DGEMM update, 4 other), the summed milliseconds,
- * the algorithmic work (flops; bytes moved for SWAP) and the number of timed
- * intervals, then clears the record. ms, work, count: host arrays of 5, any
- * may be NULL. Returns HPL_ERR_CUDA if an event query fails.
+ * (0 PFACT or the mixed-precision diagonal inverse + L21, 1 SWAP, 2 DTRSM,
+ * 3 trailing update, 4 preconditioner / outer product, 5 FP64 -> FP32 copy,
+ * 6 FP64 residuals and matrix-vector products, 7 whole refinement, which
+ * contains 4 and 6), the summed milliseconds, the algorithmic work (flops;
+ * bytes moved for 1, 5 and 6) and the number of timed intervals, then clears
+ * the record. ms, work, count: host arrays of 8, any may be NULL. Returns
+ * HPL_ERR_CUDA if an event query fails.
  * hplgb_last_error: text of the last CUDA error the library met.
  */
 long long hplgb_launch_count(void);

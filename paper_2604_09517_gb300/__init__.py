@@ -227,7 +227,7 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
     return out
 
 
-def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = REFINE_GMRES, max_iter: int = 50,
+def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
               info: Info | None = None, prec: int = PREC_BF16):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
@@ -258,7 +258,7 @@ def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536, refine: int = RE
     return X, info, ws
 
 
-def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: torch.Tensor, nb: int = 1536,
+def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: torch.Tensor, nb: int = 3072,
                       want_grad_a: bool = True, refine: int = REFINE_GMRES, max_iter: int = 50, gmres_m: int = 30,
                       tol: float = 16.0):
     """Adjoint of X = A^-1 B from the factor mxp_solve left in ws: (grad_B, grad_A, info)."""
@@ -287,7 +287,7 @@ class SolveFn(torch.autograd.Function):
     A must be FP64, square, column-major and diagonally dominant."""
 
     @staticmethod
-    def forward(ctx, A, B, nb=1536):
+    def forward(ctx, A, B, nb=3072):
         Ac = A if A.stride(0) == 1 else A.t().contiguous().t()
         Bm = B.reshape(B.shape[0], -1) if B.dim() == 1 else B
         Bc = colmajor(Bm.shape[0], Bm.shape[1], device=A.device)
@@ -313,7 +313,7 @@ class SolveFn(torch.autograd.Function):
         return gA, gB, None
 
 
-def solve(A: torch.Tensor, B: torch.Tensor, nb: int = 1536) -> torch.Tensor:
+def solve(A: torch.Tensor, B: torch.Tensor, nb: int = 3072) -> torch.Tensor:
     """Differentiable mixed-precision solve X = A^-1 B (see SolveFn)."""
     return SolveFn.apply(A, B, nb)
 
@@ -397,7 +397,7 @@ class Batch:
         return recs if s is None else recs[0]
 
 
-def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 1536):
+def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 3072):
     """(F, Dinv) views of the block factor that mxp_solve leaves in its workspace."""
     nb = min(nb, n)
     f_bytes = 4 * n * n
@@ -444,7 +444,7 @@ def gemm_fp8(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None
     return C
 
 
-PHASES = ("pfact", "swap", "trsm", "update", "other")
+PHASES = ("pfact", "swap", "trsm", "update", "other", "convert", "resid", "refine")
 
 
 def launch_count() -> int:
@@ -458,9 +458,9 @@ def set_phase_timing(on: bool) -> None:
 def phase_times() -> dict:
     """Per-phase {name: (ms, work, intervals)} since timing was switched on."""
     import numpy as np
-    ms = np.zeros(5)
-    work = np.zeros(5)
-    cnt = np.zeros(5, dtype=np.int64)
+    ms = np.zeros(len(PHASES))
+    work = np.zeros(len(PHASES))
+    cnt = np.zeros(len(PHASES), dtype=np.int64)
     _check(load().hplgb_phase_times(ms.ctypes.data, work.ctypes.data, cnt.ctypes.data), "hplgb_phase_times")
     return {name: (float(ms[i]), float(work[i]), int(cnt[i])) for i, name in enumerate(PHASES)}
 

@@ -55,7 +55,17 @@ int get_ctx(DeviceCtx** out);
 void count_launch();
 
 // Optional per-phase timers (phases of the paper's per-panel cost model).
-enum Phase { PH_PANEL = 0, PH_SWAP = 1, PH_TRSM = 2, PH_UPDATE = 3, PH_OTHER = 4, PH_COUNT = 5 };
+enum Phase {
+    PH_PANEL = 0,     // PFACT (FP64) / diagonal-block inverse and L21 (mixed precision)
+    PH_SWAP = 1,
+    PH_TRSM = 2,
+    PH_UPDATE = 3,
+    PH_OTHER = 4,     // preconditioner applications, outer products
+    PH_CONVERT = 5,   // FP64 -> FP32 copy of the matrix (mixed precision)
+    PH_RESID = 6,     // FP64 residuals and matrix-vector products (refinement)
+    PH_REFINE = 7,    // the whole refinement of one right-hand side (contains 4 and 6)
+    PH_COUNT = 8
+};
 int phase_begin(cudaStream_t s);                                   // -1 when timing is off
 void phase_end(int slot, cudaStream_t s, int phase, double work);  // work: flops or bytes
 

@@ -23,16 +23,24 @@
 namespace hplgb {
 namespace tc {
 
-constexpr int BM = 128, BN = 256;
+constexpr int BM = 128;
 constexpr int BKB = 128;                 // K bytes per stage: one 128-byte swizzle row
-constexpr int STAGES = 4;
 constexpr int A_BYTES = BM * BKB;
-constexpr int B_BYTES = BN * BKB;
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int TMEM_COLS = 2 * BN;
 constexpr int THREADS = 320;
 constexpr int GROUP_M = 32;
-constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
+
+// Tile width BN: 256 for large products; 128 when a product has fewer
+// 128 x 256 tiles than the GPU has SMs (the 1536 x 1536 Newton-Schulz
+// products), which doubles the CTAs at work.
+template <int BN_>
+struct Tile {
+    static constexpr int BN = BN_;
+    static constexpr int B_BYTES = BN * BKB;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr int TMEM_COLS = 2 * BN;            // two accumulators
+    static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
+};
 
 // Operand kinds: 0 = BF16 (kind::f16, 2 bytes, 64 K per stage), 1 = FP8 E4M3
 // (kind::f8f6f4, 1 byte, 128 K per stage). Either way one MMA consumes 32
@@ -45,14 +53,17 @@ struct Kind;
 template <>
 struct Kind<0> {
     static constexpr int ELEM = 2;
-    static constexpr uint32_t IDESC =
-        (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static constexpr uint32_t FORMATS = (1u << 4) | (1u << 7) | (1u << 10);
 };
 template <>
 struct Kind<1> {
     static constexpr int ELEM = 1;
-    static constexpr uint32_t IDESC = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+    static constexpr uint32_t FORMATS = (1u << 4);
 };
+template <int KIND, int BN>
+__host__ __device__ constexpr uint32_t idesc() {
+    return Kind<KIND>::FORMATS | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
 struct Params {
     int M, N, K;
@@ -126,21 +137,21 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
     return d;
 }
 
-template <int KIND>
+template <int KIND, int BN>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
     if constexpr (KIND == 0) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(Kind<0>::IDESC), "r"(accumulate)
+            "l"(adesc), "l"(bdesc), "r"(idesc<0, BN>()), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(Kind<1>::IDESC), "r"(accumulate)
+            "l"(adesc), "l"(bdesc), "r"(idesc<1, BN>()), "r"(accumulate)
             : "memory");
     }
 }
@@ -176,10 +187,11 @@ __device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, i
     nt = r / gsz;
 }
 
-template <int KIND>
+template <int KIND, int BN>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
     constexpr int BK = BKB / Kind<KIND>::ELEM;     // K elements per stage
+    constexpr int STAGES = Tile<BN>::STAGES, STAGE_BYTES = Tile<BN>::STAGE_BYTES, TMEM_COLS = Tile<BN>::TMEM_COLS;
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t full_bar[STAGES], empty_bar[STAGES], tfull_bar[2], tempty_bar[2], drain_bar;
     __shared__ uint32_t s_tmem;
@@ -262,7 +274,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                     const uint64_t ad = desc_sw128(sa), bd = desc_sw128(sa + A_BYTES);
 #pragma unroll
                     for (int kk = 0; kk < BKB / 32; kk++)     // 32 bytes of K per MMA: +2 in the address field
-                        umma<KIND>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                        umma<KIND, BN>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
                     umma_commit(&empty_bar[s]);
                 }
                 if (ok) umma_commit(&tfull_bar[acc]);
@@ -375,7 +387,7 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, i
     return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
 }
 
-template <int KIND>
+template <int KIND, int BN>
 static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                        const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                        int max_ctas, cudaStream_t s) {
@@ -393,8 +405,8 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if (st) return st;
     static bool attr_set = false;
     if (!attr_set) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          DYN_SMEM));
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::DYN_SMEM));
         attr_set = true;
     }
     int dev = 0, sms = kNumSMsGB300;
@@ -413,9 +425,14 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
-    k_gemm_tc<KIND><<<grid, THREADS, DYN_SMEM, s>>>(ma, mb, p);
+    k_gemm_tc<KIND, BN><<<grid, THREADS, Tile<BN>::DYN_SMEM, s>>>(ma, mb, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
+}
+
+// Fewer 128 x 256 tiles than SMs: use 128 x 128 tiles.
+static bool narrow_tiles(int64_t M, int64_t N) {
+    return ((M + BM - 1) / BM) * ((N + 255) / 256) < kNumSMsGB300;
 }
 
 }  // namespace tc
@@ -424,7 +441,11 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
 // one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
 int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                      float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
-    return tc::launch_kind<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns,
+                                       max_ctas, s);
+    return tc::launch_kind<0, 256>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas,
+                                   s);
 }
 
 // FP8 E4M3 operands (bytes, K contiguous); the product of row i and column j
@@ -432,7 +453,9 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s) {
-    return tc::launch_kind<1>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<1, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    return tc::launch_kind<1, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
 }
 
 }  // namespace hplgb

@@ -43,6 +43,12 @@ int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double*
 
 constexpr int kNsIters = 3;
 constexpr int kDotBlocks = 304;
+constexpr int kGemvSplitMax = 16;
+// Default panel width: with an FP32 trailing matrix each update step moves 8
+// bytes of C per 2 NB flops, so NB must be large for the update to stay
+// compute-bound (BF16 needs NB >~ 1250 at the measured HBM bandwidth, FP8
+// twice that); 3072 measured fastest for both at n = 98304.
+constexpr int64_t kMxpDefaultNb = 3072;
 
 static inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 
@@ -54,61 +60,84 @@ static inline int64_t round8(int64_t x) { return (x + 7) / 8 * 8; }
 //   trans = 0: operand row c (< cols) holds X(0..rows, c): the N x K operand
 //              for a product with X on the right (K = rows).
 // part 0 = round to nearest even, 1 = hi = bf16(x), 2 = lo = bf16(x - hi).
-// K positions in [K extent, kpad) are written as zeros.
+// nseg segments are written at column offsets seg_off + q * seg_stride, with
+// the part of segment q in bits 2q..2q+1 of `parts` (the split operands of
+// the Newton-Schulz products are [hi | hi | lo] or [hi | lo | hi]). With
+// eye2 the converted value is 2 delta_ij - X(i, j) (the 2I - R step).
+// K positions in [K extent, kpad) of each segment are written as zeros.
 __device__ __forceinline__ float bf16_part(float x, int part) {
     float h = __bfloat162float(__float2bfloat16_rn(x));
     return part == 2 ? __bfloat162float(__float2bfloat16_rn(x - h)) : h;
 }
 
+struct Seg {
+    int nseg, parts, eye2;
+    int64_t seg_off, seg_stride, kpad;
+};
+
 __global__ void __launch_bounds__(256) k_to_bf16_t(const float* __restrict__ X, int64_t ldx, int64_t rows,
-                                                   int64_t cols, int part, __nv_bfloat16* __restrict__ out,
-                                                   int64_t ldo, int64_t seg_off, int64_t kpad) {
+                                                   int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
+                                                   Seg g) {
     __shared__ float tile[32][33];
     const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
         int64_t c = c0 + i, r = r0 + tx;
-        tile[i][tx] = (c < cols && r < rows) ? X[c * ldx + r] : 0.0f;
+        float v = (c < cols && r < rows) ? X[c * ldx + r] : 0.0f;
+        if (g.eye2 && c < cols && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
+        tile[i][tx] = v;
     }
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
         int64_t r = r0 + i, c = c0 + tx;
-        if (r < rows && c < kpad) out[r * ldo + seg_off + c] = __float2bfloat16_rn(bf16_part(tile[tx][i], part));
+        if (r < rows && c < g.kpad)
+            for (int q = 0; q < g.nseg; q++)
+                out[r * ldo + g.seg_off + q * g.seg_stride + c] =
+                    __float2bfloat16_rn(bf16_part(tile[tx][i], (g.parts >> (2 * q)) & 3));
     }
 }
 
 __global__ void __launch_bounds__(256) k_to_bf16_n(const float* __restrict__ X, int64_t ldx, int64_t rows,
-                                                   int64_t cols, int part, __nv_bfloat16* __restrict__ out,
-                                                   int64_t ldo, int64_t seg_off, int64_t kpad) {
+                                                   int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
+                                                   Seg g) {
     const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;   // K index
     const int64_t c = blockIdx.y;                                  // operand row
-    if (r >= kpad || c >= cols) return;
+    if (r >= g.kpad || c >= cols) return;
     float v = r < rows ? X[c * ldx + r] : 0.0f;
-    out[c * ldo + seg_off + r] = __float2bfloat16_rn(bf16_part(v, part));
+    if (g.eye2 && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
+    for (int q = 0; q < g.nseg; q++)
+        out[c * ldo + g.seg_off + q * g.seg_stride + r] = __float2bfloat16_rn(bf16_part(v, (g.parts >> (2 * q)) & 3));
 }
 
+static int to_bf16_seg(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, uint16_t* out, int64_t ldo,
+                       Seg g, cudaStream_t s) {
+    if (trans) {
+        dim3 grid((unsigned)((g.kpad + 31) / 32), (unsigned)((rows + 31) / 32));
+        k_to_bf16_t<<<grid, dim3(32, 8), 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
+    for (int64_t c0 = 0; c0 < cols; c0 += 65535) {           // grid.y limit
+        int64_t cc = std::min<int64_t>(65535, cols - c0);
+        dim3 grid((unsigned)((g.kpad + 255) / 256), (unsigned)cc);
+        k_to_bf16_n<<<grid, 256, 0, s>>>(X + c0 * ldx, ldx, rows, cc, (__nv_bfloat16*)(out + c0 * ldo), ldo, g);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
+}
+
+// One segment, one part (the plain operand conversions).
 static int to_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, int part, uint16_t* out,
                    int64_t ldo, int64_t seg_off, int64_t kpad, cudaStream_t s) {
-    if (trans) {
-        dim3 g((unsigned)((kpad + 31) / 32), (unsigned)((rows + 31) / 32));
-        k_to_bf16_t<<<g, dim3(32, 8), 0, s>>>(X, ldx, rows, cols, part, (__nv_bfloat16*)out, ldo, seg_off, kpad);
-    } else {
-        if (cols > 65535) {
-            // split the operand rows over several launches (grid.y limit)
-            for (int64_t c0 = 0; c0 < cols; c0 += 65535) {
-                int64_t cc = std::min<int64_t>(65535, cols - c0);
-                dim3 g((unsigned)((kpad + 255) / 256), (unsigned)cc);
-                k_to_bf16_n<<<g, 256, 0, s>>>(X + c0 * ldx, ldx, rows, cc, part, (__nv_bfloat16*)(out + c0 * ldo),
-                                              ldo, seg_off, kpad);
-                HPL_LAUNCH_CHECK();
-            }
-            return HPL_OK;
-        }
-        dim3 g((unsigned)((kpad + 255) / 256), (unsigned)cols);
-        k_to_bf16_n<<<g, 256, 0, s>>>(X, ldx, rows, cols, part, (__nv_bfloat16*)out, ldo, seg_off, kpad);
-    }
-    HPL_LAUNCH_CHECK();
-    return HPL_OK;
+    Seg g{1, part, 0, seg_off, 0, kpad};
+    return to_bf16_seg(X, ldx, rows, cols, trans, out, ldo, g, s);
+}
+
+// Split operand [p0 | p1 | p2] of three segments of width kb8 (optionally of 2I - X).
+static int to_bf16_split3(const float* X, int64_t ldx, int64_t kb, int trans, int p0, int p1, int p2, int eye2,
+                          uint16_t* out, int64_t kb8, cudaStream_t s) {
+    Seg g{3, p0 | (p1 << 2) | (p2 << 4), eye2, 0, kb8, kb8};
+    return to_bf16_seg(X, ldx, kb, kb, trans, out, 3 * kb8, g, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -186,12 +215,73 @@ __global__ void __launch_bounds__(256) k_quant_cols_e4m3(const float* __restrict
 
 // ---------------------------------------------------------------------------
 // Small dense kernels.
-__global__ void k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda, float* __restrict__ F,
-                                 int64_t ldf) {
-    const int64_t total = n * n;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = t / n, i = t - j * n;
-        F[j * ldf + i] = (float)A[j * lda + i];
+// F = fl32(A): CTA x-index = 1024-row chunk, y-index strides over columns.
+__global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                        float* __restrict__ F, int64_t ldf) {
+    const int64_t i0 = (int64_t)blockIdx.x * 1024 + threadIdx.x;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        const double* a = A + j * lda;
+        float* f = F + j * ldf;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            const int64_t i = i0 + q * 256;
+            if (i < n) f[i] = (float)a[i];
+        }
+    }
+}
+
+// Column-split GEMV for the preconditioner: part[s][r] = sum over the column
+// chunk s of P(r, c) x[c]. P is FP32 column-major (rows x cols, ldp); each
+// CTA takes 128 rows (4 per lane, float4 loads when aligned) and one column
+// chunk, its 8 warps split the chunk's columns; k_gemv_combine then adds the
+// chunks in order, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_gemv_part(int64_t rows, int64_t cols, const float* __restrict__ P,
+                                                   int64_t ldp, const float* __restrict__ x, int64_t chunk,
+                                                   float* __restrict__ part, int64_t ldpart, int vec) {
+    __shared__ float red[8][129];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 128 + 4 * lane;
+    const int64_t c0 = (int64_t)blockIdx.y * chunk, c1 = min(cols, c0 + chunk);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (vec && r + 3 < rows) {
+#pragma unroll 8
+        for (int64_t c = c0 + warp; c < c1; c += 8) {
+            const float4 v = *reinterpret_cast<const float4*>(P + c * ldp + r);
+            const float xc = __ldg(x + c);
+            a0 = fmaf(v.x, xc, a0);
+            a1 = fmaf(v.y, xc, a1);
+            a2 = fmaf(v.z, xc, a2);
+            a3 = fmaf(v.w, xc, a3);
+        }
+    } else {
+        for (int64_t c = c0 + warp; c < c1; c += 8) {
+            const float xc = __ldg(x + c);
+            const float* pc = P + c * ldp;
+            if (r < rows) a0 = fmaf(pc[r], xc, a0);
+            if (r + 1 < rows) a1 = fmaf(pc[r + 1], xc, a1);
+            if (r + 2 < rows) a2 = fmaf(pc[r + 2], xc, a2);
+            if (r + 3 < rows) a3 = fmaf(pc[r + 3], xc, a3);
+        }
+    }
+    red[warp][4 * lane] = a0;
+    red[warp][4 * lane + 1] = a1;
+    red[warp][4 * lane + 2] = a2;
+    red[warp][4 * lane + 3] = a3;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int64_t rr = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        float s = 0.f;
+        for (int w = 0; w < 8; w++) s += red[w][threadIdx.x];
+        if (rr < rows) part[blockIdx.y * ldpart + rr] = s;
+    }
+}
+
+__global__ void k_gemv_combine(int64_t rows, int nsplit, const float* __restrict__ part, int64_t ldpart,
+                               float* __restrict__ y, int sub) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int q = 0; q < nsplit; q++) s += part[q * ldpart + r];
+        y[r] = sub ? y[r] - s : s;
     }
 }
 
@@ -200,14 +290,6 @@ __global__ void k_ns_init(const float* __restrict__ D, int64_t ldd, int kb, floa
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t j = t / kb, i = t - j * kb;
         X[t] = (i == j) ? 1.0f / D[j * ldd + j] : 0.0f;
-    }
-}
-
-__global__ void k_two_minus_eye(float* __restrict__ R, int kb) {
-    const int64_t total = (int64_t)kb * kb;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = t / kb, i = t - j * kb;
-        R[t] = ((i == j) ? 2.0f : 0.0f) - R[t];
     }
 }
 
@@ -224,27 +306,6 @@ __global__ void k_zero_diag_flag(const float* __restrict__ D, int64_t ldd, int k
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < kb; i += gridDim.x * blockDim.x)
         if (D[(int64_t)i * ldd + i] == 0.0f)
             atomicCAS((unsigned long long*)&info->info, 0ull, (unsigned long long)(k0 + i + 1));
-}
-
-// y (= or -=) P x, P FP32 column-major rows x cols. 32 rows per CTA (lane =
-// row), the 8 warps split the columns, partial sums combined in a fixed order.
-__global__ void __launch_bounds__(256) k_gemv32(int64_t rows, int64_t cols, const float* __restrict__ P, int64_t ldp,
-                                                const float* __restrict__ x, float* __restrict__ y, int sub) {
-    __shared__ float part[8][33];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r = (int64_t)blockIdx.x * 32 + lane;
-    float acc = 0.0f;
-    if (r < rows) {
-#pragma unroll 4
-        for (int64_t c = warp; c < cols; c += 8) acc = fmaf(P[c * ldp + r], __ldg(x + c), acc);
-    }
-    part[warp][lane] = acc;
-    __syncthreads();
-    if (warp == 0 && r < rows) {
-        float s = 0.0f;
-        for (int w = 0; w < 8; w++) s += part[w][lane];
-        y[r] = sub ? y[r] - s : s;
-    }
 }
 
 // y (= or -=) P^T x: one warp per column c of P (rows x cols, FP32 column-
@@ -396,6 +457,7 @@ struct MxpWs {
     int* err;          // device error word of the GEMM kernels
     float* sa;         // n: FP8 row scales of the update's A operand
     float* sb;         // n: FP8 column scales of the update's B operand
+    float* gpart;      // kGemvSplitMax x n: column-split GEMV partial sums
 };
 
 static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) {
@@ -429,6 +491,7 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) 
     t.err = (int*)take(sizeof(int) * 4);
     t.sa = (float*)take(sizeof(float) * n);
     t.sb = (float*)take(sizeof(float) * n);
+    t.gpart = (float*)take(sizeof(float) * kGemvSplitMax * n);
     if (w) *w = t;
     return off;
 }
@@ -447,8 +510,27 @@ struct Mxp {
 
     // r = b - op(A) x (b != NULL, scaled residual into sr if given) or r = op(A) x
     int resid(const double* x, const double* b, double* r, double* sr) {
-        return trans ? launch_residual_vec_t(n, A, lda, x, b, r, sr, w.resws, s)
-                     : launch_residual_vec(n, A, lda, x, b, r, sr, w.resws, s);
+        int slot = phase_begin(s);
+        int st = trans ? launch_residual_vec_t(n, A, lda, x, b, r, sr, w.resws, s)
+                       : launch_residual_vec(n, A, lda, x, b, r, sr, w.resws, s);
+        phase_end(slot, s, PH_RESID, 8.0 * n * n);
+        return st;
+    }
+
+    // y (= or -=) P x for an FP32 column-major panel (rows x cols, ldp)
+    int gemv(int64_t rows, int64_t cols, const float* P, int64_t ldp, const float* x, float* y, int sub) {
+        if (rows <= 0) return HPL_OK;
+        const int64_t rb = (rows + 127) / 128;
+        int64_t nsplit = std::min<int64_t>(kGemvSplitMax, std::max<int64_t>(1, (1216 + rb - 1) / rb));
+        nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, cols / 64));
+        const int64_t chunk = (cols + nsplit - 1) / nsplit;
+        nsplit = (cols + chunk - 1) / chunk;
+        const int vec = (ldp % 4 == 0) && (((uintptr_t)P & 15) == 0);
+        k_gemv_part<<<dim3((unsigned)rb, (unsigned)nsplit), 256, 0, s>>>(rows, cols, P, ldp, x, chunk, w.gpart, n, vec);
+        HPL_LAUNCH_CHECK();
+        k_gemv_combine<<<grid_for(rows), 256, 0, s>>>(rows, (int)nsplit, w.gpart, n, y, sub);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
     }
 
     int dot(const double* a, const double* b, double* out, int take_sqrt) {
@@ -463,8 +545,11 @@ struct Mxp {
     int factor(hpl_info* info) {
         const int64_t ldf = n;
         HPL_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, s));
-        k_f64_to_f32_mat<<<grid_for(n * n), 256, 0, s>>>(n, A, lda, w.F, ldf);
+        int cslot = phase_begin(s);
+        k_f64_to_f32_mat<<<dim3((unsigned)((n + 1023) / 1024), (unsigned)std::min<int64_t>(n, 2048)), 256, 0, s>>>(
+            n, A, lda, w.F, ldf);
         HPL_LAUNCH_CHECK();
+        phase_end(cslot, s, PH_CONVERT, 12.0 * n * n);
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
             float* D = w.F + k0 * ldf + k0;
@@ -475,25 +560,15 @@ struct Mxp {
             HPL_LAUNCH_CHECK();
             int st;
             // split D as the A operand: [hi | hi | lo]
-            if ((st = to_bf16(D, ldf, kb, kb, 1, 1, w.nsD, K3, 0, kb8, s))) return st;
-            if ((st = to_bf16(D, ldf, kb, kb, 1, 1, w.nsD, K3, kb8, kb8, s))) return st;
-            if ((st = to_bf16(D, ldf, kb, kb, 1, 2, w.nsD, K3, 2 * kb8, kb8, s))) return st;
+            if ((st = to_bf16_split3(D, ldf, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
             for (int it = 0; it < kNsIters; it++) {
                 // R = D X: B operand from X, [hi | lo | hi]
-                if ((st = to_bf16(w.X, kb, kb, kb, 0, 1, w.nsB, K3, 0, kb8, s))) return st;
-                if ((st = to_bf16(w.X, kb, kb, kb, 0, 2, w.nsB, K3, kb8, kb8, s))) return st;
-                if ((st = to_bf16(w.X, kb, kb, kb, 0, 1, w.nsB, K3, 2 * kb8, kb8, s))) return st;
+                if ((st = to_bf16_split3(w.X, kb, kb, 0, 1, 2, 1, 0, w.nsB, kb8, s))) return st;
                 if ((st = launch_gemm_bf16(kb, kb, K3, w.nsD, K3, w.nsB, K3, w.R, kb, 0, w.err, o.timeout_ns, 0, s)))
                     return st;
-                k_two_minus_eye<<<grid_for(kb * kb), 256, 0, s>>>(w.R, (int)kb);
-                HPL_LAUNCH_CHECK();
-                // X = X T: A operand from X [hi | hi | lo], B operand from T [hi | lo | hi]
-                if ((st = to_bf16(w.X, kb, kb, kb, 1, 1, w.nsX, K3, 0, kb8, s))) return st;
-                if ((st = to_bf16(w.X, kb, kb, kb, 1, 1, w.nsX, K3, kb8, kb8, s))) return st;
-                if ((st = to_bf16(w.X, kb, kb, kb, 1, 2, w.nsX, K3, 2 * kb8, kb8, s))) return st;
-                if ((st = to_bf16(w.R, kb, kb, kb, 0, 1, w.nsB, K3, 0, kb8, s))) return st;
-                if ((st = to_bf16(w.R, kb, kb, kb, 0, 2, w.nsB, K3, kb8, kb8, s))) return st;
-                if ((st = to_bf16(w.R, kb, kb, kb, 0, 1, w.nsB, K3, 2 * kb8, kb8, s))) return st;
+                // X = X (2I - R): A operand from X [hi | hi | lo], B operand from 2I - R [hi | lo | hi]
+                if ((st = to_bf16_split3(w.X, kb, kb, 1, 1, 1, 2, 0, w.nsX, kb8, s))) return st;
+                if ((st = to_bf16_split3(w.R, kb, kb, 0, 1, 2, 1, 1, w.nsB, kb8, s))) return st;
                 if ((st = launch_gemm_bf16(kb, kb, K3, w.nsX, K3, w.nsB, K3, w.X, kb, 0, w.err, o.timeout_ns, 0, s)))
                     return st;
             }
@@ -587,21 +662,20 @@ struct Mxp {
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
             if (m2 > 0) {
-                k_gemv32<<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0,
-                                                                   y + k0 + kb, 1);
-                HPL_LAUNCH_CHECK();
+                int st = gemv(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0, y + k0 + kb, 1);
+                if (st) return st;
             }
         }
         const int64_t last = ((n - 1) / nb) * nb;
         for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
             const int64_t kb = std::min(nb, n - k0);
-            k_gemv32<<<(unsigned)((kb + 31) / 32), 256, 0, s>>>(kb, kb, w.Dinv + k0, n, y + k0, t, 0);
-            HPL_LAUNCH_CHECK();
+            int st = gemv(kb, kb, w.Dinv + k0, n, y + k0, t, 0);
+            if (st) return st;
             k_copy32<<<grid_for(kb), 256, 0, s>>>(kb, t, y + k0);
             HPL_LAUNCH_CHECK();
             if (k0 > 0) {
-                k_gemv32<<<(unsigned)((k0 + 31) / 32), 256, 0, s>>>(k0, kb, w.F + k0 * ldf, ldf, y + k0, y, 1);
-                HPL_LAUNCH_CHECK();
+                st = gemv(k0, kb, w.F + k0 * ldf, ldf, y + k0, y, 1);
+                if (st) return st;
             }
         }
         k_f32_to_f64<<<grid_for(n), 256, 0, s>>>(n, y, out);
@@ -691,6 +765,13 @@ struct Mxp {
 
     // Refine one right-hand side. Returns the HPL_* outcome.
     int refine(const double* b, double* x, int* iters, int* inner, double* sr_out, int* status) {
+        int rslot = phase_begin(s);
+        int st = refine_body(b, x, iters, inner, sr_out, status);
+        phase_end(rslot, s, PH_REFINE, 0.0);
+        return st;
+    }
+
+    int refine_body(const double* b, double* x, int* iters, int* inner, double* sr_out, int* status) {
         int st;
         if ((st = precond(b, x))) return st;
         int it = 0;
@@ -724,7 +805,7 @@ using namespace hplgb;
 
 extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts) {
     (void)nrhs;
-    Opts o = resolve_opts(opts, 1536);
+    Opts o = resolve_opts(opts, kMxpDefaultNb);
     int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
     return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr);
 }
@@ -736,7 +817,7 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     if (n <= 0 || nrhs < 0 || !A || lda < n || !info) return HPL_ERR_INVALID;
     if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
-    Opts o = resolve_opts(opts, 1536);
+    Opts o = resolve_opts(opts, kMxpDefaultNb);
     if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
     if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
     Mxp mx;
@@ -791,7 +872,7 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     if (nrhs > 0 && (!G || !gradB || ldg < n || ldgb < n)) return HPL_ERR_INVALID;
     if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
-    Opts o = resolve_opts(opts, 1536);
+    Opts o = resolve_opts(opts, kMxpDefaultNb);
     if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
     Mxp mx;
     mx.n = n;
