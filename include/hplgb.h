@@ -229,6 +229,9 @@ int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, con
  * (device, n[s]: b in, x out) are per-system pointers given in HOST arrays, as
  * are n, lda, ipiv and kind. infos: device array of count hpl_info, one per
  * system in the caller's order.
+ * variant[s] (host array, NULL = all 0) picks the system's tile shape: panel
+ * width 32 (0) or 16 (1); the package's autotuner measures both per kind and
+ * size bucket and stores the choice in a table the Python binding applies.
  * solve_batched_plan writes the work table into ws (synchronous host-to-device
  * copy; ws must hold solve_batched_workspace_size bytes) and launches nothing.
  * solve_batched_run (re)launches the planned work on `stream`: a queue reset
@@ -240,11 +243,12 @@ int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, con
 int hpl_batch_sizes(uint64_t seed, int64_t count, int64_t* n_out);
 size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind);
 int solve_batched_plan(int64_t count, const int64_t* n, double* const* A, const int64_t* lda, double* const* B,
-                       int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts, void* ws, size_t ws_bytes);
+                       int32_t* const* ipiv, const uint8_t* kind, const uint8_t* variant, const hpl_opts* opts,
+                       void* ws, size_t ws_bytes);
 int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* stream);
 int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64_t* lda, double* const* B,
-                  int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts, void* ws, size_t ws_bytes,
-                  hpl_info* infos, void* stream);
+                  int32_t* const* ipiv, const uint8_t* kind, const uint8_t* variant, const hpl_opts* opts, void* ws,
+                  size_t ws_bytes, hpl_info* infos, void* stream);
 
 /*
  * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path

@@ -96,7 +96,7 @@ def load():
             "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hpl_batch_sizes": (i32, [u64, i64, vp]),
             "solve_batched_workspace_size": (sz, [i64, vp, vp]),
-            "solve_batched_plan": (i32, [i64, vp, vp, vp, vp, vp, vp, op, vp, sz]),
+            "solve_batched_plan": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, op, vp, sz]),
             "solve_batched_run": (i32, [vp, vp, i32, vp]),
             "mxp_solve": (i32, [i64, i64, vp, i64, u64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hplgb_launch_count": (ctypes.c_longlong, []),
@@ -373,16 +373,23 @@ class Batch:
             generate(seed, 16 + 2 * s, n, n, int(self.kind[s]), out=self.matrix(s), device=self.device)
             generate(seed, 17 + 2 * s, n, 1, GEN_GENERAL, out=self.rhs(s).view(n, 1), device=self.device)
 
-    def plan(self, max_iter: int = 50, tol: float = 16.0):
+    def plan(self, max_iter: int = 50, tol: float = 16.0, variant=None):
+        """Write the work table. variant: per-system tile shape (0: panel 32,
+        1: panel 16); None takes it from the autotuner's table."""
+        import numpy as np
+        from . import autotune
         lib = load()
         need = lib.solve_batched_workspace_size(self.count, self.n.ctypes.data, self.kind.ctypes.data)
         if self.ws is None or self.ws.numel() < need:
             self.ws = workspace(need, self.device)
+        if variant is None:
+            variant = autotune.variants(self.n, self.kind)
+        self.variant = np.ascontiguousarray(np.broadcast_to(variant, (self.count,)), dtype=np.uint8)
         opts = make_opts(max_iter=max_iter, tol=tol)
         torch.cuda.synchronize(self.device)
         _check(lib.solve_batched_plan(self.count, self.n.ctypes.data, self.pA, self.lda.ctypes.data, self.pB,
-                                      self.pP, self.kind.ctypes.data, ctypes.byref(opts), _ptr(self.ws),
-                                      self.ws.numel()), "solve_batched_plan")
+                                      self.pP, self.kind.ctypes.data, self.variant.ctypes.data, ctypes.byref(opts),
+                                      _ptr(self.ws), self.ws.numel()), "solve_batched_plan")
 
     def run(self, max_ctas: int = 0):
         _check(load().solve_batched_run(_ptr(self.ws), _ptr(self.infos), max_ctas, _stream(self.device)),

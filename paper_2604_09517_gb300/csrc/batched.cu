@@ -31,10 +31,10 @@
 namespace hplgb {
 namespace bt {
 
-constexpr int NB = 32;             // panel width
+constexpr int NBMAX = 32;          // widest panel (storage); variants use 32 or 16
 constexpr int NMAX = 512;          // largest system handled
 constexpr int THREADS = 256;
-constexpr int PS = NB + 1;         // SMEM panel row stride (doubles)
+constexpr int PS = NBMAX + 1;      // SMEM panel row stride (doubles)
 
 struct Sys {
     long long n, lda;
@@ -42,11 +42,13 @@ struct Sys {
     double* b;        // right-hand side in, solution out
     int32_t* ipiv;    // kind 0
     float* W;         // kind 1: FP32 block factor (n x n, ld n)
-    float* Dinv;      // kind 1: D_k^-1 (n x NB, ld n)
+    float* Dinv;      // kind 1: D_k^-1 (n x NBMAX, ld n)
     double* r;        // kind 1: FP64 residual / correction scratch (2n)
     float* y32;       // kind 1: FP32 scratch (2n)
     int kind;
     int pad;
+    int variant;      // panel width: 0 -> 32, 1 -> 16 (chosen by the autotuner's table)
+    int pad2;
 };
 
 struct Header {
@@ -84,6 +86,7 @@ __device__ __forceinline__ double block_max(double v, double* red) {
 
 // Update C (rows r0.., cols c0..; m x nn) -= L (m x kb, in the SMEM panel at
 // panel row offset prow) * U (kb x nn, global rows k0.., cols c0..).
+template <int NB>
 __device__ void upd64(double* A, long long lda, const double* P, int prow, int m, int nn, int kb, long long r0,
                       long long c0, long long k0, double* Us) {
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -128,6 +131,7 @@ __device__ void upd64(double* A, long long lda, const double* P, int prow, int m
     }
 }
 
+template <int NB>
 __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long* redi, hpl_info* info) {
     const int n = (int)S.n;
     const long long lda = S.lda;
@@ -217,7 +221,7 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
                 }
             }
             __syncthreads();
-            upd64(A, lda, P, kb, m, m, kb, c1, c1, k0, Us);
+            upd64<NB>(A, lda, P, kb, m, m, kb, c1, c1, k0, Us);
         }
     }
     __syncthreads();
@@ -276,6 +280,7 @@ __device__ void gemm32(int m, int nn, int kb, const float* A, long long lda, con
 
 // Block LU without pivoting of W (FP32 copy of A); D^-1 in Dinv. X, R: SMEM
 // NB x NB FP32 scratch.
+template <int NB>
 __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* info) {
     const int n = (int)S.n;
     float* W = S.W;
@@ -337,6 +342,7 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* 
 }
 
 // out = M^-1 v (FP64 in and out), M the block factor, FP32 inside.
+template <int NB>
 __device__ void precond32(const Sys& S, const double* v, double* out) {
     const int n = (int)S.n;
     float* y = S.y32;
@@ -398,15 +404,16 @@ __device__ double resid64(const Sys& S, const double* x, const double* b, double
     return rmax / (0x1p-53 * (amax * xmax + bmax) * (double)n);
 }
 
+template <int NB>
 __device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float* T, double* red, hpl_info* info) {
     const int n = (int)S.n;
-    blocklu32(S, X, R, T, info);
+    blocklu32<NB>(S, X, R, T, info);
     double* bx = S.b;             // b in, x out
     double* r = S.r;
     double* b0 = S.r + n;         // keep b
     for (int i = threadIdx.x; i < n; i += THREADS) b0[i] = bx[i];
     __syncthreads();
-    precond32(S, b0, bx);
+    precond32<NB>(S, b0, bx);
     int it = 0;
     double sr = INFINITY;
     int status = HPL_ERR_NOT_CONVERGED;
@@ -415,7 +422,7 @@ __device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float
         if (!(sr == sr) || sr == INFINITY) { status = HPL_ERR_NONFINITE; break; }
         if (sr < H->tol) { status = HPL_OK; break; }
         if (it >= H->max_iter) break;
-        precond32(S, r, r);
+        precond32<NB>(S, r, r);
         for (int i = threadIdx.x; i < n; i += THREADS) bx[i] += r[i];
         __syncthreads();
         it++;
@@ -428,12 +435,12 @@ __device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float
     }
 }
 
-constexpr size_t SMEM = sizeof(double) * (NMAX * PS + NB * 65) + sizeof(float) * 3 * NB * NB;
+constexpr size_t SMEM = sizeof(double) * (NMAX * PS + NBMAX * 65) + sizeof(float) * 3 * NBMAX * NBMAX;
 
 }  // namespace bt
 
 // Workspace: header, system table, then per dominant system W (n x n FP32),
-// Dinv (n x NB FP32), r (2n FP64), y32 (2n FP32).
+// Dinv (n x NBMAX FP32), r (2n FP64), y32 (2n FP32).
 static size_t batched_ws_layout(int64_t count, const int64_t* n, const uint8_t* kind, std::vector<size_t>* offs) {
     size_t off = align_up(sizeof(bt::Header), 256);
     off = align_up(off + sizeof(bt::Sys) * (size_t)count, 256);
@@ -443,7 +450,7 @@ static size_t batched_ws_layout(int64_t count, const int64_t* n, const uint8_t* 
         if (offs) (*offs)[s] = off;
         int64_t m = n[s];
         off = align_up(off + sizeof(float) * m * m, 256);
-        off = align_up(off + sizeof(float) * m * bt::NB, 256);
+        off = align_up(off + sizeof(float) * m * bt::NBMAX, 256);
         off = align_up(off + sizeof(double) * 2 * m, 256);
         off = align_up(off + sizeof(float) * 2 * m, 256);
     }
@@ -460,17 +467,18 @@ extern "C" size_t solve_batched_workspace_size(int64_t count, const int64_t* n, 
 }
 
 extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const* A, const int64_t* lda,
-                                  double* const* B, int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts,
-                                  void* ws, size_t ws_bytes) {
+                                  double* const* B, int32_t* const* ipiv, const uint8_t* kind, const uint8_t* variant,
+                                  const hpl_opts* opts, void* ws, size_t ws_bytes) {
     if (count <= 0 || count > 0x7fffffff || !n || !A || !lda || !B || !kind || !ws) return HPL_ERR_INVALID;
     for (int64_t s = 0; s < count; s++) {
         if (n[s] < 1 || n[s] > bt::NMAX || lda[s] < n[s] || !A[s] || !B[s] || kind[s] > 1) return HPL_ERR_INVALID;
         if (kind[s] == 0 && (!ipiv || !ipiv[s])) return HPL_ERR_INVALID;
+        if (variant && variant[s] > 1) return HPL_ERR_INVALID;
     }
     std::vector<size_t> offs;
     size_t need = batched_ws_layout(count, n, kind, &offs);
     if (ws_bytes < need) return HPL_ERR_NOMEM;
-    Opts o = resolve_opts(opts, bt::NB);
+    Opts o = resolve_opts(opts, bt::NBMAX);
     // longest first: FP64 work costs ~64x FP32 work on this part
     std::vector<double> cost((size_t)count);
     for (int64_t s = 0; s < count; s++) {
@@ -493,13 +501,14 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
         S.ipiv = kind[s] == 0 ? ipiv[s] : nullptr;
         S.kind = kind[s];
         S.pad = (int)s;                     // original index: infos are written in the caller's order
+        S.variant = variant ? variant[s] : 0;
         if (kind[s] == 1) {
             int64_t m = n[s];
             size_t off = offs[s];
             S.W = (float*)(base + off);
             off = align_up(off + sizeof(float) * m * m, 256);
             S.Dinv = (float*)(base + off);
-            off = align_up(off + sizeof(float) * m * bt::NB, 256);
+            off = align_up(off + sizeof(float) * m * bt::NBMAX, 256);
             S.r = (double*)(base + off);
             off = align_up(off + sizeof(double) * 2 * m, 256);
             S.y32 = (float*)(base + off);
@@ -547,9 +556,9 @@ extern "C" int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* 
 }
 
 extern "C" int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64_t* lda,
-                             double* const* B, int32_t* const* ipiv, const uint8_t* kind, const hpl_opts* opts,
-                             void* ws, size_t ws_bytes, hpl_info* infos, void* stream) {
-    int st = solve_batched_plan(count, n, A, lda, B, ipiv, kind, opts, ws, ws_bytes);
+                             double* const* B, int32_t* const* ipiv, const uint8_t* kind, const uint8_t* variant,
+                             const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* infos, void* stream) {
+    int st = solve_batched_plan(count, n, A, lda, B, ipiv, kind, variant, opts, ws, ws_bytes);
     if (st) return st;
     return solve_batched_run(ws, infos, 0, stream);
 }
@@ -564,9 +573,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
     __shared__ int s_idx;
     double* P = bsm;
     double* Us = bsm + NMAX * PS;
-    float* X = (float*)(Us + NB * 65);
-    float* R = X + NB * NB;
-    float* T = R + NB * NB;
+    float* X = (float*)(Us + NBMAX * 65);
+    float* R = X + NBMAX * NBMAX;
+    float* T = R + NBMAX * NBMAX;
     for (;;) {
         if (threadIdx.x == 0) s_idx = (int)atomicAdd(&H->counter, 1u);
         __syncthreads();
@@ -583,8 +592,13 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
             info->inner_iters = 0;
         }
         __syncthreads();
-        if (S.kind == 0) lu64(S, P, Us, red, redi, info);
-        else mxp_one(S, H, X, R, T, red, info);
+        if (S.kind == 0) {
+            if (S.variant) lu64<16>(S, P, Us, red, redi, info);
+            else lu64<32>(S, P, Us, red, redi, info);
+        } else {
+            if (S.variant) mxp_one<16>(S, H, X, R, T, red, info);
+            else mxp_one<32>(S, H, X, R, T, red, info);
+        }
         __syncthreads();
     }
 }

@@ -74,3 +74,14 @@ def test_batch_sizes_host_function_matches_oracle(lib, orc):
     lib.hpl_batch_sizes.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_void_p]
     assert lib.hpl_batch_sizes(1, 4096, out.ctypes.data) == 0
     assert np.array_equal(out, orc.batch_sizes(1, 4096))
+
+
+def test_autotune_table_lookup():
+    """The batched tile-shape table maps (kind, size bucket) to a variant."""
+    import numpy as np
+    from paper_2604_09517_gb300 import autotune
+    assert list(autotune.bucket_of([32, 63, 64, 127, 128, 255, 256, 512])) == [0, 0, 1, 1, 2, 2, 3, 3]
+    table = {"GPU-X": {"choice": {"0": [1, 0, 0, 0], "1": [0, 1, 1, 0]}}}
+    got = autotune.variants([40, 100, 300, 40, 200], [0, 0, 0, 1, 1], table, "GPU-X")
+    assert list(got) == [1, 0, 0, 0, 1]
+    assert list(autotune.variants([40, 300], [0, 1], {}, "GPU-X")) == [0, 0]

@@ -37,7 +37,8 @@ def _check_system(orc, bt, s, A0, b0, emulate=True):
     else:
         assert np.abs(x - x64).max() / np.abs(x64).max() <= 2 * 16 * n * EPS * kappa
         if emulate:
-            emu = orc.mxp_solve(A0, b0, 32, prec=orc.PREC_BF16, refine=0)
+            nbv = 16 if bt.variant[s] else 32
+            emu = orc.mxp_solve(A0, b0, nbv, prec=orc.PREC_BF16, refine=0)
             assert abs(rec["iters"] - emu["iters"]) <= 2, (s, rec, emu["iters"])
 
 
@@ -47,6 +48,19 @@ def test_batched_small_mixed(hpl, orc):
     A0 = [_np(bt.matrix(s)).copy(order="F") for s in range(bt.count)]
     b0 = [_np(bt.rhs(s)).copy() for s in range(bt.count)]
     bt.plan()
+    bt.run()
+    torch.cuda.synchronize()
+    for s in range(bt.count):
+        _check_system(orc, bt, s, A0[s], b0[s])
+
+
+@pytest.mark.parametrize("variant", [0, 1])
+def test_batched_both_tile_variants(hpl, orc, variant):
+    import torch
+    bt = _make(hpl, 6, 24)
+    A0 = [_np(bt.matrix(s)).copy(order="F") for s in range(bt.count)]
+    b0 = [_np(bt.rhs(s)).copy() for s in range(bt.count)]
+    bt.plan(variant=variant)
     bt.run()
     torch.cuda.synchronize()
     for s in range(bt.count):
