@@ -239,7 +239,7 @@ def round_e4m3(x: float) -> float:
     return float(_load().orc_round_e4m3(float(x)))
 
 
-NS_ITERS = 3
+NS_ITERS = 2
 
 
 def mxp_factor(A, nb: int, prec: int = PREC_BF16, ns_iters: int = NS_ITERS):

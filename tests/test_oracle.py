@@ -317,7 +317,10 @@ def test_mxp_factor_fp32_mode_is_block_lu(orc):
     interchange on a diagonally dominant matrix)."""
     n, nb = 96, 32
     A = orc.generate(4, orc.STREAM_A, n, n, dominant=True)
-    F, Dinv, info = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    # at n = 96 the matrix is only weakly dominant (diagonal ~24 against
+    # off-diagonal block row sums ~8): a third Newton-Schulz step brings the
+    # inverse to FP32 accuracy
+    F, Dinv, info = orc.mxp_factor(A, nb, orc.PREC_FP32, ns_iters=3)
     assert info == 0
     L, U = orc.block_lu_parts(F, nb)
     assert np.abs(A - L @ U).max() / np.abs(A).max() < 1e-6
@@ -390,7 +393,8 @@ def test_mxp_preconditioner_is_block_lu_inverse(orc):
     n, nb = 128, 32
     A = orc.generate(15, orc.STREAM_A, n, n, dominant=True)
     b = orc.generate(15, orc.STREAM_B, n, 1)[:, 0].astype(np.float32).astype(np.float64)
-    F, Dinv, _ = orc.mxp_factor(A, nb, orc.PREC_FP32)
+    # weakly dominant at n = 128: three Newton-Schulz steps for an FP32-accurate D^-1
+    F, Dinv, _ = orc.mxp_factor(A, nb, orc.PREC_FP32, ns_iters=3)
     out = orc.mxp_refine(A, F, Dinv, nb, b, refine=0, max_iter=0)
     L, U = orc.block_lu_parts(F, nb)
     x_ref = np.linalg.solve(L @ U, b)
