@@ -62,6 +62,7 @@ def parse():
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--mxp-n", type=int, default=98304)
     ap.add_argument("--mxp-nb", type=int, default=3072)
+    ap.add_argument("--mxp-fp8-nb", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -231,9 +232,12 @@ def run_batched(a, d: Dist, dev):
     import paper_2604_09517_gb300 as hpl
 
     count = a.batched_count
-    n = hpl.batch_sizes(a.seed, count)
-    kind = np.array([0 if s < count // 2 else 1 for s in range(count)], dtype=np.uint8)
-    bt = hpl.Batch(n, kind, device=dev)
+    n_all = hpl.batch_sizes(a.seed, count)
+    kind_all = np.array([0 if s < count // 2 else 1 for s in range(count)], dtype=np.uint8)
+    # several GPUs: each rank solves its share of the systems, no exchange
+    ids = np.nonzero(hpl.batch_shard(n_all, kind_all, d.world) == d.rank)[0] if d.world > 1 else np.arange(count)
+    n, kind = n_all[ids], kind_all[ids]
+    bt = hpl.Batch(n, kind, device=dev, ids=ids)
     bt.generate(a.seed)
     bt.plan()
     bt.run()
@@ -263,16 +267,18 @@ def run_batched(a, d: Dist, dev):
         d.barrier()
         step_ms.append(e0.elapsed_time(e1))
     recs = bt.info()
-    ok = sum(1 for r in recs if r["status"] == 0)
-    work = float(sum(flops(int(m)) for m in n))
+    ok = int(d.sum(float(sum(1 for r in recs if r["status"] == 0))))
+    work = float(sum(flops(int(m)) for m in n_all))
     total_ms = d.max(sum(step_ms))
-    value = d.sum(work * len(step_ms)) / (total_ms * 1e-3) / 1e12
-    fp64_work = float(sum(flops(int(m)) for m, k in zip(n, kind) if k == 0))
+    value = work * len(step_ms) / (total_ms * 1e-3) / 1e12
+    fp64_work = float(sum(flops(int(m)) for m, k in zip(n_all, kind_all) if k == 0))
+    dom = [r["iters"] for r, k in zip(recs, kind) if k == 1]
     return {"workload": f"batched_{count}_n32to512_half_fp64_half_bf16ir", "systems": count, "value": value,
             "unit": "TFLOP/s", "ms_per_step": total_ms / len(step_ms), "solved_ok": ok,
             "flops_per_step": work, "fp64_share_of_flops": fp64_work / work, "cuda_graph": True,
-            "gpu_launches_per_step": 1,
-            "max_refine_iters": max(r["iters"] for r in recs[count // 2:])}
+            "gpu_launches_per_step": 1, "scaling": "strong" if d.world > 1 else None,
+            "systems_per_rank": int(len(ids)),
+            "max_refine_iters": int(d.max(float(max(dom) if dom else 0)))}
 
 
 def run_adjoint(a, d: Dist, dev):
@@ -310,22 +316,66 @@ def run_adjoint(a, d: Dist, dev):
             "grad_a_outer_product_gflop": 2.0 * n * n * nrhs / 1e9}
 
 
-def run_mxp(a, d: Dist, dev, fp64_value, prec=0):
-    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
-    block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
-    prec = 1) + FP64 GMRES refinement."""
+def run_small(a, d: Dist, dev):
+    """The small HPL case: n = 1024, NB = 64, no look-ahead (16 panel steps,
+    latency-bound). The 8 MB matrix fits in L2, so L2 is flushed (a 256 MB
+    write) before each timed solve; the oracle's time for the same system is
+    reported beside it."""
     import torch
 
     import paper_2604_09517_gb300 as hpl
 
-    n, nb, seed = a.mxp_n, a.mxp_nb, a.seed
-    A = hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
+    n, nb, seed, reps = 1024, 64, a.seed, 20
+    A = hpl.colmajor(n, n, device=dev)
+    b = torch.empty(n, dtype=torch.float64, device=dev)
+    ipiv = torch.empty(n, dtype=torch.int32, device=dev)
+    info = hpl.Info(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    times = []
+    for it in range(a.warmup + reps):
+        hpl.generate(seed, hpl.STREAM_A, n, n, out=A)
+        hpl.generate(seed, hpl.STREAM_B, n, 1, out=b.view(n, 1))
+        flush.fill_(it & 0xff)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        hpl.lu_factor(A, nb=nb, lookahead=0, ipiv=ipiv, info=info)
+        hpl.lu_solve(A, ipiv, b)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        if it >= a.warmup:
+            times.append(e0.elapsed_time(e1))
+    ms = sum(times) / len(times)
+    out = {"workload": "hpl_fp64_lu_n1024_nb64_no_lookahead", "ms_per_solve": ms, "median_ms": statistics.median(times),
+           "value": flops(n) / (ms * 1e-3) / 1e12, "unit": "TFLOP/s", "solves": reps,
+           "status": info.read()["status_name"], "l2": "flushed (256 MB write) before each timed solve"}
+    if d.rank == 0 and not a.no_cpu:
+        dt, cores, _ = time_oracle(n, seed)
+        out["cpu_oracle_ms"] = dt * 1e3
+        out["cpu_oracle_cores"] = cores
+    del A, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False):
+    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
+    block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
+    prec = 1) + FP64 GMRES refinement. regen: the library regenerates A from
+    the seed instead of reading a stored FP64 copy."""
+    import torch
+
+    import paper_2604_09517_gb300 as hpl
+
+    n, nb, seed = a.mxp_n, (a.mxp_fp8_nb if prec else a.mxp_nb), a.seed
+    A = None if regen else hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
     b = hpl.generate(seed, hpl.STREAM_B, n, 1, device=dev)[:, 0].contiguous()
     X = hpl.colmajor(n, 1, device=dev)
     info = hpl.Info(dev)
     ws = None
     for _ in range(a.warmup):
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
     hpl.set_phase_timing(True)
@@ -337,7 +387,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0):
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = hpl.launch_count()
         e0.record(stream)
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed)
         e1.record(stream)
         launches += hpl.launch_count() - l0
         torch.cuda.synchronize(dev)
@@ -356,14 +406,15 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0):
     del A, X, ws
     torch.cuda.empty_cache()
     tag = "fp8e4m3" if prec else "bf16"
-    return {"workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres", "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
+    return {"workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
             "ms_per_step": total_ms / len(step_ms), "steps": a.steps, "warmup": a.warmup,
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
             "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,
             "fp64_lu_time_at_this_n_s": flops(n) / (fp64_value * 1e12) if fp64_value else None,
             f"fraction_of_{tag}_peak": value / peak, "gpu_launches": int(launches),
-            "matrix": "uniform[-0.5,0.5) FP64, diagonal = row sum of |a_ij| (diagonally dominant)",
+            "matrix": "uniform[-0.5,0.5) FP64, diagonal = row sum of |a_ij| (diagonally dominant)"
+                      + ("; regenerated from the seed, never stored" if regen else "; stored FP64"),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None, "traffic": None,
                          "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
@@ -443,6 +494,16 @@ def run_ours(a, d: Dist):
     peak = NUM_SMS * FP64_FLOP_PER_CLK_PER_SM * MAX_SM_MHZ * 1e6 / 1e12
     phase_report = {k: {"ms_per_step": v[0] / max(len(step_ms), 1), "launch_intervals": v[2]}
                     for k, v in phases.items() if v[2]}
+    # achieved rates of the phases: SWAP in HBM GB/s (its timer's work is the
+    # bytes the interchanges move), PFACT in GFLOP/s and in HBM GB/s with one
+    # read and one write of each panel as its algorithmic traffic
+    panel_bytes = sum(2.0 * 8.0 * (n - k0) * min(nb, n - k0) for k0 in range(0, n, nb)) * len(step_ms)
+    for k, unit in (("swap", "GB/s"), ("pfact", "GFLOP/s"), ("trsm", "GFLOP/s"), ("update", "GFLOP/s")):
+        if k in phase_report and phases[k][0] > 0:
+            phase_report[k]["rate"] = phases[k][1] / (phases[k][0] * 1e-3) / 1e9
+            phase_report[k]["rate_unit"] = unit
+    if "pfact" in phase_report and phases["pfact"][0] > 0:
+        phase_report["pfact"]["hbm_gbs"] = panel_bytes / (phases["pfact"][0] * 1e-3) / 1e9
 
     # end to end through the public API with host buffers
     e2e = None
@@ -483,8 +544,10 @@ def run_ours(a, d: Dist):
 
     del A, b, b0, ipiv, ws, sws
     torch.cuda.empty_cache()
+    small = run_small(a, d, dev)
     mxp = None if a.no_mxp else run_mxp(a, d, dev, value)
     mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1)
+    mxp_regen = None if a.no_mxp else run_mxp(a, d, dev, value, regen=True)
     batched = None if a.no_batched else run_batched(a, d, dev)
     adjoint = None if a.no_adjoint else run_adjoint(a, d, dev)
 
@@ -500,7 +563,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report,
-                "fraction_of_fp64_peak": value / peak, "mxp": mxp, "mxp_fp8": mxp_fp8, "batched": batched, "adjoint": adjoint}
+                "fraction_of_fp64_peak": value / peak, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_regenerated": mxp_regen, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 

@@ -67,7 +67,7 @@ typedef struct {
     int32_t refine;      /* HPL_REFINE_* (default GMRES) */
     int32_t max_iter;    /* outer refinement iterations (default 50) */
     int32_t gmres_m;     /* Arnoldi steps per GMRES cycle (default 30) */
-    int32_t reserved;
+    int32_t ns_iters;    /* Newton-Schulz steps of each diagonal-block inverse, mixed precision (default 2, <= 8) */
     double tol;          /* scaled-residual target (default 16) */
     int64_t timeout_ns;  /* limit for any device-side wait (default 20 s) */
 } hpl_opts;
@@ -193,8 +193,12 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * align256(4 n^2). opts->prec = HPL_PREC_FP8_E4M3 runs the trailing update
  * with FP8 E4M3 operands instead (one power-of-two scale per row of L21 and
  * per column of A12 over the panel width, applied in the GEMM epilogue; the
- * panel product L21 = A21 D^-1 keeps BF16). A == NULL returns
- * HPL_ERR_INVALID; seed is reserved.
+ * panel product L21 = A21 D^-1 keeps BF16).
+ * A == NULL (lda ignored) solves with the HPL-MxP matrix of `seed` (stream 0,
+ * HPL_GEN_DIAG_DOMINANT, as hpl_generate defines it) without storing it: the
+ * FP32 working copy is generated directly and every FP64 residual regenerates
+ * the entries (the diagonal is kept in ws), so the 8 n^2 bytes of an FP64 A
+ * are never needed. seed is ignored when A != NULL.
  */
 size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts);
 int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B, int64_t ldb,
@@ -241,6 +245,16 @@ int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, con
  * n_s = 32 + (draw s of generator stream 2 mod 481), into a host array.
  */
 int hpl_batch_sizes(uint64_t seed, int64_t count, int64_t* n_out);
+/*
+ * hpl_batch_shard — host only, no GPU needed: splits the systems of a batch
+ * over `world` ranks, one GPU each (the systems are independent, so no data
+ * is exchanged between ranks). Longest estimated time first, each system to
+ * the rank with the least estimated work so far, lowest rank on ties;
+ * deterministic, so every rank computes the same split. n, kind: host arrays
+ * of count entries; owner: host array of count int32 receiving each system's
+ * rank. HPL_ERR_INVALID for count < 0, world < 1, n < 1 or kind > 1.
+ */
+int hpl_batch_shard(int64_t count, const int64_t* n, const uint8_t* kind, int32_t world, int32_t* owner);
 size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind);
 int solve_batched_plan(int64_t count, const int64_t* n, double* const* A, const int64_t* lda, double* const* B,
                        int32_t* const* ipiv, const uint8_t* kind, const uint8_t* variant, const hpl_opts* opts,

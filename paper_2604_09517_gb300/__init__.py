@@ -53,7 +53,7 @@ class HplError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int64), ("lookahead", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64)]
+                ("ns_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64)]
 
 
 def library_path() -> str:
@@ -95,6 +95,7 @@ def load():
             "mxp_workspace_size": (sz, [i64, i64, op]),
             "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hpl_batch_sizes": (i32, [u64, i64, vp]),
+            "hpl_batch_shard": (i32, [i64, vp, vp, i32, vp]),
             "solve_batched_workspace_size": (sz, [i64, vp, vp]),
             "solve_batched_plan": (i32, [i64, vp, vp, vp, vp, vp, vp, vp, op, vp, sz]),
             "solve_batched_run": (i32, [vp, vp, i32, vp]),
@@ -227,34 +228,38 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
     return out
 
 
-def mxp_solve(A: torch.Tensor, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
+def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-              info: Info | None = None, prec: int = PREC_BF16):
+              info: Info | None = None, prec: int = PREC_BF16, seed: int = 0):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
 
-    Returns (X, info, ws); ws holds the block factor afterwards (see mxp_factor_views).
+    A = None solves with the dominant generated matrix of `seed` without storing
+    it (the library regenerates its entries). Returns (X, info, ws); ws holds
+    the block factor afterwards (see mxp_factor_views).
     """
     lib = load()
-    n = A.shape[0]
+    n = B.shape[0]
+    dev = B.device
     vec = B.dim() == 1
     Bm = B.reshape(n, 1) if vec else B
     if Bm.stride(0) != 1:
-        Bc = colmajor(n, Bm.shape[1], device=A.device)
+        Bc = colmajor(n, Bm.shape[1], device=dev)
         Bc.copy_(Bm)
         Bm = Bc
     nrhs = Bm.shape[1]
     opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec)
     if X is None:
-        X = colmajor(n, nrhs, device=A.device)
+        X = colmajor(n, nrhs, device=dev)
     Xm = X.view(n, 1) if X.dim() == 1 else X
     need = lib.mxp_workspace_size(n, nrhs, ctypes.byref(opts))
     if ws is None or ws.numel() < need:
-        ws = workspace(need, A.device)
+        ws = workspace(need, dev)
     if info is None:
-        info = Info(A.device)
-    _check(lib.mxp_solve(n, nrhs, _ptr(A), _ld(A), 0, _ptr(Bm), _ld(Bm) if nrhs > 1 else n, _ptr(Xm),
+        info = Info(dev)
+    a_ptr, a_ld = (None, n) if A is None else (_ptr(A), _ld(A))
+    _check(lib.mxp_solve(n, nrhs, a_ptr, a_ld, seed, _ptr(Bm), _ld(Bm) if nrhs > 1 else n, _ptr(Xm),
                          _ld(Xm) if nrhs > 1 else n, ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(),
-                         _stream(A.device)), "mxp_solve")
+                         _stream(dev)), "mxp_solve")
     return X, info, ws
 
 
@@ -326,20 +331,35 @@ def batch_sizes(seed: int, count: int):
     return out
 
 
+def batch_shard(n, kind, world: int):
+    """Rank (0..world-1) that solves each system when a batch is split over
+    world GPUs (host only; every rank computes the same split)."""
+    import numpy as np
+    n = np.ascontiguousarray(n, dtype=np.int64)
+    kind = np.ascontiguousarray(kind, dtype=np.uint8)
+    owner = np.empty(n.shape[0], dtype=np.int32)
+    _check(load().hpl_batch_shard(n.shape[0], n.ctypes.data, kind.ctypes.data, world, owner.ctypes.data),
+           "hpl_batch_shard")
+    return owner
+
+
 class Batch:
     """Device buffers and the plan of a batched solve.
 
     System s has size n[s] and kind[s] (0: general, pivoted FP64; 1: diagonally
     dominant, BF16 factor + FP64 refinement); its matrix (column-major, ld n[s])
     and right-hand side live in two flat FP64 buffers at offsets a_off[s] and
-    b_off[s]; generate() fills them from generator streams 16+2s and 17+2s.
+    b_off[s]; generate() fills them from generator streams 16+2g and 17+2g,
+    g = ids[s] the system's index in the whole batch (default s; a rank that
+    solves a share of a batch passes the ids of its systems).
     """
 
-    def __init__(self, n, kind, device="cuda"):
+    def __init__(self, n, kind, device="cuda", ids=None):
         import numpy as np
         self.n = np.ascontiguousarray(n, dtype=np.int64)
         self.kind = np.ascontiguousarray(kind, dtype=np.uint8)
         self.count = len(self.n)
+        self.ids = np.arange(self.count, dtype=np.int64) if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
         self.device = device
         sq = self.n * self.n
         self.a_off = np.concatenate([[0], np.cumsum(sq)[:-1]]).astype(np.int64)
@@ -369,9 +389,9 @@ class Batch:
 
     def generate(self, seed: int):
         for s in range(self.count):
-            n = int(self.n[s])
-            generate(seed, 16 + 2 * s, n, n, int(self.kind[s]), out=self.matrix(s), device=self.device)
-            generate(seed, 17 + 2 * s, n, 1, GEN_GENERAL, out=self.rhs(s).view(n, 1), device=self.device)
+            n, g = int(self.n[s]), int(self.ids[s])
+            generate(seed, 16 + 2 * g, n, n, int(self.kind[s]), out=self.matrix(s), device=self.device)
+            generate(seed, 17 + 2 * g, n, 1, GEN_GENERAL, out=self.rhs(s).view(n, 1), device=self.device)
 
     def plan(self, max_iter: int = 50, tol: float = 16.0, variant=None):
         """Write the work table. variant: per-system tile shape (0: panel 32,

@@ -47,6 +47,7 @@ extern "C" void hpl_default_opts(hpl_opts* o) {
     o->refine = HPL_REFINE_GMRES;
     o->max_iter = 50;
     o->gmres_m = 30;
+    o->ns_iters = 2;
     o->tol = 16.0;
     o->timeout_ns = hplgb::kDefaultTimeoutNs;
 }
@@ -64,6 +65,7 @@ Opts resolve_opts(const hpl_opts* o, int64_t default_nb) {
     r.refine = o->refine;
     r.max_iter = o->max_iter > 0 ? o->max_iter : d.max_iter;
     r.gmres_m = o->gmres_m > 0 ? o->gmres_m : d.gmres_m;
+    r.ns_iters = o->ns_iters > 0 ? o->ns_iters : d.ns_iters;
     r.tol = o->tol > 0 ? o->tol : d.tol;
     r.timeout_ns = o->timeout_ns > 0 ? o->timeout_ns : d.timeout_ns;
     return r;

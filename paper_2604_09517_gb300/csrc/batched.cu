@@ -301,7 +301,7 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* 
             for (int i = 0; i < kb; i++)
                 if (D[(long long)i * n + i] == 0.0f && !first_zero) first_zero = k0 + i + 1;
         __syncthreads();
-        for (int it = 0; it < 3; it++) {
+        for (int it = 0; it < 3; it++) {     // 3 steps: systems this small are only weakly dominant
             gemm32(kb, kb, kb, D, n, X, NB, R, NB, 0, 1);               // R = D X
             __syncthreads();
             for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
@@ -461,6 +461,37 @@ static size_t batched_ws_layout(int64_t count, const int64_t* n, const uint8_t* 
 
 using namespace hplgb;
 
+// Estimated time of one system: FP64 work costs ~64x FP32 work on this part;
+// a dominant system adds a few FP64 refinement passes over its matrix.
+static double system_cost(int64_t n, uint8_t kind) {
+    const double m = (double)n;
+    return kind == 0 ? 64.0 * m * m * m / 3.0 : m * m * m / 3.0 + 3.0 * 64.0 * m * m;
+}
+
+// Split the systems over `world` ranks (one GPU each): longest first, each to
+// the rank with the least estimated work so far (lowest rank on ties). Host
+// only; every rank computes the same split, so no exchange is needed.
+extern "C" int hpl_batch_shard(int64_t count, const int64_t* n, const uint8_t* kind, int32_t world, int32_t* owner) {
+    if (count < 0 || world < 1 || (count > 0 && (!n || !kind || !owner))) return HPL_ERR_INVALID;
+    std::vector<double> cost((size_t)count);
+    for (int64_t s = 0; s < count; s++) {
+        if (n[s] < 1 || kind[s] > 1) return HPL_ERR_INVALID;
+        cost[s] = system_cost(n[s], kind[s]);
+    }
+    std::vector<int64_t> order((size_t)count);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::vector<double> load((size_t)world, 0.0);
+    for (int64_t s : order) {
+        int32_t best = 0;
+        for (int32_t r = 1; r < world; r++)
+            if (load[r] < load[best]) best = r;
+        owner[s] = best;
+        load[best] += cost[s];
+    }
+    return HPL_OK;
+}
+
 extern "C" size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind) {
     if (count <= 0 || !n || !kind) return 256;
     return batched_ws_layout(count, n, kind, nullptr);
@@ -478,13 +509,11 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
     std::vector<size_t> offs;
     size_t need = batched_ws_layout(count, n, kind, &offs);
     if (ws_bytes < need) return HPL_ERR_NOMEM;
+    if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, bt::NBMAX);
-    // longest first: FP64 work costs ~64x FP32 work on this part
+    // longest first
     std::vector<double> cost((size_t)count);
-    for (int64_t s = 0; s < count; s++) {
-        double m = (double)n[s];
-        cost[s] = kind[s] == 0 ? 64.0 * m * m * m / 3.0 : m * m * m / 3.0 + 3.0 * 64.0 * m * m;
-    }
+    for (int64_t s = 0; s < count; s++) cost[s] = system_cost(n[s], kind[s]);
     std::vector<int64_t> order((size_t)count);
     std::iota(order.begin(), order.end(), 0);
     std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });

@@ -37,6 +37,7 @@ struct Opts {
     int refine;
     int max_iter;
     int gmres_m;
+    int ns_iters;
     double tol;
     int64_t timeout_ns;
 };

@@ -7,6 +7,8 @@
 // 53 bits scaled to [0,1) and shifted by -0.5 (exact). The paper says only
 // that the HPL matrix is random (Sec. III-A.1) and that HPL-MxP has a scalable
 // generator (Sec. II-B); this definition is the library's own.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace hplgb {
@@ -74,6 +76,71 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
         }
         A[i * lda + i] = u128_to_double_rn(hi, lo) * 0x1p-53;
     }
+}
+
+// ---------------------------------------------------------------------------
+// The dominant matrix straight into an FP32 working copy, for a
+// mixed-precision solve that keeps no FP64 copy of A (its residuals
+// regenerate the entries). Every entry is the FP64 generated value rounded to
+// nearest FP32, exactly what converting a stored FP64 matrix gives.
+
+// Rows in blocks of 256 (blockIdx.x), columns strided over gridDim.y.
+__global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, float* __restrict__ F, int64_t ldf) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
+        uint64_t h = sm64_mix(key + (uint64_t)(j * n + i + 1) * kGamma);
+        F[j * ldf + i] = __double2float_rn((double)(h >> 11) * 0x1p-53 - 0.5);
+    }
+}
+
+// As k_dominant_diag, with the entries regenerated instead of read:
+// |a_ij| / 2^-53 = |(h >> 11) - 2^52| exactly. Writes the FP64 diagonal to
+// diag and its FP32 rounding onto the diagonal of F.
+__global__ void __launch_bounds__(256) k_dominant_diag_gen(uint64_t key, int64_t n, double* __restrict__ diag,
+                                                           float* __restrict__ F, int64_t ldf) {
+    __shared__ uint64_t s_lo[8][32], s_hi[8][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+    uint64_t lo = 0, hi = 0;
+    if (i < n) {
+        for (int64_t j = warp; j < n; j += 8) {
+            uint64_t m = sm64_mix(key + (uint64_t)(j * n + i + 1) * kGamma) >> 11;
+            uint64_t u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
+            uint64_t nl = lo + u;
+            hi += (nl < lo);
+            lo = nl;
+        }
+    }
+    s_lo[warp][lane] = lo;
+    s_hi[warp][lane] = hi;
+    __syncthreads();
+    if (warp == 0 && i < n) {
+        for (int w = 1; w < 8; w++) {
+            uint64_t nl = lo + s_lo[w][lane];
+            hi += s_hi[w][lane] + (nl < lo);
+            lo = nl;
+        }
+        const double d = u128_to_double_rn(hi, lo) * 0x1p-53;
+        diag[i] = d;
+        F[i * ldf + i] = __double2float_rn(d);
+    }
+}
+
+// Stream 0 (the matrix) of seed, kind HPL_GEN_DIAG_DOMINANT, n x n, as FP32
+// into F (ldf >= n) with the FP64 diagonal into diag (n doubles); returns the
+// stream key the residual kernels regenerate from in *key_out.
+int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
+                                 cudaStream_t s) {
+    const uint64_t key = sm64_host_mix(seed + 1 * kGamma);
+    if (key_out) *key_out = key;
+    if (n <= 0) return HPL_OK;
+    k_generate_f32<<<dim3((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(n, 1024)), 256, 0, s>>>(key, n, F,
+                                                                                                           ldf);
+    HPL_LAUNCH_CHECK();
+    k_dominant_diag_gen<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(key, n, diag, F, ldf);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
 }
 
 }  // namespace hplgb

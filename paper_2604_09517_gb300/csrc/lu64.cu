@@ -577,6 +577,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
     if (o.nb < 1 || o.nb > 512) return HPL_ERR_INVALID;
     size_t need = lu_ws_layout(o.nb, nullptr, nullptr);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
+    if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     if (n == 0) return HPL_OK;

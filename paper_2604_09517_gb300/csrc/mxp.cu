@@ -36,12 +36,14 @@ int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t l
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s);
 size_t residual_ws_bytes(int64_t n);
-int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
-                        double* sr, void* ws, cudaStream_t s);
-int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
-                          double* sr, void* ws, cudaStream_t s);
+int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, const double* diag,
+                        const double* anorm, const double* x, const double* b, double* r, double* sr, void* ws,
+                        cudaStream_t s);
+int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
+                                 cudaStream_t s);
+int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, double* anorm, int norm_mode, const double* x,
+                          const double* b, double* r, double* sr, void* ws, cudaStream_t s);
 
-constexpr int kNsIters = 3;
 constexpr int kDotBlocks = 304;
 constexpr int kGemvSplitMax = 16;
 // Default panel width: with an FP32 trailing matrix each update step moves 8
@@ -216,6 +218,36 @@ __global__ void __launch_bounds__(256) k_quant_cols_e4m3(const float* __restrict
 // ---------------------------------------------------------------------------
 // Small dense kernels.
 // F = fl32(A): CTA x-index = 1024-row chunk, y-index strides over columns.
+// ||A||_inf for the refinement's stopping test, taken once per solve from the
+// FP32 working copy before it is factored (each |a_ij| within 2^-24 of the FP64
+// value): row sums of |F| over column chunks, then the largest row.
+__global__ void __launch_bounds__(256) k_abs_rowsum_part(int64_t n, const float* __restrict__ F, int64_t ldf,
+                                                         int chunks, float* __restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cw = (n + chunks - 1) / chunks;
+    const int64_t j0 = (int64_t)blockIdx.y * cw, j1 = std::min<int64_t>(n, j0 + cw);
+    float s0 = 0.0f, s1 = 0.0f;
+    int64_t j = j0;
+#pragma unroll 4
+    for (; j + 1 < j1; j += 2) {
+        s0 += fabsf(F[j * ldf + i]);
+        s1 += fabsf(F[(j + 1) * ldf + i]);
+    }
+    if (j < j1) s0 += fabsf(F[j * ldf + i]);
+    part[(int64_t)blockIdx.y * n + i] = s0 + s1;
+}
+
+__global__ void __launch_bounds__(256) k_abs_rowsum_max(int64_t n, int chunks, const float* __restrict__ part,
+                                                        unsigned long long* out) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    double v = 0.0;
+    if (i < n)
+        for (int c = 0; c < chunks; c++) v += (double)part[(int64_t)c * n + i];
+    for (int off = 16; off > 0; off >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, off));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
 __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda,
                                                         float* __restrict__ F, int64_t ldf) {
     const int64_t i0 = (int64_t)blockIdx.x * 1024 + threadIdx.x;
@@ -458,6 +490,7 @@ struct MxpWs {
     float* sa;         // n: FP8 row scales of the update's A operand
     float* sb;         // n: FP8 column scales of the update's B operand
     float* gpart;      // kGemvSplitMax x n: column-split GEMV partial sums
+    double* gdiag;     // n: FP64 diagonal of a regenerated matrix (A == NULL)
 };
 
 static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) {
@@ -492,6 +525,7 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) 
     t.sa = (float*)take(sizeof(float) * n);
     t.sb = (float*)take(sizeof(float) * n);
     t.gpart = (float*)take(sizeof(float) * kGemvSplitMax * n);
+    t.gdiag = (double*)take(sizeof(double) * n);
     if (w) *w = t;
     return off;
 }
@@ -504,15 +538,22 @@ struct Mxp {
     Opts o;
     MxpWs w;
     cudaStream_t s;
-    const double* A;
+    const double* A;        // FP64 matrix, or NULL: regenerated from seed
     int64_t lda;
+    uint64_t seed = 0;
+    uint64_t key = 0;       // generator stream key of the regenerated matrix
     bool trans = false;     // solve A^T x = b with the same factor (the adjoint)
+    bool tnorm_ready = false;   // ||A^T||_inf cached in w.scal[7]
 
     // r = b - op(A) x (b != NULL, scaled residual into sr if given) or r = op(A) x
     int resid(const double* x, const double* b, double* r, double* sr) {
         int slot = phase_begin(s);
-        int st = trans ? launch_residual_vec_t(n, A, lda, x, b, r, sr, w.resws, s)
-                       : launch_residual_vec(n, A, lda, x, b, r, sr, w.resws, s);
+        // ||A||_inf (w.scal[6]) comes from the factorization; ||A^T||_inf
+        // (w.scal[7]) from the first transposed residual that needs it
+        int st = trans ? launch_residual_vec_t(n, A, lda, w.scal + 7, sr ? (tnorm_ready ? 2 : 1) : 0, x, b, r, sr,
+                                               w.resws, s)
+                       : launch_residual_vec(n, A, lda, key, w.gdiag, w.scal + 6, x, b, r, sr, w.resws, s);
+        if (trans && sr && b) tnorm_ready = true;
         phase_end(slot, s, PH_RESID, 8.0 * n * n);
         return st;
     }
@@ -546,10 +587,22 @@ struct Mxp {
         const int64_t ldf = n;
         HPL_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, s));
         int cslot = phase_begin(s);
-        k_f64_to_f32_mat<<<dim3((unsigned)((n + 1023) / 1024), (unsigned)std::min<int64_t>(n, 2048)), 256, 0, s>>>(
-            n, A, lda, w.F, ldf);
+        if (A) {
+            k_f64_to_f32_mat<<<dim3((unsigned)((n + 1023) / 1024), (unsigned)std::min<int64_t>(n, 2048)), 256, 0,
+                               s>>>(n, A, lda, w.F, ldf);
+            HPL_LAUNCH_CHECK();
+        } else {
+            int st = launch_generate_dominant_f32(seed, n, w.F, ldf, w.gdiag, &key, s);
+            if (st) return st;
+        }
+        HPL_CUDA_TRY(cudaMemsetAsync(w.scal + 6, 0, sizeof(double), s));
+        k_abs_rowsum_part<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, w.F, ldf,
+                                                                                          kGemvSplitMax, w.gpart);
         HPL_LAUNCH_CHECK();
-        phase_end(cslot, s, PH_CONVERT, 12.0 * n * n);
+        k_abs_rowsum_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, kGemvSplitMax, w.gpart,
+                                                                     (unsigned long long*)(w.scal + 6));
+        HPL_LAUNCH_CHECK();
+        phase_end(cslot, s, PH_CONVERT, A ? 16.0 * n * n : 8.0 * n * n);
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
             float* D = w.F + k0 * ldf + k0;
@@ -561,7 +614,7 @@ struct Mxp {
             int st;
             // split D as the A operand: [hi | hi | lo]
             if ((st = to_bf16_split3(D, ldf, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
-            for (int it = 0; it < kNsIters; it++) {
+            for (int it = 0; it < o.ns_iters; it++) {
                 // R = D X: B operand from X, [hi | lo | hi]
                 if ((st = to_bf16_split3(w.X, kb, kb, 0, 1, 2, 1, 0, w.nsB, kb8, s))) return st;
                 if ((st = launch_gemm_bf16(kb, kb, K3, w.nsD, K3, w.nsB, K3, w.R, kb, 0, w.err, o.timeout_ns, 0, s)))
@@ -583,7 +636,7 @@ struct Mxp {
                 if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
                 if ((st = launch_gemm_bf16(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0, w.err, o.timeout_ns, 0, s)))
                     return st;
-                phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
+                phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
                 // A22 -= L21 A12
                 slot = phase_begin(s);
                 if (o.prec == HPL_PREC_FP8_E4M3) {
@@ -606,7 +659,7 @@ struct Mxp {
                 }
                 phase_end(slot, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
             } else {
-                phase_end(slot, s, PH_PANEL, 2.0 * kNsIters * 2.0 * 3.0 * kb * kb * kb);
+                phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb);
             }
         }
         return HPL_OK;
@@ -813,13 +866,13 @@ extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* op
 extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
                          int64_t ldb, double* X, int64_t ldx, const hpl_opts* opts, void* ws, size_t ws_bytes,
                          hpl_info* info, void* stream) {
-    (void)seed;
-    if (n <= 0 || nrhs < 0 || !A || lda < n || !info) return HPL_ERR_INVALID;
+    if (n <= 0 || nrhs < 0 || (A && lda < n) || !info) return HPL_ERR_INVALID;
     if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, kMxpDefaultNb);
     if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
     if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
+    if (o.ns_iters > 8) return HPL_ERR_INVALID;
     Mxp mx;
     mx.n = n;
     mx.nb = std::min<int64_t>(o.nb, n);
@@ -828,8 +881,10 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     mx.s = (cudaStream_t)stream;
     mx.A = A;
     mx.lda = lda;
+    mx.seed = seed;
     size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
+    if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
     mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
@@ -885,6 +940,7 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     mx.trans = true;
     size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
     if (ws_bytes < need) return HPL_ERR_NOMEM;
+    if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
     mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));

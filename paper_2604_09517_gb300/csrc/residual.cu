@@ -76,9 +76,12 @@ __device__ __forceinline__ float abs_as_float(double a) {
 // want_norm: 0 skips the row sums of |a_ij| (plain matrix-vector product),
 // 1 sums them in FP32 from abs_as_float (the refinement's stopping test),
 // 2 sums them in FP64 (the HPL acceptance check).
+// A == NULL regenerates the entries from key (hpl_generate's definition); for
+// the dominant matrix the diagonal is skipped here and added per row later,
+// either from the exact row sums accumulated here (diag == NULL) or from diag.
 __global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __restrict__ A, int64_t lda,
-                                                     uint64_t key, int dominant, const double* __restrict__ x,
-                                                     ResWs w, int want_norm) {
+                                                     uint64_t key, int dominant, const double* __restrict__ diag,
+                                                     const double* __restrict__ x, ResWs w, int want_norm) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     const int chunk = blockIdx.y;
     const int64_t cw = (n + kResChunks - 1) / kResChunks;
@@ -123,6 +126,18 @@ __global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __
             }
             r += r1;
         }
+    } else if (dominant && diag) {
+        // diagonal known: plain regenerated product over the off-diagonal entries
+        float sf = 0.0f;
+        for (int64_t j = j0; j < j1; j++) {
+            if (j == i) continue;
+            uint64_t h = res_mix(key + (uint64_t)(j * n + i + 1) * 0x9E3779B97F4A7C15ull);
+            double a = (double)(h >> 11) * 0x1p-53 - 0.5;
+            r = fma(a, x[j], r);
+            if (want_norm == 2) s += fabs(a);
+            else if (want_norm == 1) sf += abs_as_float(a);
+        }
+        if (want_norm == 1) s = (double)sf;
     } else {
         for (int64_t j = j0; j < j1; j++) {
             uint64_t h = res_mix(key + (uint64_t)(j * n + i + 1) * 0x9E3779B97F4A7C15ull);
@@ -148,7 +163,11 @@ __device__ __forceinline__ void atomic_max_nonneg(unsigned long long* p, double 
     atomicMax(p, (unsigned long long)__double_as_longlong(v));
 }
 
-__global__ void __launch_bounds__(256) k_res_rows(int64_t n, int regen_dominant, const double* __restrict__ x,
+// regen_dominant: the diagonal was skipped by k_res_partial; it is diag[i] if
+// diag is given, else the row's exact sum of |a_ij| rounded once. anorm: a
+// known ||A||_inf (the row sums were not formed), else NULL.
+__global__ void __launch_bounds__(256) k_res_rows(int64_t n, int regen_dominant, const double* __restrict__ diag,
+                                                  const double* __restrict__ anorm, const double* __restrict__ x,
                                                   const double* __restrict__ b, ResWs w) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     double mr = 0.0, ma = 0.0, mx = 0.0, mb = 0.0;
@@ -163,13 +182,13 @@ __global__ void __launch_bounds__(256) k_res_rows(int64_t n, int regen_dominant,
             lo = nl;
         }
         if (regen_dominant) {
-            double d = res_u128_to_double(hi, lo) * 0x1p-53;
+            double d = diag ? diag[i] : res_u128_to_double(hi, lo) * 0x1p-53;
             r = fma(d, x[i], r);
             s += d;
         }
         r -= b[i];
         mr = fabs(r);
-        ma = s;
+        ma = anorm ? *anorm : s;
         mx = fabs(x[i]);
         mb = fabs(b[i]);
     }
@@ -199,13 +218,16 @@ __global__ void k_res_final(int64_t n, const unsigned long long* maxima, double*
 
 // Residual vector and matrix-vector product for the refinement loop: after
 // k_res_partial, r_i = b_i - sum of the row's partials (b != NULL) or
-// r_i = sum of the partials (b == NULL, i.e. r = A x).
-__global__ void __launch_bounds__(256) k_res_vec(int64_t n, const double* __restrict__ b, ResWs w,
+// r_i = sum of the partials (b == NULL, i.e. r = A x); diag != NULL adds the
+// diagonal term diag_i x_i that a regenerating k_res_partial skipped.
+__global__ void __launch_bounds__(256) k_res_vec(int64_t n, const double* __restrict__ diag,
+                                                 const double* __restrict__ x, const double* __restrict__ b, ResWs w,
                                                  double* __restrict__ r) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     double s = 0.0;
     for (int c = 0; c < kResChunks; c++) s += w.part_r[c * n + i];
+    if (diag) s = fma(diag[i], x[i], s);
     r[i] = b ? b[i] - s : s;
 }
 
@@ -214,18 +236,24 @@ __global__ void __launch_bounds__(256) k_res_vec(int64_t n, const double* __rest
 // and the column sums of |a_ij| (the row sums of A^T) into part_a[0..n).
 __global__ void __launch_bounds__(256) k_res_cols_t(int64_t n, const double* __restrict__ A, int64_t lda,
                                                     const double* __restrict__ x, const double* __restrict__ b,
-                                                    double* __restrict__ r, double* __restrict__ csum) {
+                                                    double* __restrict__ r, double* __restrict__ csum,
+                                                    int want_norm) {
     const int lane = threadIdx.x & 31;
     const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (j >= n) return;
     const double* col = A + j * lda;
     double s = 0.0;
     float a = 0.0f;
+    if (want_norm) {
 #pragma unroll 4
-    for (int64_t i = lane; i < n; i += 32) {
-        double v = col[i];
-        s = fma(v, x[i], s);
-        a += abs_as_float(v);
+        for (int64_t i = lane; i < n; i += 32) {
+            double v = col[i];
+            s = fma(v, x[i], s);
+            a += abs_as_float(v);
+        }
+    } else {
+#pragma unroll 4
+        for (int64_t i = lane; i < n; i += 32) s = fma(col[i], x[i], s);
     }
     for (int off = 16; off > 0; off >>= 1) {
         s += __shfl_down_sync(0xffffffffu, s, off);
@@ -237,14 +265,18 @@ __global__ void __launch_bounds__(256) k_res_cols_t(int64_t n, const double* __r
     }
 }
 
+// anorm_in: a known ||A^T||_inf (csum not formed), else NULL; anorm_out: if
+// given (and zeroed), receives max_i csum[i] for later calls.
 __global__ void __launch_bounds__(256) k_res_max_t(int64_t n, const double* __restrict__ r,
-                                                   const double* __restrict__ csum, const double* __restrict__ x,
+                                                   const double* __restrict__ csum,
+                                                   const double* __restrict__ anorm_in,
+                                                   unsigned long long* anorm_out, const double* __restrict__ x,
                                                    const double* __restrict__ b, unsigned long long* maxima) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     double mr = 0.0, ma = 0.0, mx = 0.0, mb = 0.0;
     if (i < n) {
         mr = fabs(r[i]);
-        ma = csum[i];
+        ma = anorm_in ? *anorm_in : csum[i];
         mx = fabs(x[i]);
         mb = fabs(b[i]);
     }
@@ -260,20 +292,27 @@ __global__ void __launch_bounds__(256) k_res_max_t(int64_t n, const double* __re
         atomic_max_nonneg(&maxima[1], ma);
         atomic_max_nonneg(&maxima[2], mx);
         atomic_max_nonneg(&maxima[3], mb);
+        if (anorm_out) atomic_max_nonneg(anorm_out, ma);
     }
 }
 
 // r = b - A^T x (or A^T x when b == NULL), with the scaled residual of the
 // transposed system (||A^T||_inf = max column sum of |A|) into sr if given.
-int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
-                          double* sr, void* ws, cudaStream_t s) {
+// anorm (device double) caches that norm across calls: norm_mode 0 ignores
+// it, 1 computes the norm and stores it there, 2 uses the stored value.
+int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, double* anorm, int norm_mode, const double* x,
+                          const double* b, double* r, double* sr, void* ws, cudaStream_t s) {
     ResWs w;
     res_ws_layout(n, &w, (char*)ws);
-    k_res_cols_t<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(n, A, lda, x, b, r, w.part_a);
+    const bool use = norm_mode == 2 && anorm, store = norm_mode == 1 && anorm;
+    k_res_cols_t<<<(unsigned)((n + 7) / 8), 256, 0, s>>>(n, A, lda, x, b, r, w.part_a, sr && b && !use);
     HPL_LAUNCH_CHECK();
     if (sr && b) {
         HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
-        k_res_max_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, r, w.part_a, x, b, w.maxima);
+        if (store) HPL_CUDA_TRY(cudaMemsetAsync(anorm, 0, sizeof(double), s));
+        k_res_max_t<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, r, w.part_a, use ? anorm : nullptr,
+                                                                store ? (unsigned long long*)anorm : nullptr, x, b,
+                                                                w.maxima);
         HPL_LAUNCH_CHECK();
         k_res_final<<<1, 1, 0, s>>>(n, w.maxima, sr);
         HPL_LAUNCH_CHECK();
@@ -283,20 +322,26 @@ int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, const double*
 
 size_t residual_ws_bytes(int64_t n) { return res_ws_layout(n > 0 ? n : 1, nullptr, nullptr); }
 
-// r = b - A x (b != NULL) or r = A x (b == NULL), A stored column-major (FP64).
-// With sr != NULL (and b != NULL) also the scaled residual of x.
-int launch_residual_vec(int64_t n, const double* A, int64_t lda, const double* x, const double* b, double* r,
-                        double* sr, void* ws, cudaStream_t s) {
+// r = b - A x (b != NULL) or r = A x (b == NULL), A stored column-major (FP64),
+// or, with A == NULL, the dominant generated matrix of key (the generator's
+// stream key) regenerated entry by entry with its diagonal taken from diag.
+// With sr != NULL (and b != NULL) also the scaled residual of x, with
+// ||A||_inf read from anorm (device) if given, else summed here in FP32.
+int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, const double* diag,
+                        const double* anorm, const double* x, const double* b, double* r, double* sr, void* ws,
+                        cudaStream_t s) {
+    if (!A && !diag) return HPL_ERR_INVALID;
     ResWs w;
     res_ws_layout(n, &w, (char*)ws);
+    const double* dg = A ? nullptr : diag;
     dim3 g1((unsigned)((n + 255) / 256), kResChunks);
-    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, 0, 0, x, w, sr != nullptr);
+    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, key, A ? 0 : 1, dg, x, w, (sr && !anorm) ? 1 : 0);
     HPL_LAUNCH_CHECK();
-    k_res_vec<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, b, w, r);
+    k_res_vec<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, dg, x, b, w, r);
     HPL_LAUNCH_CHECK();
     if (sr && b) {
         HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
-        k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, 0, x, b, w);
+        k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, dg != nullptr, dg, anorm, x, b, w);
         HPL_LAUNCH_CHECK();
         k_res_final<<<1, 1, 0, s>>>(n, w.maxima, sr);
         HPL_LAUNCH_CHECK();
@@ -312,9 +357,10 @@ int launch_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t see
     HPL_CUDA_TRY(cudaMemsetAsync(w.maxima, 0, sizeof(unsigned long long) * 4, s));
     uint64_t key = res_mix(seed + 1ull * 0x9E3779B97F4A7C15ull);    // stream 0 of the generator
     dim3 g1((unsigned)((n + 255) / 256), kResChunks);
-    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, key, kind == HPL_GEN_DIAG_DOMINANT, x, w, 2);
+    k_res_partial<<<g1, 256, 0, s>>>(n, A, lda, key, kind == HPL_GEN_DIAG_DOMINANT, nullptr, x, w, 2);
     HPL_LAUNCH_CHECK();
-    k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, !A && kind == HPL_GEN_DIAG_DOMINANT, x, b, w);
+    k_res_rows<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, !A && kind == HPL_GEN_DIAG_DOMINANT, nullptr, nullptr,
+                                                           x, b, w);
     HPL_LAUNCH_CHECK();
     k_res_final<<<1, 1, 0, s>>>(n, w.maxima, out);
     HPL_LAUNCH_CHECK();
@@ -333,5 +379,6 @@ extern "C" int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint
     if (A && lda < n) return HPL_ERR_INVALID;
     if (kind != HPL_GEN_GENERAL && kind != HPL_GEN_DIAG_DOMINANT) return HPL_ERR_INVALID;
     if (!ws || ws_bytes < residual_ws_bytes(n)) return HPL_ERR_NOMEM;
+    if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     return launch_scaled_residual(n, A, lda, seed, kind, x, b, out, ws, (cudaStream_t)stream);
 }

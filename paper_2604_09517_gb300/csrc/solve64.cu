@@ -186,6 +186,7 @@ extern "C" int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, 
     if (n == 0 || nrhs == 0) return HPL_OK;
     size_t need = solve_ws_layout(n, nullptr, nullptr, nullptr, nullptr);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
+    if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     int *cnt, *dst, *src;
     solve_ws_layout(n, &cnt, &dst, &src, (char*)ws);
     const int nblk = (int)((n + kPivBlock - 1) / kPivBlock);

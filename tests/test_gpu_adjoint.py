@@ -82,7 +82,7 @@ def test_adjoint_n4096_64rhs(hpl, orc):
     sides, forward BF16 factor + FP64 refinement, backward on the saved factor,
     compared with the oracle's FP64 adjoint."""
     import torch
-    n, nrhs, nb = 4096, 64, 1536
+    n, nrhs, nb = 4096, 64, 2048
     A = hpl.generate(23, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT)
     B = hpl.generate(23, hpl.STREAM_B, n, nrhs)
     G = torch.from_numpy(np.random.default_rng(7).standard_normal((n, nrhs))).cuda()

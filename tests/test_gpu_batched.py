@@ -38,7 +38,7 @@ def _check_system(orc, bt, s, A0, b0, emulate=True):
         assert np.abs(x - x64).max() / np.abs(x64).max() <= 2 * 16 * n * EPS * kappa
         if emulate:
             nbv = 16 if bt.variant[s] else 32
-            emu = orc.mxp_solve(A0, b0, nbv, prec=orc.PREC_BF16, refine=0)
+            emu = orc.mxp_solve(A0, b0, nbv, prec=orc.PREC_BF16, refine=0, ns_iters=3)   # as the batched kernel
             assert abs(rec["iters"] - emu["iters"]) <= 2, (s, rec, emu["iters"])
 
 
@@ -138,3 +138,29 @@ def test_batched_full_4096(hpl, orc):
     assert all(r["status"] == 0 for r in recs), [i for i, r in enumerate(recs) if r["status"]][:5]
     for s in sample:
         _check_system(orc, bt, int(s), A0[int(s)], b0[int(s)], emulate=False)
+
+
+def test_batched_share_matches_whole_batch(hpl):
+    """One rank's share of a batch split over two GPUs (Batch with the global
+    system ids) generates and solves exactly the systems of the whole batch:
+    matrices, solutions and pivots are bit-identical."""
+    import torch
+    n = hpl.batch_sizes(5, 32)
+    kind = np.array([0] * 16 + [1] * 16, dtype=np.uint8)
+    whole = hpl.Batch(n, kind)
+    whole.generate(5)
+    whole.plan()
+    whole.run()
+    owner = hpl.batch_shard(n, kind, 2)
+    for r in (0, 1):
+        ids = np.nonzero(owner == r)[0]
+        part = hpl.Batch(n[ids], kind[ids], ids=ids)
+        part.generate(5)
+        part.plan()
+        part.run()
+        torch.cuda.synchronize()
+        for j, g in enumerate(ids):
+            assert torch.equal(part.rhs(j), whole.rhs(int(g)))
+            if kind[g] == 0:
+                assert torch.equal(part.pivots(j), whole.pivots(int(g)))
+                assert torch.equal(part.matrix(j), whole.matrix(int(g)))

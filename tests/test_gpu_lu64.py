@@ -166,10 +166,12 @@ def test_invalid_arguments(hpl):
     n = 64
     A = hpl.generate(1, 0, n, n)
     lib = hpl.load()
-    small = torch.empty(16, dtype=torch.uint8, device="cuda")
     ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
     info = hpl.Info()
     opts = hpl.make_opts(nb=64)
+    # a workspace of the full size, declared as 16 bytes: were the size check
+    # missing, the launch would still stay inside memory the test owns
+    small = hpl.workspace(lib.lu_factor_workspace_size(n, ctypes.byref(opts)))
     st = lib.lu_factor(n, A.data_ptr(), n, ipiv.data_ptr(), ctypes.byref(opts), small.data_ptr(), 16,
                        info.ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 6                                   # HPL_ERR_NOMEM, nothing launched
