@@ -1,22 +1,31 @@
-// BF16 tensor-core GEMM for the mixed-precision factorization (paper
-// Sec. III-A.2: factorization and trailing updates in low precision; the
-// Aurora runs used "BF16-optimized kernels" with FP32 accumulation, Table I).
+// Tensor-core GEMM for the mixed-precision factorization (paper Sec. III-A.2:
+// factorization and trailing updates in low precision; the Aurora runs used
+// "BF16-optimized kernels" with FP32 accumulation, Table I), BF16 or FP8 E4M3
+// operands.
 //
 //   C (FP32, column-major, ldc) = sub ? C - A * B^T : A * B^T
-//   A: M x K BF16, K contiguous (row stride lda elements)
-//   B: N x K BF16, K contiguous (row stride ldb elements)
+//   A: M x K, K contiguous (row stride lda elements)
+//   B: N x K, K contiguous (row stride ldb elements)
 //
-// Blackwell design: a persistent, warp-specialised kernel, one CTA per SM.
-//   warp 0      : TMA producer (cp.async.bulk.tensor, 128B swizzle, 4 stages)
+// Blackwell design: persistent, warp-specialised kernels, one CTA per SM.
+//   warp 0      : TMA producer (cp.async.bulk.tensor, 128B swizzle)
 //   warp 1      : TMEM allocator and single-thread tcgen05.mma issuer
 //   warps 2..9  : epilogue (tcgen05.ld from TMEM, FP32 read-modify-write of C)
-// Tiles are 128 x 256 with a 64-wide K step (one 128-byte swizzle row); the
-// accumulator lives in TMEM, double buffered (2 x 256 columns), so the
-// epilogue of one tile overlaps the MMAs of the next. Tiles are walked in
-// bands of GROUP_M row tiles so the A band stays in L2 while B streams.
+// The accumulator lives in TMEM, double buffered, so the epilogue of one tile
+// overlaps the MMAs of the next; K advances 128 bytes per stage (one swizzle
+// row). Tiles are walked in bands of row tiles so the A band stays in L2
+// while B streams.
+//   k_gemm_tc      : one CTA per 128 x BN tile (BN 256, or 128 for products
+//                    with fewer tiles than SMs), 4 (6) stages.
+//   k_gemm_tc_pair : two CTAs of a cluster per 256 x 256 tile with
+//                    tcgen05.mma.cta_group::2, 7 stages of half the bytes;
+//                    used for products of moderate size that have a 256 x 256
+//                    tile for every pair of SMs.
 // Every wait is bounded by a %globaltimer deadline; on expiry the CTA raises
 // an error flag, drains what it has in flight, frees TMEM and returns.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 
@@ -27,10 +36,20 @@ constexpr int BM = 128;
 constexpr int BKB = 128;                 // K bytes per stage: one 128-byte swizzle row
 constexpr int A_BYTES = BM * BKB;
 constexpr int THREADS = 320;
-constexpr int GROUP_M = 32;
+// Row tiles per band of the tile walk (measured on GB300 at M = N = 49152 and
+// 95232, K = 3072: BF16 16 and FP8 32 for the single-CTA kernel).
+template <int KIND>
+constexpr int group_m() { return KIND == 0 ? 16 : 32; }
+constexpr int GROUP_M_PAIR = 16;
+// The pair kernel only for products up to this size (M x N): under the power
+// cap, with FP32 C read and written every step, the single-CTA kernel is as
+// fast or faster on the large trailing updates.
+#ifndef HPLGB_PAIR_MAX_MN
+#define HPLGB_PAIR_MAX_MN (16384LL * 16384LL)
+#endif
 
 // Tile width BN: 256 for large products; 128 when a product has fewer
-// 128 x 256 tiles than the GPU has SMs (the 1536 x 1536 Newton-Schulz
+// 128 x 256 tiles than the GPU has SMs (small Newton-Schulz
 // products), which doubles the CTAs at work.
 template <int BN_>
 struct Tile {
@@ -74,6 +93,7 @@ struct Params {
     long long timeout_ns;
     const float* sa;       // optional per-row scale of the product (M)
     const float* sb;       // optional per-column scale of the product (N)
+    int group_m;           // row tiles per band of the tile walk
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -177,11 +197,11 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-__device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, int& mt, int& nt) {
-    const int per_group = GROUP_M * nt_count;
+__device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, int group, int& mt, int& nt) {
+    const int per_group = group * nt_count;
     const int g = t / per_group;
-    const int first = g * GROUP_M;
-    const int gsz = min(mt_count - first, GROUP_M);
+    const int first = g * group;
+    const int gsz = min(mt_count - first, group);
     const int r = t - g * per_group;
     mt = first + r % gsz;
     nt = r / gsz;
@@ -237,7 +257,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             bool ok = true;
             for (int t = blockIdx.x; t < ntiles && ok; t += gridDim.x) {
                 int mt, nt;
-                tile_coords(t, mt_count, nt_count, mt, nt);
+                tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
                 for (int kb = 0; kb < nk; kb++, it++) {
                     const int s = it % STAGES;
                     const uint32_t ph = (it / STAGES) & 1;
@@ -286,8 +306,10 @@ __global__ void __launch_bounds__(THREADS, 1)
     } else {
         // ---------------- epilogue: warps 2..9 ----------------
         // warp w reads TMEM lane quarter (w & 3) and the column half (w - 2) / 4
-        // of the tile; the C values of the next 32-column chunk are loaded
-        // before the current chunk is stored, so loads stay in flight.
+        // of the tile. The C values of a tile's first 32-column chunk are
+        // requested before its accumulator is ready (the HBM read overlaps the
+        // wait for the MMAs), and those of the next chunk before the current
+        // chunk is stored, so loads stay in flight.
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
         const int row_in_tile = quarter * 32 + lane;
@@ -295,10 +317,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint32_t tcount = 0;
         for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tcount++) {
             int mt, nt;
-            tile_coords(t, mt_count, nt_count, mt, nt);
+            tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
             const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
-            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
-            tc_fence_after();
             const int row = mt * BM + row_in_tile;
             const bool row_ok = row < p.M;
             const int cbase = nt * BN + half * (BN / 2);
@@ -309,6 +329,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                 for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? cp[(long long)j * p.ldc] : 0.0f;
             }
+            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
+            tc_fence_after();
 #pragma unroll 1
             for (int c = 0; c < CHUNKS; c++) {
                 uint32_t r[32];
@@ -350,6 +372,267 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (warp == 1)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
                      : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// Pair kernel: the two CTAs of a cluster (two SMs) compute one 256 x 256 tile
+// together with tcgen05.mma.cta_group::2. Each CTA stages only its own 128
+// rows of A and its own 128 rows of B per K step (32 KB for BF16), half the
+// bytes per SM of the 128 x 256 single-CTA tile for the same MMA work, so
+// seven stages fit in shared memory and the loads run further ahead.
+//   leader (cluster rank 0): warp 0 TMA producer, warp 1 MMA issuer for the
+//     pair (reads the A and B halves from both CTAs' shared memory, writes
+//     rows 0..127 of the tile into its TMEM and rows 128..255 into the peer's)
+//   peer (rank 1): warp 0 TMA producer
+//   both: warps 2..9 epilogue of their own 128 rows.
+// Both CTAs' loads of a stage complete on the leader's full barrier (TMA with
+// .cta_group::2), which the leader arms with the bytes of both; the MMA
+// commits arrive on the stage's empty barrier and on the accumulator barrier
+// of both CTAs (multicast); both CTAs' epilogue warps arrive on the leader's
+// tempty barrier.
+constexpr int PAIR_ROWS = 128;                 // rows of A and of B staged by each CTA
+constexpr int PAIR_STAGE_BYTES = 2 * PAIR_ROWS * BKB;
+constexpr int PAIR_STAGES = 7;
+constexpr int PAIR_DYN_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024;
+
+template <int KIND>
+__host__ __device__ constexpr uint32_t idesc_pair() {
+    return Kind<KIND>::FORMATS | ((uint32_t)(256 >> 3) << 17) | ((uint32_t)(256 >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_id() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_count() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%nclusterid.x;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the same variable in CTA `rank` of the cluster
+__device__ __forceinline__ uint32_t cluster_addr(const void* p, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void mbar_arrive_remote(uint32_t caddr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(caddr) : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on a
+// barrier of either CTA of the pair (cluster address), e.g. the leader's.
+__device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* map, uint32_t bar_cluster, int x,
+                                                 int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.cta_group::2 [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar_cluster)
+        : "memory");
+}
+
+template <int KIND>
+__device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    if constexpr (KIND == 0) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc_pair<0>()), "r"(accumulate)
+            : "memory");
+    } else {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc_pair<1>()), "r"(accumulate)
+            : "memory");
+    }
+}
+// arrive on the barrier at this offset in both CTAs once the issued MMAs are done
+__device__ __forceinline__ void umma_commit_pair_both(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"((uint16_t)3)
+        : "memory");
+}
+__device__ __forceinline__ void umma_commit_pair_own(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int KIND>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
+    k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    constexpr int BK = BKB / Kind<KIND>::ELEM;
+    constexpr int HALF = PAIR_ROWS * BKB;       // bytes of one operand half per stage
+    extern __shared__ __align__(1024) unsigned char dsm[];
+    __shared__ __align__(8) uint64_t full_bar[PAIR_STAGES], empty_bar[PAIR_STAGES];
+    __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
+    __shared__ uint32_t s_tmem;
+    __shared__ volatile int s_abort;
+
+    unsigned char* tiles = (unsigned char*)(((uintptr_t)dsm + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const uint32_t rank = cluster_rank();
+    const int pair = (int)cluster_id(), npairs = (int)cluster_count();
+    const int mt_count = (p.M + 255) / 256, nt_count = (p.N + 255) / 256;
+    const int ntiles = mt_count * nt_count;
+    const int nk = (p.K + BK - 1) / BK;
+    const uint64_t deadline = globaltimer_ns() + (uint64_t)p.timeout_ns;
+
+    if (threadIdx.x == 0) {
+        s_abort = 0;
+        for (int s = 0; s < PAIR_STAGES; s++) {
+            mbar_init(&full_bar[s], 1);      // the leader's producer arms it for both CTAs' bytes
+            mbar_init(&empty_bar[s], 1);
+        }
+        for (int a = 0; a < 2; a++) {
+            mbar_init(&tfull_bar[a], 1);
+            mbar_init(&tempty_bar[a], 16);     // the 8 epilogue warps of each CTA
+        }
+        mbar_init(&drain_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                     "r"(512)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    cluster_sync_all();      // both CTAs' barriers initialised and TMEM allocated
+    tc_fence_after();
+    const uint32_t tmem_base = s_tmem;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---------------- TMA producer (each CTA: its own halves) ----------------
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+            asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+            uint32_t it = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs) {
+                int mt, nt;
+                tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
+                for (int kb = 0; kb < nk; kb++, it++) {
+                    const int s = it % PAIR_STAGES;
+                    const uint32_t ph = (it / PAIR_STAGES) & 1;
+                    if (!mbar_wait(&empty_bar[s], ph ^ 1, deadline, &s_abort, p.err)) { ok = false; break; }
+                    unsigned char* sa = tiles + s * PAIR_STAGE_BYTES;
+                    if (rank == 0) mbar_expect_tx(&full_bar[s], 2 * PAIR_STAGE_BYTES);
+                    const uint32_t fb = cluster_addr(&full_bar[s], 0);
+                    tma_load_2d_pair(sa, &tmA, fb, kb * BK, mt * 256 + (int)rank * PAIR_ROWS);
+                    tma_load_2d_pair(sa + HALF, &tmB, fb, kb * BK, nt * 256 + (int)rank * PAIR_ROWS);
+                }
+            }
+            if (!ok) {
+                // the loads in flight complete on the leader's barriers, which
+                // this CTA cannot watch: give them time to land before exit
+                const uint64_t t0 = globaltimer_ns();
+                while (globaltimer_ns() - t0 < 200000ull) __nanosleep(1000);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0 && rank == 0) {
+            // ---------------- MMA issuer for the pair (leader) ----------------
+            uint32_t it = 0, tcount = 0;
+            bool ok = true;
+            for (int t = pair; t < ntiles && ok; t += npairs, tcount++) {
+                const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+                if (!mbar_wait(&tempty_bar[acc], aph ^ 1, deadline, &s_abort, p.err)) { ok = false; break; }
+                tc_fence_after();
+                const uint32_t d_tmem = tmem_base + acc * 256;
+                for (int kb = 0; kb < nk; kb++, it++) {
+                    const int s = it % PAIR_STAGES;
+                    const uint32_t ph = (it / PAIR_STAGES) & 1;
+                    if (!mbar_wait(&full_bar[s], ph, deadline, &s_abort, p.err)) { ok = false; break; }
+                    tc_fence_after();
+                    const uint32_t sa = smem_u32(tiles + s * PAIR_STAGE_BYTES);
+                    const uint64_t ad = desc_sw128(sa), bd = desc_sw128(sa + HALF);
+#pragma unroll
+                    for (int kk = 0; kk < BKB / 32; kk++)
+                        umma_pair<KIND>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                    umma_commit_pair_both(&empty_bar[s]);
+                }
+                if (ok) umma_commit_pair_both(&tfull_bar[acc]);
+            }
+            umma_commit_pair_own(&drain_bar);
+            mbar_wait(&drain_bar, 0, deadline + 1000000000ull, &s_abort, p.err);
+        }
+    } else {
+        // ---------------- epilogue: warps 2..9 of each CTA, its own 128 rows ----------------
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        const int row_in_tile = (int)rank * PAIR_ROWS + quarter * 32 + lane;
+        constexpr int CHUNKS = 128 / 32;
+        const uint32_t tempty_leader[2] = {cluster_addr(&tempty_bar[0], 0), cluster_addr(&tempty_bar[1], 0)};
+        uint32_t tcount = 0;
+        for (int t = pair; t < ntiles; t += npairs, tcount++) {
+            int mt, nt;
+            tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
+            const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+            const int row = mt * 256 + row_in_tile;
+            const bool row_ok = row < p.M;
+            const int cbase = nt * 256 + half * 128;
+            float* cp = p.C + (long long)cbase * p.ldc + row;
+            const int ncol = min(128, p.N - cbase);
+            float cv[32];
+            if (p.sub) {
+#pragma unroll
+                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? cp[(long long)j * p.ldc] : 0.0f;
+            }
+            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < CHUNKS; c++) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * 256 + half * 128 + c * 32, r);
+                float nv[32];
+                if (p.sub && c + 1 < CHUNKS) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int jj = (c + 1) * 32 + j;
+                        nv[j] = (row_ok && jj < ncol) ? cp[(long long)jj * p.ldc] : 0.0f;
+                    }
+                }
+                tmem_wait_ld();
+                if (row_ok) {
+                    const float rs = p.sa ? p.sa[row] : 1.0f;
+#pragma unroll
+                    for (int j = 0; j < 32; j++) {
+                        const int jj = c * 32 + j;
+                        if (jj < ncol) {
+                            float v = __uint_as_float(r[j]) * rs;
+                            if (p.sb) v *= p.sb[cbase + jj];
+                            cp[(long long)jj * p.ldc] = p.sub ? cv[j] - v : v;
+                        }
+                    }
+                }
+                if (p.sub && c + 1 < CHUNKS) {
+#pragma unroll
+                    for (int j = 0; j < 32; j++) cv[j] = nv[j];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_remote(tempty_leader[acc]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();      // the leader's MMAs have drained; no CTA touches the other any more
+    tc_fence_after();
+    if (warp == 1)
+        asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(512) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -425,9 +708,66 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
+    p.group_m = group_m<KIND>();
     k_gemm_tc<KIND, BN><<<grid, THREADS, Tile<BN>::DYN_SMEM, s>>>(ma, mb, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
+}
+
+// The pair kernel: grid = 2 x min(tiles, clusters that fit at once).
+template <int KIND>
+static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
+                       const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                       int max_ctas, cudaStream_t s) {
+    constexpr int elem = Kind<KIND>::ELEM;
+    if (M <= 0 || N <= 0) return HPL_OK;
+    if (K <= 0) return HPL_ERR_INVALID;
+    if (M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return HPL_ERR_INVALID;
+    if (lda < K || ldb < K || ldc < M || (lda * elem) % 16 || (ldb * elem) % 16) return HPL_ERR_INVALID;
+    if (((uintptr_t)A | (uintptr_t)B) & 15) return HPL_ERR_INVALID;
+    CUtensorMap ma, mb;
+    int st = make_map(&ma, A, M, K, lda, PAIR_ROWS, elem);
+    if (st) return st;
+    st = make_map(&mb, B, N, K, ldb, PAIR_ROWS, elem);
+    if (st) return st;
+    static int max_pairs = 0;
+    if (!max_pairs) {
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc_pair<KIND>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_DYN_SMEM));
+        int dev = 0, sms = kNumSMsGB300;
+        HPL_CUDA_TRY(cudaGetDevice(&dev));
+        HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = PAIR_DYN_SMEM;
+        int nc = 0;
+        HPL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_gemm_tc_pair<KIND>, &cfg));
+        max_pairs = nc > 0 ? nc : sms / 2;
+    }
+    const int64_t ntiles = ((M + 255) / 256) * ((N + 255) / 256);
+    int pairs = (int)std::min<int64_t>(ntiles, max_pairs);
+    if (max_ctas > 0) pairs = std::max(1, std::min(pairs, max_ctas / 2));
+    Params p;
+    p.M = (int)M;
+    p.N = (int)N;
+    p.K = (int)K;
+    p.C = C;
+    p.ldc = ldc;
+    p.sub = sub;
+    p.err = err;
+    p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
+    p.sa = sa;
+    p.sb = sb;
+    p.group_m = GROUP_M_PAIR;
+    k_gemm_tc_pair<KIND><<<2 * pairs, THREADS, PAIR_DYN_SMEM, s>>>(ma, mb, p);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+// A product of moderate size with a 256 x 256 tile for every SM pair: the pair kernel.
+static bool pair_tiles(int64_t M, int64_t N) {
+    return M * N <= HPLGB_PAIR_MAX_MN && ((M + 255) / 256) * ((N + 255) / 256) >= kNumSMsGB300 / 2;
 }
 
 // Fewer 128 x 256 tiles than SMs: use 128 x 128 tiles.
@@ -441,6 +781,8 @@ static bool narrow_tiles(int64_t M, int64_t N) {
 // one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
 int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                      float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
+    if (tc::pair_tiles(M, N))
+        return tc::launch_pair<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns,
                                        max_ctas, s);
@@ -453,6 +795,8 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s) {
+    if (tc::pair_tiles(M, N))
+        return tc::launch_pair<1>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<1, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
     return tc::launch_kind<1, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);

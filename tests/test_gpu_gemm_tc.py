@@ -28,7 +28,10 @@ def _case(hpl, M, N, K, sub, seed, ld_pad=0):
 @pytest.mark.parametrize("M,N,K,sub", [(128, 256, 64, True), (128, 256, 128, False), (1, 1, 8, True),
                                        (300, 500, 200, True), (257, 513, 72, False), (129, 255, 64, True),
                                        (1536, 1536, 1536, True), (2048, 4096, 1536, True),
-                                       (4000, 300, 1024, False)])
+                                       (4000, 300, 1024, False),
+                                       # >= 76 tiles of 256 x 256: the two-SM pair kernel, ragged edges,
+                                       # K tails, and a last tile row whose second half lies beyond M
+                                       (2304, 2304, 704, True), (2500, 2100, 200, True), (2404, 2300, 136, False)])
 def test_gemm_bf16_matches_fp64(hpl, M, N, K, sub):
     _case(hpl, M, N, K, sub, seed=M + N + K)
 
@@ -47,7 +50,8 @@ def test_gemm_bf16_rejects_bad_strides(hpl):
 
 
 @pytest.mark.parametrize("M,N,K,sub,scaled", [(128, 256, 128, True, False), (300, 500, 208, True, True),
-                                              (1536, 2048, 1536, True, True), (257, 129, 64, False, True)])
+                                              (1536, 2048, 1536, True, True), (257, 129, 64, False, True),
+                                              (2304, 2560, 256, True, True), (2404, 2100, 208, True, True)])
 def test_gemm_fp8_matches_fp64(hpl, M, N, K, sub, scaled):
     import torch
     g = torch.Generator(device="cuda").manual_seed(M + N + K)

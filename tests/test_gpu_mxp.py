@@ -18,7 +18,8 @@ def _system(hpl, n, seed):
     return A, b
 
 
-@pytest.mark.parametrize("n,nb", [(256, 64), (512, 128), (1000, 256), (300, 100), (7, 64), (1, 8), (2048, 512)])
+@pytest.mark.parametrize("n,nb", [(256, 64), (512, 128), (1000, 256), (300, 100), (7, 64), (1, 8), (2048, 512),
+                                  (2560, 256)])     # updates of >= 76 tiles of 256 x 256: the pair kernel
 def test_mxp_factor_matches_oracle(hpl, orc, n, nb):
     import torch
     A, b = _system(hpl, n, 3)
