@@ -38,6 +38,10 @@ MAX_SM_MHZ = 2070.0
 # capture of an m=7936, n=7680, k=256 launch (959.8 MB for 31.21 GFLOP); the
 # traffic of an update launch scales with its C tile, i.e. with flops at fixed k.
 DGEMM_DRAM_BYTES_PER_FLOP = 959.8e6 / 31.21e9
+# Same for the tcgen05 trailing update of the mixed-precision solve, from one
+# ncu capture each of a step-0 update at n = 24576 (BF16: m = 21504, k = 3072,
+# 5.264 GB for 2.841 TFLOP; FP8: m = 20480, k = 4096, 3.820 GB for 3.436 TFLOP).
+MXP_DRAM_BYTES_PER_FLOP = {0: 5.264e9 / 2.841e12, 1: 3.820e9 / 3.436e12}
 
 
 def flops(n: int) -> float:
@@ -416,7 +420,8 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False):
             "matrix": "uniform[-0.5,0.5) FP64, diagonal = row sum of |a_ij| (diagonally dominant)"
                       + ("; regenerated from the seed, never stored" if regen else "; stored FP64"),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak if achieved else None, "traffic": None,
+                         "frac": achieved / peak if achieved else None,
+                         "traffic": MXP_DRAM_BYTES_PER_FLOP[prec] * upd_flops / upd_cnt if upd_cnt else None,
                          "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
                          "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec else ""),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},

@@ -237,15 +237,19 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf(
             }
         }
         __syncthreads();
-        // scale the column below the diagonal and rank-1 update of the leaf
+        // scale the column below the diagonal (one true division per row: FP64
+        // instructions are scarce on this part, so no lane repeats another's),
+        // then the rank-1 update of the leaf's remaining columns, a warp per row
         if (piv != 0.0) {
-            const double pl = (lane < w) ? s_piv[lane] : 0.0;
-            int rs = (int)max((int64_t)0, rowj + 1 - c0 - rbeg);
-            for (int r = rs + warp; r < nloc; r += kLeafThreads / 32) {
-                double v = (lane < w) ? sm[r * S + lane] : 0.0;
-                double l = __shfl_sync(0xffffffffu, v, j) / piv;
-                if (lane == j) sm[r * S + lane] = l;
-                else if (lane > j && lane < w) sm[r * S + lane] = fma(-l, pl, v);
+            const int rs = (int)max((int64_t)0, rowj + 1 - c0 - rbeg);
+            for (int r = rs + tid; r < nloc; r += kLeafThreads) sm[r * S + j] = sm[r * S + j] / piv;
+            __syncthreads();
+            if (j + 1 < w) {
+                const double pl = (lane < w) ? s_piv[lane] : 0.0;
+                for (int r = rs + warp; r < nloc; r += kLeafThreads / 32) {
+                    const double l = sm[r * S + j];
+                    if (lane > j && lane < w) sm[r * S + lane] = fma(-l, pl, sm[r * S + lane]);
+                }
             }
         }
         __syncthreads();
