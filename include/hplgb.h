@@ -194,6 +194,11 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * with FP8 E4M3 operands instead (one power-of-two scale per row of L21 and
  * per column of A12 over the panel width, applied in the GEMM epilogue; the
  * panel product L21 = A21 D^-1 keeps BF16).
+ * With nrhs > 1 and opts->refine == HPL_REFINE_IR (and A stored) the columns
+ * are refined together: each step forms R = B - A X for all of them as one
+ * FP64 product and applies the factor to all of them at once (FP32 block
+ * triangular solves); the workspace then also holds these block buffers, so
+ * mxp_workspace_size depends on nrhs and opts->refine.
  * A == NULL (lda ignored) solves with the HPL-MxP matrix of `seed` (stream 0,
  * HPL_GEN_DIAG_DOMINANT, as hpl_generate defines it) without storing it: the
  * FP32 working copy is generated directly and every FP64 residual regenerates
@@ -212,7 +217,10 @@ int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t se
  * mxp_solve of the same A with the same n and opts: its saved block factor is
  * reused (transposed: M^-T = L^-T U^-T as preconditioner) and each column of
  * G (n x nrhs, ldg) is refined in FP64 against A^T to the scaled-residual
- * tolerance, into gradB (ldgb). X (ldx) is the forward solution; gradA
+ * tolerance, into gradB (ldgb); with nrhs > 1 and opts->refine ==
+ * HPL_REFINE_IR the columns are refined together as in mxp_solve (ws must
+ * then hold mxp_workspace_size(n, nrhs, opts) bytes for this nrhs). X (ldx)
+ * is the forward solution; gradA
  * (n x n, ldga) is written, not accumulated. info as for mxp_solve (residuals
  * of the transposed system). Blocks the host like mxp_solve.
  */

@@ -289,7 +289,9 @@ def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: tor
 class SolveFn(torch.autograd.Function):
     """X = A^-1 B with the mixed-precision forward (BF16 block LU + FP64
     refinement) and the hand-written adjoint backward on the saved factor.
-    A must be FP64, square, column-major and diagonally dominant."""
+    A must be FP64, square, column-major and diagonally dominant. Several
+    right-hand sides are refined together (classic refinement on the block);
+    one right-hand side uses GMRES-based refinement."""
 
     @staticmethod
     def forward(ctx, A, B, nb=3072):
@@ -297,19 +299,21 @@ class SolveFn(torch.autograd.Function):
         Bm = B.reshape(B.shape[0], -1) if B.dim() == 1 else B
         Bc = colmajor(Bm.shape[0], Bm.shape[1], device=A.device)
         Bc.copy_(Bm)
-        X, info, ws = mxp_solve(Ac.detach(), Bc, nb=nb)
+        refine = REFINE_IR if Bc.shape[1] > 1 else REFINE_GMRES
+        X, info, ws = mxp_solve(Ac.detach(), Bc, nb=nb, refine=refine)
         rec = info.read()
         if rec["status"] != 0:
             raise HplError(rec["status"], "SolveFn.forward")
         ctx.save_for_backward(Ac.detach(), X)
-        ctx.ws, ctx.nb, ctx.vec = ws, nb, B.dim() == 1
+        ctx.ws, ctx.nb, ctx.vec, ctx.refine = ws, nb, B.dim() == 1, refine
         out = X.clone()
         return out[:, 0] if ctx.vec else out
 
     @staticmethod
     def backward(ctx, G):
         A, X = ctx.saved_tensors
-        gB, gA, info = lu_solve_backward(A, X, G, ctx.ws, nb=ctx.nb, want_grad_a=ctx.needs_input_grad[0])
+        gB, gA, info = lu_solve_backward(A, X, G, ctx.ws, nb=ctx.nb, want_grad_a=ctx.needs_input_grad[0],
+                                         refine=ctx.refine)
         rec = info.read()
         if rec["status"] != 0:
             raise HplError(rec["status"], "SolveFn.backward")

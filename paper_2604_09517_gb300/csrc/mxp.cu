@@ -356,6 +356,158 @@ __global__ void __launch_bounds__(256) k_gemvT32(int64_t rows, int64_t cols, con
     if (lane == 0) y[c] = sub ? y[c] - acc : acc;
 }
 
+// ---------------------------------------------------------------------------
+// Several right-hand sides at once: classic refinement on the whole block,
+// with the FP64 residual R = B - op(A) X as one DFMA product split over K and
+// the preconditioner as FP32 block triangular solves with the factor's panels.
+constexpr int kBlkSplit = 4;     // K slices of the block residual
+
+// part[z] (m x nn, ld m) = op(A)(rows, K slice z) X(K slice z, cols), op(A) =
+// A (TA = false, A m x kk column-major) or A^T (TA = true, A kk x m).
+template <bool TA>
+__global__ void __launch_bounds__(256) k_dgemm_part(int64_t m, int64_t nn, int64_t kk, int64_t kchunk,
+                                                    const double* __restrict__ A, int64_t lda,
+                                                    const double* __restrict__ X, int64_t ldx,
+                                                    double* __restrict__ part) {
+    __shared__ double As[16][65], Xs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * 64, col0 = (int64_t)blockIdx.y * 64;
+    const int64_t kb0 = (int64_t)blockIdx.z * kchunk, kb1 = min(kk, kb0 + kchunk);
+    double acc[4][4] = {};
+    for (int64_t k0 = kb0; k0 < kb1; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kq, r;
+            if (TA) { r = e >> 4; kq = e & 15; }        // A^T: contiguous along K
+            else { kq = e >> 6; r = e & 63; }
+            const bool ok = k0 + kq < kb1 && row0 + r < m;
+            As[kq][r] = ok ? (TA ? A[(row0 + r) * lda + k0 + kq] : A[(k0 + kq) * lda + row0 + r]) : 0.0;
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int c = e >> 4, kq = e & 15;
+            const bool ok = k0 + kq < kb1 && col0 + c < nn;
+            Xs[kq][c] = ok ? X[(col0 + c) * ldx + k0 + kq] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kq = 0; kq < 16; kq++) {
+            double a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kq][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Xs[kq][ty + 16 * j];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double* P = part + (int64_t)blockIdx.z * nn * m;
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
+            if (r < m && c < nn) P[c * m + r] = acc[i][j];
+        }
+}
+
+// R = B - (sum of the K slices, in slice order); per column the largest |R|,
+// |X| and |B| (bit patterns of non-negative doubles, atomicMax) into cmax.
+__global__ void __launch_bounds__(256) k_resid_blk_finish(int64_t m, int64_t nn, int split,
+                                                          const double* __restrict__ part,
+                                                          const double* __restrict__ B, int64_t ldb,
+                                                          double* __restrict__ R, int64_t ldr,
+                                                          const double* __restrict__ X, int64_t ldx,
+                                                          unsigned long long* cmax) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, c = blockIdx.y;
+    double ar = 0.0, ax = 0.0, ab = 0.0;
+    if (i < m) {
+        double acc = 0.0;
+        for (int q = 0; q < split; q++) acc += part[((int64_t)q * nn + c) * m + i];
+        const double b = B[c * ldb + i], r = b - acc;
+        R[c * ldr + i] = r;
+        ar = fabs(r);
+        if (ar != ar) ar = __longlong_as_double(0x7ff0000000000000LL);
+        ax = fabs(X[c * ldx + i]);
+        ab = fabs(b);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        ar = fmax(ar, __shfl_down_sync(0xffffffffu, ar, off));
+        ax = fmax(ax, __shfl_down_sync(0xffffffffu, ax, off));
+        ab = fmax(ab, __shfl_down_sync(0xffffffffu, ab, off));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMax(&cmax[3 * c], (unsigned long long)__double_as_longlong(ar));
+        atomicMax(&cmax[3 * c + 1], (unsigned long long)__double_as_longlong(ax));
+        atomicMax(&cmax[3 * c + 2], (unsigned long long)__double_as_longlong(ab));
+    }
+}
+
+// C (m x nn, FP32) = or -= op(A) (m x kk) B (kk x nn), FP32 accumulation;
+// op(A)(i, q) = A[q * lda + i] (TA = false) or A[i * lda + q] (TA = true).
+template <bool TA>
+__global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk, const float* __restrict__ A,
+                                               int64_t lda, const float* __restrict__ B, int64_t ldb,
+                                               float* __restrict__ C, int64_t ldc, int sub) {
+    __shared__ float As[16][65], Bs[16][65];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int64_t row0 = (int64_t)blockIdx.x * 64, col0 = (int64_t)blockIdx.y * 64;
+    float acc[4][4] = {};
+    for (int64_t k0 = 0; k0 < kk; k0 += 16) {
+        for (int e = tid; e < 16 * 64; e += 256) {
+            int kq, r;
+            if (TA) { r = e >> 4; kq = e & 15; }
+            else { kq = e >> 6; r = e & 63; }
+            const bool ok = k0 + kq < kk && row0 + r < m;
+            As[kq][r] = ok ? (TA ? A[(row0 + r) * lda + k0 + kq] : A[(k0 + kq) * lda + row0 + r]) : 0.0f;
+        }
+        for (int e = tid; e < 16 * 64; e += 256) {
+            const int c = e >> 4, kq = e & 15;
+            const bool ok = k0 + kq < kk && col0 + c < nn;
+            Bs[kq][c] = ok ? B[(col0 + c) * ldb + k0 + kq] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kq = 0; kq < 16; kq++) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) a[i] = As[kq][tx + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; j++) b[j] = Bs[kq][ty + 16 * j];
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
+            if (r < m && c < nn) C[c * ldc + r] = sub ? C[c * ldc + r] - acc[i][j] : acc[i][j];
+        }
+}
+
+// Y (FP32, ld ldy) = X (FP64, ld ldx), m x nn; and back (add: Y += X).
+__global__ void k_f64_to_f32_blk(int64_t m, int64_t nn, const double* __restrict__ X, int64_t ldx,
+                                 float* __restrict__ Y, int64_t ldy) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, c = blockIdx.y;
+    if (i < m) Y[c * ldy + i] = (float)X[c * ldx + i];
+}
+__global__ void k_f32_to_f64_blk(int64_t m, int64_t nn, const float* __restrict__ Y, int64_t ldy,
+                                 double* __restrict__ X, int64_t ldx, int add) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, c = blockIdx.y;
+    if (i < m) X[c * ldx + i] = add ? X[c * ldx + i] + (double)Y[c * ldy + i] : (double)Y[c * ldy + i];
+}
+__global__ void k_copy32_blk(int64_t m, int64_t nn, const float* __restrict__ S, int64_t lds, float* __restrict__ D,
+                             int64_t ldd) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, c = blockIdx.y;
+    if (i < m) D[c * ldd + i] = S[c * lds + i];
+}
+
 // grad_A = -G X^T for G, X n x k (FP64, column-major): 64 x 64 output tiles,
 // k staged 16 at a time in shared memory, 4 x 4 DFMA register tiles.
 __global__ void __launch_bounds__(256) k_outer_neg(int64_t n, int64_t k, const double* __restrict__ G, int64_t ldg,
@@ -491,9 +643,15 @@ struct MxpWs {
     float* sb;         // n: FP8 column scales of the update's B operand
     float* gpart;      // kGemvSplitMax x n: column-split GEMV partial sums
     double* gdiag;     // n: FP64 diagonal of a regenerated matrix (A == NULL)
+    // block refinement of nrhs_blk right-hand sides (absent when 0)
+    float* Yb;         // n x nrhs_blk FP32
+    float* Tb;         // nb x nrhs_blk FP32
+    double* Rb;        // n x nrhs_blk FP64 residuals / corrections
+    double* partb;     // kBlkSplit x n x nrhs_blk FP64 K slices of the residual
+    unsigned long long* cmax;   // 3 x nrhs_blk column maxima
 };
 
-static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) {
+static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, int64_t nrhs_blk = 0) {
     const int64_t nb8 = round8(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -526,6 +684,11 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base) 
     t.sb = (float*)take(sizeof(float) * n);
     t.gpart = (float*)take(sizeof(float) * kGemvSplitMax * n);
     t.gdiag = (double*)take(sizeof(double) * n);
+    t.Yb = (float*)take(sizeof(float) * n * nrhs_blk);
+    t.Tb = (float*)take(sizeof(float) * nb * nrhs_blk);
+    t.Rb = (double*)take(sizeof(double) * n * nrhs_blk);
+    t.partb = (double*)take(sizeof(double) * kBlkSplit * n * nrhs_blk);
+    t.cmax = (unsigned long long*)take(sizeof(unsigned long long) * 3 * nrhs_blk);
     if (w) *w = t;
     return off;
 }
@@ -850,17 +1013,141 @@ struct Mxp {
         *sr_out = sr;
         return check_err(status);
     }
+
+    // ---- several right-hand sides: classic refinement on the block ----
+    int64_t nblk = 0;       // right-hand sides of the block buffers in w
+
+    dim3 grid_blk(int64_t rows, int64_t cols) const { return dim3((unsigned)((rows + 255) / 256), (unsigned)cols); }
+
+    // C (rows x k) -= or = op(P) (rows x kk) Y (kk x k), FP32
+    int sgemm(bool ta, int64_t rows, int64_t kk, const float* P, int64_t ldp, const float* Y, int64_t ldy, float* C,
+              int64_t ldc, int64_t k, int sub) {
+        if (rows <= 0 || kk <= 0 || k <= 0) return HPL_OK;
+        dim3 g((unsigned)((rows + 63) / 64), (unsigned)((k + 63) / 64));
+        if (ta) k_sgemm<true><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
+        else k_sgemm<false><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
+
+    // Z (FP64, n x k, ldz) = M^-1 R or M^-T R (trans), R = w.Rb; add: Z += ...
+    int precond_blk(int64_t k, double* Z, int64_t ldz, int add) {
+        const int64_t ldf = n;
+        float* Y = w.Yb;
+        float* T = w.Tb;
+        int slot = phase_begin(s), st;
+        k_f64_to_f32_blk<<<grid_blk(n, k), 256, 0, s>>>(n, k, w.Rb, n, Y, n);
+        HPL_LAUNCH_CHECK();
+        const int64_t last = ((n - 1) / nb) * nb;
+        if (!trans) {
+            for (int64_t k0 = 0; k0 < n; k0 += nb) {
+                const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+                if ((st = sgemm(false, m2, kb, w.F + k0 * ldf + k0 + kb, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
+                    return st;
+            }
+            for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+                const int64_t kb = std::min(nb, n - k0);
+                if ((st = sgemm(false, kb, kb, w.Dinv + k0, n, Y + k0, n, T, nb, k, 0))) return st;
+                k_copy32_blk<<<grid_blk(kb, k), 256, 0, s>>>(kb, k, T, nb, Y + k0, n);
+                HPL_LAUNCH_CHECK();
+                if ((st = sgemm(false, k0, kb, w.F + k0 * ldf, ldf, Y + k0, n, Y, n, k, 1))) return st;
+            }
+        } else {
+            for (int64_t k0 = 0; k0 < n; k0 += nb) {
+                const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+                if ((st = sgemm(true, kb, kb, w.Dinv + k0, n, Y + k0, n, T, nb, k, 0))) return st;
+                k_copy32_blk<<<grid_blk(kb, k), 256, 0, s>>>(kb, k, T, nb, Y + k0, n);
+                HPL_LAUNCH_CHECK();
+                if ((st = sgemm(true, m2, kb, w.F + (k0 + kb) * ldf + k0, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
+                    return st;
+            }
+            for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
+                const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
+                if ((st = sgemm(true, kb, m2, w.F + k0 * ldf + k0 + kb, ldf, Y + k0 + kb, n, Y + k0, n, k, 1)))
+                    return st;
+            }
+        }
+        k_f32_to_f64_blk<<<grid_blk(n, k), 256, 0, s>>>(n, k, Y, n, Z, ldz, add);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_OTHER, (4.0 * n * n + 4.0 * n * nb) * (double)k);
+        return HPL_OK;
+    }
+
+    // w.Rb = B - op(A) X for k columns, with each column's largest |r|, |x|,
+    // |b| in w.cmax
+    int resid_blk(int64_t k, const double* B, int64_t ldb, const double* X, int64_t ldx) {
+        int slot = phase_begin(s);
+        const int64_t kchunk = ((n + kBlkSplit - 1) / kBlkSplit + 15) / 16 * 16;
+        dim3 g((unsigned)((n + 63) / 64), (unsigned)((k + 63) / 64), (unsigned)kBlkSplit);
+        if (trans) k_dgemm_part<true><<<g, 256, 0, s>>>(n, k, n, kchunk, A, lda, X, ldx, w.partb);
+        else k_dgemm_part<false><<<g, 256, 0, s>>>(n, k, n, kchunk, A, lda, X, ldx, w.partb);
+        HPL_LAUNCH_CHECK();
+        HPL_CUDA_TRY(cudaMemsetAsync(w.cmax, 0, sizeof(unsigned long long) * 3 * k, s));
+        k_resid_blk_finish<<<grid_blk(n, k), 256, 0, s>>>(n, k, kBlkSplit, w.partb, B, ldb, w.Rb, n, X, ldx,
+                                                          w.cmax);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_RESID, 8.0 * n * n + 2.0 * n * n * (double)k);
+        return HPL_OK;
+    }
+
+    // Refine k right-hand sides together: X = M^-1 B, then X += M^-1 (B - A X)
+    // until every column's scaled residual is below tol.
+    int refine_block(int64_t k, const double* B, int64_t ldb, double* X, int64_t ldx, int* iters, double* sr_out,
+                     int* status) {
+        int rslot = phase_begin(s), st;
+        double anorm = 0.0;
+        if (trans && !tnorm_ready) {        // ||A^T||_inf once, through one transposed residual
+            if ((st = resid(B, B, w.r, w.scal))) return st;
+        }
+        if ((st = read_scalar(w.scal + (trans ? 7 : 6), &anorm))) return st;
+        for (int64_t c = 0; c < k; c++)
+            HPL_CUDA_TRY(cudaMemcpyAsync(w.Rb + c * n, B + c * ldb, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+        if ((st = precond_blk(k, X, ldx, 0))) return st;
+        std::vector<unsigned long long> cm((size_t)(3 * k));
+        int it = 0;
+        double worst = INFINITY;
+        *status = HPL_ERR_NOT_CONVERGED;
+        for (;;) {
+            if ((st = resid_blk(k, B, ldb, X, ldx))) return st;
+            HPL_CUDA_TRY(cudaMemcpyAsync(cm.data(), w.cmax, sizeof(unsigned long long) * 3 * k,
+                                         cudaMemcpyDeviceToHost, s));
+            HPL_CUDA_TRY(cudaStreamSynchronize(s));
+            worst = 0.0;
+            bool finite = true;
+            for (int64_t c = 0; c < k; c++) {
+                double r, xm, bm;
+                memcpy(&r, &cm[3 * c], 8);
+                memcpy(&xm, &cm[3 * c + 1], 8);
+                memcpy(&bm, &cm[3 * c + 2], 8);
+                const double den = 0x1p-53 * (anorm * xm + bm) * (double)n;
+                const double sr = den > 0.0 ? r / den : (r > 0.0 ? INFINITY : 0.0);
+                if (!std::isfinite(sr)) finite = false;
+                worst = std::max(worst, sr);
+            }
+            if (!finite) { *status = HPL_ERR_NONFINITE; break; }
+            if (worst < o.tol) { *status = HPL_OK; break; }
+            if (it >= o.max_iter) break;
+            if ((st = precond_blk(k, X, ldx, 1))) return st;
+            it++;
+        }
+        *iters = it;
+        *sr_out = worst;
+        phase_end(rslot, s, PH_REFINE, 0.0);
+        return check_err(status);
+    }
 };
 
 }  // namespace hplgb
 
 using namespace hplgb;
 
+// Right-hand sides refined as one block: several, with classic refinement.
+static int64_t block_rhs(int64_t nrhs, const Opts& o) { return (nrhs > 1 && o.refine == HPL_REFINE_IR) ? nrhs : 0; }
+
 extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts) {
-    (void)nrhs;
     Opts o = resolve_opts(opts, kMxpDefaultNb);
     int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
-    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr);
+    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o));
 }
 
 extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
@@ -882,10 +1169,11 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     mx.A = A;
     mx.lda = lda;
     mx.seed = seed;
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
+    mx.nblk = A ? block_rhs(nrhs, o) : 0;       // the block residual reads a stored A
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk);
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     int st = mx.factor(info);
@@ -898,13 +1186,18 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     int worst = HPL_OK;
     double worst_sr = 0.0;
     int max_it = 0, inner = 0;
-    for (int64_t c = 0; c < nrhs; c++) {
-        int it = 0, status = HPL_OK;
-        double sr = 0.0;
-        if ((st = mx.refine(B + c * ldb, X + c * ldx, &it, &inner, &sr, &status))) return st;
-        if (status != HPL_OK && worst == HPL_OK) worst = status;
-        max_it = std::max(max_it, it);
-        worst_sr = std::max(worst_sr, sr);
+    if (mx.nblk) {
+        if ((st = mx.refine_block(nrhs, B, ldb, X, ldx, &max_it, &worst_sr, &worst))) return st;
+        inner = max_it + 1;
+    } else {
+        for (int64_t c = 0; c < nrhs; c++) {
+            int it = 0, status = HPL_OK;
+            double sr = 0.0;
+            if ((st = mx.refine(B + c * ldb, X + c * ldx, &it, &inner, &sr, &status))) return st;
+            if (status != HPL_OK && worst == HPL_OK) worst = status;
+            max_it = std::max(max_it, it);
+            worst_sr = std::max(worst_sr, sr);
+        }
     }
     h.status = worst;
     if (h.info != 0 && worst == HPL_OK) h.status = HPL_ERR_SINGULAR;
@@ -938,22 +1231,28 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     mx.A = A;
     mx.lda = lda;
     mx.trans = true;
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr);
+    mx.nblk = block_rhs(nrhs, o);
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk);
     if (ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws);
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk);
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     HPL_CUDA_TRY(cudaMemsetAsync(mx.w.err, 0, sizeof(int) * 4, s));
     int st, worst = HPL_OK, max_it = 0, inner = 0;
     double worst_sr = 0.0;
-    for (int64_t c = 0; c < nrhs; c++) {
-        int it = 0, status = HPL_OK;
-        double sr = 0.0;
-        if ((st = mx.refine(G + c * ldg, gradB + c * ldgb, &it, &inner, &sr, &status))) return st;
-        if (status != HPL_OK && worst == HPL_OK) worst = status;
-        max_it = std::max(max_it, it);
-        worst_sr = std::max(worst_sr, sr);
+    if (mx.nblk) {
+        if ((st = mx.refine_block(nrhs, G, ldg, gradB, ldgb, &max_it, &worst_sr, &worst))) return st;
+        inner = max_it + 1;
+    } else {
+        for (int64_t c = 0; c < nrhs; c++) {
+            int it = 0, status = HPL_OK;
+            double sr = 0.0;
+            if ((st = mx.refine(G + c * ldg, gradB + c * ldgb, &it, &inner, &sr, &status))) return st;
+            if (status != HPL_OK && worst == HPL_OK) worst = status;
+            max_it = std::max(max_it, it);
+            worst_sr = std::max(worst_sr, sr);
+        }
     }
     if (gradA && nrhs > 0) {
         dim3 g((unsigned)((n + 63) / 64), (unsigned)((n + 63) / 64));

@@ -45,14 +45,15 @@ def test_adjoint_matches_finite_differences_n64(hpl, orc):
         assert abs(fd - gB[i, c]) <= 1e-6 * max(1.0, abs(gB[i, c])), (i, c, fd, gB[i, c])
 
 
-@pytest.mark.parametrize("n,nrhs,nb", [(512, 4, 128), (1000, 2, 256)])
-def test_adjoint_matches_oracle(hpl, orc, n, nrhs, nb):
+@pytest.mark.parametrize("refine", [1, 0])     # GMRES per column; classic refinement on the block
+@pytest.mark.parametrize("n,nrhs,nb", [(512, 4, 128), (1000, 2, 256), (777, 70, 128)])
+def test_adjoint_matches_oracle(hpl, orc, n, nrhs, nb, refine):
     import torch
     A = hpl.generate(22, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT)
     B = hpl.generate(22, hpl.STREAM_B, n, nrhs)
     G = torch.from_numpy(np.random.default_rng(6).standard_normal((n, nrhs))).cuda()
-    X, info, ws = hpl.mxp_solve(A, B, nb=nb)
-    gB, gA, binfo = hpl.lu_solve_backward(A, X, G, ws, nb=nb)
+    X, info, ws = hpl.mxp_solve(A, B, nb=nb, refine=refine)
+    gB, gA, binfo = hpl.lu_solve_backward(A, X, G, ws, nb=nb, refine=refine)
     torch.cuda.synchronize()
     assert info.read()["status"] == 0 and binfo.read()["status"] == 0
     ogB, ogA = orc.adjoint(_np(A), _np(X), _np(G))
@@ -60,7 +61,8 @@ def test_adjoint_matches_oracle(hpl, orc, n, nrhs, nb):
     assert np.abs(_np(gA) - ogA).max() <= 1e-9 * np.abs(ogA).max()
 
 
-def test_adjoint_closed_forms(hpl):
+@pytest.mark.parametrize("refine", [1, 0])
+def test_adjoint_closed_forms(hpl, refine):
     import torch
     n, nrhs = 48, 2
     d = torch.tensor([2.0 ** (k % 5 - 2) for k in range(n)], dtype=torch.float64, device="cuda")
@@ -69,15 +71,16 @@ def test_adjoint_closed_forms(hpl):
     A.diagonal().copy_(d)
     G = torch.arange(n * nrhs, dtype=torch.float64, device="cuda").reshape(n, nrhs) / 7.0
     B = torch.ones(n, nrhs, dtype=torch.float64, device="cuda")
-    X, info, ws = hpl.mxp_solve(A, B, nb=16)
-    gB, gA, _ = hpl.lu_solve_backward(A, X, G, ws, nb=16)
+    X, info, ws = hpl.mxp_solve(A, B, nb=16, refine=refine)
+    gB, gA, _ = hpl.lu_solve_backward(A, X, G, ws, nb=16, refine=refine)
     torch.cuda.synchronize()
     assert torch.allclose(gB, G / d[:, None], rtol=1e-12, atol=0)
     assert torch.allclose(gA, -gB @ X.t(), rtol=1e-14, atol=1e-300)
 
 
 @pytest.mark.slow
-def test_adjoint_n4096_64rhs(hpl, orc):
+@pytest.mark.parametrize("refine", [1, 0])
+def test_adjoint_n4096_64rhs(hpl, orc, refine):
     """The differentiable-solve configuration: n = 4096 dominant A, 64 right-hand
     sides, forward BF16 factor + FP64 refinement, backward on the saved factor,
     compared with the oracle's FP64 adjoint."""
@@ -86,8 +89,8 @@ def test_adjoint_n4096_64rhs(hpl, orc):
     A = hpl.generate(23, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT)
     B = hpl.generate(23, hpl.STREAM_B, n, nrhs)
     G = torch.from_numpy(np.random.default_rng(7).standard_normal((n, nrhs))).cuda()
-    X, info, ws = hpl.mxp_solve(A, B, nb=nb)
-    gB, gA, binfo = hpl.lu_solve_backward(A, X, G, ws, nb=nb)
+    X, info, ws = hpl.mxp_solve(A, B, nb=nb, refine=refine)
+    gB, gA, binfo = hpl.lu_solve_backward(A, X, G, ws, nb=nb, refine=refine)
     torch.cuda.synchronize()
     assert info.read()["status"] == 0 and binfo.read()["status"] == 0
     ogB, ogA = orc.adjoint(_np(A), _np(X), _np(G))

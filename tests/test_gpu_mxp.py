@@ -134,6 +134,45 @@ def test_mxp_full_size_n98304(hpl, orc, prec, stored):
     assert orc.scaled_residual_gen(seed, n, True, _np(x)[:, 0], _np(b)) < 16
 
 
+@pytest.mark.parametrize("n,nrhs,nb,prec", [(1000, 7, 256, 0), (777, 70, 128, 1), (130, 2, 64, 0)])
+def test_mxp_block_refinement(hpl, orc, n, nrhs, nb, prec):
+    """Several right-hand sides with classic refinement: the columns are refined
+    together (block residual, block preconditioner); every column meets the
+    residual test (recomputed by the oracle) and the forward-error bound."""
+    import torch
+    A = hpl.generate(9, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT)
+    B = hpl.generate(9, hpl.STREAM_B, n, nrhs)
+    X, info, ws = hpl.mxp_solve(A, B, nb=nb, refine=hpl.REFINE_IR, prec=prec)
+    torch.cuda.synchronize()
+    rec = info.read()
+    assert rec["status"] == 0 and rec["scaled_residual"] < 16, rec
+    A0, B0, Xg = _np(A).copy(order="F"), _np(B), _np(X)
+    kappa = np.linalg.cond(A0, np.inf)
+    for c in range(nrhs):
+        assert orc.scaled_residual(A0, Xg[:, c].copy(), B0[:, c].copy()) < 16, c
+        x64, _ = orc.solve(A0, B0[:, c].copy())
+        assert np.abs(Xg[:, c] - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * kappa, c
+    # the same columns refined one by one (GMRES) agree to the same bound
+    Xs, info1, _ = hpl.mxp_solve(A, B, nb=nb, prec=prec)
+    torch.cuda.synchronize()
+    assert info1.read()["status"] == 0
+    assert np.abs(_np(Xs) - Xg).max() / np.abs(Xg).max() < 4 * 16 * n * EPS * kappa
+
+
+def test_mxp_regenerated_matrix_several_rhs(hpl, orc):
+    """A = NULL with several right-hand sides and classic refinement: the
+    block residual needs the stored matrix, so the columns are refined one by
+    one against the regenerated matrix."""
+    import torch
+    n, nrhs, seed = 300, 3, 4
+    B = hpl.generate(seed, hpl.STREAM_B, n, nrhs)
+    X, info, _ = hpl.mxp_solve(None, B, nb=64, refine=hpl.REFINE_IR, seed=seed)
+    torch.cuda.synchronize()
+    assert info.read()["status"] == 0
+    for c in range(nrhs):
+        assert orc.scaled_residual_gen(seed, n, True, _np(X)[:, c].copy(), _np(B)[:, c].copy()) < 16
+
+
 @pytest.mark.parametrize("n,nb,prec", [(1000, 256, 0), (777, 128, 1), (64, 64, 0), (1, 8, 0)])
 def test_mxp_regenerated_matrix(hpl, orc, n, nb, prec):
     """A = NULL: the library generates the FP32 working copy itself and
