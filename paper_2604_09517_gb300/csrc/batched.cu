@@ -106,6 +106,9 @@ __device__ void upd64(double* A, long long lda, const double* P, int prow, int m
                     int r = ti + tx + 16 * i, c = tj + ty + 16 * j;
                     acc[i][j] = (r < m && c < nn) ? A[(c0 + c) * lda + r0 + r] : 0.0;
                 }
+            // 16-row / 16-column groups entirely outside the matrix are skipped
+            // (CTA-uniform bounds): FP64 issue slots are the scarce resource
+            const int ni = min(4, (m - ti + 15) / 16), nj = min(4, (nn - tj + 15) / 16);
             for (int kq = 0; kq < kb; kq++) {
                 double a[4], bb[4];
 #pragma unroll
@@ -117,8 +120,11 @@ __device__ void upd64(double* A, long long lda, const double* P, int prow, int m
                 for (int j = 0; j < 4; j++) bb[j] = Us[kq * 65 + ty + 16 * j];
 #pragma unroll
                 for (int j = 0; j < 4; j++)
+                    if (j < nj) {
 #pragma unroll
-                    for (int i = 0; i < 4; i++) acc[i][j] = fma(-a[i], bb[j], acc[i][j]);
+                        for (int i = 0; i < 4; i++)
+                            if (i < ni) acc[i][j] = fma(-a[i], bb[j], acc[i][j]);
+                    }
             }
 #pragma unroll
             for (int j = 0; j < 4; j++)
@@ -226,24 +232,53 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
     }
     __syncthreads();
     if (threadIdx.x == 0 && first_zero) info->info = first_zero;
-    // solve: P b, L forward, U backward (column-oriented, one sync per column)
+    // solve: P b, then L forward and U backward in blocks of 32 rows: warp 0
+    // solves the diagonal block with shuffles, then every thread updates its
+    // rows outside the block. Each b_i sees the same FMAs in the same order as
+    // column-by-column substitution, with two block barriers per 32 columns.
     double* b = S.b;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (threadIdx.x == 0)
         for (int k = 0; k < n; k++) {
             int p = S.ipiv[k];
             if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
         }
     __syncthreads();
-    for (int j = 0; j < n; j++) {
-        const double xj = b[j];
-        for (int i = j + 1 + threadIdx.x; i < n; i += THREADS) b[i] = fma(-A[(long long)j * lda + i], xj, b[i]);
+    for (int j0 = 0; j0 < n; j0 += 32) {
+        const int jb = min(32, n - j0);
+        if (warp == 0) {
+            double v = lane < jb ? b[j0 + lane] : 0.0;
+            for (int j = 0; j < jb; j++) {
+                const double xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane > j && lane < jb) v = fma(-A[(long long)(j0 + j) * lda + j0 + lane], xj, v);
+            }
+            if (lane < jb) b[j0 + lane] = v;
+        }
+        __syncthreads();
+        for (int i = j0 + jb + threadIdx.x; i < n; i += THREADS) {
+            double acc = b[i];
+            for (int j = 0; j < jb; j++) acc = fma(-A[(long long)(j0 + j) * lda + i], b[j0 + j], acc);
+            b[i] = acc;
+        }
         __syncthreads();
     }
-    for (int j = n - 1; j >= 0; j--) {
-        if (threadIdx.x == 0) b[j] = b[j] / A[(long long)j * lda + j];
+    for (int j1 = n; j1 > 0; j1 -= 32) {
+        const int j0 = max(0, j1 - 32), jb = j1 - j0;
+        if (warp == 0) {
+            double v = lane < jb ? b[j0 + lane] : 0.0;
+            for (int j = jb - 1; j >= 0; j--) {
+                if (lane == j) v = v / A[(long long)(j0 + j) * lda + j0 + j];
+                const double xj = __shfl_sync(0xffffffffu, v, j);
+                if (lane < j) v = fma(-A[(long long)(j0 + j) * lda + j0 + lane], xj, v);
+            }
+            if (lane < jb) b[j0 + lane] = v;
+        }
         __syncthreads();
-        const double xj = b[j];
-        for (int i = threadIdx.x; i < j; i += THREADS) b[i] = fma(-A[(long long)j * lda + i], xj, b[i]);
+        for (int i = threadIdx.x; i < j0; i += THREADS) {
+            double acc = b[i];
+            for (int j = jb - 1; j >= 0; j--) acc = fma(-A[(long long)(j0 + j) * lda + i], b[j0 + j], acc);
+            b[i] = acc;
+        }
         __syncthreads();
     }
     if (threadIdx.x == 0) info->status = first_zero ? HPL_ERR_SINGULAR : HPL_OK;
@@ -280,8 +315,55 @@ __device__ void gemm32(int m, int nn, int kb, const float* A, long long lda, con
 
 // Block LU without pivoting of W (FP32 copy of A); D^-1 in Dinv. X, R: SMEM
 // NB x NB FP32 scratch.
+// A22 (m x m, ld ld) -= bf16(L21) (m x kb) bf16(A12) (kb x m), FP32
+// accumulation in increasing k, then one subtraction (the order of gemm32):
+// the operands are rounded once into shared memory (scratch: 2 m kb floats),
+// then 64 x 64 output tiles with a 4 x 4 register tile per thread.
+__device__ void upd32(int m, int kb, const float* L21, const float* A12, float* A22, long long ld, float* scratch) {
+    float* Lr = scratch;              // Lr[q * m + i] = bf16(L21(i, q))
+    float* Ur = scratch + m * kb;     // Ur[j * kb + q] = bf16(A12(q, j))
+    for (int e = threadIdx.x; e < m * kb; e += THREADS) {
+        const int q = e / m, i = e - q * m;
+        Lr[e] = bfr(L21[(long long)q * ld + i]);
+    }
+    for (int e = threadIdx.x; e < m * kb; e += THREADS) {
+        const int j = e / kb, q = e - j * kb;
+        Ur[e] = bfr(A12[(long long)j * ld + q]);
+    }
+    __syncthreads();
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    for (int tj = 0; tj < m; tj += 64)
+        for (int ti = 0; ti < m; ti += 64) {
+            float acc[4][4] = {};
+            int r[4], c[4];
+#pragma unroll
+            for (int i = 0; i < 4; i++) {
+                r[i] = min(ti + tx + 16 * i, m - 1);
+                c[i] = min(tj + ty + 16 * i, m - 1);
+            }
+            for (int q = 0; q < kb; q++) {
+                float a[4], b[4];
+#pragma unroll
+                for (int i = 0; i < 4; i++) a[i] = Lr[q * m + r[i]];
+#pragma unroll
+                for (int j = 0; j < 4; j++) b[j] = Ur[c[j] * kb + q];
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+#pragma unroll
+                    for (int i = 0; i < 4; i++) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++)
+#pragma unroll
+                for (int i = 0; i < 4; i++) {
+                    const int rr = ti + tx + 16 * i, cc = tj + ty + 16 * j;
+                    if (rr < m && cc < m) A22[(long long)cc * ld + rr] -= acc[i][j];
+                }
+        }
+}
+
 template <int NB>
-__device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* info) {
+__device__ void blocklu32(const Sys& S, float* X, float* R, float* T, float* scratch, hpl_info* info) {
     const int n = (int)S.n;
     float* W = S.W;
     for (int e = threadIdx.x; e < n * n; e += THREADS) {
@@ -333,7 +415,7 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, hpl_info* 
                 }
                 __syncthreads();
             }
-            gemm32(m, m, kb, A21, n, A12, n, A22, n, 1, 0);              // A22 -= L21 A12
+            upd32(m, kb, A21, A12, A22, n, scratch);                   // A22 -= L21 A12
             __syncthreads();
         }
     }
@@ -380,16 +462,22 @@ __device__ void precond32(const Sys& S, const double* v, double* out) {
     __syncthreads();
 }
 
-// r = b - A x (FP64), returns the HPL scaled residual.
-__device__ double resid64(const Sys& S, const double* x, const double* b, double* r, double* red) {
+// r = b - A x (FP64), returns the HPL scaled residual. ||A||_inf is summed on
+// the first call (*anorm < 0) and reused after (FP64 instructions are scarce).
+__device__ double resid64(const Sys& S, const double* x, const double* b, double* r, double* red, double* anorm) {
     const int n = (int)S.n;
+    const bool sum_norm = *anorm < 0.0;
     double rmax = 0.0, amax = 0.0, xmax = 0.0, bmax = 0.0;
     for (int i = threadIdx.x; i < n; i += THREADS) {
         double s = 0.0, a = 0.0;
-        for (int j = 0; j < n; j++) {
-            double v = S.A[(long long)j * S.lda + i];
-            s = fma(v, x[j], s);
-            a += fabs(v);
+        if (sum_norm) {
+            for (int j = 0; j < n; j++) {
+                double v = S.A[(long long)j * S.lda + i];
+                s = fma(v, x[j], s);
+                a += fabs(v);
+            }
+        } else {
+            for (int j = 0; j < n; j++) s = fma(S.A[(long long)j * S.lda + i], x[j], s);
         }
         r[i] = b[i] - s;
         rmax = fmax(rmax, fabs(r[i]) != fabs(r[i]) ? INFINITY : fabs(r[i]));
@@ -398,16 +486,18 @@ __device__ double resid64(const Sys& S, const double* x, const double* b, double
         bmax = fmax(bmax, fabs(b[i]));
     }
     rmax = block_max(rmax, red);
-    amax = block_max(amax, red);
+    if (sum_norm) *anorm = block_max(amax, red);
+    amax = *anorm;
     xmax = block_max(xmax, red);
     bmax = block_max(bmax, red);
     return rmax / (0x1p-53 * (amax * xmax + bmax) * (double)n);
 }
 
 template <int NB>
-__device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float* T, double* red, hpl_info* info) {
+__device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float* T, float* scratch, double* red,
+                        hpl_info* info) {
     const int n = (int)S.n;
-    blocklu32<NB>(S, X, R, T, info);
+    blocklu32<NB>(S, X, R, T, scratch, info);
     double* bx = S.b;             // b in, x out
     double* r = S.r;
     double* b0 = S.r + n;         // keep b
@@ -415,10 +505,10 @@ __device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float
     __syncthreads();
     precond32<NB>(S, b0, bx);
     int it = 0;
-    double sr = INFINITY;
+    double sr = INFINITY, anorm = -1.0;
     int status = HPL_ERR_NOT_CONVERGED;
     for (;;) {
-        sr = resid64(S, bx, b0, r, red);
+        sr = resid64(S, bx, b0, r, red, &anorm);
         if (!(sr == sr) || sr == INFINITY) { status = HPL_ERR_NONFINITE; break; }
         if (sr < H->tol) { status = HPL_OK; break; }
         if (it >= H->max_iter) break;
@@ -625,8 +715,9 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
             if (S.variant) lu64<16>(S, P, Us, red, redi, info);
             else lu64<32>(S, P, Us, red, redi, info);
         } else {
-            if (S.variant) mxp_one<16>(S, H, X, R, T, red, info);
-            else mxp_one<32>(S, H, X, R, T, red, info);
+            // the FP64 panel area is free in this path: bf16 operand copies
+            if (S.variant) mxp_one<16>(S, H, X, R, T, (float*)P, red, info);
+            else mxp_one<32>(S, H, X, R, T, (float*)P, red, info);
         }
         __syncthreads();
     }
