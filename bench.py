@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--n", type=int, default=32768)
     ap.add_argument("--nb", type=int, default=256)
     ap.add_argument("--seed", type=int, default=1)
-    ap.add_argument("--cpu-sample-n", type=int, default=6144)
+    ap.add_argument("--cpu-sample-n", type=int, default=8192)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-mxp", action="store_true", help="skip the mixed-precision solve")
@@ -186,6 +186,47 @@ def time_oracle(n: int, seed: int):
     return dt, oracle.num_threads(), oracle.scaled_residual(A, x, b)
 
 
+def time_oracle_one_core(n: int, seed: int):
+    """The oracle's getrf + getrs of one n-system on a single host core (a
+    child process with OMP_NUM_THREADS=1, so the parent's thread pool is
+    untouched)."""
+    code = ("import sys, time; sys.path.insert(0, %r); import oracle; "
+            "A = oracle.generate(%d, oracle.STREAM_A, %d, %d); b = oracle.generate(%d, oracle.STREAM_B, %d, 1)[:, 0]; "
+            "t0 = time.perf_counter(); LU, ip, info, _ = oracle.getrf(A); x = oracle.getrs(LU, ip, b); "
+            "print(time.perf_counter() - t0)") % (ROOT, seed, n, n, seed, n)
+    env = dict(os.environ, OMP_NUM_THREADS="1")
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=600)
+    return float(out.stdout.strip().splitlines()[-1])
+
+
+def time_oracle_batched(seed: int, count: int, sample: int):
+    """The oracle on a sample of the batched workload's systems (the first
+    sample/2 general ones and the first sample/2 dominant ones), and the
+    whole batch extrapolated by credited flops of each kind."""
+    import numpy as np
+
+    import oracle
+    n = oracle.batch_sizes(seed, count)
+    half = count // 2
+    t = {0: 0.0, 1: 0.0}
+    fl = {0: 0.0, 1: 0.0}
+    for s in list(range(sample // 2)) + list(range(half, half + sample // 2)):
+        kind = 0 if s < half else 1
+        m = int(n[s])
+        A = oracle.generate(seed, oracle.batch_stream_a(s), m, m, dominant=bool(kind))
+        b = oracle.generate(seed, oracle.batch_stream_b(s), m, 1)[:, 0]
+        t0 = time.perf_counter()
+        if kind == 0:
+            oracle.solve(A, b)
+        else:
+            oracle.mxp_solve(A, b, 16, prec=oracle.PREC_BF16, refine=0, ns_iters=3)
+        t[kind] += time.perf_counter() - t0
+        fl[kind] += flops(m)
+    total_fl = {k: sum(flops(int(m)) for s, m in enumerate(n) if (s >= half) == bool(k)) for k in (0, 1)}
+    est = sum(t[k] * total_fl[k] / fl[k] for k in (0, 1) if fl[k] > 0)
+    return sum(t.values()), est, oracle.num_threads()
+
+
 def run_reference(a, d: Dist):
     if d.rank != 0:
         return
@@ -277,7 +318,14 @@ def run_batched(a, d: Dist, dev):
     value = work * len(step_ms) / (total_ms * 1e-3) / 1e12
     fp64_work = float(sum(flops(int(m)) for m, k in zip(n_all, kind_all) if k == 0))
     dom = [r["iters"] for r, k in zip(recs, kind) if k == 1]
-    return {"workload": f"batched_{count}_n32to512_half_fp64_half_bf16ir", "systems": count, "value": value,
+    extra = {}
+    if d.rank == 0 and not a.no_cpu:
+        sample = min(64, count)
+        t_s, t_est, cores = time_oracle_batched(a.seed, count, sample)
+        extra = {"cpu_oracle_sample": f"{sample} systems ({sample // 2} general, {sample // 2} dominant), "
+                                      f"{t_s:.2f} s on {cores} cores; whole batch extrapolated by flops of each kind",
+                 "cpu_oracle_extrapolated_ms": t_est * 1e3}
+    return {**extra, "workload": f"batched_{count}_n32to512_half_fp64_half_bf16ir", "systems": count, "value": value,
             "unit": "TFLOP/s", "ms_per_step": total_ms / len(step_ms), "solved_ok": ok,
             "flops_per_step": work, "fp64_share_of_flops": fp64_work / work, "cuda_graph": True,
             "gpu_launches_per_step": 1, "scaling": "strong" if d.world > 1 else None,
@@ -313,13 +361,88 @@ def run_adjoint(a, d: Dist, dev):
             fwd.append(e0.elapsed_time(e1))
             bwd.append(e1.elapsed_time(e2))
     fi, bi = info.read(), binfo.read()
-    return {"workload": "diff_solve_n4096_nrhs64", "refinement": "classic, all 64 columns as one block",
+    extra = {}
+    if d.rank == 0 and not a.no_cpu:
+        import oracle
+        A0, B0, G0 = A.cpu().numpy(), B.cpu().numpy(), G.cpu().numpy()
+        t0 = time.perf_counter()
+        X0, _ = oracle.solve(A0, B0)
+        t1 = time.perf_counter()
+        oracle.adjoint(A0, X0, G0)
+        t2 = time.perf_counter()
+        extra = {"cpu_oracle_forward_ms": (t1 - t0) * 1e3, "cpu_oracle_backward_ms": (t2 - t1) * 1e3,
+                 "cpu_oracle_cores": oracle.num_threads(),
+                 "cpu_oracle_kind": "FP64 getrf+getrs; adjoint = its own FP64 LU, transposed solves, outer product"}
+    return {**extra, "workload": "diff_solve_n4096_nrhs64", "refinement": "classic, all 64 columns as one block",
             "forward_ms": sum(fwd) / len(fwd),
             "backward_ms": sum(bwd) / len(bwd), "forward_status": fi["status_name"],
             "backward_status": binfo.read()["status_name"], "forward_scaled_residual": fi["scaled_residual"],
             "backward_scaled_residual": bi["scaled_residual"], "forward_iters": fi["iters"],
             "backward_iters": bi["iters"],
             "grad_a_outer_product_gflop": 2.0 * n * n * nrhs / 1e9}
+
+
+def step_model(recs, n: int, nb: int, measured_ms: float):
+    """Per-step phase times of the last timed FP64 solve and a fit of the
+    per-step performance model (paper Sec. III-A.1, without the broadcast on
+    one GPU): step k costs SWAP(k) + TRSM(k) + max(update(k), PFACT(k+1)),
+    the panel of step k+1 running beside the update. Each phase time is fitted
+    as work / rate + fixed cost by least squares."""
+    import numpy as np
+    ph, st, ms, wk = recs["phase"], recs["step"], recs["ms"], recs["work"]
+    # the last solve: from the last record of PFACT step 0 on
+    first = np.nonzero((ph == 0) & (st == 0))[0]
+    if first.size == 0:
+        return None
+    sel = np.arange(first[-1], ph.size)
+    ph, st, ms, wk = ph[sel], st[sel], ms[sel], wk[sel]
+    nsteps = (n + nb - 1) // nb
+    t = np.zeros((4, nsteps))
+    w = np.zeros((4, nsteps))
+    for p_, k_, m_, w_ in zip(ph, st, ms, wk):
+        if 0 <= p_ <= 3 and 0 <= k_ < nsteps:
+            t[p_, k_] += m_
+            w[p_, k_] += w_
+
+    def fit(p_):
+        mask = w[p_] > 0
+        if mask.sum() < 1:
+            return None, None
+        x, y = w[p_][mask], t[p_][mask]
+        if mask.sum() < 2 or np.ptp(x) <= 1e-6 * x.max():
+            return y.sum() / x.sum(), 0.0          # same work every step: a rate only
+        X = np.stack([x, np.ones(x.size)], axis=1)
+        coef, *_ = np.linalg.lstsq(X, y, rcond=None)
+        return coef[0], coef[1]
+
+    fits = {p_: fit(p_) for p_ in range(4)}
+
+    def pred(p_, k_):
+        a_, b_ = fits[p_]
+        return a_ * w[p_, k_] + b_ if a_ is not None and w[p_, k_] > 0 else 0.0
+
+    total = 0.0
+    exposed, swap_over = None, None
+    for k_ in range(nsteps):
+        tu = pred(3, k_)
+        tp = pred(0, k_ + 1) if k_ + 1 < nsteps else 0.0
+        total += pred(1, k_) + pred(2, k_) + max(tu, tp)
+        if exposed is None and t[0, k_ + 1 if k_ + 1 < nsteps else k_] > t[3, k_] and k_ + 1 < nsteps:
+            exposed = k_
+        if swap_over is None and t[1, k_] > t[3, k_] and t[3, k_] > 0:
+            swap_over = k_
+    rate = lambda p_, scale: (1.0 / fits[p_][0] / scale) if fits[p_][0] else None
+    every = max(1, nsteps // 8)
+    rows = [[k_, n - k_ * nb, round(t[3, k_], 3), round(t[0, k_], 3), round(t[1, k_], 3), round(t[2, k_], 3)]
+            for k_ in range(0, nsteps, every)]
+    return {"model": "T_k = SWAP_k + TRSM_k + max(UPDATE_k, PFACT_{k+1}); phase = work / rate + fixed (least squares)",
+            "fit": {"update_tflops": rate(3, 1e9), "update_fixed_ms": fits[3][1],
+                    "pfact_gflops": rate(0, 1e6), "pfact_fixed_ms": fits[0][1],
+                    "swap_gbs": rate(1, 1e6), "swap_fixed_ms": fits[1][1],
+                    "trsm_gflops": rate(2, 1e6), "trsm_fixed_ms": fits[2][1]},
+            "predicted_ms": total, "measured_ms": measured_ms,
+            "panel_not_hidden_from_step": exposed, "swap_exceeds_update_from_step": swap_over,
+            "steps_columns": ["k", "rows", "update_ms", "pfact_ms", "swap_ms", "trsm_ms"], "steps": rows}
 
 
 def run_small(a, d: Dist, dev):
@@ -360,12 +483,13 @@ def run_small(a, d: Dist, dev):
         dt, cores, _ = time_oracle(n, seed)
         out["cpu_oracle_ms"] = dt * 1e3
         out["cpu_oracle_cores"] = cores
+        out["cpu_oracle_one_core_ms"] = time_oracle_one_core(n, seed) * 1e3
     del A, flush
     torch.cuda.empty_cache()
     return out
 
 
-def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False):
+def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
     """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
     block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
     prec = 1) + FP64 GMRES refinement. regen: the library regenerates A from
@@ -412,7 +536,17 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False):
     del A, X, ws
     torch.cuda.empty_cache()
     tag = "fp8e4m3" if prec else "bf16"
-    return {"workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
+    # the factorization alone: the step minus its refinement phase
+    refine_ms = phases["refine"][0] / len(step_ms) if phases["refine"][2] else 0.0
+    factor_ms = total_ms / len(step_ms) - refine_ms
+    factor_tf = (2.0 * n ** 3 / 3.0) / (factor_ms * 1e-3) / 1e12 if factor_ms > 0 else None
+    extra = {"factor_ms": factor_ms, "refine_ms": refine_ms, "factor_tflops": factor_tf,
+             f"factor_fraction_of_{tag}_peak": factor_tf / peak if factor_tf else None}
+    if cpu and cpu.get("seconds_at_sample_n"):
+        sn = a.cpu_sample_n
+        extra["cpu_oracle_fp64_lu_extrapolated_s"] = cpu["seconds_at_sample_n"] * (n / sn) ** 3
+        extra["cpu_oracle_basis"] = f"oracle FP64 getrf+getrs at n={sn} x (n/{sn})^3"
+    return {**extra, "workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
             "ms_per_step": total_ms / len(step_ms), "steps": a.steps, "warmup": a.warmup,
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
@@ -484,6 +618,7 @@ def run_ours(a, d: Dist):
         torch.cuda.synchronize(dev)
         d.barrier()
         step_ms.append(e0.elapsed_time(e1))
+    recs = hpl.phase_records()
     phases = hpl.phase_times()
     hpl.set_phase_timing(False)
     clk = clocks.stop()
@@ -493,6 +628,7 @@ def run_ours(a, d: Dist):
     total_ms = d.max(sum(step_ms))
     total_flops = d.sum(flops(n) * len(step_ms))
     value = total_flops / (total_ms * 1e-3) / 1e12
+    model = step_model(recs, n, nb, step_ms[-1])
 
     # roofline of the dominant kernel: the DGEMM trailing update (DFMA, FP64 ALU bound)
     upd_ms, upd_flops, upd_cnt = phases["update"]
@@ -545,15 +681,17 @@ def run_ours(a, d: Dist):
     cpu = None
     if d.rank == 0 and d.world == 1 and not a.no_cpu:
         dt, cores, _ = time_oracle(a.cpu_sample_n, seed)
+        scale = (n / a.cpu_sample_n) ** 3
         cpu = {"value": flops(a.cpu_sample_n) / dt / 1e12, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                "sample": f"oracle getrf+getrs (unblocked FP64, OpenMP) of one n={a.cpu_sample_n} system, "
-                         f"{dt:.1f} s"}
+                         f"{dt:.1f} s; n={n} extrapolated by n^3: {dt * scale:.0f} s",
+               "seconds_at_sample_n": dt, "extrapolated_seconds_at_n": dt * scale}
 
     del A, b, b0, ipiv, ws, sws
     torch.cuda.empty_cache()
     small = run_small(a, d, dev)
-    mxp = None if a.no_mxp else run_mxp(a, d, dev, value)
-    mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1)
+    mxp = None if a.no_mxp else run_mxp(a, d, dev, value, cpu=cpu)
+    mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1, cpu=cpu)
     mxp_regen = None if a.no_mxp else run_mxp(a, d, dev, value, regen=True)
     batched = None if a.no_batched else run_batched(a, d, dev)
     adjoint = None if a.no_adjoint else run_adjoint(a, d, dev)
@@ -569,7 +707,7 @@ def run_ours(a, d: Dist):
                              "kernel": "k_dgemm_sub (DFMA trailing update)",
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
-                "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report,
+                "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report, "step_model": model,
                 "fraction_of_fp64_peak": value / peak, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_regenerated": mxp_regen, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 

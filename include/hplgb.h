@@ -312,11 +312,20 @@ int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t ld
  * bytes moved for 1, 5 and 6) and the number of timed intervals, then clears
  * the record. ms, work, count: host arrays of 8, any may be NULL. Returns
  * HPL_ERR_CUDA if an event query fails.
+ * hplgb_phase_records returns the same intervals one by one, in the order
+ * they were opened, without clearing them (call it before hplgb_phase_times):
+ * phase id, factorization step k (lu_factor; -1 elsewhere), start relative to
+ * the first interval and duration in ms, algorithmic work. Host arrays of cap
+ * entries, any may be NULL; *count receives the number of intervals (which
+ * may exceed cap). This is the per-step breakdown the paper's performance
+ * model is written in.
  * hplgb_last_error: text of the last CUDA error the library met.
  */
 long long hplgb_launch_count(void);
 void hplgb_set_phase_timing(int on);
 int hplgb_phase_times(double* ms, double* work, long long* count);
+int hplgb_phase_records(int32_t* phase, int32_t* step, double* start_ms, double* ms, double* work, long long cap,
+                        long long* count);
 const char* hplgb_last_error(void);
 
 #ifdef __cplusplus

@@ -103,6 +103,7 @@ def load():
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
+            "hplgb_phase_records": (i32, [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -494,6 +495,22 @@ def phase_times() -> dict:
     cnt = np.zeros(len(PHASES), dtype=np.int64)
     _check(load().hplgb_phase_times(ms.ctypes.data, work.ctypes.data, cnt.ctypes.data), "hplgb_phase_times")
     return {name: (float(ms[i]), float(work[i]), int(cnt[i])) for i, name in enumerate(PHASES)}
+
+
+def phase_records(cap: int = 1 << 16) -> dict:
+    """The timed intervals one by one (call before phase_times, which clears
+    them): numpy arrays phase, step, start_ms, ms, work."""
+    import numpy as np
+    ph = np.zeros(cap, dtype=np.int32)
+    st = np.zeros(cap, dtype=np.int32)
+    t0 = np.zeros(cap)
+    ms = np.zeros(cap)
+    wk = np.zeros(cap)
+    cnt = ctypes.c_longlong(0)
+    _check(load().hplgb_phase_records(ph.ctypes.data, st.ctypes.data, t0.ctypes.data, ms.ctypes.data, wk.ctypes.data,
+                                      cap, ctypes.byref(cnt)), "hplgb_phase_records")
+    k = min(cnt.value, cap)
+    return {"phase": ph[:k], "step": st[:k], "start_ms": t0[:k], "ms": ms[:k], "work": wk[:k]}
 
 
 def flops(n: int) -> float:

@@ -105,6 +105,7 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 struct PhaseRec {
     cudaEvent_t a, b;
     int phase;
+    int step;      // factorization step k, or -1
     double work;
     bool used;
 };
@@ -127,11 +128,12 @@ int phase_begin(cudaStream_t s) {
     return idx;
 }
 
-void phase_end(int slot, cudaStream_t s, int phase, double work) {
+void phase_end(int slot, cudaStream_t s, int phase, double work, int step) {
     if (slot < 0) return;
     std::lock_guard<std::mutex> lk(g_ph_mu);
     PhaseRec& r = g_ph[slot];
     r.phase = phase;
+    r.step = step;
     r.work = work;
     r.used = cudaEventRecord(r.b, s) == cudaSuccess;
 }
@@ -144,6 +146,33 @@ extern "C" void hplgb_set_phase_timing(int on) {
     std::lock_guard<std::mutex> lk(hplgb::g_ph_mu);
     hplgb::g_ph_on = on;
     hplgb::g_ph_next = 0;
+}
+
+extern "C" int hplgb_phase_records(int32_t* phase, int32_t* step, double* start_ms, double* ms, double* work,
+                                   long long cap, long long* count) {
+    using namespace hplgb;
+    std::lock_guard<std::mutex> lk(g_ph_mu);
+    long long k = 0;
+    int first = -1;
+    for (size_t i = 0; i < g_ph_next; i++) {
+        PhaseRec& r = g_ph[i];
+        if (!r.used) continue;
+        if (cudaEventSynchronize(r.b) != cudaSuccess) return HPL_ERR_CUDA;
+        if (first < 0) first = (int)i;
+        if (k < cap) {
+            float t = 0.0f, t0 = 0.0f;
+            if (cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) return HPL_ERR_CUDA;
+            if (cudaEventElapsedTime(&t0, g_ph[first].a, r.a) != cudaSuccess) return HPL_ERR_CUDA;
+            if (phase) phase[k] = r.phase;
+            if (step) step[k] = r.step;
+            if (start_ms) start_ms[k] = t0;
+            if (ms) ms[k] = t;
+            if (work) work[k] = r.work;
+        }
+        k++;
+    }
+    if (count) *count = k;
+    return HPL_OK;
 }
 
 extern "C" int hplgb_phase_times(double* ms, double* work, long long* count) {

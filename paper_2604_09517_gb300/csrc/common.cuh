@@ -68,7 +68,7 @@ enum Phase {
     PH_COUNT = 8
 };
 int phase_begin(cudaStream_t s);                                   // -1 when timing is off
-void phase_end(int slot, cudaStream_t s, int phase, double work);  // work: flops or bytes
+void phase_end(int slot, cudaStream_t s, int phase, double work, int step = -1);  // work: flops or bytes
 
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

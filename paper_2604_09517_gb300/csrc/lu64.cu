@@ -618,7 +618,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
                                                            w.perm_dst + par * 2 * nb, w.perm_src + par * 2 * nb);
         HPL_LAUNCH_CHECK();
         // getrf of an m x kb panel: m kb^2 - kb^3/3 flops (leading terms)
-        phase_end(slot, ps, PH_PANEL, pm * kb * kb - (double)kb * kb * kb / 3.0);
+        phase_end(slot, ps, PH_PANEL, pm * kb * kb - (double)kb * kb * kb / 3.0, (int)k);
         return HPL_OK;
     };
 
@@ -642,7 +642,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
                                              w.perm_src + par * 2 * nb);
             HPL_LAUNCH_CHECK();
             // at most 2 kb rows move: read + write of each moved element
-            phase_end(slot, s, PH_SWAP, 2.0 * 2.0 * kb * (double)ncols_out * sizeof(double));
+            phase_end(slot, s, PH_SWAP, 2.0 * 2.0 * kb * (double)ncols_out * sizeof(double), (int)k);
         }
         if (c1 < n) {
             // DTRSM on the block row, then DGEMM: look-ahead columns first
@@ -650,13 +650,13 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
             int slot = phase_begin(s);
             st = launch_trsm(A, lda, c0, kb, c1, n, s);
             if (st) return st;
-            phase_end(slot, s, PH_TRSM, (double)kb * (kb - 1) * (double)m2);
+            phase_end(slot, s, PH_TRSM, (double)kb * (kb - 1) * (double)m2, (int)k);
             const int64_t la_cols = std::min(nb, n - c1);
             slot = phase_begin(s);
             st = launch_dgemm_sub(m2, la_cols, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda, A + c1 * lda + c1,
                                   lda, s);
             if (st) return st;
-            phase_end(slot, s, PH_UPDATE, 2.0 * m2 * la_cols * kb);
+            phase_end(slot, s, PH_UPDATE, 2.0 * m2 * la_cols * kb, (int)k);
             if (la) {
                 HPL_CUDA_TRY(cudaEventRecord(ev_la, s));
                 HPL_CUDA_TRY(cudaStreamWaitEvent(ps, ev_la, 0));
@@ -668,7 +668,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
                 st = launch_dgemm_sub(m2, n - c1 - la_cols, kb, A + c0 * lda + c1, lda, A + (c1 + la_cols) * lda + c0,
                                       lda, A + (c1 + la_cols) * lda + c1, lda, s);
                 if (st) return st;
-                phase_end(slot, s, PH_UPDATE, 2.0 * m2 * (n - c1 - la_cols) * kb);
+                phase_end(slot, s, PH_UPDATE, 2.0 * m2 * (n - c1 - la_cols) * kb, (int)k);
             }
             if (!la) {
                 st = panel(k + 1);

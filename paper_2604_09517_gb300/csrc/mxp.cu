@@ -248,18 +248,32 @@ __global__ void __launch_bounds__(256) k_abs_rowsum_max(int64_t n, int chunks, c
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
 
+// FP32 working copy F of A; on the way, the row sums of |F| over `stripes`
+// column stripes into part[stripe][row] (the refinement's ||A||_inf, reduced
+// by k_abs_rowsum_max), so the norm costs no extra pass over the matrix.
 __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda,
-                                                        float* __restrict__ F, int64_t ldf) {
-    const int64_t i0 = (int64_t)blockIdx.x * 1024 + threadIdx.x;
-    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
-        const double* a = A + j * lda;
-        float* f = F + j * ldf;
-#pragma unroll
-        for (int q = 0; q < 4; q++) {
-            const int64_t i = i0 + q * 256;
-            if (i < n) f[i] = (float)a[i];
-        }
+                                                        float* __restrict__ F, int64_t ldf, int stripes,
+                                                        float* __restrict__ part) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
+    const int64_t cw = (n + stripes - 1) / stripes;
+    const int64_t j0 = (int64_t)blockIdx.y * cw, j1 = std::min<int64_t>(n, j0 + cw);
+    float s0 = 0.0f, s1 = 0.0f;
+    int64_t j = j0;
+#pragma unroll 4
+    for (; j + 1 < j1; j += 2) {
+        const float f0 = (float)A[j * lda + i], f1 = (float)A[(j + 1) * lda + i];
+        F[j * ldf + i] = f0;
+        F[(j + 1) * ldf + i] = f1;
+        s0 += fabsf(f0);
+        s1 += fabsf(f1);
     }
+    if (j < j1) {
+        const float f0 = (float)A[j * lda + i];
+        F[j * ldf + i] = f0;
+        s0 += fabsf(f0);
+    }
+    part[(int64_t)blockIdx.y * n + i] = s0 + s1;
 }
 
 // Column-split GEMV for the preconditioner: part[s][r] = sum over the column
@@ -751,21 +765,21 @@ struct Mxp {
         HPL_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, s));
         int cslot = phase_begin(s);
         if (A) {
-            k_f64_to_f32_mat<<<dim3((unsigned)((n + 1023) / 1024), (unsigned)std::min<int64_t>(n, 2048)), 256, 0,
-                               s>>>(n, A, lda, w.F, ldf);
+            k_f64_to_f32_mat<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, A, lda, w.F, ldf,
+                                                                                            kGemvSplitMax, w.gpart);
             HPL_LAUNCH_CHECK();
         } else {
             int st = launch_generate_dominant_f32(seed, n, w.F, ldf, w.gdiag, &key, s);
             if (st) return st;
+            k_abs_rowsum_part<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, w.F, ldf,
+                                                                                              kGemvSplitMax, w.gpart);
+            HPL_LAUNCH_CHECK();
         }
         HPL_CUDA_TRY(cudaMemsetAsync(w.scal + 6, 0, sizeof(double), s));
-        k_abs_rowsum_part<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, w.F, ldf,
-                                                                                          kGemvSplitMax, w.gpart);
-        HPL_LAUNCH_CHECK();
         k_abs_rowsum_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, kGemvSplitMax, w.gpart,
                                                                      (unsigned long long*)(w.scal + 6));
         HPL_LAUNCH_CHECK();
-        phase_end(cslot, s, PH_CONVERT, A ? 16.0 * n * n : 8.0 * n * n);
+        phase_end(cslot, s, PH_CONVERT, A ? 12.0 * n * n : 8.0 * n * n);
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
             float* D = w.F + k0 * ldf + k0;
