@@ -70,6 +70,9 @@ typedef struct {
     int32_t ns_iters;    /* Newton-Schulz steps of each diagonal-block inverse, mixed precision (default 2, <= 8) */
     double tol;          /* scaled-residual target (default 16) */
     int64_t timeout_ns;  /* limit for any device-side wait (default 20 s) */
+    int32_t fp64_emulation; /* lu_factor: 0 = DFMA trailing update (default); 1 = the same update on the BF16
+                               tensor cores with FP64 accuracy (sliced products, see lu_factor) */
+    int32_t reserved;
 } hpl_opts;
 
 /* Result record, written on the device. Caller-allocated in device memory. */

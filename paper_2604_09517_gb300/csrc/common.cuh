@@ -40,6 +40,7 @@ struct Opts {
     int ns_iters;
     double tol;
     int64_t timeout_ns;
+    int fp64_emulation;
 };
 Opts resolve_opts(const hpl_opts* o, int64_t default_nb);
 

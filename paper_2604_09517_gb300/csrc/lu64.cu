@@ -11,6 +11,8 @@
 // and every FP64 phase is bound by the same FP64 pipe; keeping that pipe busy
 // is what look-ahead is for. The panel runs on a second, higher-priority
 // stream, so its CTAs take SMs as soon as update CTAs retire.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "common.cuh"
@@ -37,6 +39,13 @@ struct Cand {
     double vals[kLeafW];
 };
 
+// FP64 accuracy from the BF16 tensor cores (opts.fp64_emulation): see
+// emu_update below.
+constexpr int kEmuSlices = 11;         // 6-bit slices: 66 bits below the top bit of each row / column
+constexpr int kEmuBits = 6;
+constexpr int kEmuGroups = kEmuSlices; // weights 2^-6g, g = 2 .. kEmuSlices + 1
+constexpr int64_t kEmuChunk = 8192;    // columns of the trailing matrix per combine pass
+
 struct LuWs {
     PanelSync* sync;
     Cand* slots;        // [2][kMaxPanelCtas]
@@ -44,9 +53,19 @@ struct LuWs {
     int* perm_cnt;      // [2]
     int* perm_dst;      // [2][2*nb]
     int* perm_src;      // [2][2*nb]
+    int* emu_err;       // error word of the tensor-core GEMMs of the emulated update
+    size_t base_bytes;  // the part above, cleared at every factorization
+    // emulated update (absent unless requested)
+    uint16_t* sA;       // n x (kEmuSlices kbp) BF16 slices of L21, row-major
+    uint16_t* sB;       // n x (kEmuSlices kbp) BF16 slices of U12 (one column per row), slots reversed
+    int* eA;            // n row exponents of L21
+    int* eB;            // n column exponents of U12
+    float* cg;          // kEmuGroups x n x kEmuChunk FP32 group products
 };
 
-static size_t lu_ws_layout(int64_t nb, LuWs* w, char* base) {
+static int64_t emu_kbp(int64_t nb) { return (nb + 7) / 8 * 8; }
+
+static size_t lu_ws_layout(int64_t nb, LuWs* w, char* base, int64_t n_emu = 0) {
     size_t off = 0;
     auto take = [&](size_t bytes) {
         size_t o = off;
@@ -59,6 +78,14 @@ static size_t lu_ws_layout(int64_t nb, LuWs* w, char* base) {
     void* p3 = take(sizeof(int) * 2);
     void* p4 = take(sizeof(int) * 2 * 2 * nb);
     void* p5 = take(sizeof(int) * 2 * 2 * nb);
+    void* p6 = take(sizeof(int) * 4);
+    const size_t base_bytes = off;
+    const int64_t kbp = emu_kbp(nb), ne = n_emu;
+    void* q0 = take(sizeof(uint16_t) * ne * kEmuSlices * kbp);
+    void* q1 = take(sizeof(uint16_t) * ne * kEmuSlices * kbp);
+    void* q2 = take(sizeof(int) * ne);
+    void* q3 = take(sizeof(int) * ne);
+    void* q4 = take(sizeof(float) * kEmuGroups * ne * std::min<int64_t>(ne, kEmuChunk));
     if (w) {
         w->sync = (PanelSync*)p0;
         w->slots = (Cand*)p1;
@@ -66,6 +93,13 @@ static size_t lu_ws_layout(int64_t nb, LuWs* w, char* base) {
         w->perm_cnt = (int*)p3;
         w->perm_dst = (int*)p4;
         w->perm_src = (int*)p5;
+        w->emu_err = (int*)p6;
+        w->base_bytes = base_bytes;
+        w->sA = (uint16_t*)q0;
+        w->sB = (uint16_t*)q1;
+        w->eA = (int*)q2;
+        w->eB = (int*)q3;
+        w->cg = (float*)q4;
     }
     return off;
 }
@@ -478,12 +512,187 @@ __global__ void __launch_bounds__(256) k_dgemm_sub(int64_t m, int64_t nn, int64_
         }
 }
 
-__global__ void k_lu_finish(hpl_info* info, const PanelSync* sync) {
+__global__ void k_lu_finish(hpl_info* info, const PanelSync* sync, const int* emu_err) {
     if (threadIdx.x == 0 && blockIdx.x == 0) {
-        if (sync->abort) info->status = HPL_ERR_TIMEOUT;
+        if (sync->abort || *emu_err) info->status = HPL_ERR_TIMEOUT;
         else if (info->info != 0) info->status = HPL_ERR_SINGULAR;
         else info->status = HPL_OK;
     }
+}
+
+// ---------------------------------------------------------------------------
+// Trailing update with FP64 accuracy on the BF16 tensor cores (sliced products
+// after Ozaki, Ogita, Oishi & Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication", 2012; not
+// in the paper). Row i of L21 is 2^eA_i sum_s a_s 2^-6s and column j of U12 is
+// 2^eB_j sum_t b_t 2^-6t, with integer slices |a_s|, |b_t| < 64 (exact in
+// BF16) truncated from the 66 bits below the top bit of the row / column (so
+// that entries well below their row's or column's largest still keep about
+// 53 bits). A group g = s + t of slice products summed over at most
+// (g-1) kb <= 11 * 256 terms stays below 2^24, so one BF16 tensor-core product
+// with FP32 accumulation per group is exact; the groups are combined in 64-bit
+// integers and rounded to FP64:
+//   C(i,j) -= 2^(eA_i + eB_j) sum_{g=2..12} 2^-6g C_g(i,j).
+// Products with s + t > 12 are left out (below 2^(eA_i+eB_j-72) kb in size).
+
+__device__ __forceinline__ int emu_exp(unsigned long long absbits) {   // |x| < 2^e for the largest |x|
+    return absbits ? (int)(absbits >> 52) - 1022 : 0;
+}
+
+// 66-bit fixed-point magnitude of x relative to 2^e (|x| < 2^e), truncated,
+// as hi (the top 36 bits, slices 1..6) and lo (the next 30 bits, slices 7..11)
+__device__ __forceinline__ void emu_fixed(double x, int e, unsigned long long& hi, unsigned long long& lo) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
+    const int E = (int)(u >> 52);
+    hi = lo = 0ull;
+    if (E == 0) return;                            // zero and subnormals: below 2^-1022
+    const unsigned long long mant = (u & 0xfffffffffffffull) | (1ull << 52);
+    // x / 2^e = mant * 2^(E - 1075 - e); the 66-bit fixed point F = mant * 2^(E - 1009 - e)
+    const int sh = E - 1009 - e;                   // <= 13 since |x| < 2^e
+    // F = (hi << 30) | lo with hi < 2^36, lo < 2^30
+    if (sh >= 0) {                                 // F = mant << sh (< 2^66)
+        hi = mant >> (30 - sh);
+        lo = (mant << sh) & ((1ull << 30) - 1);
+    } else if (sh > -53) {
+        const unsigned long long f = mant >> (-sh);    // < 2^53: fits 64 bits
+        hi = f >> 30;
+        lo = f & ((1ull << 30) - 1);
+    }
+}
+
+// One warp per row i of L21 (m x kb, column-major): exponent and the
+// kEmuSlices slices into sA[i][s * kbp + q] (zeros for q >= kb).
+__global__ void __launch_bounds__(256) k_emu_slice_rows(int64_t m, int kb, int kbp, const double* __restrict__ L,
+                                                        int64_t ldl, __nv_bfloat16* __restrict__ sA, int64_t lds,
+                                                        int* __restrict__ eA) {
+    const int lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (i >= m) return;
+    unsigned long long mx = 0;
+    for (int q = lane; q < kb; q += 32) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(L[(int64_t)q * ldl + i]) & 0x7fffffffffffffffull;
+        mx = u > mx ? u : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    const int e = emu_exp(mx);
+    if (lane == 0) eA[i] = e;
+    __nv_bfloat16* row = sA + i * lds;
+    for (int q = lane; q < kbp; q += 32) {
+        const double x = q < kb ? L[(int64_t)q * ldl + i] : 0.0;
+        unsigned long long fh, fl;
+        emu_fixed(x, e, fh, fl);
+        const bool neg = x < 0.0;
+#pragma unroll
+        for (int sl = 1; sl <= kEmuSlices; sl++) {
+            const int a = sl <= 6 ? (int)((fh >> (36 - kEmuBits * sl)) & 63ull)
+                                  : (int)((fl >> (30 - kEmuBits * (sl - 6))) & 63ull);
+            row[(sl - 1) * kbp + q] = __int2bfloat16_rn(neg ? -a : a);
+        }
+    }
+}
+
+// One warp per column j of U12 (kb x nn, column-major): exponent and slices
+// into sB[j][(kEmuSlices - t) * kbp + q] (slot order reversed, so that the
+// B operand of group g is the last g-1 slots).
+__global__ void __launch_bounds__(256) k_emu_slice_cols(int64_t nn, int kb, int kbp, const double* __restrict__ U,
+                                                        int64_t ldu, __nv_bfloat16* __restrict__ sB, int64_t lds,
+                                                        int* __restrict__ eB) {
+    const int lane = threadIdx.x & 31;
+    const int64_t j = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (j >= nn) return;
+    const double* col = U + j * ldu;
+    unsigned long long mx = 0;
+    for (int q = lane; q < kb; q += 32) {
+        const unsigned long long u = (unsigned long long)__double_as_longlong(col[q]) & 0x7fffffffffffffffull;
+        mx = u > mx ? u : mx;
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, mx, off);
+        mx = o > mx ? o : mx;
+    }
+    const int e = emu_exp(mx);
+    if (lane == 0) eB[j] = e;
+    __nv_bfloat16* out = sB + j * lds;
+    for (int q = lane; q < kbp; q += 32) {
+        const double x = q < kb ? col[q] : 0.0;
+        unsigned long long fh, fl;
+        emu_fixed(x, e, fh, fl);
+        const bool neg = x < 0.0;
+#pragma unroll
+        for (int t = 1; t <= kEmuSlices; t++) {
+            const int b = t <= 6 ? (int)((fh >> (36 - kEmuBits * t)) & 63ull)
+                                 : (int)((fl >> (30 - kEmuBits * (t - 6))) & 63ull);
+            out[(kEmuSlices - t) * kbp + q] = __int2bfloat16_rn(neg ? -b : b);
+        }
+    }
+}
+
+// C(i, j) -= 2^(eA_i + eB_j) sum_g 2^-6g C_g(i, j) for an m x nc block; the
+// group products are exact integers below 2^24 in FP32 (cg[g-2], ld m).
+__global__ void __launch_bounds__(256) k_emu_combine(int64_t m, int64_t nc, const float* __restrict__ cg,
+                                                     const int* __restrict__ eA, const int* __restrict__ eB,
+                                                     double* __restrict__ C, int64_t ldc) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, j = blockIdx.y;
+    if (i >= m || j >= nc) return;
+    const int64_t stride = m * nc, at = j * m + i;
+    long long hi = 0, lo = 0;          // in units of 2^-36 (g = 2..6) and 2^-72 (g = 7..12)
+#pragma unroll
+    for (int g = 2; g <= 6; g++) hi += (long long)__float2int_rn(cg[(g - 2) * stride + at]) * (1ll << (kEmuBits * (6 - g)));
+#pragma unroll
+    for (int g = 7; g <= kEmuSlices + 1; g++)
+        lo += (long long)__float2int_rn(cg[(g - 2) * stride + at]) * (1ll << (kEmuBits * (kEmuSlices + 1 - g)));
+    const double v = fma((double)lo, 0x1p-36, (double)hi);               // sum in units of 2^-36
+    const int e = eA[i] + eB[j] - 36;
+    const double scale = (e > -1022 && e < 1024) ? __longlong_as_double((long long)(e + 1023) << 52)   // 2^e
+                                                 : ldexp(1.0, e);
+    double* c = C + j * ldc + i;
+    *c = fma(-v, scale, *c);
+}
+
+int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s);
+
+// Slices of one step: L21 (m x kb, ld ldl) and the kb x nn block row U12 (ld ldu).
+static int emu_slice(const LuWs& w, int64_t m, int64_t nn, int kb, const double* L, int64_t ldl, const double* U,
+                     int64_t ldu, cudaStream_t s) {
+    const int kbp = (int)emu_kbp(kb);
+    const int64_t lds = (int64_t)kEmuSlices * kbp;
+    if (m > 0) {
+        k_emu_slice_rows<<<(unsigned)((m + 7) / 8), 256, 0, s>>>(m, kb, kbp, L, ldl, (__nv_bfloat16*)w.sA, lds, w.eA);
+        HPL_LAUNCH_CHECK();
+    }
+    if (nn > 0) {
+        k_emu_slice_cols<<<(unsigned)((nn + 7) / 8), 256, 0, s>>>(nn, kb, kbp, U, ldu, (__nv_bfloat16*)w.sB, lds, w.eB);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
+}
+
+// C (m x nn, ld ldc) -= L21 U12 for the block-row columns col0 .. col0+nn of
+// the sliced step, with FP64 accuracy on the tensor cores.
+static int emu_update(const LuWs& w, int64_t m, int64_t nn, int kb, int64_t col0, double* C, int64_t ldc, int* err,
+                      int64_t timeout_ns, cudaStream_t s) {
+    if (m <= 0 || nn <= 0 || kb <= 0) return HPL_OK;
+    const int kbp = (int)emu_kbp(kb);
+    const int64_t lds = (int64_t)kEmuSlices * kbp;
+    for (int64_t j0 = 0; j0 < nn; j0 += kEmuChunk) {
+        const int64_t nc = std::min<int64_t>(kEmuChunk, nn - j0);
+        for (int g = 2; g <= kEmuSlices + 1; g++) {
+            const int64_t K = (int64_t)(g - 1) * kbp;
+            const uint16_t* Bg = w.sB + (col0 + j0) * lds + (int64_t)(kEmuSlices - (g - 1)) * kbp;
+            int st = launch_gemm_bf16(m, nc, K, w.sA, lds, Bg, lds, w.cg + (int64_t)(g - 2) * m * nc, m, 0, err,
+                                      timeout_ns, 0, s);
+            if (st) return st;
+        }
+        k_emu_combine<<<dim3((unsigned)((m + 255) / 256), (unsigned)nc), 256, 0, s>>>(m, nc, w.cg, w.eA,
+                                                                                      w.eB + col0 + j0,
+                                                                                      C + j0 * ldc, ldc);
+        HPL_LAUNCH_CHECK();
+    }
+    return HPL_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -567,9 +776,8 @@ static int max_coop_leaf_ctas(int num_sms, int64_t n) {
 using namespace hplgb;
 
 extern "C" size_t lu_factor_workspace_size(int64_t n, const hpl_opts* opts) {
-    (void)n;
     Opts o = resolve_opts(opts, 256);
-    return lu_ws_layout(o.nb, nullptr, nullptr);
+    return lu_ws_layout(o.nb, nullptr, nullptr, o.fp64_emulation ? std::max<int64_t>(n, 0) : 0);
 }
 
 extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts, void* ws,
@@ -579,15 +787,18 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, 256);
     if (o.nb < 1 || o.nb > 512) return HPL_ERR_INVALID;
-    size_t need = lu_ws_layout(o.nb, nullptr, nullptr);
+    const bool emu = o.fp64_emulation != 0;
+    if (o.fp64_emulation < 0 || o.fp64_emulation > 1 || (emu && o.nb > 256)) return HPL_ERR_INVALID;
+    const int64_t n_emu = emu ? n : 0;
+    size_t need = lu_ws_layout(o.nb, nullptr, nullptr, n_emu);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
     if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     cudaStream_t s = (cudaStream_t)stream;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     if (n == 0) return HPL_OK;
     LuWs w;
-    lu_ws_layout(o.nb, &w, (char*)ws);
-    HPL_CUDA_TRY(cudaMemsetAsync(ws, 0, need, s));
+    lu_ws_layout(o.nb, &w, (char*)ws, n_emu);
+    HPL_CUDA_TRY(cudaMemsetAsync(ws, 0, w.base_bytes, s));
 
     DeviceCtx* ctx = nullptr;
     int st = get_ctx(&ctx);
@@ -653,8 +864,14 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
             phase_end(slot, s, PH_TRSM, (double)kb * (kb - 1) * (double)m2, (int)k);
             const int64_t la_cols = std::min(nb, n - c1);
             slot = phase_begin(s);
-            st = launch_dgemm_sub(m2, la_cols, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda, A + c1 * lda + c1,
-                                  lda, s);
+            if (emu) {
+                st = emu_slice(w, m2, n - c1, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda, s);
+                if (st) return st;
+                st = emu_update(w, m2, la_cols, kb, 0, A + c1 * lda + c1, lda, w.emu_err, o.timeout_ns, s);
+            } else {
+                st = launch_dgemm_sub(m2, la_cols, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda,
+                                      A + c1 * lda + c1, lda, s);
+            }
             if (st) return st;
             phase_end(slot, s, PH_UPDATE, 2.0 * m2 * la_cols * kb, (int)k);
             if (la) {
@@ -665,8 +882,12 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
             }
             if (n - c1 - la_cols > 0) {
                 slot = phase_begin(s);
-                st = launch_dgemm_sub(m2, n - c1 - la_cols, kb, A + c0 * lda + c1, lda, A + (c1 + la_cols) * lda + c0,
-                                      lda, A + (c1 + la_cols) * lda + c1, lda, s);
+                if (emu)
+                    st = emu_update(w, m2, n - c1 - la_cols, kb, la_cols, A + (c1 + la_cols) * lda + c1, lda,
+                                    w.emu_err, o.timeout_ns, s);
+                else
+                    st = launch_dgemm_sub(m2, n - c1 - la_cols, kb, A + c0 * lda + c1, lda,
+                                          A + (c1 + la_cols) * lda + c0, lda, A + (c1 + la_cols) * lda + c1, lda, s);
                 if (st) return st;
                 phase_end(slot, s, PH_UPDATE, 2.0 * m2 * (n - c1 - la_cols) * kb, (int)k);
             }
@@ -680,7 +901,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
         HPL_CUDA_TRY(cudaEventRecord(ev_join, ps));
         HPL_CUDA_TRY(cudaStreamWaitEvent(s, ev_join, 0));
     }
-    k_lu_finish<<<1, 32, 0, s>>>(info, w.sync);
+    k_lu_finish<<<1, 32, 0, s>>>(info, w.sync, w.emu_err);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }

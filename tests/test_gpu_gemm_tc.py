@@ -74,3 +74,23 @@ def test_gemm_fp8_matches_fp64(hpl, M, N, K, sub, scaled):
     err = (C.double() - ref).abs()
     tol = (K * 2.0 ** -23 + 1e-6) * bound + 2.0 ** -23 * C0.double().abs()
     assert (err > tol).sum().item() == 0, err.max().item()
+
+
+@pytest.mark.parametrize("M,N,K", [(256, 512, 2304), (2304, 2560, 1536), (130, 70, 264)])
+def test_gemm_bf16_small_integer_products_are_exact(hpl, M, N, K):
+    """Integer BF16 operands below 2^6 in magnitude: every product and every
+    partial sum is an integer below 2^24, so the FP32 accumulation in tensor
+    memory must return the exact integer dot products (the property the
+    sliced FP64 emulation of the trailing update relies on)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
+    ld = (K + 7) // 8 * 8
+    Ai = torch.randint(-63, 64, (M, ld), device="cuda", generator=g)
+    Bi = torch.randint(-63, 64, (N, ld), device="cuda", generator=g)
+    A, B = Ai.to(torch.bfloat16)[:, :K], Bi.to(torch.bfloat16)[:, :K]
+    C = hpl.colmajor(M, N, dtype=torch.float32)
+    C.zero_()
+    hpl.gemm_bf16(A, B, C, sub=False)
+    exact = Ai[:, :K].double() @ Bi[:, :K].double().t()     # integers below 2^53: exact in FP64
+    assert exact.abs().max().item() < 2 ** 24
+    assert torch.equal(C.double(), exact)

@@ -31,11 +31,11 @@ def test_generate_large_sampled(hpl, orc):
     assert np.array_equal(_to_np(A), want)
 
 
-def _factor_and_check(hpl, orc, n, nb, lookahead, seed=1):
+def _factor_and_check(hpl, orc, n, nb, lookahead, seed=1, emu=0):
     import torch
     A = hpl.generate(seed, hpl.STREAM_A, n, n)
     A0 = _to_np(A).copy(order="F")
-    ipiv, info = hpl.lu_factor(A, nb=nb, lookahead=lookahead)
+    ipiv, info = hpl.lu_factor(A, nb=nb, lookahead=lookahead, fp64_emulation=emu)
     torch.cuda.synchronize()
     rec = info.read()
     assert rec["status"] == 0 and rec["info"] == 0, rec
@@ -59,6 +59,40 @@ def _factor_and_check(hpl, orc, n, nb, lookahead, seed=1):
                                       (1024, 64, 1), (1500, 256, 1), (2048, 512, 1)])
 def test_lu_factor_matches_oracle(hpl, orc, n, nb, la):
     _factor_and_check(hpl, orc, n, nb, la)
+
+
+@pytest.mark.parametrize("n,nb,la", [(1000, 64, 1), (777, 128, 0), (2048, 256, 1), (3000, 256, 1)])
+def test_lu_fp64_emulation_matches_oracle(hpl, orc, n, nb, la):
+    """The trailing update on the BF16 tensor cores with FP64 accuracy (sliced
+    products): pivots equal the oracle's, the backward error is at the FP64
+    level, and the factors agree with the DFMA factorization to rounding."""
+    import torch
+    A0, A, ipiv, LUo, ipo = _factor_and_check(hpl, orc, n, nb, la, seed=3, emu=1)
+    An = hpl.generate(3, hpl.STREAM_A, n, n)
+    ipn, infon = hpl.lu_factor(An, nb=nb, lookahead=la)
+    torch.cuda.synchronize()
+    assert torch.equal(ipiv, ipn)
+    # two FP64-accurate factorizations in different rounding orders: the
+    # emulated factors differ from the DFMA ones no more than the DFMA ones
+    # differ from the oracle's (the differences grow with the conditioning)
+    LU, LUn = _to_np(A), _to_np(An)
+    d_ref = max(np.abs(LUn - LUo).max(), 1e-14 * np.abs(LUn).max())
+    assert np.abs(LU - LUn).max() <= 10 * d_ref, (np.abs(LU - LUn).max(), d_ref)
+
+
+def test_lu_fp64_emulation_rejects_wide_panels(hpl):
+    """The exactness argument needs panels of at most 256 columns."""
+    import ctypes
+    import torch
+    lib = hpl.load()
+    n = 600
+    A = hpl.generate(1, hpl.STREAM_A, n, n)
+    ipiv = torch.empty(n, dtype=torch.int32, device="cuda")
+    info = hpl.Info()
+    opts = hpl.make_opts(nb=512, fp64_emulation=1)
+    ws = hpl.workspace(lib.lu_factor_workspace_size(n, ctypes.byref(opts)))
+    assert lib.lu_factor(n, A.data_ptr(), n, ipiv.data_ptr(), ctypes.byref(opts), ws.data_ptr(), ws.numel(),
+                         info.ptr(), torch.cuda.current_stream().cuda_stream) == 1
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6, 7, 8])
