@@ -118,6 +118,14 @@ int hpl_generate(uint64_t seed, uint64_t stream_id, int64_t m, int64_t ncols, in
  * With look-ahead the call forks work onto a second, higher-priority stream
  * and joins it back into `stream` before returning; ordering with respect to
  * `stream` is as for a single kernel launch.
+ * opts->fp64_emulation = 1 (not in the paper) computes the trailing update on
+ * the BF16 tensor cores with FP64 accuracy: each row of L21 and column of U12
+ * is cut into 11 integer slices of 6 bits (exact in BF16), the slice products
+ * are summed exactly by the tensor cores in 11 groups and combined in 64-bit
+ * integers, and the result is rounded to FP64; the panel, swaps and TRSM stay
+ * FP64. It needs NB <= 256 (HPL_ERR_INVALID otherwise) and a larger
+ * workspace, about 44 n (min(n, 8192) + NB) bytes more (lu_factor_workspace_size
+ * depends on n then: 12 GB at n = 32768).
  */
 size_t lu_factor_workspace_size(int64_t n, const hpl_opts* opts);
 int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts,
