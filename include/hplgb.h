@@ -72,7 +72,10 @@ typedef struct {
     int64_t timeout_ns;  /* limit for any device-side wait (default 20 s) */
     int32_t fp64_emulation; /* lu_factor: 0 = DFMA trailing update (default); 1 = the same update on the BF16
                                tensor cores with FP64 accuracy (sliced products, see lu_factor) */
-    int32_t reserved;
+    int32_t pfact;       /* lu_factor panel leaves: 0 = auto (default: a leaf whose rows fit in the shared
+                            memory of one thread-block cluster runs on that cluster, others on a
+                            grid-cooperative launch); 1 = grid-cooperative leaves only. Same pivots and
+                            factors either way. */
 } hpl_opts;
 
 /* Result record, written on the device. Caller-allocated in device memory. */

@@ -54,7 +54,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int64), ("lookahead", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("ns_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64),
-                ("fp64_emulation", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("fp64_emulation", ctypes.c_int32), ("pfact", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -143,11 +143,11 @@ def colmajor(m: int, n: int, dtype=torch.float64, device="cuda", ld: int | None 
 
 def make_opts(nb: int = 0, lookahead: int = 1, prec: int = PREC_BF16, refine: int = REFINE_GMRES,
               max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0, timeout_ns: int = 0,
-              fp64_emulation: int = 0) -> Opts:
+              fp64_emulation: int = 0, pfact: int = 0) -> Opts:
     o = Opts()
     load().hpl_default_opts(ctypes.byref(o))
     o.nb, o.lookahead, o.prec, o.refine = nb, lookahead, prec, refine
-    o.fp64_emulation = fp64_emulation
+    o.fp64_emulation, o.pfact = fp64_emulation, pfact
     o.max_iter, o.gmres_m, o.tol = max_iter, gmres_m, tol
     if timeout_ns:
         o.timeout_ns = timeout_ns
@@ -186,13 +186,15 @@ def generate(seed: int, stream_id: int, m: int, ncols: int, kind: int = GEN_GENE
 
 
 def lu_factor(A: torch.Tensor, nb: int = 256, lookahead: int = 1, ipiv: torch.Tensor | None = None,
-              ws: torch.Tensor | None = None, info: Info | None = None, fp64_emulation: int = 0):
+              ws: torch.Tensor | None = None, info: Info | None = None, fp64_emulation: int = 0,
+              pfact: int = 0):
     """In-place LU with partial pivoting. Returns (ipiv, info). fp64_emulation=1
-    runs the trailing update on the BF16 tensor cores with FP64 accuracy."""
+    runs the trailing update on the BF16 tensor cores with FP64 accuracy;
+    pfact=1 keeps every panel leaf on the grid-cooperative kernel."""
     lib = load()
     n = A.shape[0]
     assert A.shape == (n, n) and A.dtype == torch.float64 and A.is_cuda
-    opts = make_opts(nb=nb, lookahead=lookahead, fp64_emulation=fp64_emulation)
+    opts = make_opts(nb=nb, lookahead=lookahead, fp64_emulation=fp64_emulation, pfact=pfact)
     if ipiv is None:
         ipiv = torch.empty(max(n, 1), dtype=torch.int32, device=A.device)
     need = lib.lu_factor_workspace_size(n, ctypes.byref(opts))

@@ -69,6 +69,7 @@ Opts resolve_opts(const hpl_opts* o, int64_t default_nb) {
     r.tol = o->tol > 0 ? o->tol : d.tol;
     r.timeout_ns = o->timeout_ns > 0 ? o->timeout_ns : d.timeout_ns;
     r.fp64_emulation = o->fp64_emulation;
+    r.pfact = o->pfact;
     return r;
 }
 

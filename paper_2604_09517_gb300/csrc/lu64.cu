@@ -32,6 +32,10 @@ constexpr int kLeafW = 32;          // widest leaf of the recursive panel
 constexpr int kLeafStride = 33;     // SMEM row stride (doubles) of the leaf
 constexpr int kLeafThreads = 256;
 constexpr int kMaxPanelCtas = 512;
+// panels up to this many rows are factored by the cluster leaf when they fit
+#ifndef HPLGB_CLUSTER_LEAF_MAX_ROWS
+#define HPLGB_CLUSTER_LEAF_MAX_ROWS (1LL << 40)
+#endif
 
 struct Cand {
     double absval;
@@ -294,6 +298,192 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf(
     }
 }
 
+// Magnitude key of a double for the pivot search: for |v| not NaN the IEEE
+// bit pattern orders like the value, so the comparison runs on the integer
+// pipe (FP64 compares issue at the FP64 rate, which is scarce on this part).
+// NaN gets -1 and is never chosen, as with a floating-point ">".
+__device__ __forceinline__ long long mag_key(double v) {
+    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+    return b > 0x7ff0000000000000LL ? -1LL : b;
+}
+__device__ __forceinline__ bool key_better(long long k, long long r, long long bk, long long br) {
+    return k > bk || (k == bk && r < br);
+}
+// butterfly max over the warp: every lane ends with the winner
+__device__ __forceinline__ void warp_best(long long& k, long long& r) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        long long ok = __shfl_xor_sync(0xffffffffu, k, off);
+        long long orr = __shfl_xor_sync(0xffffffffu, r, off);
+        if (key_better(ok, orr, k, r)) { k = ok; r = orr; }
+    }
+}
+
+// PFACT leaf on one thread-block cluster, for panels whose rows fit in the
+// cluster's shared memory (the short panels of a small matrix or of the last
+// steps of a large one). Same pivots and arithmetic as k_panel_leaf (first
+// row of largest magnitude, true division, one rank-1 update per column),
+// organised around two facts of this part: FP64 instructions are scarce
+// (about 2 FMA per clock per SM, and a warp instruction costs the same
+// however few of its lanes are active), and a cluster barrier with
+// distributed shared memory is much cheaper than a grid barrier through
+// global memory.
+//  * Pivot search on integer keys (mag_key); the search for column j + 1 is
+//    fused into the rank-1 update of column j, by the threads that produce
+//    column j + 1's new values.
+//  * The rank-1 update maps threads densely onto the active (row, column)
+//    pairs, so no FP64 instruction runs for finished columns.
+//  * Exchange: per column every CTA publishes its candidate (key, row, values)
+//    and, its owner, the diagonal row in its own shared memory; one cluster
+//    barrier; then warp 0 of every CTA reads the C candidates and the two rows
+//    from the publishers. Publications alternate between two buffers by
+//    column parity: a CTA rewrites buffer j & 1 only after the cluster barrier
+//    of column j + 1, which every reader of column j has passed.
+// W: leaf width bound (32 or 64; w <= W columns are factored).
+template <int W>
+__global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
+    int64_t n, double* __restrict__ A, int64_t lda, int64_t c0, int w, int rows_per, int64_t pc0, int64_t pw,
+    int32_t* __restrict__ ipiv, hpl_info* info) {
+    constexpr int S = W + 1;
+    constexpr int NW = kLeafThreads / 32;
+    extern __shared__ double sm[];
+    __shared__ double pub_vals[2][W], pub_diag[2][W];
+    __shared__ long long pub_key[2], pub_row[2];
+    __shared__ double s_piv[W], s_diag[W];
+    __shared__ long long s_wk[NW], s_wr[NW];
+    __shared__ long long s_p;
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned C = gridDim.x;                        // the launch is one cluster
+    const unsigned me = cluster_rank();
+    const int64_t m = n - c0;
+    const int64_t rbeg = (int64_t)me * rows_per;
+    const int nloc = (int)max((int64_t)0, min((int64_t)rows_per, m - rbeg));
+    const long long kNone = 0x7fffffffffffffffLL;
+    const long long grow0 = c0 + rbeg;                   // global row of local row 0
+
+    for (int idx = tid; idx < nloc * w; idx += kLeafThreads) {
+        int c = idx / nloc, r = idx - c * nloc;
+        sm[r * S + c] = A[(c0 + c) * lda + grow0 + r];
+    }
+    const int64_t nother = pw - w;
+    const int64_t gtid = (int64_t)me * kLeafThreads + tid;
+    __syncthreads();
+    // this thread's candidate for column 0
+    long long bk = -1, br = kNone;
+    for (int r = tid; r < nloc; r += kLeafThreads) {
+        long long k = mag_key(sm[r * S]);
+        if (key_better(k, grow0 + r, bk, br)) { bk = k; br = grow0 + r; }
+    }
+
+    for (int j = 0; j < w; j++) {
+        const int par = j & 1;
+        const int64_t rowj = c0 + j;
+        const int64_t rd = rowj - grow0;                 // local index of the diagonal row
+        warp_best(bk, br);
+        if (lane == 0) { s_wk[warp] = bk; s_wr[warp] = br; }
+        __syncthreads();
+        if (warp == 0) {
+            long long k = lane < NW ? s_wk[lane] : -1, r = lane < NW ? s_wr[lane] : kNone;
+            warp_best(k, r);
+            if (lane == 0) { pub_key[par] = k; pub_row[par] = r; }
+            if (r != kNone)
+                for (int c = lane; c < w; c += 32) pub_vals[par][c] = sm[(int)(r - grow0) * S + c];
+        } else if (warp == 1 && rd >= 0 && rd < nloc) {
+            for (int c = lane; c < w; c += 32) pub_diag[par][c] = sm[rd * S + c];
+        }
+        cluster_sync_all();
+        if (warp == 0) {
+            long long gk = -1, gr = kNone, gw = -1;
+            for (unsigned q = lane; q < C; q += 32) {
+                long long k = ld_cluster_s64(cluster_addr(&pub_key[par], q));
+                long long r = ld_cluster_s64(cluster_addr(&pub_row[par], q));
+                if (key_better(k, r, gk, gr)) { gk = k; gr = r; gw = (long long)q; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                long long ok = __shfl_xor_sync(0xffffffffu, gk, off);
+                long long orr = __shfl_xor_sync(0xffffffffu, gr, off);
+                long long ow = __shfl_xor_sync(0xffffffffu, gw, off);
+                if (key_better(ok, orr, gk, gr)) { gk = ok; gr = orr; gw = ow; }
+            }
+            if (gr == kNone) { gr = rowj; gw = -1; }     // only NaN in the column: keep the diagonal row
+            const unsigned downer = (unsigned)(j / rows_per);
+            for (int c = lane; c < w; c += 32) {
+                double dv = ld_cluster_f64(cluster_addr(&pub_diag[par][c], downer));
+                s_diag[c] = dv;
+                s_piv[c] = gw >= 0 ? ld_cluster_f64(cluster_addr(&pub_vals[par][c], (unsigned)gw)) : dv;
+            }
+            if (lane == 0) s_p = gr;
+        }
+        __syncthreads();
+        const long long p = s_p;
+        const double piv = s_piv[j];
+        if (me == 0 && tid == 0) {
+            ipiv[rowj] = (int32_t)p;
+            if (piv == 0.0) atomicCAS((unsigned long long*)&info->info, 0ull, (unsigned long long)(rowj + 1));
+        }
+        const int64_t rp = p - grow0;
+        const bool swap = p != rowj;
+        // interchange rows rowj and p (row p's column j is written by the scaling
+        // below when there is one), scale the column below the diagonal with one
+        // true division per row, interchange in the panel's other columns
+        if (swap && tid < w) {
+            if (rp >= 0 && rp < nloc && (tid != j || piv == 0.0)) sm[rp * S + tid] = s_diag[tid];
+            if (rd >= 0 && rd < nloc) sm[rd * S + tid] = s_piv[tid];
+        }
+        const int rs = (int)max((int64_t)0, (int64_t)(rowj + 1 - grow0));
+        if (piv != 0.0)
+            for (int r = rs + tid; r < nloc; r += kLeafThreads) {
+                const double v = (swap && r == rp) ? s_diag[j] : sm[r * S + j];
+                sm[r * S + j] = v / piv;
+            }
+        if (swap)
+            for (int64_t o = gtid; o < nother; o += (int64_t)C * kLeafThreads) {
+                int64_t col = pc0 + (o < c0 - pc0 ? o : o + w);
+                double* cp = A + col * lda;
+                double t = cp[rowj];
+                cp[rowj] = cp[p];
+                cp[p] = t;
+            }
+        __syncthreads();
+        // rank-1 update of columns (j, w) on rows >= rs, threads dense over the
+        // active pairs; the producers of column j + 1 track its pivot candidate
+        bk = -1;
+        br = kNone;
+        if (j + 1 < w) {
+            const int ncol = w - j - 1, nr = nloc - rs;
+            if (piv != 0.0) {
+                int q = tid / ncol, cc = tid - q * ncol;
+                const int dq = kLeafThreads / ncol, dc = kLeafThreads - dq * ncol;
+                while (q < nr) {
+                    const int r = rs + q, c = j + 1 + cc;
+                    const double a = fma(-sm[r * S + j], s_piv[c], sm[r * S + c]);
+                    sm[r * S + c] = a;
+                    if (cc == 0) {
+                        long long k = mag_key(a);
+                        if (key_better(k, grow0 + r, bk, br)) { bk = k; br = grow0 + r; }
+                    }
+                    cc += dc;
+                    q += dq;
+                    if (cc >= ncol) { cc -= ncol; q++; }
+                }
+            } else {
+                for (int r = rs + tid; r < nloc; r += kLeafThreads) {
+                    long long k = mag_key(sm[r * S + j + 1]);
+                    if (key_better(k, grow0 + r, bk, br)) { bk = k; br = grow0 + r; }
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int idx = tid; idx < nloc * w; idx += kLeafThreads) {
+        int c = idx / nloc, r = idx - c * nloc;
+        A[(c0 + c) * lda + grow0 + r] = sm[r * S + c];
+    }
+    cluster_sync_all();          // no CTA leaves while another may still read its publications
+}
+
 // ---------------------------------------------------------------------------
 // SWAP: the sequential interchanges ipiv[k0 .. k0+kb) as a gather. One warp
 // replays them on a list of touched positions and emits (dst, src) pairs with
@@ -311,15 +501,17 @@ __global__ void k_perm_pairs(const int32_t* __restrict__ ipiv, int64_t k0_base, 
     src += (int64_t)blockIdx.x * 2 * pb;
     int* pos = psm;               // [2*pb]
     int* con = psm + 2 * pb;      // [2*pb]
+    int* pv = psm + 4 * pb;       // [pb] the block's pivots, read once (coalesced)
     const int lane = threadIdx.x;
     for (int i = lane; i < kb; i += 32) {
         pos[i] = (int)(k0 + i);
         con[i] = (int)(k0 + i);
+        pv[i] = ipiv[k0 + i];
     }
     __syncwarp();
     int L = kb;
     for (int i = 0; i < kb; i++) {
-        int p = ipiv[k0 + i];
+        int p = pv[i];
         if (p <= k0 + i || p >= n_total) continue;
         int q;
         if (p < k0 + kb) {
@@ -407,6 +599,38 @@ __global__ void __launch_bounds__(256) k_laswp_gather(double* __restrict__ A, in
 // runs forward substitution; 16 thread groups split the rows.
 constexpr int kTrsmCols = 16;
 
+// kk <= 64: L11 staged in shared memory once (the loop above re-reads a
+// column of L from L2 at every step, which at this size is latency, not
+// work), COLS columns of B per CTA, loads and stores coalesced along rows.
+template <int COLS>
+__global__ void __launch_bounds__(256) k_trsm_lunit_small(double* __restrict__ A, int64_t lda, int64_t r0, int kk,
+                                                          int64_t cb, int64_t ce) {
+    constexpr int G = 256 / COLS;
+    __shared__ double Ls[64][65];
+    __shared__ double xs[64][COLS];
+    const int c = threadIdx.x % COLS, g = threadIdx.x / COLS;
+    const int64_t cbase = cb + (int64_t)blockIdx.x * COLS;
+    const int ncol = (int)min((int64_t)COLS, ce - cbase);
+    for (int idx = threadIdx.x; idx < kk * kk; idx += 256) {
+        const int j = idx / kk, i = idx - j * kk;
+        if (i > j) Ls[i][j] = A[(r0 + j) * lda + r0 + i];
+    }
+    for (int idx = threadIdx.x; idx < kk * COLS; idx += 256) {
+        const int cc = idx / kk, i = idx - cc * kk;
+        xs[i][cc] = cc < ncol ? A[(cbase + cc) * lda + r0 + i] : 0.0;
+    }
+    for (int j = 0; j < kk - 1; j++) {
+        __syncthreads();
+        const double xj = xs[j][c];
+        for (int i = j + 1 + g; i < kk; i += G) xs[i][c] = fma(-Ls[i][j], xj, xs[i][c]);
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < kk * ncol; idx += 256) {
+        const int cc = idx / kk, i = idx - cc * kk;
+        A[(cbase + cc) * lda + r0 + i] = xs[i][cc];
+    }
+}
+
 __global__ void __launch_bounds__(256) k_trsm_lunit(double* __restrict__ A, int64_t lda, int64_t r0, int kk,
                                                     int64_t cb, int64_t ce) {
     extern __shared__ double xs[];            // [kk][16]
@@ -426,10 +650,13 @@ __global__ void __launch_bounds__(256) k_trsm_lunit(double* __restrict__ A, int6
 }
 
 // ---------------------------------------------------------------------------
-// DGEMM: C -= A * B in FP64 with DFMA. 64x64 CTA tile, k-step 16, 256
-// threads with a 4x4 register tile, cp.async double buffering. C is loaded
-// into the accumulators first so every entry sees c - sum(a*b) accumulated in
-// increasing k, as in the unblocked elimination.
+// DGEMM: C -= A * B in FP64 with DFMA. TB x TB CTA tile (64, or 32 when
+// 64-wide tiles would leave SMs idle: one 64 x 64 x 64 tile is ~60 us of a
+// single SM's FP64 pipe, so small trailing matrices want more, smaller
+// tiles), k-step 16, 256 threads with a (TB/16)^2 register tile, cp.async
+// double buffering. C is loaded into the accumulators first so every entry
+// sees c - sum(a*b) accumulated in increasing k, as in the unblocked
+// elimination; the result does not depend on TB.
 constexpr int kGB = 64, kGK = 16;
 
 __device__ __forceinline__ void cp_async8(void* smem, const void* gmem, bool pred) {
@@ -441,25 +668,28 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N)); }
 
+template <int TB>
 __global__ void __launch_bounds__(256) k_dgemm_sub(int64_t m, int64_t nn, int64_t kk, const double* __restrict__ A,
                                                    int64_t lda, const double* __restrict__ B, int64_t ldb,
                                                    double* __restrict__ C, int64_t ldc) {
-    __shared__ __align__(16) double As[2][kGK][kGB + 1];
-    __shared__ __align__(16) double Bs[2][kGK][kGB + 1];
+    constexpr int R = TB / 16;                     // register tile R x R
+    constexpr int LQ = TB * kGK / 256;             // elements of a k-slab each thread loads per operand
+    __shared__ __align__(16) double As[2][kGK][TB + 1];
+    __shared__ __align__(16) double Bs[2][kGK][TB + 1];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-    const int64_t row0 = (int64_t)blockIdx.x * kGB, col0 = (int64_t)blockIdx.y * kGB;
+    const int64_t row0 = (int64_t)blockIdx.x * TB, col0 = (int64_t)blockIdx.y * TB;
 
     auto load_tile = [&](int buf, int64_t k0) {
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < LQ; q++) {
             int e = tid + 256 * q;
-            int kq = e >> 6, r = e & 63;
+            int kq = e / TB, r = e % TB;
             bool ok = (row0 + r < m) && (k0 + kq < kk);
             const double* g = ok ? A + (k0 + kq) * lda + row0 + r : A;
             cp_async8(&As[buf][kq][r], g, ok);
         }
 #pragma unroll
-        for (int q = 0; q < 4; q++) {
+        for (int q = 0; q < LQ; q++) {
             int e = tid + 256 * q;
             int c = e >> 4, kq = e & 15;
             bool ok = (col0 + c < nn) && (k0 + kq < kk);
@@ -469,11 +699,11 @@ __global__ void __launch_bounds__(256) k_dgemm_sub(int64_t m, int64_t nn, int64_
         cp_async_commit();
     };
 
-    double acc[4][4];
+    double acc[R][R];
 #pragma unroll
-    for (int j = 0; j < 4; j++)
+    for (int j = 0; j < R; j++)
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < R; i++) {
             int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
             acc[i][j] = (r < m && c < nn) ? C[c * ldc + r] : 0.0;
         }
@@ -491,22 +721,22 @@ __global__ void __launch_bounds__(256) k_dgemm_sub(int64_t m, int64_t nn, int64_
         __syncthreads();
 #pragma unroll
         for (int kq = 0; kq < kGK; kq++) {
-            double a[4], b[4];
+            double a[R], b[R];
 #pragma unroll
-            for (int i = 0; i < 4; i++) a[i] = As[buf][kq][tx + 16 * i];
+            for (int i = 0; i < R; i++) a[i] = As[buf][kq][tx + 16 * i];
 #pragma unroll
-            for (int j = 0; j < 4; j++) b[j] = Bs[buf][kq][ty + 16 * j];
+            for (int j = 0; j < R; j++) b[j] = Bs[buf][kq][ty + 16 * j];
 #pragma unroll
-            for (int j = 0; j < 4; j++)
+            for (int j = 0; j < R; j++)
 #pragma unroll
-                for (int i = 0; i < 4; i++) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
+                for (int i = 0; i < R; i++) acc[i][j] = fma(-a[i], b[j], acc[i][j]);
         }
         __syncthreads();
     }
 #pragma unroll
-    for (int j = 0; j < 4; j++)
+    for (int j = 0; j < R; j++)
 #pragma unroll
-        for (int i = 0; i < 4; i++) {
+        for (int i = 0; i < R; i++) {
             int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
             if (r < m && c < nn) C[c * ldc + r] = acc[i][j];
         }
@@ -702,14 +932,31 @@ int launch_dgemm_sub(int64_t m, int64_t nn, int64_t kk, const double* A, int64_t
                      double* C, int64_t ldc, cudaStream_t s) {
     if (m <= 0 || nn <= 0 || kk <= 0) return HPL_OK;
     dim3 grid((unsigned)((m + kGB - 1) / kGB), (unsigned)((nn + kGB - 1) / kGB));
+    if ((int64_t)grid.x * grid.y < 4 * kNumSMsGB300) {
+        // fewer than four waves of 64-wide tiles: quarter-size tiles fill the SMs
+        dim3 g32((unsigned)((m + 31) / 32), (unsigned)((nn + 31) / 32));
+        if (g32.y > 65535) return HPL_ERR_INVALID;
+        k_dgemm_sub<32><<<g32, 256, 0, s>>>(m, nn, kk, A, lda, B, ldb, C, ldc);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
     if (grid.y > 65535) return HPL_ERR_INVALID;
-    k_dgemm_sub<<<grid, 256, 0, s>>>(m, nn, kk, A, lda, B, ldb, C, ldc);
+    k_dgemm_sub<64><<<grid, 256, 0, s>>>(m, nn, kk, A, lda, B, ldb, C, ldc);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
 
 static int launch_trsm(double* A, int64_t lda, int64_t r0, int kk, int64_t cb, int64_t ce, cudaStream_t s) {
     if (ce <= cb || kk <= 1) return HPL_OK;
+    if (kk <= 64) {
+        if ((ce - cb) / 16 >= kNumSMsGB300) {
+            k_trsm_lunit_small<16><<<(unsigned)((ce - cb + 15) / 16), 256, 0, s>>>(A, lda, r0, kk, cb, ce);
+        } else {
+            k_trsm_lunit_small<8><<<(unsigned)((ce - cb + 7) / 8), 256, 0, s>>>(A, lda, r0, kk, cb, ce);
+        }
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
     size_t smem = sizeof(double) * kk * kTrsmCols;
     unsigned grid = (unsigned)((ce - cb + kTrsmCols - 1) / kTrsmCols);
     k_trsm_lunit<<<grid, 256, smem, s>>>(A, lda, r0, kk, cb, ce);
@@ -719,7 +966,50 @@ static int launch_trsm(double* A, int64_t lda, int64_t r0, int kk, int64_t cb, i
 
 struct PanelPlan {
     int max_coop;   // co-resident leaf CTAs
+    int max_cluster;  // largest cluster the cluster leaf may use (0: none)
 };
+
+constexpr int kClusterLeafRows = 64;             // rows per CTA the cluster leaf aims for
+constexpr size_t kClusterLeafSmem = 200 * 1024;  // dynamic shared memory bound per CTA
+
+// The cluster leaf for columns [c0, c0+w) when the panel's rows fit; returns
+// 1 (nothing launched) when they do not.
+static int launch_leaf_cluster(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64_t pc0, int64_t pw,
+                               int32_t* ipiv, hpl_info* info, const PanelPlan& pp, cudaStream_t s) {
+    if (pp.max_cluster < 1 || w > 64) return 1;
+    const int64_t m = n - c0;
+    const int W = w <= 32 ? 32 : 64;
+    const size_t row_bytes = sizeof(double) * (W + 1);
+    const int64_t cap_rows = (int64_t)(kClusterLeafSmem / row_bytes);
+    int C = (int)std::min<int64_t>((m + kClusterLeafRows - 1) / kClusterLeafRows, pp.max_cluster);
+    if (C < 1) C = 1;
+    int64_t rows_per = (m + C - 1) / C;
+    if (rows_per > cap_rows) {
+        C = pp.max_cluster;
+        rows_per = (m + C - 1) / C;
+        if (rows_per > cap_rows) return 1;
+    }
+    const size_t smem = row_bytes * (size_t)std::max<int64_t>(rows_per, 1);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(kLeafThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const int rp = (int)rows_per;
+    if (W == 32)
+        HPL_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_leaf_cl<32>, n, A, lda, c0, w, rp, pc0, pw, ipiv, info));
+    else
+        HPL_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_panel_leaf_cl<64>, n, A, lda, c0, w, rp, pc0, pw, ipiv, info));
+    count_launch();
+    return HPL_OK;
+}
 
 static int launch_leaf(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64_t pc0, int64_t pw,
                        int32_t* ipiv, const LuWs& ws, hpl_info* info, int64_t timeout_ns, const PanelPlan& pp,
@@ -742,6 +1032,10 @@ static int launch_leaf(int64_t n, double* A, int64_t lda, int64_t c0, int w, int
 // NB panel [pc0, pc0+pw): left half, TRSM + GEMM on the right half, right half.
 static int panel_rec(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64_t pc0, int64_t pw, int32_t* ipiv,
                      const LuWs& ws, hpl_info* info, int64_t timeout_ns, const PanelPlan& pp, cudaStream_t s) {
+    if (w <= 64 && n - c0 <= HPLGB_CLUSTER_LEAF_MAX_ROWS) {
+        int st = launch_leaf_cluster(n, A, lda, c0, w, pc0, pw, ipiv, info, pp, s);
+        if (st != 1) return st;
+    }
     if (w <= kLeafW) return launch_leaf(n, A, lda, c0, w, pc0, pw, ipiv, ws, info, timeout_ns, pp, s);
     int w1 = ((w / 2 + kLeafW - 1) / kLeafW) * kLeafW;
     if (w1 >= w) w1 = kLeafW;
@@ -753,6 +1047,41 @@ static int panel_rec(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64
                           A + (c0 + w1) * lda + c0 + w1, lda, s);
     if (st) return st;
     return panel_rec(n, A, lda, c0 + w1, w - w1, pc0, pw, ipiv, ws, info, timeout_ns, pp, s);
+}
+
+// Largest cluster (16, else the portable 8) on which the cluster leaf can run
+// with its largest shared-memory footprint; 0 when none can.
+static int max_leaf_cluster() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    int best = 0;
+    const void* fns[2] = {(const void*)k_panel_leaf_cl<32>, (const void*)k_panel_leaf_cl<64>};
+    for (const void* f : fns) {
+        cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClusterLeafSmem);
+        cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    }
+    for (int c : {16, 8}) {
+        bool ok = true;
+        for (const void* f : fns) {
+            cudaLaunchConfig_t cfg = {};
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = (unsigned)c;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.gridDim = dim3((unsigned)c);
+            cfg.blockDim = dim3(kLeafThreads);
+            cfg.dynamicSmemBytes = kClusterLeafSmem;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            int nclusters = 0;
+            if (cudaOccupancyMaxActiveClusters(&nclusters, f, &cfg) != cudaSuccess || nclusters < 1) ok = false;
+        }
+        cudaGetLastError();
+        if (ok) { best = c; break; }
+    }
+    cached = best;
+    return best;
 }
 
 static int max_coop_leaf_ctas(int num_sms, int64_t n) {
@@ -789,6 +1118,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
     if (o.nb < 1 || o.nb > 512) return HPL_ERR_INVALID;
     const bool emu = o.fp64_emulation != 0;
     if (o.fp64_emulation < 0 || o.fp64_emulation > 1 || (emu && o.nb > 256)) return HPL_ERR_INVALID;
+    if (o.pfact < 0 || o.pfact > 1) return HPL_ERR_INVALID;
     const int64_t n_emu = emu ? n : 0;
     size_t need = lu_ws_layout(o.nb, nullptr, nullptr, n_emu);
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
@@ -805,6 +1135,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
     if (st) return st;
     PanelPlan pp;
     pp.max_coop = max_coop_leaf_ctas(ctx->num_sms, n);
+    pp.max_cluster = o.pfact == 0 ? max_leaf_cluster() : 0;
     HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_trsm_lunit, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)(sizeof(double) * 512 * kTrsmCols)));
 
@@ -825,7 +1156,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
         int r = panel_rec(n, A, lda, c0, kb, c0, kb, ipiv, w, info, o.timeout_ns, pp, ps);
         if (r) return r;
         int par = (int)(k & 1);
-        k_perm_pairs<<<1, 32, sizeof(int) * 4 * kb, ps>>>(ipiv, c0, kb, c0 + kb, n, w.perm_cnt + par,
+        k_perm_pairs<<<1, 32, sizeof(int) * 5 * kb, ps>>>(ipiv, c0, kb, c0 + kb, n, w.perm_cnt + par,
                                                            w.perm_dst + par * 2 * nb, w.perm_src + par * 2 * nb);
         HPL_LAUNCH_CHECK();
         // getrf of an m x kb panel: m kb^2 - kb^3/3 flops (leading terms)
@@ -862,7 +1193,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
             st = launch_trsm(A, lda, c0, kb, c1, n, s);
             if (st) return st;
             phase_end(slot, s, PH_TRSM, (double)kb * (kb - 1) * (double)m2, (int)k);
-            const int64_t la_cols = std::min(nb, n - c1);
+            const int64_t la_cols = la ? std::min(nb, n - c1) : n - c1;   // no look-ahead: one update
             slot = phase_begin(s);
             if (emu) {
                 st = emu_slice(w, m2, n - c1, kb, A + c0 * lda + c1, lda, A + c1 * lda + c0, lda, s);

@@ -57,6 +57,11 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ LU
         int i = trans ? a : c, j = trans ? c : a;        // coalesced along the contiguous index
         Ts[i][j] = tri_at(LU, lda, b0 + i, b0 + j, trans);
     }
+    // reciprocals of the diagonal, all at once: the substitution then multiplies
+    // (one FP64 division is a chain of FP64 instructions, scarce on this part)
+    __shared__ double Tinv[kTB];
+    __syncthreads();
+    if (!unit && threadIdx.x < bs) Tinv[threadIdx.x] = 1.0 / Ts[threadIdx.x][threadIdx.x];
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int64_t c = warp; c < nrhs; c += blockDim.x / 32) {
@@ -67,7 +72,7 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ LU
         if (lower) {
             for (int j = 0; j < bs; j++) {
                 const int hj = j >> 5, lj = j & 31;
-                if (!unit && lane == lj) y[hj] = y[hj] / Ts[j][j];
+                if (!unit && lane == lj) y[hj] = y[hj] * Tinv[j];
                 const double xj = __shfl_sync(0xffffffffu, y[hj], lj);
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(256) k_trsv_diag(const double* __restrict__ LU
         } else {
             for (int j = bs - 1; j >= 0; j--) {
                 const int hj = j >> 5, lj = j & 31;
-                if (!unit && lane == lj) y[hj] = y[hj] / Ts[j][j];
+                if (!unit && lane == lj) y[hj] = y[hj] * Tinv[j];
                 const double xj = __shfl_sync(0xffffffffu, y[hj], lj);
 #pragma unroll
                 for (int h = 0; h < 2; h++) {
@@ -190,7 +195,7 @@ extern "C" int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, 
     int *cnt, *dst, *src;
     solve_ws_layout(n, &cnt, &dst, &src, (char*)ws);
     const int nblk = (int)((n + kPivBlock - 1) / kPivBlock);
-    k_perm_pairs<<<nblk, 32, sizeof(int) * 4 * kPivBlock, s>>>(ipiv, 0, kPivBlock, n, n, cnt, dst, src);
+    k_perm_pairs<<<nblk, 32, sizeof(int) * 5 * kPivBlock, s>>>(ipiv, 0, kPivBlock, n, n, cnt, dst, src);
     HPL_LAUNCH_CHECK();
     if (info) {
         k_check_udiag<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, LU, lda, info);
