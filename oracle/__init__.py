@@ -83,6 +83,8 @@ def _load():
             "orc_lu_sample_diff": (None, [u64, i64, ctypes.c_int, dp, i64, i64p, i64, i64p, i64p, dp]),
             "orc_round_bf16": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_e4m3": (ctypes.c_float, [ctypes.c_float]),
+            "orc_round_fp16": (ctypes.c_float, [ctypes.c_float]),
+            "orc_round_operand_ext": (None, [ctypes.c_int, fp, i64, i64, i64, ctypes.c_int]),
             "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, ctypes.c_int, fp, i64, fp]),
             "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, i64, fp, i64, fp, dp, dp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
@@ -228,7 +230,8 @@ def lu_sample_diff(seed: int, n: int, dominant: bool, LU, ipiv, si, sj) -> np.nd
 
 PREC_BF16 = 0
 PREC_FP8 = 1
-PREC_FP32 = 2
+PREC_FP16 = 2
+PREC_FP32 = 3
 
 
 def round_bf16(x: float) -> float:
@@ -237,6 +240,19 @@ def round_bf16(x: float) -> float:
 
 def round_e4m3(x: float) -> float:
     return float(_load().orc_round_e4m3(float(x)))
+
+
+def round_fp16(x: float) -> float:
+    return float(_load().orc_round_fp16(float(x)))
+
+
+def round_operand(prec: int, X, kdim_is_rows: bool) -> np.ndarray:
+    """An FP32 operand rounded as the factorization rounds it (dequantised):
+    kdim_is_rows for a B operand (K x cols), else an A operand (rows x K)."""
+    X = np.asfortranarray(np.asarray(X, dtype=np.float32)).copy(order="F")
+    r, c = X.shape
+    _load().orc_round_operand_ext(prec, _fp(X), r, c, max(r, 1), int(bool(kdim_is_rows)))
+    return X
 
 
 NS_ITERS = 2

@@ -29,13 +29,15 @@
  *       LAPACK getrf via scipy, closed forms, ||PA-LU|| invariant.
  *   orc_scaled_residual(_gen) : closed forms and a hand-computed case.
  *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine).
+ *   orc_round_fp16 : NumPy's float16 cast (library routine).
  *   orc_mxp_factor : FP32 mode equals unpivoted LU; BF16 mode error bound.
  *   orc_mxp_solve : converged x equals the FP64 LU solution; iteration
  *       behaviour with an exact preconditioner (one step).
  *   orc_adjoint : central finite differences and torch.linalg.solve autograd.
- *   FP8 operand encoding (prec = 1): element rounding pinned; the per-block
- *       scale choice is this build's reading, parity for FP8 iteration
- *       counts is unpinned (only convergence is checked).
+ *   FP8 and FP16 operand encodings (prec = 1, 2): element rounding pinned;
+ *       the per-row / per-column scale choice is a reading (the paper fixes
+ *       none), pinned by a brute-force check of its defining property;
+ *       iteration counts for FP8 are unpinned (only convergence is checked).
  */
 #include <math.h>
 #include <stdint.h>
@@ -338,7 +340,12 @@ void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU
  *     over the whole contraction index, the smallest one that keeps
  *     amax/scale <= 448; FP8 applies to the trailing update, the panel
  *     product L21 = A21 D^-1 keeps BF16 operands;
- *     prec = 2: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
+ *     prec = 2: FP16 (IEEE binary16), round to nearest even, scaled like FP8
+ *     with the bound 65504 (the entries of L21 are about 1/n and would sit in
+ *     FP16's subnormal range unscaled), in the panel product L21 = A21 D^-1
+ *     as well as in the trailing update (its 3 extra fraction bits over BF16
+ *     are lost if L21 is formed from BF16 operands);
+ *     prec = 3: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
  *     mode.                                                                  */
 
 /* BF16 round-to-nearest-even of a float: keep 8 significant bits. Written from
@@ -370,13 +377,32 @@ float orc_round_e4m3(float x) {
     return (float)copysign(q, (double)x);
 }
 
+/* IEEE binary16 round-to-nearest-even: normals 2^-14 .. 65504 with 10
+ * fraction bits, subnormals k * 2^-24, overflow to infinity (from 65520 up,
+ * the midpoint between 65504 and 2^16). Written from the format definition. */
+float orc_round_fp16(float x) {
+    if (x == 0.0f || !isfinite(x)) return x;
+    double a = fabs((double)x);
+    double spacing;
+    if (a < 0x1p-14) spacing = 0x1p-24;
+    else {
+        int e;
+        frexp(a, &e);                           /* a in [2^(e-1), 2^e) */
+        spacing = ldexp(1.0, e - 1 - 10);
+    }
+    double q = nearbyint(a / spacing) * spacing;
+    if (q > 65504.0) q = INFINITY;
+    return (float)copysign(q, (double)x);
+}
+
 /* Scale exponent for a block with max magnitude amax: smallest e with
- * amax * 2^-e <= 448. Returns 0 for an all-zero block. */
-static int orc_e4m3_block_exp(double amax) {
+ * amax * 2^-e <= bound (448 for E4M3, 65504 for FP16). Returns 0 for an
+ * all-zero block. */
+static int orc_block_exp(double amax, double bound) {
     if (amax == 0.0) return 0;
-    int e = (int)ceil(log2(amax / 448.0));
-    while (ldexp(amax, -e) > 448.0) e++;
-    while (e > -127 && ldexp(amax, -(e - 1)) <= 448.0) e--;
+    int e = (int)ceil(log2(amax / bound));
+    while (ldexp(amax, -e) > bound) e++;
+    while (e > -127 && ldexp(amax, -(e - 1)) <= bound) e--;
     return e;
 }
 
@@ -385,31 +411,38 @@ static int orc_e4m3_block_exp(double amax) {
  * operand, k x ncols) or along columns (the A operand, mrows x k). The result
  * is the dequantised value, stored as float. */
 static void orc_round_operand(int prec, float* X, int64_t r, int64_t c, int64_t ld, int kdim_is_rows) {
-    if (prec == 2) return;
+    if (prec == 3) return;
     if (prec == 0) {
         for (int64_t j = 0; j < c; j++)
             for (int64_t i = 0; i < r; i++) X[j * ld + i] = orc_round_bf16(X[j * ld + i]);
         return;
     }
-    /* FP8 with one scale per operand row (A) or column (B), i.e. per 1 x K
-     * tile along the whole contraction index. */
+    /* FP8 or FP16 with one scale per operand row (A) or column (B), i.e. per
+     * 1 x K tile along the whole contraction index. */
+    const double bound = prec == 1 ? 448.0 : 65504.0;
+    float (*rnd)(float) = prec == 1 ? orc_round_e4m3 : orc_round_fp16;
     if (kdim_is_rows) {
         for (int64_t j = 0; j < c; j++) {
             double amax = 0.0;
             for (int64_t i = 0; i < r; i++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
-            int e = orc_e4m3_block_exp(amax);
+            int e = orc_block_exp(amax, bound);
             for (int64_t i = 0; i < r; i++)
-                X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+                X[j * ld + i] = (float)ldexp(rnd((float)ldexp(X[j * ld + i], -e)), e);
         }
     } else {
         for (int64_t i = 0; i < r; i++) {
             double amax = 0.0;
             for (int64_t j = 0; j < c; j++) if (fabs(X[j * ld + i]) > amax) amax = fabs(X[j * ld + i]);
-            int e = orc_e4m3_block_exp(amax);
+            int e = orc_block_exp(amax, bound);
             for (int64_t j = 0; j < c; j++)
-                X[j * ld + i] = (float)ldexp(orc_round_e4m3((float)ldexp(X[j * ld + i], -e)), e);
+                X[j * ld + i] = (float)ldexp(rnd((float)ldexp(X[j * ld + i], -e)), e);
         }
     }
+}
+
+/* Exported for the tests: the operand rounding above, in place. */
+void orc_round_operand_ext(int prec, float* X, int64_t r, int64_t c, int64_t ld, int kdim_is_rows) {
+    orc_round_operand(prec, X, r, c, ld, kdim_is_rows);
 }
 
 /* C (m x n, ldc) = sub ? C - A*B : A*B, with A (m x k, lda) and B (k x n, ldb)
@@ -501,7 +534,7 @@ int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, 
         for (int64_t c = 0; c < kb; c++)
             if (D[c * lda + c] == 0.0f && !info) info = k0 + c + 1;
         /* 1. D^-1 by Newton-Schulz */
-        orc_newton_schulz(kb, D, lda, ns_iters, prec != 2, X);
+        orc_newton_schulz(kb, D, lda, ns_iters, prec != 3, X);
         for (int64_t j = 0; j < kb; j++)
             for (int64_t i = 0; i < kb; i++) Dinv[j * n + k0 + i] = X[j * kb + i];
         int64_t m = n - k0 - kb;
@@ -515,7 +548,7 @@ int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, 
         /* 2. L21 = A21 Dinv with low-precision operands */
         memcpy(Xq, X, sizeof(float) * kb * kb);
         for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
-        const int pprec = prec == 2 ? 2 : 0;             /* the panel product stays BF16 */
+        const int pprec = prec == 1 ? 0 : prec;          /* FP8: the panel product stays BF16 */
         orc_round_operand(pprec, t21, m, kb, m, 0);      /* A operand: k along columns */
         orc_round_operand(pprec, Xq, kb, kb, kb, 1);     /* B operand: k along rows    */
         orc_gemm32(m, kb, kb, t21, m, Xq, kb, A21, lda, 0);

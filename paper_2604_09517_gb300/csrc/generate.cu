@@ -32,7 +32,7 @@ __global__ void k_generate(uint64_t key, int64_t m, int64_t ncols, double* __res
          t += (int64_t)gridDim.x * blockDim.x) {
         int64_t j = t / m, i = t - j * m;
         uint64_t h = sm64_mix(key + (uint64_t)(t + 1) * kGamma);
-        A[j * lda + i] = (double)(h >> 11) * 0x1p-53 - 0.5;
+        A[j * lda + i] = gen_value(h);
     }
 }
 
@@ -58,8 +58,12 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
     uint64_t lo = 0, hi = 0;
     if (i < n) {
         for (int64_t j = warp; j < n; j += 8) {
-            double a = A[j * lda + i];
-            uint64_t u = (uint64_t)(fabs(a) * 0x1p53);    // exact: |a| is k * 2^-53, k < 2^52
+            // |a| / 2^-53, exact: |a| = k * 2^-53 with k <= 2^52; taken from the bits
+            // (integer operations) as (2^52 + fraction) >> (1022 - biased exponent)
+            const unsigned long long bits = (unsigned long long)__double_as_longlong(A[j * lda + i]);
+            const int e = (int)((bits >> 52) & 0x7ff);
+            const int sh = 1022 - e;
+            uint64_t u = (e == 0 || sh >= 64) ? 0 : (((bits & ((1ull << 52) - 1)) | (1ull << 52)) >> sh);
             uint64_t nl = lo + u;
             hi += (nl < lo);
             lo = nl;
@@ -88,10 +92,9 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, float* __restrict__ F, int64_t ldf) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
-    for (int64_t j = blockIdx.y; j < n; j += gridDim.y) {
-        uint64_t h = sm64_mix(key + (uint64_t)(j * n + i + 1) * kGamma);
-        F[j * ldf + i] = __double2float_rn((double)(h >> 11) * 0x1p-53 - 0.5);
-    }
+    const uint64_t step = (uint64_t)gridDim.y * (uint64_t)n * kGamma;
+    uint64_t z = key + ((uint64_t)blockIdx.y * (uint64_t)n + (uint64_t)i + 1) * kGamma;
+    for (int64_t j = blockIdx.y; j < n; j += gridDim.y, z += step) F[j * ldf + i] = gen_value_f32(sm64_mix(z));
 }
 
 // As k_dominant_diag, with the entries regenerated instead of read:

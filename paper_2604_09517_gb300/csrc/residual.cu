@@ -126,22 +126,34 @@ __global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __
             }
             r += r1;
         }
-    } else if (dominant && diag) {
-        // diagonal known: plain regenerated product over the off-diagonal entries
+    } else if (dominant && diag && want_norm != 2) {
+        // diagonal known: plain regenerated product over the off-diagonal
+        // entries, one FP64 instruction (the FMA) per entry
+        const uint64_t step = (uint64_t)n * 0x9E3779B97F4A7C15ull;
+        uint64_t z = key + ((uint64_t)j0 * (uint64_t)n + (uint64_t)i + 1) * 0x9E3779B97F4A7C15ull;
+        double r1 = 0.0;
         float sf = 0.0f;
-        for (int64_t j = j0; j < j1; j++) {
-            if (j == i) continue;
-            uint64_t h = res_mix(key + (uint64_t)(j * n + i + 1) * 0x9E3779B97F4A7C15ull);
-            double a = (double)(h >> 11) * 0x1p-53 - 0.5;
-            r = fma(a, x[j], r);
-            if (want_norm == 2) s += fabs(a);
-            else if (want_norm == 1) sf += abs_as_float(a);
+        int64_t j = j0;
+        for (; j + 1 < j1; j += 2, z += 2 * step) {
+            const double a0 = j == i ? 0.0 : gen_value(res_mix(z));
+            const double a1 = j + 1 == i ? 0.0 : gen_value(res_mix(z + step));
+            r = fma(a0, x[j], r);
+            r1 = fma(a1, x[j + 1], r1);
+            if (want_norm == 1) sf += abs_as_float(a0) + abs_as_float(a1);
         }
+        if (j < j1) {
+            const double a0 = j == i ? 0.0 : gen_value(res_mix(z));
+            r = fma(a0, x[j], r);
+            if (want_norm == 1) sf += abs_as_float(a0);
+        }
+        r += r1;
         if (want_norm == 1) s = (double)sf;
     } else {
-        for (int64_t j = j0; j < j1; j++) {
-            uint64_t h = res_mix(key + (uint64_t)(j * n + i + 1) * 0x9E3779B97F4A7C15ull);
-            double a = (double)(h >> 11) * 0x1p-53 - 0.5;
+        const uint64_t step = (uint64_t)n * 0x9E3779B97F4A7C15ull;
+        uint64_t z = key + ((uint64_t)j0 * (uint64_t)n + (uint64_t)i + 1) * 0x9E3779B97F4A7C15ull;
+        for (int64_t j = j0; j < j1; j++, z += step) {
+            uint64_t h = res_mix(z);
+            double a = gen_value(h);
             if (dominant) {
                 uint64_t m = h >> 11, u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
                 uint64_t nl = lo + u;

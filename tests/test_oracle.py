@@ -309,6 +309,43 @@ def test_round_e4m3_matches_torch(orc):
     assert orc.round_e4m3(1000.0) == 448.0 and orc.round_e4m3(-500.0) == -448.0
 
 
+def test_round_fp16_matches_numpy(orc):
+    """IEEE binary16 round-to-nearest-even against NumPy's float16 cast:
+    normals, subnormals (spacing 2^-24), exact ties, the overflow threshold."""
+    rng = np.random.default_rng(3)
+    vals = (rng.standard_normal(4000) * 2.0 ** rng.integers(-30, 17, 4000)).astype(np.float32)
+    ties = np.array([(2 * k + 1) * 2.0 ** (e - 11) for e in range(-13, 16) for k in (1024, 1500, 2047)],
+                    dtype=np.float32)                                  # halfway between two binary16 values
+    sub = np.array([(k + 0.5) * 2.0 ** -24 for k in range(-40, 40)], dtype=np.float32)
+    edge = np.float32([65504.0, 65519.0, 65520.0, -65520.0, 2.0 ** -14, 2.0 ** -25, 2.0 ** -26, 0.0, -0.0])
+    vals = np.concatenate([vals, ties, -ties, sub, edge])
+    with np.errstate(over="ignore"):
+        want = vals.astype(np.float16).astype(np.float32)
+    got = np.array([orc.round_fp16(v) for v in vals], dtype=np.float32)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("prec,bound,rnd", [(1, 448.0, "round_e4m3"), (2, 65504.0, "round_fp16")])
+def test_scaled_operand_rounding(orc, prec, bound, rnd):
+    """FP8 / FP16 operands: per A-operand row (per B-operand column) the scale
+    is the smallest power of two 2^e with max|x| 2^-e <= bound (found here by
+    brute force over e), and every entry is 2^e round(x 2^-e)."""
+    rng = np.random.default_rng(prec)
+    X = (rng.standard_normal((37, 23)) * 10.0 ** rng.integers(-9, 6, (37, 1))).astype(np.float32)
+    X[5, :] = 0.0                                       # an all-zero row keeps scale 1
+    f = getattr(orc, rnd)
+    for kdim_is_rows, Y in ((False, X), (True, X.T.copy())):
+        Q = orc.round_operand(prec, Y, kdim_is_rows)
+        lines = range(Y.shape[1]) if kdim_is_rows else range(Y.shape[0])
+        for t in lines:
+            y = Y[:, t] if kdim_is_rows else Y[t, :]
+            q = Q[:, t] if kdim_is_rows else Q[t, :]
+            amax = float(np.abs(y.astype(np.float64)).max())
+            e = 0 if amax == 0.0 else min(e for e in range(-160, 160) if amax * 2.0 ** -e <= bound)
+            want = np.array([np.ldexp(f(float(np.ldexp(np.float64(v), -e))), e) for v in y], dtype=np.float32)
+            assert np.array_equal(q, want), (kdim_is_rows, t)
+
+
 # --- HPL-MxP emulation ---------------------------------------------------------------
 
 def test_mxp_factor_fp32_mode_is_block_lu(orc):
@@ -337,7 +374,7 @@ def test_mxp_factor_fp32_mode_is_block_lu(orc):
 def test_newton_schulz_inverse_accuracy(orc):
     n, nb = 512, 256
     A = orc.generate(14, orc.STREAM_A, n, n, dominant=True)
-    for prec, tol in ((orc.PREC_BF16, 2e-5), (orc.PREC_FP8, 2e-5), (orc.PREC_FP32, 5e-6)):
+    for prec, tol in ((orc.PREC_BF16, 2e-5), (orc.PREC_FP8, 2e-5), (orc.PREC_FP16, 2e-5), (orc.PREC_FP32, 5e-6)):
         F, Dinv, _ = orc.mxp_factor(A, nb, prec)
         for k0 in range(0, n, nb):
             s = slice(k0, k0 + nb)
@@ -358,10 +395,13 @@ def test_mxp_factor_lowprec_error_levels(orc):
         L, U = orc.block_lu_parts(F, nb)
         return np.abs(A - L @ U).max() / np.abs(A[~np.eye(n, dtype=bool)]).max()
 
-    e32, e16, e8 = err(orc.PREC_FP32), err(orc.PREC_BF16), err(orc.PREC_FP8)
+    e32, e16, e8, eh = err(orc.PREC_FP32), err(orc.PREC_BF16), err(orc.PREC_FP8), err(orc.PREC_FP16)
     assert e32 < 1e-4
     assert e32 < e16 < 2.0 ** -6
     assert e16 < e8 < 2.0 ** -2
+    # FP16 keeps 11 significant bits against BF16's 8 (and its scale keeps L21
+    # out of the subnormal range)
+    assert e32 < eh < e16 / 4
 
 
 def test_mxp_factor_diagonal_matrix_exact(orc):
