@@ -41,7 +41,8 @@ DGEMM_DRAM_BYTES_PER_FLOP = 959.8e6 / 31.21e9
 # Same for the tcgen05 trailing update of the mixed-precision solve, from one
 # ncu capture each of a step-0 update at n = 24576 (BF16: m = 21504, k = 3072,
 # 5.264 GB for 2.841 TFLOP; FP8: m = 20480, k = 4096, 3.820 GB for 3.436 TFLOP).
-MXP_DRAM_BYTES_PER_FLOP = {0: 5.264e9 / 2.841e12, 1: 3.820e9 / 3.436e12}
+# FP16 (the BF16 kernel with F16 inputs): not captured, reported as null.
+MXP_DRAM_BYTES_PER_FLOP = {0: 5.264e9 / 2.841e12, 1: 3.820e9 / 3.436e12, 2: None}
 
 
 def flops(n: int) -> float:
@@ -550,14 +551,15 @@ def run_small(a, d: Dist, dev):
 
 def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
     """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
-    block-LU factor on the tcgen05 tensor cores (BF16 update, or FP8 E4M3 with
-    prec = 1) + FP64 GMRES refinement. regen: the library regenerates A from
-    the seed instead of reading a stored FP64 copy."""
+    block-LU factor on the tcgen05 tensor cores (BF16 update; FP8 E4M3 with
+    prec = 1, NB = 4096; scaled FP16 with prec = 2) + FP64 GMRES refinement.
+    regen: the library regenerates A from the seed instead of reading a
+    stored FP64 copy."""
     import torch
 
     import paper_2604_09517_gb300 as hpl
 
-    n, nb, seed = a.mxp_n, (a.mxp_fp8_nb if prec else a.mxp_nb), a.seed
+    n, nb, seed = a.mxp_n, (a.mxp_fp8_nb if prec == 1 else a.mxp_nb), a.seed
     A = None if regen else hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
     b = hpl.generate(seed, hpl.STREAM_B, n, 1, device=dev)[:, 0].contiguous()
     X = hpl.colmajor(n, 1, device=dev)
@@ -591,10 +593,10 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
     upd_ms, upd_flops, upd_cnt = phases["update"]
     achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
     # FP8 dense peak: the measured BF16 peak times the nominal FP8/BF16 ratio (4.5 / 2.25)
-    peak = peaks["bf16_tflops_sustained"] * (2.0 if prec else 1.0)
+    peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == 1 else 1.0)
     del A, X, ws
     torch.cuda.empty_cache()
-    tag = "fp8e4m3" if prec else "bf16"
+    tag = {0: "bf16", 1: "fp8e4m3", 2: "fp16"}[prec]
     # the factorization alone: the step minus its refinement phase
     refine_ms = phases["refine"][0] / len(step_ms) if phases["refine"][2] else 0.0
     factor_ms = total_ms / len(step_ms) - refine_ms
@@ -616,9 +618,10 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
                       + ("; regenerated from the seed, never stored" if regen else "; stored FP64"),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": MXP_DRAM_BYTES_PER_FLOP[prec] * upd_flops / upd_cnt if upd_cnt else None,
+                         "traffic": (MXP_DRAM_BYTES_PER_FLOP[prec] * upd_flops / upd_cnt
+                                     if upd_cnt and MXP_DRAM_BYTES_PER_FLOP[prec] else None),
                          "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
-                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec else ""),
+                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec == 1 else ""),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
             "phases": {k: {"ms_per_step": v[0] / len(step_ms), "intervals": v[2]} for k, v in phases.items() if v[2]}}
 
@@ -752,6 +755,7 @@ def run_ours(a, d: Dist):
     small = run_small(a, d, dev)
     mxp = None if a.no_mxp else run_mxp(a, d, dev, value, cpu=cpu)
     mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1, cpu=cpu)
+    mxp_fp16 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=2, cpu=cpu)
     mxp_regen = None if a.no_mxp else run_mxp(a, d, dev, value, regen=True)
     batched = None if a.no_batched else run_batched(a, d, dev)
     adjoint = None if a.no_adjoint else run_adjoint(a, d, dev)
@@ -768,7 +772,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report, "step_model": model,
-                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_regenerated": mxp_regen, "batched": batched, "adjoint": adjoint}
+                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_fp16": mxp_fp16, "mxp_regenerated": mxp_regen, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 

@@ -29,6 +29,7 @@ GEN_GENERAL = 0
 GEN_DIAG_DOMINANT = 1
 PREC_BF16 = 0
 PREC_FP8_E4M3 = 1
+PREC_FP16 = 2
 REFINE_IR = 0
 REFINE_GMRES = 1
 STREAM_A = 0
@@ -93,6 +94,7 @@ def load():
             "hpl_scaled_residual": (i32, [i64, vp, i64, u64, i32, vp, vp, vp, vp, sz, vp]),
             "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
             "hplgb_gemm_fp8": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, vp, vp, i64, i32, vp, vp]),
+            "hplgb_gemm_f16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, vp, vp, i64, i32, vp, vp]),
             "mxp_workspace_size": (sz, [i64, i64, op]),
             "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hpl_batch_sizes": (i32, [u64, i64, vp]),
@@ -479,6 +481,23 @@ def gemm_fp8(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None
     e = int(err.item())
     if e:
         raise HplError(e, "hplgb_gemm_fp8 (device)")
+    return C
+
+
+def gemm_f16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None, sub: bool = True) -> torch.Tensor:
+    """C = C - (A B^T) * sa sb^T (sub) or the product, A and B float16 with K contiguous."""
+    lib = load()
+    assert A.dtype == torch.float16 and B.dtype == torch.float16 and C.dtype == torch.float32
+    assert A.stride(1) == 1 and B.stride(1) == 1 and C.stride(0) == 1
+    M, K = A.shape
+    N = B.shape[0]
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    _check(lib.hplgb_gemm_f16(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(sa), _ptr(sb), _ptr(C),
+                              _ld(C), int(sub), _ptr(err), _stream(C.device)), "hplgb_gemm_f16")
+    torch.cuda.current_stream(C.device).synchronize()
+    e = int(err.item())
+    if e:
+        raise HplError(e, "hplgb_gemm_f16 (device)")
     return C
 
 

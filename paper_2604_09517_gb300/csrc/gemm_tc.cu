@@ -39,7 +39,7 @@ constexpr int THREADS = 320;
 // Row tiles per band of the tile walk (measured on GB300 at M = N = 49152 and
 // 95232, K = 3072: BF16 16 and FP8 32 for the single-CTA kernel).
 template <int KIND>
-constexpr int group_m() { return KIND == 0 ? 16 : 32; }
+constexpr int group_m() { return KIND == 1 ? 32 : 16; }
 constexpr int GROUP_M_PAIR = 16;
 // The pair kernel only for products up to this size (M x N): under the power
 // cap, with FP32 C read and written every step, the single-CTA kernel is as
@@ -62,10 +62,11 @@ struct Tile {
 };
 
 // Operand kinds: 0 = BF16 (kind::f16, 2 bytes, 64 K per stage), 1 = FP8 E4M3
-// (kind::f8f6f4, 1 byte, 128 K per stage). Either way one MMA consumes 32
-// bytes of K (16 BF16 or 32 E4M3 values).
+// (kind::f8f6f4, 1 byte, 128 K per stage), 2 = FP16 (kind::f16, 2 bytes).
+// Either way one MMA consumes 32 bytes of K (16 BF16 / FP16 or 32 E4M3
+// values); A and B always have the same type.
 // Instruction descriptor: D = F32 (bits 4-5 = 1); A and B formats in bits
-// 7-9 and 10-12 (BF16 = 1 for kind::f16; E4M3 = 0 for kind::f8f6f4); both
+// 7-9 and 10-12 (kind::f16: F16 = 0, BF16 = 1; kind::f8f6f4: E4M3 = 0); both
 // K-major (bits 15, 16 = 0); N >> 3 at bits 17-22; M >> 4 at bits 24-28.
 template <int KIND>
 struct Kind;
@@ -77,6 +78,11 @@ struct Kind<0> {
 template <>
 struct Kind<1> {
     static constexpr int ELEM = 1;
+    static constexpr uint32_t FORMATS = (1u << 4);
+};
+template <>
+struct Kind<2> {
+    static constexpr int ELEM = 2;
     static constexpr uint32_t FORMATS = (1u << 4);
 };
 template <int KIND, int BN>
@@ -158,12 +164,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 
 template <int KIND, int BN>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    if constexpr (KIND == 0) {
+    if constexpr (KIND == 0 || KIND == 2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc<0, BN>()), "r"(accumulate)
+            "l"(adesc), "l"(bdesc), "r"(idesc<KIND, BN>()), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
@@ -425,12 +431,12 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
 
 template <int KIND>
 __device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    if constexpr (KIND == 0) {
+    if constexpr (KIND == 0 || KIND == 2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
             "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
-            "l"(adesc), "l"(bdesc), "r"(idesc_pair<0>()), "r"(accumulate)
+            "l"(adesc), "l"(bdesc), "r"(idesc_pair<KIND>()), "r"(accumulate)
             : "memory");
     } else {
         asm volatile(
@@ -787,6 +793,17 @@ int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t l
     return tc::launch_kind<1, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
 }
 
+// FP16 operands (K contiguous) with the same per-row / per-column scales.
+int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                    int max_ctas, cudaStream_t s) {
+    if (tc::pair_tiles(M, N))
+        return tc::launch_pair<2>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<2, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    return tc::launch_kind<2, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+}
+
 }  // namespace hplgb
 
 using namespace hplgb;
@@ -802,4 +819,11 @@ extern "C" int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A,
                               int32_t* err, void* stream) {
     if (!err || !C || !A || !B) return HPL_ERR_INVALID;
     return launch_gemm_fp8(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
+}
+
+extern "C" int hplgb_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                              int64_t ldb, const float* sa, const float* sb, float* C, int64_t ldc, int sub,
+                              int32_t* err, void* stream) {
+    if (!err || !C || !A || !B) return HPL_ERR_INVALID;
+    return launch_gemm_f16(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
 }

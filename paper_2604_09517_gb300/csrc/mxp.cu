@@ -20,6 +20,7 @@
 // host), x += d. The host reads one scalar per GMRES step and per outer
 // iteration, so mxp_solve returns only when the solve is done.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 
 #include <algorithm>
@@ -32,6 +33,9 @@ namespace hplgb {
 
 int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                      float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s);
+int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
+                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                    int max_ctas, cudaStream_t s);
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s);
@@ -159,11 +163,37 @@ __device__ __forceinline__ unsigned char to_e4m3(float x) {
     return (unsigned char)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
 }
 
+// Scaled low-precision operands (FMT 1 = FP8 E4M3, 2 = FP16): one
+// power-of-two scale per operand row (A) or column (B), the smallest 2^e with
+// max|x| 2^-e within the format's largest finite value (448 for E4M3,
+// 65504 = (1 - 2^-11) 2^16 for FP16).
+__device__ __forceinline__ int f16_scale_exp(float amax) {
+    if (!(amax > 0.0f) || !isfinite(amax)) return 0;
+    int E;
+    float f = frexpf(amax, &E);
+    return f <= 0.99951171875f ? E - 16 : E - 15;
+}
+template <int FMT>
+struct LowFmt;
+template <>
+struct LowFmt<1> {
+    using T = unsigned char;
+    static __device__ __forceinline__ int scale_exp(float amax) { return e4m3_scale_exp(amax); }
+    static __device__ __forceinline__ T cvt(float x) { return to_e4m3(x); }
+};
+template <>
+struct LowFmt<2> {
+    using T = uint16_t;
+    static __device__ __forceinline__ int scale_exp(float amax) { return f16_scale_exp(amax); }
+    static __device__ __forceinline__ T cvt(float x) { return __half_as_ushort(__float2half_rn(x)); }
+};
+
 // A operand: X (rows x cols, column-major) -> out row r = X(r, :) (K = cols),
 // sa[r] = 2^e. 32 rows per CTA, the 8 warps split the columns.
-__global__ void __launch_bounds__(256) k_quant_rows_e4m3(const float* __restrict__ X, int64_t ldx, int64_t rows,
-                                                         int64_t cols, unsigned char* __restrict__ out, int64_t ldo,
-                                                         int64_t kpad, float* __restrict__ sa) {
+template <int FMT>
+__global__ void __launch_bounds__(256) k_quant_rows(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                    int64_t cols, typename LowFmt<FMT>::T* __restrict__ out,
+                                                    int64_t ldo, int64_t kpad, float* __restrict__ sa) {
     __shared__ float part[8][33];
     __shared__ float inv[32];
     __shared__ float tile[32][33];
@@ -178,7 +208,7 @@ __global__ void __launch_bounds__(256) k_quant_rows_e4m3(const float* __restrict
     if (warp == 0) {
         float m = 0.0f;
         for (int w = 0; w < 8; w++) m = fmaxf(m, part[w][lane]);
-        const int e = e4m3_scale_exp(m);
+        const int e = LowFmt<FMT>::scale_exp(m);
         inv[lane] = ldexpf(1.0f, -e);
         if (r < rows) sa[r] = ldexpf(1.0f, e);
     }
@@ -191,7 +221,7 @@ __global__ void __launch_bounds__(256) k_quant_rows_e4m3(const float* __restrict
         __syncthreads();
         for (int i = warp; i < 32; i += 8) {
             const int64_t rr = r0 + i, c = c0 + lane;
-            if (rr < rows && c < kpad) out[rr * ldo + c] = to_e4m3(tile[i][lane] * inv[i]);
+            if (rr < rows && c < kpad) out[rr * ldo + c] = LowFmt<FMT>::cvt(tile[i][lane] * inv[i]);
         }
         __syncthreads();
     }
@@ -199,9 +229,10 @@ __global__ void __launch_bounds__(256) k_quant_rows_e4m3(const float* __restrict
 
 // B operand: X (K rows x cols, column-major) -> out row c = X(:, c), sb[c] = 2^e.
 // One warp per column.
-__global__ void __launch_bounds__(256) k_quant_cols_e4m3(const float* __restrict__ X, int64_t ldx, int64_t rows,
-                                                         int64_t cols, unsigned char* __restrict__ out, int64_t ldo,
-                                                         int64_t kpad, float* __restrict__ sb) {
+template <int FMT>
+__global__ void __launch_bounds__(256) k_quant_cols(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                    int64_t cols, typename LowFmt<FMT>::T* __restrict__ out,
+                                                    int64_t ldo, int64_t kpad, float* __restrict__ sb) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= cols) return;
@@ -209,10 +240,10 @@ __global__ void __launch_bounds__(256) k_quant_cols_e4m3(const float* __restrict
     float amax = 0.0f;
     for (int64_t r = lane; r < rows; r += 32) amax = fmaxf(amax, fabsf(col[r]));
     for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
-    const int e = e4m3_scale_exp(amax);
+    const int e = LowFmt<FMT>::scale_exp(amax);
     const float inv = ldexpf(1.0f, -e);
     if (lane == 0) sb[c] = ldexpf(1.0f, e);
-    for (int64_t r = lane; r < kpad; r += 32) out[c * ldo + r] = to_e4m3(r < rows ? col[r] * inv : 0.0f);
+    for (int64_t r = lane; r < kpad; r += 32) out[c * ldo + r] = LowFmt<FMT>::cvt(r < rows ? col[r] * inv : 0.0f);
 }
 
 // ---------------------------------------------------------------------------
@@ -653,8 +684,8 @@ struct MxpWs {
     double* scal;      // 4 device scalars (sr, beta, ...)
     float* y32;        // 2n FP32 scratch
     int* err;          // device error word of the GEMM kernels
-    float* sa;         // n: FP8 row scales of the update's A operand
-    float* sb;         // n: FP8 column scales of the update's B operand
+    float* sa;         // n: FP8 / FP16 row scales of a scaled product's A operand
+    float* sb;         // n: FP8 / FP16 column scales of its B operand
     float* gpart;      // kGemvSplitMax x n: column-split GEMV partial sums
     double* gdiag;     // n: FP64 diagonal of a regenerated matrix (A == NULL)
     // block refinement of nrhs_blk right-hand sides (absent when 0)
@@ -808,11 +839,22 @@ struct Mxp {
                 float* A21 = w.F + k0 * ldf + k0 + kb;
                 float* A12 = w.F + (k0 + kb) * ldf + k0;
                 float* A22 = w.F + (k0 + kb) * ldf + k0 + kb;
-                // L21 = A21 D^-1
-                if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
-                if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
-                if ((st = launch_gemm_bf16(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0, w.err, o.timeout_ns, 0, s)))
-                    return st;
+                // L21 = A21 D^-1 (FP16 operands with scales for FP16, else BF16)
+                if (o.prec == HPL_PREC_FP16) {
+                    k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa);
+                    HPL_LAUNCH_CHECK();
+                    k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb);
+                    HPL_LAUNCH_CHECK();
+                    if ((st = launch_gemm_f16(m2, kb, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A21, ldf, 0, w.err,
+                                              o.timeout_ns, 0, s)))
+                        return st;
+                } else {
+                    if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
+                    if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                    if ((st = launch_gemm_bf16(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0, w.err, o.timeout_ns, 0,
+                                               s)))
+                        return st;
+                }
                 phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
                 // A22 -= L21 A12
                 slot = phase_begin(s);
@@ -820,11 +862,19 @@ struct Mxp {
                     const int64_t kb16 = (kb + 15) / 16 * 16;
                     uint8_t* qa = (uint8_t*)w.opA;
                     uint8_t* qb = (uint8_t*)w.opB;
-                    k_quant_rows_e4m3<<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa);
+                    k_quant_rows<1><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa);
                     HPL_LAUNCH_CHECK();
-                    k_quant_cols_e4m3<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb);
+                    k_quant_cols<1><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb);
                     HPL_LAUNCH_CHECK();
                     if ((st = launch_gemm_fp8(m2, m2, kb, qa, kb16, qb, kb16, w.sa, w.sb, A22, ldf, 1, w.err,
+                                              o.timeout_ns, 0, s)))
+                        return st;
+                } else if (o.prec == HPL_PREC_FP16) {
+                    k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa);
+                    HPL_LAUNCH_CHECK();
+                    k_quant_cols<2><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, w.opB, kb8, kb8, w.sb);
+                    HPL_LAUNCH_CHECK();
+                    if ((st = launch_gemm_f16(m2, m2, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A22, ldf, 1, w.err,
                                               o.timeout_ns, 0, s)))
                         return st;
                 } else {
@@ -1171,7 +1221,7 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, kMxpDefaultNb);
-    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return HPL_ERR_INVALID;
     if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
     if (o.ns_iters > 8) return HPL_ERR_INVALID;
     Mxp mx;
@@ -1235,7 +1285,7 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
     if (n > 0x7fffffff) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, kMxpDefaultNb);
-    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3)) return HPL_ERR_INVALID;
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return HPL_ERR_INVALID;
     Mxp mx;
     mx.n = n;
     mx.nb = std::min<int64_t>(o.nb, n);

@@ -76,6 +76,35 @@ def test_gemm_fp8_matches_fp64(hpl, M, N, K, sub, scaled):
     assert (err > tol).sum().item() == 0, err.max().item()
 
 
+@pytest.mark.parametrize("M,N,K,sub,scaled", [(128, 256, 128, True, False), (300, 500, 200, True, True),
+                                              (1536, 2048, 1536, True, True), (257, 129, 64, False, True),
+                                              (2304, 2560, 256, True, True), (2404, 2100, 200, True, True)])
+def test_gemm_f16_matches_fp64(hpl, M, N, K, sub, scaled):
+    """FP16 operands (kind::f16 with F16 inputs), optional power-of-two row and
+    column scales, against the FP64 product of the same FP16 values."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M + N + K + 1)
+    ld = (K + 7) // 8 * 8
+    A = (torch.randn(M, ld, device="cuda", generator=g) * 1000).to(torch.float16)[:, :K]
+    B = (torch.randn(N, ld, device="cuda", generator=g) * 1000).to(torch.float16)[:, :K]
+    sa = torch.pow(2.0, torch.randint(-20, 4, (M,), device="cuda", generator=g).float()) if scaled else None
+    sb = torch.pow(2.0, torch.randint(-4, 4, (N,), device="cuda", generator=g).float()) if scaled else None
+    C = hpl.colmajor(M, N, dtype=torch.float32)
+    C.copy_(torch.randn(M, N, device="cuda", generator=g))
+    C0 = C.clone()
+    hpl.gemm_f16(A, B, C, sa, sb, sub=sub)
+    Ad, Bd = A.double(), B.double()
+    if scaled:
+        Ad = Ad * sa.double()[:, None]
+        Bd = Bd * sb.double()[:, None]
+    prod = Ad @ Bd.t()
+    ref = C0.double() - prod if sub else prod
+    bound = Ad.abs() @ Bd.abs().t()
+    err = (C.double() - ref).abs()
+    tol = (K * 2.0 ** -23 + 1e-6) * bound + 2.0 ** -23 * C0.double().abs()
+    assert (err > tol).sum().item() == 0, err.max().item()
+
+
 @pytest.mark.parametrize("M,N,K", [(256, 512, 2304), (2304, 2560, 1536), (130, 70, 264)])
 def test_gemm_bf16_small_integer_products_are_exact(hpl, M, N, K):
     """Integer BF16 operands below 2^6 in magnitude: every product and every
