@@ -87,61 +87,75 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 // mixed-precision solve that keeps no FP64 copy of A (its residuals
 // regenerate the entries). Every entry is the FP64 generated value rounded to
 // nearest FP32, exactly what converting a stored FP64 matrix gives.
-
-// Rows in blocks of 256 (blockIdx.x), columns strided over gridDim.y.
-__global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, float* __restrict__ F, int64_t ldf) {
+//
+// One pass over the entries: rows in blocks of 256 (blockIdx.x), `chunks`
+// column chunks (blockIdx.y). Per (row, chunk) the kernel writes the FP32
+// entries, the exact sum of |a_ij| / 2^-53 = |(h >> 11) - 2^52| over the
+// chunk in 128 bits (the diagonal's dominance, all j), and the FP32 sum of
+// |fl32(a_ij)| over the chunk's off-diagonal entries (||A||_inf for the
+// refinement's stopping test).
+__global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, float* __restrict__ F, int64_t ldf,
+                                                      int chunks, uint64_t* __restrict__ plo,
+                                                      uint64_t* __restrict__ phi, float* __restrict__ pf) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
-    const uint64_t step = (uint64_t)gridDim.y * (uint64_t)n * kGamma;
-    uint64_t z = key + ((uint64_t)blockIdx.y * (uint64_t)n + (uint64_t)i + 1) * kGamma;
-    for (int64_t j = blockIdx.y; j < n; j += gridDim.y, z += step) F[j * ldf + i] = gen_value_f32(sm64_mix(z));
+    const int64_t cw = (n + chunks - 1) / chunks;
+    const int64_t j0 = (int64_t)blockIdx.y * cw, j1 = std::min<int64_t>(n, j0 + cw);
+    const uint64_t step = (uint64_t)n * kGamma;
+    uint64_t z = key + ((uint64_t)j0 * (uint64_t)n + (uint64_t)i + 1) * kGamma;
+    uint64_t lo = 0, hi = 0;
+    float sf = 0.0f;
+    for (int64_t j = j0; j < j1; j++, z += step) {
+        const uint64_t h = sm64_mix(z);
+        const float v = gen_value_f32(h);
+        F[j * ldf + i] = v;
+        const uint64_t m = h >> 11, u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
+        const uint64_t nl = lo + u;
+        hi += (nl < lo);
+        lo = nl;
+        sf += j == i ? 0.0f : fabsf(v);
+    }
+    plo[(int64_t)blockIdx.y * n + i] = lo;
+    phi[(int64_t)blockIdx.y * n + i] = hi;
+    pf[(int64_t)blockIdx.y * n + i] = sf;
 }
 
-// As k_dominant_diag, with the entries regenerated instead of read:
-// |a_ij| / 2^-53 = |(h >> 11) - 2^52| exactly. Writes the FP64 diagonal to
-// diag and its FP32 rounding onto the diagonal of F.
-__global__ void __launch_bounds__(256) k_dominant_diag_gen(uint64_t key, int64_t n, double* __restrict__ diag,
-                                                           float* __restrict__ F, int64_t ldf) {
-    __shared__ uint64_t s_lo[8][32], s_hi[8][32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t i = (int64_t)blockIdx.x * 32 + lane;
+// Per row: the exact row sum over the chunks, rounded once, is the FP64
+// diagonal (into diag); its FP32 rounding goes onto F's diagonal and into the
+// row's norm partial of the chunk that holds column i.
+__global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks, const uint64_t* __restrict__ plo,
+                                                           const uint64_t* __restrict__ phi, double* __restrict__ diag,
+                                                           float* __restrict__ F, int64_t ldf, float* __restrict__ pf) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
+    if (i >= n) return;
     uint64_t lo = 0, hi = 0;
-    if (i < n) {
-        for (int64_t j = warp; j < n; j += 8) {
-            uint64_t m = sm64_mix(key + (uint64_t)(j * n + i + 1) * kGamma) >> 11;
-            uint64_t u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
-            uint64_t nl = lo + u;
-            hi += (nl < lo);
-            lo = nl;
-        }
+    for (int c = 0; c < chunks; c++) {
+        const uint64_t nl = lo + plo[(int64_t)c * n + i];
+        hi += phi[(int64_t)c * n + i] + (nl < lo);
+        lo = nl;
     }
-    s_lo[warp][lane] = lo;
-    s_hi[warp][lane] = hi;
-    __syncthreads();
-    if (warp == 0 && i < n) {
-        for (int w = 1; w < 8; w++) {
-            uint64_t nl = lo + s_lo[w][lane];
-            hi += s_hi[w][lane] + (nl < lo);
-            lo = nl;
-        }
-        const double d = u128_to_double_rn(hi, lo) * 0x1p-53;
-        diag[i] = d;
-        F[i * ldf + i] = __double2float_rn(d);
-    }
+    const double d = u128_to_double_rn(hi, lo) * 0x1p-53;
+    diag[i] = d;
+    const float f = __double2float_rn(d);
+    F[i * ldf + i] = f;
+    const int64_t cw = (n + chunks - 1) / chunks;
+    pf[(i / cw) * n + i] += fabsf(f);
 }
 
 // Stream 0 (the matrix) of seed, kind HPL_GEN_DIAG_DOMINANT, n x n, as FP32
 // into F (ldf >= n) with the FP64 diagonal into diag (n doubles); returns the
-// stream key the residual kernels regenerate from in *key_out.
+// stream key the residual kernels regenerate from in *key_out. plo, phi
+// (chunks x n each) are scratch; pf (chunks x n) receives the row sums of
+// |F| split by column chunk.
 int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
-                                 cudaStream_t s) {
+                                 int chunks, uint64_t* plo, uint64_t* phi, float* pf, cudaStream_t s) {
     const uint64_t key = sm64_host_mix(seed + 1 * kGamma);
     if (key_out) *key_out = key;
     if (n <= 0) return HPL_OK;
-    k_generate_f32<<<dim3((unsigned)((n + 255) / 256), (unsigned)std::min<int64_t>(n, 1024)), 256, 0, s>>>(key, n, F,
-                                                                                                           ldf);
+    k_generate_f32<<<dim3((unsigned)((n + 255) / 256), (unsigned)chunks), 256, 0, s>>>(key, n, F, ldf, chunks, plo,
+                                                                                     phi, pf);
     HPL_LAUNCH_CHECK();
-    k_dominant_diag_gen<<<(unsigned)((n + 31) / 32), 256, 0, s>>>(key, n, diag, F, ldf);
+    k_dominant_diag_fin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, chunks, plo, phi, diag, F, ldf, pf);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }

@@ -44,6 +44,7 @@ int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, c
                         const double* anorm, const double* x, const double* b, double* r, double* sr, void* ws,
                         cudaStream_t s);
 int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
+                                 int chunks, uint64_t* plo, uint64_t* phi, float* pf,
                                  cudaStream_t s);
 int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, double* anorm, int norm_mode, const double* x,
                           const double* b, double* r, double* sr, void* ws, cudaStream_t s);
@@ -248,27 +249,10 @@ __global__ void __launch_bounds__(256) k_quant_cols(const float* __restrict__ X,
 
 // ---------------------------------------------------------------------------
 // Small dense kernels.
-// F = fl32(A): CTA x-index = 1024-row chunk, y-index strides over columns.
 // ||A||_inf for the refinement's stopping test, taken once per solve from the
 // FP32 working copy before it is factored (each |a_ij| within 2^-24 of the FP64
-// value): row sums of |F| over column chunks, then the largest row.
-__global__ void __launch_bounds__(256) k_abs_rowsum_part(int64_t n, const float* __restrict__ F, int64_t ldf,
-                                                         int chunks, float* __restrict__ part) {
-    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
-    if (i >= n) return;
-    const int64_t cw = (n + chunks - 1) / chunks;
-    const int64_t j0 = (int64_t)blockIdx.y * cw, j1 = std::min<int64_t>(n, j0 + cw);
-    float s0 = 0.0f, s1 = 0.0f;
-    int64_t j = j0;
-#pragma unroll 4
-    for (; j + 1 < j1; j += 2) {
-        s0 += fabsf(F[j * ldf + i]);
-        s1 += fabsf(F[(j + 1) * ldf + i]);
-    }
-    if (j < j1) s0 += fabsf(F[j * ldf + i]);
-    part[(int64_t)blockIdx.y * n + i] = s0 + s1;
-}
-
+// value): the conversion (stored A) or the generator (regenerated A) leaves
+// row sums of |F| per column chunk; the largest row is taken here.
 __global__ void __launch_bounds__(256) k_abs_rowsum_max(int64_t n, int chunks, const float* __restrict__ part,
                                                         unsigned long long* out) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -687,6 +671,8 @@ struct MxpWs {
     float* sa;         // n: FP8 / FP16 row scales of a scaled product's A operand
     float* sb;         // n: FP8 / FP16 column scales of its B operand
     float* gpart;      // kGemvSplitMax x n: column-split GEMV partial sums
+    uint64_t* glo;     // kGemvSplitMax x n: exact row-sum partials of a regenerated matrix (low words)
+    uint64_t* ghi;     // kGemvSplitMax x n: (high words)
     double* gdiag;     // n: FP64 diagonal of a regenerated matrix (A == NULL)
     // block refinement of nrhs_blk right-hand sides (absent when 0)
     float* Yb;         // n x nrhs_blk FP32
@@ -728,6 +714,8 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, 
     t.sa = (float*)take(sizeof(float) * n);
     t.sb = (float*)take(sizeof(float) * n);
     t.gpart = (float*)take(sizeof(float) * kGemvSplitMax * n);
+    t.glo = (uint64_t*)take(sizeof(uint64_t) * kGemvSplitMax * n);
+    t.ghi = (uint64_t*)take(sizeof(uint64_t) * kGemvSplitMax * n);
     t.gdiag = (double*)take(sizeof(double) * n);
     t.Yb = (float*)take(sizeof(float) * n * nrhs_blk);
     t.Tb = (float*)take(sizeof(float) * nb * nrhs_blk);
@@ -800,11 +788,10 @@ struct Mxp {
                                                                                             kGemvSplitMax, w.gpart);
             HPL_LAUNCH_CHECK();
         } else {
-            int st = launch_generate_dominant_f32(seed, n, w.F, ldf, w.gdiag, &key, s);
+            // one pass: the FP32 entries, the exact diagonal and the norm's row sums
+            int st = launch_generate_dominant_f32(seed, n, w.F, ldf, w.gdiag, &key, kGemvSplitMax, w.glo, w.ghi,
+                                                  w.gpart, s);
             if (st) return st;
-            k_abs_rowsum_part<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, w.F, ldf,
-                                                                                              kGemvSplitMax, w.gpart);
-            HPL_LAUNCH_CHECK();
         }
         HPL_CUDA_TRY(cudaMemsetAsync(w.scal + 6, 0, sizeof(double), s));
         k_abs_rowsum_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, kGemvSplitMax, w.gpart,
