@@ -138,7 +138,8 @@ __device__ void upd64(double* A, long long lda, const double* P, int prow, int m
 }
 
 template <int NB>
-__device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long* redi, hpl_info* info) {
+__device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long long* redi, hpl_info* info) {
+    __shared__ int s_np, s_dst[2 * NBMAX], s_src[2 * NBMAX], s_pos[2 * NBMAX], s_con[2 * NBMAX];
     const int n = (int)S.n;
     const long long lda = S.lda;
     double* A = S.A;
@@ -152,27 +153,23 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
         }
         __syncthreads();
         for (int j = 0; j < kb; j++) {
-            // argmax of |P(j.., j)|, first index on ties
-            double bv = -1.0;
-            long long br = 0x7fffffffffffffffLL;
+            // argmax of |P(j.., j)|, first index on ties, on integer keys
+            // (mag_key: no FP64 compares, which issue at the FP64 rate)
+            long long bk = -1, br = 0x7fffffffffffffffLL;
             for (int r = j + threadIdx.x; r < pm; r += THREADS) {
-                double v = fabs(P[r * PS + j]);
-                if (v > bv || (v == bv && r < br)) { bv = v; br = r; }
+                const long long k = mag_key(P[r * PS + j]);
+                if (key_better(k, r, bk, br)) { bk = k; br = r; }
             }
-            for (int off = 16; off > 0; off >>= 1) {
-                double ov = __shfl_down_sync(0xffffffffu, bv, off);
-                long long orr = __shfl_down_sync(0xffffffffu, br, off);
-                if (ov > bv || (ov == bv && orr < br)) { bv = ov; br = orr; }
-            }
+            warp_best(bk, br);
             const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
             __syncthreads();
-            if (lane == 0) { red[warp] = bv; redi[warp] = br; }
+            if (lane == 0) { redk[warp] = bk; redi[warp] = br; }
             __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int w = 1; w < THREADS / 32; w++)
-                    if (red[w] > bv || (red[w] == bv && redi[w] < br)) { bv = red[w]; br = redi[w]; }
-                if (br == 0x7fffffffffffffffLL) br = j;          // only NaN: keep the diagonal row
-                redi[THREADS / 32] = br;
+            if (warp == 0) {
+                long long k = lane < THREADS / 32 ? redk[lane] : -1;
+                long long r = lane < THREADS / 32 ? redi[lane] : 0x7fffffffffffffffLL;
+                warp_best(k, r);
+                if (lane == 0) redi[THREADS / 32] = r == 0x7fffffffffffffffLL ? j : r;   // only NaN: keep row j
             }
             __syncthreads();
             const int p = (int)redi[THREADS / 32];
@@ -201,30 +198,120 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
             A[(long long)(k0 + c) * lda + k0 + r] = P[r * PS + c];
         }
         __syncthreads();
-        // interchanges on the other columns, in order, one thread per column
-        for (int c = threadIdx.x; c < n; c += THREADS) {
-            if (c >= k0 && c < k0 + kb) continue;
-            double* col = A + (long long)c * lda;
-            for (int j = 0; j < kb; j++) {
-                int p = S.ipiv[k0 + j];
-                if (p != k0 + j) {
-                    double t = col[k0 + j];
-                    col[k0 + j] = col[p];
-                    col[p] = t;
+        // interchanges on the other columns. Panels of 16: warp 0 replays the kb
+        // swaps on the list of touched rows and emits the gather pairs
+        // new[dst] = old[src]; then one thread per column reads all sources
+        // before it writes (one round of independent loads instead of kb
+        // dependent swaps through L2). Panels of 32 (the pairs would not fit a
+        // thread's registers): the swaps in order, one thread per column.
+        if constexpr (NB > 16) {
+            for (int c = threadIdx.x; c < n; c += THREADS) {
+                if (c >= k0 && c < k0 + kb) continue;
+                double* col = A + (long long)c * lda;
+                for (int j = 0; j < kb; j++) {
+                    int p = S.ipiv[k0 + j];
+                    if (p != k0 + j) {
+                        double t = col[k0 + j];
+                        col[k0 + j] = col[p];
+                        col[p] = t;
+                    }
                 }
             }
+        } else {
+        if (threadIdx.x < 32) {
+            const int lane = threadIdx.x;
+            for (int i = lane; i < kb; i += 32) s_pos[i] = s_con[i] = k0 + i;
+            __syncwarp();
+            int L = kb;
+            for (int j = 0; j < kb; j++) {
+                const int p = S.ipiv[k0 + j];
+                if (p == k0 + j) continue;
+                int q;
+                if (p < k0 + kb) {
+                    q = p - k0;
+                } else {
+                    q = -1;
+                    for (int base = kb; base < L && q < 0; base += 32) {
+                        const int e = base + lane;
+                        const unsigned bal = __ballot_sync(0xffffffffu, e < L && s_pos[e] == p);
+                        if (bal) q = base + __ffs(bal) - 1;
+                    }
+                    if (q < 0) {
+                        q = L;
+                        if (lane == 0) s_pos[L] = s_con[L] = p;
+                        L++;
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    const int t = s_con[j];
+                    s_con[j] = s_con[q];
+                    s_con[q] = t;
+                }
+                __syncwarp();
+            }
+            int cnt = 0;
+            for (int b = 0; b < L; b += 32) {
+                const int e = b + lane;
+                const bool mv = e < L && s_pos[e] != s_con[e];
+                const unsigned bal = __ballot_sync(0xffffffffu, mv);
+                if (mv) {
+                    const int o = cnt + __popc(bal & ((1u << lane) - 1));
+                    s_dst[o] = s_pos[e];
+                    s_src[o] = s_con[e];
+                }
+                cnt += __popc(bal);
+            }
+            if (lane == 0) s_np = cnt;
+        }
+        __syncthreads();
+        {
+            const int np = s_np;
+            for (int c = threadIdx.x; c < n; c += THREADS) {
+                if (c >= k0 && c < k0 + kb) continue;
+                double* col = A + (long long)c * lda;
+                double v[2 * NB];
+#pragma unroll
+                for (int t = 0; t < 2 * NB; t++)
+                    if (t < np) v[t] = col[s_src[t]];
+#pragma unroll
+                for (int t = 0; t < 2 * NB; t++)
+                    if (t < np) col[s_dst[t]] = v[t];
+            }
+        }
         }
         __syncthreads();
         const int c1 = k0 + kb, m = n - c1;
         if (m > 0) {
-            // U12 = L11^-1 A12, one thread per column
+            // U12 = L11^-1 A12, one thread per column; panels of 16 keep the
+            // column's kb entries in registers (same FMAs in the same order)
+            if constexpr (NB > 16) {
+                for (int c = c1 + threadIdx.x; c < n; c += THREADS) {
+                    double* col = A + (long long)c * lda + k0;
+                    for (int i = 1; i < kb; i++) {
+                        double s = col[i];
+                        for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], col[q], s);
+                        col[i] = s;
+                    }
+                }
+            } else
             for (int c = c1 + threadIdx.x; c < n; c += THREADS) {
                 double* col = A + (long long)c * lda + k0;
-                for (int i = 1; i < kb; i++) {
-                    double s = col[i];
-                    for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], col[q], s);
-                    col[i] = s;
+                double x[NB];
+#pragma unroll
+                for (int i = 0; i < NB; i++) x[i] = i < kb ? col[i] : 0.0;
+#pragma unroll
+                for (int i = 1; i < NB; i++) {
+                    if (i < kb) {
+                        double s = x[i];
+#pragma unroll
+                        for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], x[q], s);
+                        x[i] = s;
+                    }
                 }
+#pragma unroll
+                for (int i = 1; i < NB; i++)
+                    if (i < kb) col[i] = x[i];
             }
             __syncthreads();
             upd64<NB>(A, lda, P, kb, m, m, kb, c1, c1, k0, Us);
@@ -247,10 +334,16 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
     for (int j0 = 0; j0 < n; j0 += 32) {
         const int jb = min(32, n - j0);
         if (warp == 0) {
+            // lane holds row j0 + lane of the diagonal block in registers, so
+            // the dependent chain per column is one shuffle and one FMA
+            double t[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) t[j] = (j < jb && lane < jb) ? A[(long long)(j0 + j) * lda + j0 + lane] : 0.0;
             double v = lane < jb ? b[j0 + lane] : 0.0;
-            for (int j = 0; j < jb; j++) {
+#pragma unroll
+            for (int j = 0; j < 32; j++) {
                 const double xj = __shfl_sync(0xffffffffu, v, j);
-                if (lane > j && lane < jb) v = fma(-A[(long long)(j0 + j) * lda + j0 + lane], xj, v);
+                if (lane > j && lane < jb) v = fma(-t[j], xj, v);
             }
             if (lane < jb) b[j0 + lane] = v;
         }
@@ -265,11 +358,21 @@ __device__ void lu64(const Sys& S, double* P, double* Us, double* red, long long
     for (int j1 = n; j1 > 0; j1 -= 32) {
         const int j0 = max(0, j1 - 32), jb = j1 - j0;
         if (warp == 0) {
+            // as above, with the reciprocals of the diagonal taken once per
+            // block, all lanes at once (an FP64 division is a chain of FP64
+            // instructions; in the substitution it would be on the critical path)
+            double t[32];
+#pragma unroll
+            for (int j = 0; j < 32; j++) t[j] = (j < jb && lane < jb) ? A[(long long)(j0 + j) * lda + j0 + lane] : 0.0;
+            const double rinv = lane < jb ? 1.0 / A[(long long)(j0 + lane) * lda + j0 + lane] : 0.0;
             double v = lane < jb ? b[j0 + lane] : 0.0;
-            for (int j = jb - 1; j >= 0; j--) {
-                if (lane == j) v = v / A[(long long)(j0 + j) * lda + j0 + j];
-                const double xj = __shfl_sync(0xffffffffu, v, j);
-                if (lane < j) v = fma(-A[(long long)(j0 + j) * lda + j0 + lane], xj, v);
+#pragma unroll
+            for (int j = 31; j >= 0; j--) {
+                if (j < jb) {
+                    if (lane == j) v = v * rinv;
+                    const double xj = __shfl_sync(0xffffffffu, v, j);
+                    if (lane < j) v = fma(-t[j], xj, v);
+                }
             }
             if (lane < jb) b[j0 + lane] = v;
         }
@@ -688,6 +791,7 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
                                                             hpl_info* infos) {
     extern __shared__ double bsm[];
     __shared__ double red[THREADS / 32 + 1];
+    __shared__ long long redk[THREADS / 32 + 1];
     __shared__ long long redi[THREADS / 32 + 1];
     __shared__ int s_idx;
     double* P = bsm;
@@ -712,8 +816,8 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
         }
         __syncthreads();
         if (S.kind == 0) {
-            if (S.variant) lu64<16>(S, P, Us, red, redi, info);
-            else lu64<32>(S, P, Us, red, redi, info);
+            if (S.variant) lu64<16>(S, P, Us, redk, redi, info);
+            else lu64<32>(S, P, Us, redk, redi, info);
         } else {
             // the FP64 panel area is free in this path: bf16 operand copies
             if (S.variant) mxp_one<16>(S, H, X, R, T, (float*)P, red, info);

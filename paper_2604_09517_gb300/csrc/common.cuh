@@ -145,6 +145,27 @@ __device__ __forceinline__ float gen_value_f32(uint64_t h) {
     return __uint_as_float(bits);
 }
 
+// Magnitude key of a double for the pivot search: for |v| not NaN the IEEE
+// bit pattern orders like the value, so the comparison runs on the integer
+// pipe (FP64 compares issue at the FP64 rate, which is scarce on this part).
+// NaN gets -1 and is never chosen, as with a floating-point ">".
+__device__ __forceinline__ long long mag_key(double v) {
+    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
+    return b > 0x7ff0000000000000LL ? -1LL : b;
+}
+__device__ __forceinline__ bool key_better(long long k, long long r, long long bk, long long br) {
+    return k > bk || (k == bk && r < br);
+}
+// butterfly max over the warp: every lane ends with the winner
+__device__ __forceinline__ void warp_best(long long& k, long long& r) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        long long ok = __shfl_xor_sync(0xffffffffu, k, off);
+        long long orr = __shfl_xor_sync(0xffffffffu, r, off);
+        if (key_better(ok, orr, k, r)) { k = ok; r = orr; }
+    }
+}
+
 // Align a byte offset up.
 __host__ __device__ __forceinline__ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 

@@ -298,27 +298,6 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf(
     }
 }
 
-// Magnitude key of a double for the pivot search: for |v| not NaN the IEEE
-// bit pattern orders like the value, so the comparison runs on the integer
-// pipe (FP64 compares issue at the FP64 rate, which is scarce on this part).
-// NaN gets -1 and is never chosen, as with a floating-point ">".
-__device__ __forceinline__ long long mag_key(double v) {
-    const long long b = __double_as_longlong(v) & 0x7fffffffffffffffLL;
-    return b > 0x7ff0000000000000LL ? -1LL : b;
-}
-__device__ __forceinline__ bool key_better(long long k, long long r, long long bk, long long br) {
-    return k > bk || (k == bk && r < br);
-}
-// butterfly max over the warp: every lane ends with the winner
-__device__ __forceinline__ void warp_best(long long& k, long long& r) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        long long ok = __shfl_xor_sync(0xffffffffu, k, off);
-        long long orr = __shfl_xor_sync(0xffffffffu, r, off);
-        if (key_better(ok, orr, k, r)) { k = ok; r = orr; }
-    }
-}
-
 // PFACT leaf on one thread-block cluster, for panels whose rows fit in the
 // cluster's shared memory (the short panels of a small matrix or of the last
 // steps of a large one). Same pivots and arithmetic as k_panel_leaf (first

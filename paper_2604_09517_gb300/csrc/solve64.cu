@@ -151,6 +151,150 @@ static size_t solve_ws_layout(int64_t n, int** cnt, int** dst, int** src, char* 
     return std::max<size_t>(off, 256);
 }
 
+// Both triangles for one right-hand side (no transpose, P b applied) on one
+// thread-block cluster: the latency-bound case of a small matrix, where the
+// per-block kernel launches of tri_solve dominate. Blocks of 64 rows are
+// dealt round-robin to the C CTAs (CTA c owns blocks c, c + C, ...; its part
+// of the right-hand side stays in shared memory throughout). Step by step
+// (forward: block 0 up; backward: the last block down) the owner solves the
+// diagonal block with one warp (upper: reciprocals of the diagonal taken once
+// per block), one cluster barrier publishes the solved block, every CTA reads
+// it through distributed shared memory and subtracts its product with the
+// off-diagonal blocks of the rows it owns. A solved block is never written
+// again, so no publication needs a second buffer.
+__global__ void __launch_bounds__(256) k_trsv_cluster(int64_t n, const double* __restrict__ LU, int64_t lda,
+                                                      double* __restrict__ b) {
+    extern __shared__ double xs[];            // this CTA's blocks of b / x, 64 each
+    __shared__ double T[kTB][kTB + 1];
+    __shared__ double xb[kTB];
+    __shared__ double part[4][kTB];
+    __shared__ double rinv[kTB];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned C = gridDim.x, me = cluster_rank();
+    const int nblk = (int)((n + kTB - 1) / kTB);
+    for (int q = (int)me, lq = 0; q < nblk; q += (int)C, lq++)
+        for (int i = tid; i < kTB; i += 256) xs[lq * kTB + i] = (int64_t)q * kTB + i < n ? b[(int64_t)q * kTB + i] : 0.0;
+    __syncthreads();
+    for (int phase = 0; phase < 2; phase++) {
+        const bool lower = phase == 0;
+        for (int st = 0; st < nblk; st++) {
+            const int blk = lower ? st : nblk - 1 - st;
+            const unsigned owner = (unsigned)(blk % (int)C);
+            const int bs = (int)std::min<int64_t>(kTB, n - (int64_t)blk * kTB);
+            const int64_t b0 = (int64_t)blk * kTB;
+            if (me == owner) {
+                for (int idx = tid; idx < bs * bs; idx += 256) {
+                    const int j = idx / bs, i = idx - j * bs;
+                    T[i][j] = LU[(b0 + j) * lda + b0 + i];
+                }
+                __syncthreads();
+                if (!lower && tid < bs) rinv[tid] = 1.0 / T[tid][tid];
+                __syncthreads();
+                if (warp == 0) {
+                    double* y = xs + (blk / (int)C) * kTB;
+                    double v0 = lane < bs ? y[lane] : 0.0, v1 = lane + 32 < bs ? y[lane + 32] : 0.0;
+                    if (lower) {
+                        for (int j = 0; j < bs; j++) {
+                            const double xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+                            if (lane > j && lane < bs) v0 = fma(-T[lane][j], xj, v0);
+                            if (lane + 32 > j && lane + 32 < bs) v1 = fma(-T[lane + 32][j], xj, v1);
+                        }
+                    } else {
+                        for (int j = bs - 1; j >= 0; j--) {
+                            if (lane == (j & 31)) {
+                                if (j < 32) v0 *= rinv[j];
+                                else v1 *= rinv[j];
+                            }
+                            const double xj = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+                            if (lane < j) v0 = fma(-T[lane][j], xj, v0);
+                            if (lane + 32 < j) v1 = fma(-T[lane + 32][j], xj, v1);
+                        }
+                    }
+                    if (lane < bs) y[lane] = v0;
+                    if (lane + 32 < bs) y[lane + 32] = v1;
+                }
+            }
+            cluster_sync_all();
+            if (tid < bs) xb[tid] = ld_cluster_f64(cluster_addr(&xs[(blk / (int)C) * kTB + tid], owner));
+            __syncthreads();
+            for (int q = (int)me, lq = 0; q < nblk; q += (int)C, lq++) {
+                if (lower ? q <= blk : q >= blk) continue;
+                const int rs = (int)std::min<int64_t>(kTB, n - (int64_t)q * kTB);
+                const int i = tid & 63, g = tid >> 6;
+                double acc = 0.0;
+                if (i < rs)
+                    for (int j = g * 16; j < g * 16 + 16 && j < bs; j++)
+                        acc = fma(LU[(b0 + j) * lda + (int64_t)q * kTB + i], xb[j], acc);
+                part[g][i] = acc;
+                __syncthreads();
+                if (tid < rs) xs[lq * kTB + tid] -= (part[0][tid] + part[1][tid]) + (part[2][tid] + part[3][tid]);
+                __syncthreads();
+            }
+        }
+        cluster_sync_all();          // every read of this phase's publications is done
+    }
+    for (int q = (int)me, lq = 0; q < nblk; q += (int)C, lq++)
+        for (int i = tid; i < kTB; i += 256)
+            if ((int64_t)q * kTB + i < n) b[(int64_t)q * kTB + i] = xs[lq * kTB + i];
+}
+
+constexpr int kTrsvClusterBlocksPerCta = 8;
+
+// Cluster size for k_trsv_cluster (16, else the portable 8; 0 = unavailable).
+static int trsv_cluster_max() {
+    static int cached = -1;
+    if (cached >= 0) return cached;
+    int best = 0;
+    const void* f = (const void*)k_trsv_cluster;
+    cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = (unsigned)c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3((unsigned)c);
+        cfg.blockDim = dim3(256);
+        cfg.dynamicSmemBytes = sizeof(double) * kTB * kTrsvClusterBlocksPerCta;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) == cudaSuccess && nc >= 1) {
+            best = c;
+            break;
+        }
+    }
+    cudaGetLastError();
+    cached = best;
+    return best;
+}
+
+// One launch for both triangles when the system fits one cluster; returns 1
+// (nothing launched) otherwise.
+static int solve_cluster(int64_t n, const double* LU, int64_t lda, double* b, cudaStream_t s) {
+    const int cmax = trsv_cluster_max();
+    const int64_t nblk = (n + kTB - 1) / kTB;
+    if (cmax < 1 || nblk > (int64_t)cmax * kTrsvClusterBlocksPerCta) return 1;
+    const int C = (int)std::min<int64_t>(nblk, cmax);
+    const int R = (int)((nblk + C - 1) / C);
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3((unsigned)C);
+    cfg.blockDim = dim3(256);
+    cfg.dynamicSmemBytes = sizeof(double) * kTB * R;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HPL_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_trsv_cluster, n, LU, lda, b));
+    count_launch();
+    return HPL_OK;
+}
+
 // One triangle: forward (lower) or backward (upper) blocked substitution.
 static int tri_solve(int64_t n, const double* LU, int64_t lda, int lower, int unit, int trans, double* B, int64_t ldb,
                      int64_t nrhs, cudaStream_t s) {
@@ -204,6 +348,10 @@ extern "C" int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, 
     if (!trans) {
         k_apply_perm<<<(unsigned)nrhs, 512, 0, s>>>(n, nblk, cnt, dst, src, 0, B, ldb);
         HPL_LAUNCH_CHECK();
+        if (nrhs == 1) {
+            int st = solve_cluster(n, LU, lda, B, s);
+            if (st != 1) return st;
+        }
         int st = tri_solve(n, LU, lda, 1, 1, 0, B, ldb, nrhs, s);
         if (st) return st;
         st = tri_solve(n, LU, lda, 0, 0, 0, B, ldb, nrhs, s);
