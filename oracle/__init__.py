@@ -85,7 +85,9 @@ def _load():
             "orc_round_e4m3": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_fp16": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_operand_ext": (None, [ctypes.c_int, fp, i64, i64, i64, ctypes.c_int]),
-            "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, ctypes.c_int, fp, i64, fp]),
+            "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, i64, fp]),
+            "orc_to_bf16_storage": (None, [i64, i64, dp, i64, fp, i64]),
+            "orc_round_bf16_d": (ctypes.c_float, [ctypes.c_double]),
             "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, i64, fp, i64, fp, dp, dp, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
             "orc_adjoint": (i64, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64]),
@@ -234,6 +236,11 @@ PREC_FP16 = 2
 PREC_FP32 = 3
 
 
+def round_bf16_d(x: float) -> float:
+    """A double rounded once to BF16 (round to nearest even)."""
+    return float(_load().orc_round_bf16_d(float(x)))
+
+
 def round_bf16(x: float) -> float:
     return float(_load().orc_round_bf16(float(x)))
 
@@ -258,17 +265,27 @@ def round_operand(prec: int, X, kdim_is_rows: bool) -> np.ndarray:
 NS_ITERS = 2
 
 
-def mxp_factor(A, nb: int, prec: int = PREC_BF16, ns_iters: int = NS_ITERS):
-    """Block LU without pivoting of FP32(A) (see oracle.c). Returns (F, Dinv, info).
+STORAGE_FP32 = 0
+STORAGE_BF16 = 1
+
+
+def mxp_factor(A, nb: int, prec: int = PREC_BF16, ns_iters: int = NS_ITERS, storage: int = STORAGE_FP32):
+    """Block LU without pivoting of the FP32 (storage 0) or BF16 (storage 1)
+    working copy of A (see oracle.c). Returns (F, Dinv, info).
 
     F holds L21 blocks below the diagonal, the block rows A12 above it and the
     Schur-complemented diagonal blocks D_k on it; Dinv (n x nb) holds D_k^-1
     in rows k0..k0+kb.
     """
-    F = np.asfortranarray(np.asarray(A, dtype=np.float64).astype(np.float32))
-    n = F.shape[0]
+    A64 = _fortran(A, np.float64)
+    n = A64.shape[0]
+    if storage == STORAGE_BF16:
+        F = np.zeros((n, n), dtype=np.float32, order="F")
+        _load().orc_to_bf16_storage(n, n, _dp(A64), max(n, 1), _fp(F), max(n, 1))
+    else:
+        F = np.asfortranarray(A64.astype(np.float32))
     Dinv = np.zeros((n, nb), dtype=np.float32, order="F")
-    info = _load().orc_mxp_factor(n, nb, prec, ns_iters, _fp(F), max(n, 1), _fp(Dinv))
+    info = _load().orc_mxp_factor(n, nb, prec, ns_iters, storage, _fp(F), max(n, 1), _fp(Dinv))
     return F, Dinv, int(info)
 
 
@@ -306,8 +323,8 @@ def mxp_refine(A, F, Dinv, nb: int, b, refine: int = 1, max_iter: int = 50, gmre
 
 
 def mxp_solve(A, b, nb: int, prec: int = PREC_BF16, refine: int = 1, max_iter: int = 50,
-              gmres_m: int = 30, tol: float = 16.0, ns_iters: int = NS_ITERS):
-    F, Dinv, info = mxp_factor(A, nb, prec, ns_iters)
+              gmres_m: int = 30, tol: float = 16.0, ns_iters: int = NS_ITERS, storage: int = STORAGE_FP32):
+    F, Dinv, info = mxp_factor(A, nb, prec, ns_iters, storage)
     out = mxp_refine(A, F, Dinv, nb, b, refine, max_iter, gmres_m, tol)
     out["F"] = F
     out["Dinv"] = Dinv

@@ -360,6 +360,23 @@ float orc_round_bf16(float x) {
     return (float)r;
 }
 
+/* The same rounding applied once to a double (no intermediate FP32 rounding;
+ * the working copy of a BF16-stored factorization is taken from FP64 A). The
+ * inputs here are far inside FP32's exponent range. */
+float orc_round_bf16_d(double x) {
+    if (x == 0.0 || !isfinite(x)) return (float)x;
+    int e;
+    double f = frexp(x, &e);
+    double q = nearbyint(ldexp(f, 8));
+    return (float)ldexp(q, e - 8);
+}
+
+/* BF16 working copy of an FP64 matrix (values stored as float). */
+void orc_to_bf16_storage(int64_t m, int64_t n, const double* A, int64_t lda, float* F, int64_t ldf) {
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = 0; i < m; i++) F[j * ldf + i] = orc_round_bf16_d(A[j * lda + i]);
+}
+
 /* FP8 E4M3 (OCP "fn" variant) round-to-nearest-even with saturation to
  * +-448: normals 2^-6 .. 448 with 3 fraction bits, subnormals k * 2^-9. */
 float orc_round_e4m3(float x) {
@@ -519,13 +536,24 @@ static void orc_newton_schulz(int64_t kb, const float* D, int64_t ldd, int ns_it
     free(R); free(Dh); free(Dl); free(Xh); free(Xl); free(Th); free(Tl); free(Dc);
 }
 
+/* Storage rounding of a block (BF16 storage keeps every stored value in BF16). */
+static void orc_round_block_bf16(float* X, int64_t r, int64_t c, int64_t ld) {
+    for (int64_t j = 0; j < c; j++)
+        for (int64_t i = 0; i < r; i++) X[j * ld + i] = orc_round_bf16(X[j * ld + i]);
+}
+
 /* Block LU without pivoting of the FP32 matrix A (n x n, lda), in place:
  * below the diagonal the blocks L21 of every step, above it the block rows
  * A12 as they stood at their step, on it the Schur-complemented diagonal
  * blocks D_k. Dinv (n x nb, ld n) receives D_k^-1 in rows k0..k0+kb.
  * Returns info = 1-based index of the first exactly zero diagonal entry of a
- * D_k (Newton-Schulz cannot start there), else 0. */
-int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, int64_t lda, float* Dinv) {
+ * D_k (Newton-Schulz cannot start there), else 0.
+ * storage = 1 keeps the working matrix in BF16 (Sec. III-A.2 / the Aurora runs
+ * stored the trailing matrix in BF16 to fit a larger N): A holds BF16 values
+ * on entry, and every value written back (L21, the updated A22) is rounded to
+ * BF16 once, after its FP32 computation; storage = 0 keeps FP32. */
+int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, int storage, float* A, int64_t lda,
+                       float* Dinv) {
     int64_t info = 0;
     float* X = (float*)malloc(sizeof(float) * nb * nb);
     for (int64_t k0 = 0; k0 < n; k0 += nb) {
@@ -552,12 +580,14 @@ int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, float* A, 
         orc_round_operand(pprec, t21, m, kb, m, 0);      /* A operand: k along columns */
         orc_round_operand(pprec, Xq, kb, kb, kb, 1);     /* B operand: k along rows    */
         orc_gemm32(m, kb, kb, t21, m, Xq, kb, A21, lda, 0);
+        if (storage == 1) orc_round_block_bf16(A21, m, kb, lda);
         /* 3. trailing update A22 -= L21 A12 */
         for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A12 + j * lda, sizeof(float) * kb);
         for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A21 + j * lda, sizeof(float) * m);
         orc_round_operand(prec, t21, m, kb, m, 0);
         orc_round_operand(prec, t12, kb, m, kb, 1);
         orc_gemm32(m, m, kb, t21, m, t12, kb, A22, lda, 1);
+        if (storage == 1) orc_round_block_bf16(A22, m, m, lda);
         free(t12); free(t21); free(Xq);
     }
     free(X);

@@ -525,3 +525,71 @@ def test_adjoint_closed_forms(orc):
 
 def test_flop_count(orc):
     assert orc.flops(1024) == 2 * 1024 ** 3 / 3 + 2 * 1024 ** 2
+
+
+def _nearest_bf16_bruteforce(x: float) -> float:
+    """The BF16 value nearest to the double x (ties to an even last fraction
+    bit), by exact comparison of the candidates around x."""
+    from fractions import Fraction
+    if x == 0.0:
+        return 0.0
+    m, e = np.frexp(abs(x))                      # |x| = m 2^e, 0.5 <= m < 1
+    e = int(e)
+    cands = set()
+    for ee in (e - 1, e, e + 1):
+        base = int(np.floor(abs(x) / 2.0 ** (ee - 8)))
+        for k in range(base - 2, base + 3):
+            if 128 <= k < 256:                   # 8 significant bits
+                cands.add((k, int(ee - 8)))
+    X = Fraction(abs(x))
+    best = min(cands, key=lambda c: (abs(Fraction(c[0]) * Fraction(2) ** c[1] - X), c[0] & 1))
+    return float(np.copysign(best[0] * 2.0 ** best[1], x))
+
+
+def test_round_bf16_double_single_rounding(orc):
+    """FP64 -> BF16 in one rounding against a brute-force nearest search,
+    including doubles just off a BF16 midpoint, where rounding through FP32
+    first would land on the other neighbour."""
+    rng = np.random.default_rng(11)
+    vals = list(rng.standard_normal(3000) * 2.0 ** rng.integers(-30, 30, 3000))
+    for k in range(128, 256, 7):
+        for e in (-20, -3, 0, 5):
+            mid = (k + 0.5) * 2.0 ** e                # exact BF16 midpoint
+            vals += [mid, -mid, mid * (1 + 2.0 ** -40), mid * (1 - 2.0 ** -40)]
+    for v in vals:
+        assert orc.round_bf16_d(v) == _nearest_bf16_bruteforce(float(v)), v
+    # a double just above a midpoint whose FP32 rounding is the midpoint itself
+    x = (129 + 0.5) * 2.0 ** -7 * (1 + 2.0 ** -30)
+    assert np.float32(x) == np.float32((129 + 0.5) * 2.0 ** -7)
+    assert orc.round_bf16_d(x) == 130 * 2.0 ** -7
+
+
+def test_mxp_factor_bf16_storage(orc):
+    """BF16 storage of the working matrix: every stored value is a BF16 value;
+    one block is the FP32-storage factor of the BF16-rounded matrix (rounding
+    pinned above); the factorization error sits between the FP32-storage
+    error and the BF16 unit roundoff; the refinement still reaches the HPL
+    tolerance with an FP64-accurate solution."""
+    n, nb = 192, 64
+    A = orc.generate(5, orc.STREAM_A, n, n, dominant=True)
+    F, Dinv, info = orc.mxp_factor(A, nb, orc.PREC_BF16, storage=orc.STORAGE_BF16)
+    assert info == 0
+    assert all(orc.round_bf16(float(v)) == float(v) for v in F.ravel()[::7])
+    # one block: only the storage rounding of the input differs
+    A1 = A[:48, :48]
+    F1, D1, _ = orc.mxp_factor(A1, 64, orc.PREC_BF16, storage=orc.STORAGE_BF16)
+    Ar = np.vectorize(_nearest_bf16_bruteforce)(A1)
+    F2, D2, _ = orc.mxp_factor(Ar, 64, orc.PREC_BF16, storage=orc.STORAGE_FP32)
+    assert np.array_equal(F1, F2) and np.array_equal(D1, D2)
+
+    def err(storage):
+        Fx, _, _ = orc.mxp_factor(A, nb, orc.PREC_BF16, storage=storage)
+        L, U = orc.block_lu_parts(Fx, nb)
+        return np.abs(A - L @ U).max() / np.abs(A).max()
+    e32, e16 = err(orc.STORAGE_FP32), err(orc.STORAGE_BF16)
+    assert e32 < e16 < 2.0 ** -7
+    b = orc.generate(5, orc.STREAM_B, n, 1)[:, 0]
+    out = orc.mxp_solve(A, b, nb, refine=1, storage=orc.STORAGE_BF16)
+    assert out["status"] == 0 and orc.scaled_residual(A, out["x"], b) < 16
+    x64, _ = orc.solve(A, b)
+    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 2 * 16 * n * 2.0 ** -53 * np.linalg.cond(A, np.inf)
