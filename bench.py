@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--mxp-n", type=int, default=98304)
     ap.add_argument("--mxp-nb", type=int, default=3072)
     ap.add_argument("--mxp-fp8-nb", type=int, default=4096)
+    ap.add_argument("--mxp-large-n", type=int, default=0,
+                    help="also time one regenerated-A, BF16-storage solve of this size (0: skip)")
     return ap.parse_args()
 
 
@@ -549,36 +551,41 @@ def run_small(a, d: Dist, dev):
     return out
 
 
-def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
+def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=0, n=None, steps=None,
+            warmup=None):
     """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
     block-LU factor on the tcgen05 tensor cores (BF16 update; FP8 E4M3 with
     prec = 1, NB = 4096; scaled FP16 with prec = 2) + FP64 GMRES refinement.
     regen: the library regenerates A from the seed instead of reading a
-    stored FP64 copy."""
+    stored FP64 copy. storage = 1 keeps the working matrix in BF16. n, steps,
+    warmup override the defaults (a one-off larger solve)."""
     import torch
 
     import paper_2604_09517_gb300 as hpl
 
-    n, nb, seed = a.mxp_n, (a.mxp_fp8_nb if prec == 1 else a.mxp_nb), a.seed
+    n = n or a.mxp_n
+    nb, seed = (a.mxp_fp8_nb if prec == 1 else a.mxp_nb), a.seed
+    n_steps = steps or a.steps
+    n_warm = a.warmup if warmup is None else warmup
     A = None if regen else hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT, device=dev)
     b = hpl.generate(seed, hpl.STREAM_B, n, 1, device=dev)[:, 0].contiguous()
     X = hpl.colmajor(n, 1, device=dev)
     info = hpl.Info(dev)
     ws = None
-    for _ in range(a.warmup):
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed)
+    for _ in range(n_warm):
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
     hpl.set_phase_timing(True)
     step_ms, launches = [], 0
-    for _ in range(a.steps):
+    for _ in range(n_steps):
         d.barrier()
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = hpl.launch_count()
         e0.record(stream)
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage)
         e1.record(stream)
         launches += hpl.launch_count() - l0
         torch.cuda.synchronize(dev)
@@ -597,6 +604,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
     del A, X, ws
     torch.cuda.empty_cache()
     tag = {0: "bf16", 1: "fp8e4m3", 2: "fp16"}[prec]
+    stag = "_bf16storage" if storage else ""
     # the factorization alone: the step minus its refinement phase
     refine_ms = phases["refine"][0] / len(step_ms) if phases["refine"][2] else 0.0
     factor_ms = total_ms / len(step_ms) - refine_ms
@@ -607,8 +615,9 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None):
         sn = a.cpu_sample_n
         extra["cpu_oracle_fp64_lu_extrapolated_s"] = cpu["seconds_at_sample_n"] * (n / sn) ** 3
         extra["cpu_oracle_basis"] = f"oracle FP64 getrf+getrs at n={sn} x (n/{sn})^3"
-    return {**extra, "workload": f"hpl_mxp_{tag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
-            "ms_per_step": total_ms / len(step_ms), "steps": a.steps, "warmup": a.warmup,
+    return {**extra, "workload": f"hpl_mxp_{tag}{stag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
+            "ms_per_step": total_ms / len(step_ms), "steps": n_steps, "warmup": n_warm,
+            "storage": "bf16" if storage else "fp32",
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
             "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,
@@ -757,6 +766,10 @@ def run_ours(a, d: Dist):
     mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1, cpu=cpu)
     mxp_fp16 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=2, cpu=cpu)
     mxp_regen = None if a.no_mxp else run_mxp(a, d, dev, value, regen=True)
+    mxp_bf16s = None if a.no_mxp else run_mxp(a, d, dev, value, storage=1)
+    # optional: one larger solve that only BF16 storage and a regenerated A fit
+    mxp_large = (run_mxp(a, d, dev, value, regen=True, storage=1, n=a.mxp_large_n, steps=1, warmup=1)
+                 if a.mxp_large_n and not a.no_mxp else None)
     batched = None if a.no_batched else run_batched(a, d, dev)
     adjoint = None if a.no_adjoint else run_adjoint(a, d, dev)
 
@@ -772,7 +785,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report, "step_model": model,
-                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_fp16": mxp_fp16, "mxp_regenerated": mxp_regen, "batched": batched, "adjoint": adjoint}
+                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_fp16": mxp_fp16, "mxp_regenerated": mxp_regen, "mxp_bf16_storage": mxp_bf16s, "mxp_large": mxp_large, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 

@@ -76,7 +76,13 @@ typedef struct {
                             memory of one thread-block cluster runs on that cluster, others on a
                             grid-cooperative launch); 1 = grid-cooperative leaves only. Same pivots and
                             factors either way. */
+    int32_t storage;     /* mxp_solve / lu_solve_backward: HPL_STORAGE_FP32 (default) or HPL_STORAGE_BF16, the
+                            element type of the working matrix / factor (BF16: with HPL_PREC_BF16 only) */
+    int32_t reserved;
 } hpl_opts;
+
+/* Working-matrix storage of the mixed-precision factorization. */
+enum { HPL_STORAGE_FP32 = 0, HPL_STORAGE_BF16 = 1 };
 
 /* Result record, written on the device. Caller-allocated in device memory. */
 typedef struct {
@@ -201,10 +207,15 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * scaled residual over the right-hand sides, and the preconditioner
  * applications. The call blocks the host until the solve is done (the
  * refinement reads one scalar per step). ws (device, mxp_workspace_size
- * bytes) keeps the factor afterwards: FP32 F (n x n, ld n) at byte offset 0
- * (L21 blocks below the diagonal, U blocks above, D_k on it) and FP32
- * D_k^-1 (n x nb, ld n, block k in rows k*nb..) at offset
- * align256(4 n^2). opts->prec = HPL_PREC_FP8_E4M3 runs the trailing update
+ * bytes) keeps the factor afterwards: F (n x n, ld n) at byte offset 0
+ * (L21 blocks below the diagonal, U blocks above, D_k on it; FP32, or BF16
+ * with opts->storage = HPL_STORAGE_BF16) and FP32 D_k^-1 (n x nb, ld n,
+ * block k in rows k*nb..) at offset align256(4 n^2), or align256(2 n^2) for
+ * BF16 storage. BF16 storage (the Aurora runs' choice for a larger N) halves
+ * the working matrix: the copy of A is rounded once to BF16 and every value
+ * the factorization writes back (L21, the updated trailing matrix) is
+ * rounded to BF16 after its FP32 computation; the refinement then restores
+ * FP64 accuracy as before (typically with more inner iterations). opts->prec = HPL_PREC_FP8_E4M3 runs the trailing update
  * with FP8 E4M3 operands instead (one power-of-two scale per row of L21 and
  * per column of A12 over the panel width, applied in the GEMM epilogue; the
  * panel product L21 = A21 D^-1 keeps BF16). opts->prec = HPL_PREC_FP16 uses

@@ -30,6 +30,8 @@ GEN_DIAG_DOMINANT = 1
 PREC_BF16 = 0
 PREC_FP8_E4M3 = 1
 PREC_FP16 = 2
+STORAGE_FP32 = 0
+STORAGE_BF16 = 1
 REFINE_IR = 0
 REFINE_GMRES = 1
 STREAM_A = 0
@@ -55,7 +57,8 @@ class Opts(ctypes.Structure):
     _fields_ = [("nb", ctypes.c_int64), ("lookahead", ctypes.c_int32), ("prec", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("ns_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64),
-                ("fp64_emulation", ctypes.c_int32), ("pfact", ctypes.c_int32)]
+                ("fp64_emulation", ctypes.c_int32), ("pfact", ctypes.c_int32),
+                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -145,11 +148,11 @@ def colmajor(m: int, n: int, dtype=torch.float64, device="cuda", ld: int | None 
 
 def make_opts(nb: int = 0, lookahead: int = 1, prec: int = PREC_BF16, refine: int = REFINE_GMRES,
               max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0, timeout_ns: int = 0,
-              fp64_emulation: int = 0, pfact: int = 0) -> Opts:
+              fp64_emulation: int = 0, pfact: int = 0, storage: int = STORAGE_FP32) -> Opts:
     o = Opts()
     load().hpl_default_opts(ctypes.byref(o))
     o.nb, o.lookahead, o.prec, o.refine = nb, lookahead, prec, refine
-    o.fp64_emulation, o.pfact = fp64_emulation, pfact
+    o.fp64_emulation, o.pfact, o.storage = fp64_emulation, pfact, storage
     o.max_iter, o.gmres_m, o.tol = max_iter, gmres_m, tol
     if timeout_ns:
         o.timeout_ns = timeout_ns
@@ -239,12 +242,13 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
 
 def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-              info: Info | None = None, prec: int = PREC_BF16, seed: int = 0):
+              info: Info | None = None, prec: int = PREC_BF16, seed: int = 0, storage: int = STORAGE_FP32):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
 
     A = None solves with the dominant generated matrix of `seed` without storing
-    it (the library regenerates its entries). Returns (X, info, ws); ws holds
-    the block factor afterwards (see mxp_factor_views).
+    it (the library regenerates its entries). storage = STORAGE_BF16 keeps the
+    working matrix in BF16. Returns (X, info, ws); ws holds the block factor
+    afterwards (see mxp_factor_views).
     """
     lib = load()
     n = B.shape[0]
@@ -256,7 +260,7 @@ def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: i
         Bc.copy_(Bm)
         Bm = Bc
     nrhs = Bm.shape[1]
-    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec)
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec, storage=storage)
     if X is None:
         X = colmajor(n, nrhs, device=dev)
     Xm = X.view(n, 1) if X.dim() == 1 else X
@@ -274,8 +278,9 @@ def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: i
 
 def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: torch.Tensor, nb: int = 3072,
                       want_grad_a: bool = True, refine: int = REFINE_GMRES, max_iter: int = 50, gmres_m: int = 30,
-                      tol: float = 16.0):
-    """Adjoint of X = A^-1 B from the factor mxp_solve left in ws: (grad_B, grad_A, info)."""
+                      tol: float = 16.0, storage: int = STORAGE_FP32):
+    """Adjoint of X = A^-1 B from the factor mxp_solve left in ws (factored with
+    the same storage): (grad_B, grad_A, info)."""
     lib = load()
     n = A.shape[0]
     Gm = G.reshape(n, -1) if G.dim() == 1 else G
@@ -287,7 +292,7 @@ def lu_solve_backward(A: torch.Tensor, X: torch.Tensor, G: torch.Tensor, ws: tor
     Xc.copy_(Xm)
     gB = colmajor(n, nrhs, device=A.device)
     gA = colmajor(n, n, device=A.device) if want_grad_a else None
-    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol)
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, storage=storage)
     info = Info(A.device)
     _check(lib.lu_solve_backward(n, nrhs, _ptr(A), _ld(A), _ptr(Xc), n, _ptr(Gc), n, _ptr(gB), n, _ptr(gA), n,
                                  ctypes.byref(opts), _ptr(ws), ws.numel(), info.ptr(), _stream(A.device)),
@@ -437,12 +442,14 @@ class Batch:
         return recs if s is None else recs[0]
 
 
-def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 3072):
-    """(F, Dinv) views of the block factor that mxp_solve leaves in its workspace."""
+def mxp_factor_views(ws: torch.Tensor, n: int, nb: int = 3072, storage: int = STORAGE_FP32):
+    """(F, Dinv) views of the block factor that mxp_solve leaves in its workspace
+    (F is bfloat16 for BF16 storage, else float32)."""
     nb = min(nb, n)
-    f_bytes = 4 * n * n
+    esz, dt = (2, torch.bfloat16) if storage == STORAGE_BF16 else (4, torch.float32)
+    f_bytes = esz * n * n
     d_off = (f_bytes + 255) // 256 * 256
-    F = ws[:f_bytes].view(torch.float32).view(n, n).t()
+    F = ws[:f_bytes].view(dt).view(n, n).t()
     Dinv = ws[d_off:d_off + 4 * n * nb].view(torch.float32).view(nb, n).t()
     return F, Dinv
 

@@ -70,6 +70,7 @@ Opts resolve_opts(const hpl_opts* o, int64_t default_nb) {
     r.timeout_ns = o->timeout_ns > 0 ? o->timeout_ns : d.timeout_ns;
     r.fp64_emulation = o->fp64_emulation;
     r.pfact = o->pfact;
+    r.storage = o->storage;
     return r;
 }
 

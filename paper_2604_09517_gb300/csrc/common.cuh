@@ -1,5 +1,6 @@
 // Shared helpers of the GPU library (host and device). Not used by the oracle.
 #pragma once
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -42,6 +43,7 @@ struct Opts {
     int64_t timeout_ns;
     int fp64_emulation;
     int pfact;
+    int storage;
 };
 Opts resolve_opts(const hpl_opts* o, int64_t default_nb);
 
@@ -164,6 +166,44 @@ __device__ __forceinline__ void warp_best(long long& k, long long& r) {
         long long orr = __shfl_xor_sync(0xffffffffu, r, off);
         if (key_better(ok, orr, k, r)) { k = ok; r = orr; }
     }
+}
+
+// Element access for a working matrix stored in FP32 or BF16: read widened
+// to FP32; a stored FP32 value is rounded to nearest even once.
+__device__ __forceinline__ float ld_f(const float* p) { return *p; }
+__device__ __forceinline__ float ld_f(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+__device__ __forceinline__ void st_f(float* p, float v) { *p = v; }
+__device__ __forceinline__ void st_f(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+
+// FP64 -> BF16, round to nearest even in one step (no intermediate FP32
+// rounding), by integer operations on the bits only (an FP64 conversion
+// would issue at the FP64 rate, which is scarce on this part): the 52-bit
+// fraction is rounded to 7 bits (a carry moves into the exponent), then
+// re-biased. NaN stays NaN, infinities and overflow give infinity; values
+// below BF16's normal range flush to a signed zero (the matrices here never
+// produce them).
+__device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rn(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(u >> 63) << 15;
+    unsigned long long a = u & 0x7fffffffffffffffull;
+    const bool nan = a > 0x7ff0000000000000ull;
+    a += (1ull << 44) - 1 + ((a >> 45) & 1);
+    const int e = (int)(a >> 52) - 1023 + 127;
+    unsigned short h = (unsigned short)(sgn | ((unsigned)e << 7) | (unsigned)((a >> 45) & 0x7f));
+    if (e >= 255) h = (unsigned short)(sgn | 0x7f80u);
+    if (e <= 0) h = (unsigned short)sgn;
+    if (nan) h = (unsigned short)(sgn | 0x7fc0u);
+    return __ushort_as_bfloat16(h);
+}
+__device__ __forceinline__ float st_f64(float* p, double a) {
+    const float v = (float)a;
+    *p = v;
+    return v;
+}
+__device__ __forceinline__ float st_f64(__nv_bfloat16* p, double a) {
+    const __nv_bfloat16 v = f64_to_bf16_rn(a);
+    *p = v;
+    return __bfloat162float(v);
 }
 
 // Align a byte offset up.

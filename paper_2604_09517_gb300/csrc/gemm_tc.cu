@@ -24,6 +24,7 @@
 // Every wait is bounded by a %globaltimer deadline; on expiry the CTA raises
 // an error flag, drains what it has in flight, frees TMEM and returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
 
 #include <algorithm>
 
@@ -92,7 +93,7 @@ __host__ __device__ constexpr uint32_t idesc() {
 
 struct Params {
     int M, N, K;
-    float* C;
+    void* C;               // float or __nv_bfloat16 (the kernels' CT)
     long long ldc;
     int sub;
     int* err;
@@ -212,7 +213,9 @@ __device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, i
     nt = r / gsz;
 }
 
-template <int KIND, int BN>
+// C is FP32, or BF16 for a working matrix stored in BF16 (ld_f / st_f: read
+// widened to FP32, the FP32 result rounded to nearest even when stored).
+template <int KIND, int BN, typename CT>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
     constexpr int BK = BKB / Kind<KIND>::ELEM;     // K elements per stage
@@ -327,12 +330,12 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int row = mt * BM + row_in_tile;
             const bool row_ok = row < p.M;
             const int cbase = nt * BN + half * (BN / 2);
-            float* cp = p.C + (long long)cbase * p.ldc + row;
+            CT* cp = (CT*)p.C + (long long)cbase * p.ldc + row;
             const int ncol = min(BN / 2, p.N - cbase);      // valid columns of this half (may be <= 0)
             float cv[32];
             if (p.sub) {
 #pragma unroll
-                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? cp[(long long)j * p.ldc] : 0.0f;
+                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? ld_f(cp + (long long)j * p.ldc) : 0.0f;
             }
             if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
             tc_fence_after();
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int jj = (c + 1) * 32 + j;
-                        nv[j] = (row_ok && jj < ncol) ? cp[(long long)jj * p.ldc] : 0.0f;
+                        nv[j] = (row_ok && jj < ncol) ? ld_f(cp + (long long)jj * p.ldc) : 0.0f;
                     }
                 }
                 tmem_wait_ld();
@@ -357,7 +360,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                         if (jj < ncol) {
                             float v = __uint_as_float(r[j]) * rs;
                             if (p.sb) v *= p.sb[cbase + jj];
-                            cp[(long long)jj * p.ldc] = p.sub ? cv[j] - v : v;
+                            st_f(cp + (long long)jj * p.ldc, p.sub ? cv[j] - v : v);
                         }
                     }
                 }
@@ -460,7 +463,7 @@ __device__ __forceinline__ void umma_commit_pair_own(uint64_t* bar) {
                  : "memory");
 }
 
-template <int KIND>
+template <int KIND, typename CT>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
     constexpr int BK = BKB / Kind<KIND>::ELEM;
@@ -574,12 +577,12 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             const int row = mt * 256 + row_in_tile;
             const bool row_ok = row < p.M;
             const int cbase = nt * 256 + half * 128;
-            float* cp = p.C + (long long)cbase * p.ldc + row;
+            CT* cp = (CT*)p.C + (long long)cbase * p.ldc + row;
             const int ncol = min(128, p.N - cbase);
             float cv[32];
             if (p.sub) {
 #pragma unroll
-                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? cp[(long long)j * p.ldc] : 0.0f;
+                for (int j = 0; j < 32; j++) cv[j] = (row_ok && j < ncol) ? ld_f(cp + (long long)j * p.ldc) : 0.0f;
             }
             if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
             tc_fence_after();
@@ -592,7 +595,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
 #pragma unroll
                     for (int j = 0; j < 32; j++) {
                         const int jj = (c + 1) * 32 + j;
-                        nv[j] = (row_ok && jj < ncol) ? cp[(long long)jj * p.ldc] : 0.0f;
+                        nv[j] = (row_ok && jj < ncol) ? ld_f(cp + (long long)jj * p.ldc) : 0.0f;
                     }
                 }
                 tmem_wait_ld();
@@ -604,7 +607,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                         if (jj < ncol) {
                             float v = __uint_as_float(r[j]) * rs;
                             if (p.sb) v *= p.sb[cbase + jj];
-                            cp[(long long)jj * p.ldc] = p.sub ? cv[j] - v : v;
+                            st_f(cp + (long long)jj * p.ldc, p.sub ? cv[j] - v : v);
                         }
                     }
                 }
@@ -661,9 +664,9 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, i
     return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
 }
 
-template <int KIND, int BN>
+template <int KIND, int BN, typename CT = float>
 static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
-                       const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                       const float* sa, const float* sb, CT* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                        int max_ctas, cudaStream_t s) {
     constexpr int elem = Kind<KIND>::ELEM;
     if (M <= 0 || N <= 0) return HPL_OK;
@@ -679,7 +682,7 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if (st) return st;
     static bool attr_set = false;
     if (!attr_set) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN>,
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN, CT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::DYN_SMEM));
         attr_set = true;
     }
@@ -700,15 +703,15 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.sa = sa;
     p.sb = sb;
     p.group_m = group_m<KIND>();
-    k_gemm_tc<KIND, BN><<<grid, THREADS, Tile<BN>::DYN_SMEM, s>>>(ma, mb, p);
+    k_gemm_tc<KIND, BN, CT><<<grid, THREADS, Tile<BN>::DYN_SMEM, s>>>(ma, mb, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
 
 // The pair kernel: grid = 2 x min(tiles, clusters that fit at once).
-template <int KIND>
+template <int KIND, typename CT = float>
 static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
-                       const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
+                       const float* sa, const float* sb, CT* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                        int max_ctas, cudaStream_t s) {
     constexpr int elem = Kind<KIND>::ELEM;
     if (M <= 0 || N <= 0) return HPL_OK;
@@ -723,7 +726,7 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if (st) return st;
     static int max_pairs = 0;
     if (!max_pairs) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc_pair<KIND>,
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc_pair<KIND, CT>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_DYN_SMEM));
         int dev = 0, sms = kNumSMsGB300;
         HPL_CUDA_TRY(cudaGetDevice(&dev));
@@ -733,7 +736,7 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
         cfg.blockDim = dim3(THREADS);
         cfg.dynamicSmemBytes = PAIR_DYN_SMEM;
         int nc = 0;
-        HPL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_gemm_tc_pair<KIND>, &cfg));
+        HPL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_gemm_tc_pair<KIND, CT>, &cfg));
         max_pairs = nc > 0 ? nc : sms / 2;
     }
     const int64_t ntiles = ((M + 255) / 256) * ((N + 255) / 256);
@@ -751,7 +754,7 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.sa = sa;
     p.sb = sb;
     p.group_m = GROUP_M_PAIR;
-    k_gemm_tc_pair<KIND><<<2 * pairs, THREADS, PAIR_DYN_SMEM, s>>>(ma, mb, p);
+    k_gemm_tc_pair<KIND, CT><<<2 * pairs, THREADS, PAIR_DYN_SMEM, s>>>(ma, mb, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
@@ -791,6 +794,21 @@ int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t l
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<1, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
     return tc::launch_kind<1, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
+}
+
+// BF16 operands and a BF16 C (a working matrix stored in BF16): the FP32
+// accumulator is combined with C in FP32 and rounded once when stored.
+int launch_gemm_bf16_c16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                         int64_t ldb, uint16_t* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas,
+                         cudaStream_t s) {
+    __nv_bfloat16* Cb = reinterpret_cast<__nv_bfloat16*>(C);
+    if (tc::pair_tiles(M, N))
+        return tc::launch_pair<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, Cb, ldc, sub, err, timeout_ns, max_ctas, s);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, Cb, ldc, sub, err, timeout_ns,
+                                       max_ctas, s);
+    return tc::launch_kind<0, 256>(M, N, K, A, lda, B, ldb, nullptr, nullptr, Cb, ldc, sub, err, timeout_ns, max_ctas,
+                                   s);
 }
 
 // FP16 operands (K contiguous) with the same per-row / per-column scales.

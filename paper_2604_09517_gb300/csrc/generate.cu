@@ -83,10 +83,10 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 }
 
 // ---------------------------------------------------------------------------
-// The dominant matrix straight into an FP32 working copy, for a
+// The dominant matrix straight into an FP32 (or BF16) working copy, for a
 // mixed-precision solve that keeps no FP64 copy of A (its residuals
-// regenerate the entries). Every entry is the FP64 generated value rounded to
-// nearest FP32, exactly what converting a stored FP64 matrix gives.
+// regenerate the entries). Every entry is the FP64 generated value rounded
+// once to nearest, exactly what converting a stored FP64 matrix gives.
 //
 // One pass over the entries: rows in blocks of 256 (blockIdx.x), `chunks`
 // column chunks (blockIdx.y). Per (row, chunk) the kernel writes the FP32
@@ -94,7 +94,19 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 // chunk in 128 bits (the diagonal's dominance, all j), and the FP32 sum of
 // |fl32(a_ij)| over the chunk's off-diagonal entries (||A||_inf for the
 // refinement's stopping test).
-__global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, float* __restrict__ F, int64_t ldf,
+__device__ __forceinline__ float gen_store(float* p, uint64_t h) {
+    const float v = gen_value_f32(h);
+    *p = v;
+    return v;
+}
+__device__ __forceinline__ float gen_store(__nv_bfloat16* p, uint64_t h) {
+    const __nv_bfloat16 v = f64_to_bf16_rn(gen_value(h));
+    *p = v;
+    return __bfloat162float(v);
+}
+
+template <typename FT>
+__global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, FT* __restrict__ F, int64_t ldf,
                                                       int chunks, uint64_t* __restrict__ plo,
                                                       uint64_t* __restrict__ phi, float* __restrict__ pf) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
@@ -107,8 +119,7 @@ __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, f
     float sf = 0.0f;
     for (int64_t j = j0; j < j1; j++, z += step) {
         const uint64_t h = sm64_mix(z);
-        const float v = gen_value_f32(h);
-        F[j * ldf + i] = v;
+        const float v = gen_store(F + j * ldf + i, h);
         const uint64_t m = h >> 11, u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
         const uint64_t nl = lo + u;
         hi += (nl < lo);
@@ -123,9 +134,10 @@ __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, f
 // Per row: the exact row sum over the chunks, rounded once, is the FP64
 // diagonal (into diag); its FP32 rounding goes onto F's diagonal and into the
 // row's norm partial of the chunk that holds column i.
+template <typename FT>
 __global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks, const uint64_t* __restrict__ plo,
                                                            const uint64_t* __restrict__ phi, double* __restrict__ diag,
-                                                           float* __restrict__ F, int64_t ldf, float* __restrict__ pf) {
+                                                           FT* __restrict__ F, int64_t ldf, float* __restrict__ pf) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     uint64_t lo = 0, hi = 0;
@@ -136,26 +148,34 @@ __global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks
     }
     const double d = u128_to_double_rn(hi, lo) * 0x1p-53;
     diag[i] = d;
-    const float f = __double2float_rn(d);
-    F[i * ldf + i] = f;
+    const float f = st_f64(F + i * ldf + i, d);
     const int64_t cw = (n + chunks - 1) / chunks;
     pf[(i / cw) * n + i] += fabsf(f);
 }
 
 // Stream 0 (the matrix) of seed, kind HPL_GEN_DIAG_DOMINANT, n x n, as FP32
-// into F (ldf >= n) with the FP64 diagonal into diag (n doubles); returns the
-// stream key the residual kernels regenerate from in *key_out. plo, phi
-// (chunks x n each) are scratch; pf (chunks x n) receives the row sums of
-// |F| split by column chunk.
-int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
-                                 int chunks, uint64_t* plo, uint64_t* phi, float* pf, cudaStream_t s) {
+// (bf16 = 0) or BF16 (bf16 = 1) into F (ldf >= n) with the FP64 diagonal into
+// diag (n doubles); returns the stream key the residual kernels regenerate
+// from in *key_out. plo, phi (chunks x n each) are scratch; pf (chunks x n)
+// receives the row sums of |F| split by column chunk.
+int launch_generate_dominant_f32(uint64_t seed, int64_t n, void* F, int64_t ldf, int bf16, double* diag,
+                                 uint64_t* key_out, int chunks, uint64_t* plo, uint64_t* phi, float* pf,
+                                 cudaStream_t s) {
     const uint64_t key = sm64_host_mix(seed + 1 * kGamma);
     if (key_out) *key_out = key;
     if (n <= 0) return HPL_OK;
-    k_generate_f32<<<dim3((unsigned)((n + 255) / 256), (unsigned)chunks), 256, 0, s>>>(key, n, F, ldf, chunks, plo,
-                                                                                     phi, pf);
-    HPL_LAUNCH_CHECK();
-    k_dominant_diag_fin<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, chunks, plo, phi, diag, F, ldf, pf);
+    const dim3 g1((unsigned)((n + 255) / 256), (unsigned)chunks), g2((unsigned)((n + 255) / 256));
+    if (bf16) {
+        __nv_bfloat16* Fb = (__nv_bfloat16*)F;
+        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Fb, ldf, chunks, plo, phi, pf);
+        HPL_LAUNCH_CHECK();
+        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Fb, ldf, pf);
+    } else {
+        float* Ff = (float*)F;
+        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Ff, ldf, chunks, plo, phi, pf);
+        HPL_LAUNCH_CHECK();
+        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Ff, ldf, pf);
+    }
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }

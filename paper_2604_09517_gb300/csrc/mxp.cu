@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 #include "common.cuh"
@@ -36,6 +37,9 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
 int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s);
+int launch_gemm_bf16_c16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                         int64_t ldb, uint16_t* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas,
+                         cudaStream_t s);
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s);
@@ -43,8 +47,8 @@ size_t residual_ws_bytes(int64_t n);
 int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, const double* diag,
                         const double* anorm, const double* x, const double* b, double* r, double* sr, void* ws,
                         cudaStream_t s);
-int launch_generate_dominant_f32(uint64_t seed, int64_t n, float* F, int64_t ldf, double* diag, uint64_t* key_out,
-                                 int chunks, uint64_t* plo, uint64_t* phi, float* pf,
+int launch_generate_dominant_f32(uint64_t seed, int64_t n, void* F, int64_t ldf, int bf16, double* diag,
+                                 uint64_t* key_out, int chunks, uint64_t* plo, uint64_t* phi, float* pf,
                                  cudaStream_t s);
 int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, double* anorm, int norm_mode, const double* x,
                           const double* b, double* r, double* sr, void* ws, cudaStream_t s);
@@ -82,7 +86,8 @@ struct Seg {
     int64_t seg_off, seg_stride, kpad;
 };
 
-__global__ void __launch_bounds__(256) k_to_bf16_t(const float* __restrict__ X, int64_t ldx, int64_t rows,
+template <typename XT>
+__global__ void __launch_bounds__(256) k_to_bf16_t(const XT* __restrict__ X, int64_t ldx, int64_t rows,
                                                    int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
                                                    Seg g) {
     __shared__ float tile[32][33];
@@ -90,7 +95,7 @@ __global__ void __launch_bounds__(256) k_to_bf16_t(const float* __restrict__ X, 
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
         int64_t c = c0 + i, r = r0 + tx;
-        float v = (c < cols && r < rows) ? X[c * ldx + r] : 0.0f;
+        float v = (c < cols && r < rows) ? ld_f(X + c * ldx + r) : 0.0f;
         if (g.eye2 && c < cols && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
         tile[i][tx] = v;
     }
@@ -104,19 +109,21 @@ __global__ void __launch_bounds__(256) k_to_bf16_t(const float* __restrict__ X, 
     }
 }
 
-__global__ void __launch_bounds__(256) k_to_bf16_n(const float* __restrict__ X, int64_t ldx, int64_t rows,
+template <typename XT>
+__global__ void __launch_bounds__(256) k_to_bf16_n(const XT* __restrict__ X, int64_t ldx, int64_t rows,
                                                    int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
                                                    Seg g) {
     const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;   // K index
     const int64_t c = blockIdx.y;                                  // operand row
     if (r >= g.kpad || c >= cols) return;
-    float v = r < rows ? X[c * ldx + r] : 0.0f;
+    float v = r < rows ? ld_f(X + c * ldx + r) : 0.0f;
     if (g.eye2 && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
     for (int q = 0; q < g.nseg; q++)
         out[c * ldo + g.seg_off + q * g.seg_stride + r] = __float2bfloat16_rn(bf16_part(v, (g.parts >> (2 * q)) & 3));
 }
 
-static int to_bf16_seg(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, uint16_t* out, int64_t ldo,
+template <typename XT>
+static int to_bf16_seg(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int trans, uint16_t* out, int64_t ldo,
                        Seg g, cudaStream_t s) {
     if (trans) {
         dim3 grid((unsigned)((g.kpad + 31) / 32), (unsigned)((rows + 31) / 32));
@@ -134,7 +141,8 @@ static int to_bf16_seg(const float* X, int64_t ldx, int64_t rows, int64_t cols, 
 }
 
 // One segment, one part (the plain operand conversions).
-static int to_bf16(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, int part, uint16_t* out,
+template <typename XT>
+static int to_bf16(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int trans, int part, uint16_t* out,
                    int64_t ldo, int64_t seg_off, int64_t kpad, cudaStream_t s) {
     Seg g{1, part, 0, seg_off, 0, kpad};
     return to_bf16_seg(X, ldx, rows, cols, trans, out, ldo, g, s);
@@ -266,8 +274,9 @@ __global__ void __launch_bounds__(256) k_abs_rowsum_max(int64_t n, int chunks, c
 // FP32 working copy F of A; on the way, the row sums of |F| over `stripes`
 // column stripes into part[stripe][row] (the refinement's ||A||_inf, reduced
 // by k_abs_rowsum_max), so the norm costs no extra pass over the matrix.
+template <typename FT>
 __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda,
-                                                        float* __restrict__ F, int64_t ldf, int stripes,
+                                                        FT* __restrict__ F, int64_t ldf, int stripes,
                                                         float* __restrict__ part) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
@@ -277,18 +286,39 @@ __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double*
     int64_t j = j0;
 #pragma unroll 4
     for (; j + 1 < j1; j += 2) {
-        const float f0 = (float)A[j * lda + i], f1 = (float)A[(j + 1) * lda + i];
-        F[j * ldf + i] = f0;
-        F[(j + 1) * ldf + i] = f1;
-        s0 += fabsf(f0);
-        s1 += fabsf(f1);
+        const double d0 = A[j * lda + i], d1 = A[(j + 1) * lda + i];
+        s0 += fabsf(st_f64(F + j * ldf + i, d0));
+        s1 += fabsf(st_f64(F + (j + 1) * ldf + i, d1));
     }
     if (j < j1) {
-        const float f0 = (float)A[j * lda + i];
-        F[j * ldf + i] = f0;
-        s0 += fabsf(f0);
+        s0 += fabsf(st_f64(F + j * ldf + i, A[j * lda + i]));
     }
     part[(int64_t)blockIdx.y * n + i] = s0 + s1;
+}
+
+// BF16 working copy, two adjacent rows per thread so that a warp stores 128
+// contiguous bytes per column (whole cache lines; 32 rows of 2-byte values
+// would leave every line half written by each warp). n and ldf even.
+__global__ void __launch_bounds__(256) k_f64_to_bf16_mat2(int64_t n, const double* __restrict__ A, int64_t lda,
+                                                          __nv_bfloat16* __restrict__ F, int64_t ldf, int stripes,
+                                                          float* __restrict__ part) {
+    const int64_t i = 2 * ((int64_t)blockIdx.x * 256 + threadIdx.x);
+    if (i >= n) return;
+    const int64_t cw = (n + stripes - 1) / stripes;
+    const int64_t j0 = (int64_t)blockIdx.y * cw, j1 = std::min<int64_t>(n, j0 + cw);
+    float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll 4
+    for (int64_t j = j0; j < j1; j++) {
+        const double2 a = *reinterpret_cast<const double2*>(A + j * lda + i);
+        __nv_bfloat162 v;
+        v.x = f64_to_bf16_rn(a.x);
+        v.y = f64_to_bf16_rn(a.y);
+        *reinterpret_cast<__nv_bfloat162*>(F + j * ldf + i) = v;
+        s0 += fabsf(__bfloat162float(v.x));
+        s1 += fabsf(__bfloat162float(v.y));
+    }
+    part[(int64_t)blockIdx.y * n + i] = s0;
+    part[(int64_t)blockIdx.y * n + i + 1] = s1;
 }
 
 // Column-split GEMV for the preconditioner: part[s][r] = sum over the column
@@ -296,7 +326,15 @@ __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double*
 // CTA takes 128 rows (4 per lane, float4 loads when aligned) and one column
 // chunk, its 8 warps split the chunk's columns; k_gemv_combine then adds the
 // chunks in order, so the result does not depend on scheduling.
-__global__ void __launch_bounds__(256) k_gemv_part(int64_t rows, int64_t cols, const float* __restrict__ P,
+__device__ __forceinline__ float4 ld_f4(const float* p) { return *reinterpret_cast<const float4*>(p); }
+__device__ __forceinline__ float4 ld_f4(const __nv_bfloat16* p) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    return make_float4(__uint_as_float(u.x << 16), __uint_as_float(u.x & 0xffff0000u), __uint_as_float(u.y << 16),
+                       __uint_as_float(u.y & 0xffff0000u));
+}
+
+template <typename PT>
+__global__ void __launch_bounds__(256) k_gemv_part(int64_t rows, int64_t cols, const PT* __restrict__ P,
                                                    int64_t ldp, const float* __restrict__ x, int64_t chunk,
                                                    float* __restrict__ part, int64_t ldpart, int vec) {
     __shared__ float red[8][129];
@@ -307,7 +345,7 @@ __global__ void __launch_bounds__(256) k_gemv_part(int64_t rows, int64_t cols, c
     if (vec && r + 3 < rows) {
 #pragma unroll 8
         for (int64_t c = c0 + warp; c < c1; c += 8) {
-            const float4 v = *reinterpret_cast<const float4*>(P + c * ldp + r);
+            const float4 v = ld_f4(P + c * ldp + r);
             const float xc = __ldg(x + c);
             a0 = fmaf(v.x, xc, a0);
             a1 = fmaf(v.y, xc, a1);
@@ -317,11 +355,11 @@ __global__ void __launch_bounds__(256) k_gemv_part(int64_t rows, int64_t cols, c
     } else {
         for (int64_t c = c0 + warp; c < c1; c += 8) {
             const float xc = __ldg(x + c);
-            const float* pc = P + c * ldp;
-            if (r < rows) a0 = fmaf(pc[r], xc, a0);
-            if (r + 1 < rows) a1 = fmaf(pc[r + 1], xc, a1);
-            if (r + 2 < rows) a2 = fmaf(pc[r + 2], xc, a2);
-            if (r + 3 < rows) a3 = fmaf(pc[r + 3], xc, a3);
+            const PT* pc = P + c * ldp;
+            if (r < rows) a0 = fmaf(ld_f(pc + r), xc, a0);
+            if (r + 1 < rows) a1 = fmaf(ld_f(pc + r + 1), xc, a1);
+            if (r + 2 < rows) a2 = fmaf(ld_f(pc + r + 2), xc, a2);
+            if (r + 3 < rows) a3 = fmaf(ld_f(pc + r + 3), xc, a3);
         }
     }
     red[warp][4 * lane] = a0;
@@ -354,12 +392,13 @@ __global__ void k_ns_init(const float* __restrict__ D, int64_t ldd, int kb, floa
     }
 }
 
-__global__ void k_copy_block32(const float* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+template <typename ST>
+__global__ void k_copy_block32(const ST* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
                                float* __restrict__ dst, int64_t ldd) {
     const int64_t total = rows * cols;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         int64_t j = t / rows, i = t - j * rows;
-        dst[j * ldd + i] = src[j * lds + i];
+        dst[j * ldd + i] = ld_f(src + j * lds + i);
     }
 }
 
@@ -371,16 +410,17 @@ __global__ void k_zero_diag_flag(const float* __restrict__ D, int64_t ldd, int k
 
 // y (= or -=) P^T x: one warp per column c of P (rows x cols, FP32 column-
 // major), lanes over the rows, shuffle reduction.
-__global__ void __launch_bounds__(256) k_gemvT32(int64_t rows, int64_t cols, const float* __restrict__ P,
+template <typename PT>
+__global__ void __launch_bounds__(256) k_gemvT32(int64_t rows, int64_t cols, const PT* __restrict__ P,
                                                  int64_t ldp, const float* __restrict__ x, float* __restrict__ y,
                                                  int sub) {
     const int lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= cols) return;
-    const float* col = P + c * ldp;
+    const PT* col = P + c * ldp;
     float acc = 0.0f;
 #pragma unroll 4
-    for (int64_t r = lane; r < rows; r += 32) acc = fmaf(col[r], x[r], acc);
+    for (int64_t r = lane; r < rows; r += 32) acc = fmaf(ld_f(col + r), x[r], acc);
     for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
     if (lane == 0) y[c] = sub ? y[c] - acc : acc;
 }
@@ -475,8 +515,8 @@ __global__ void __launch_bounds__(256) k_resid_blk_finish(int64_t m, int64_t nn,
 
 // C (m x nn, FP32) = or -= op(A) (m x kk) B (kk x nn), FP32 accumulation;
 // op(A)(i, q) = A[q * lda + i] (TA = false) or A[i * lda + q] (TA = true).
-template <bool TA>
-__global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk, const float* __restrict__ A,
+template <bool TA, typename AT>
+__global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk, const AT* __restrict__ A,
                                                int64_t lda, const float* __restrict__ B, int64_t ldb,
                                                float* __restrict__ C, int64_t ldc, int sub) {
     __shared__ float As[16][65], Bs[16][65];
@@ -489,7 +529,7 @@ __global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk
             if (TA) { r = e >> 4; kq = e & 15; }
             else { kq = e >> 6; r = e & 63; }
             const bool ok = k0 + kq < kk && row0 + r < m;
-            As[kq][r] = ok ? (TA ? A[(row0 + r) * lda + k0 + kq] : A[(k0 + kq) * lda + row0 + r]) : 0.0f;
+            As[kq][r] = ok ? ld_f(TA ? A + (row0 + r) * lda + k0 + kq : A + (k0 + kq) * lda + row0 + r) : 0.0f;
         }
         for (int e = tid; e < 16 * 64; e += 256) {
             const int c = e >> 4, kq = e & 15;
@@ -648,7 +688,7 @@ __global__ void k_combine(int64_t n, int k, const double* __restrict__ Z, int64_
 // ---------------------------------------------------------------------------
 // Workspace.
 struct MxpWs {
-    float* F;          // n x n working matrix / factor (ld = n)
+    void* F;           // n x n working matrix / factor (ld = n), FP32 or BF16
     float* Dinv;       // n x nb, D_k^-1 in rows k0..k0+kb (ld = n)
     uint16_t* opA;     // BF16 operand (n x nb8)
     uint16_t* opB;     // BF16 operand (n x nb8)
@@ -682,7 +722,8 @@ struct MxpWs {
     unsigned long long* cmax;   // 3 x nrhs_blk column maxima
 };
 
-static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, int64_t nrhs_blk = 0) {
+static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, int64_t nrhs_blk = 0,
+                            int fbytes = 4) {
     const int64_t nb8 = round8(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -691,7 +732,7 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, 
         return base ? (void*)(base + o) : (void*)nullptr;
     };
     MxpWs t;
-    t.F = (float*)take(sizeof(float) * n * n);
+    t.F = take((size_t)fbytes * n * n);
     t.Dinv = (float*)take(sizeof(float) * n * nb);
     t.opA = (uint16_t*)take(2 * n * nb8);
     t.opB = (uint16_t*)take(2 * n * nb8);
@@ -728,6 +769,7 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, 
 
 static unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 152 * 16); }
 
+template <typename FT>
 struct Mxp {
     int64_t n, nb;
     int m;
@@ -740,6 +782,19 @@ struct Mxp {
     uint64_t key = 0;       // generator stream key of the regenerated matrix
     bool trans = false;     // solve A^T x = b with the same factor (the adjoint)
     bool tnorm_ready = false;   // ||A^T||_inf cached in w.scal[7]
+    static constexpr bool kBf16 = std::is_same<FT, __nv_bfloat16>::value;
+
+    FT* F() const { return (FT*)w.F; }
+
+    // the factor's product into the working matrix: C (FT) = or -= A B^T
+    int gemm_c(int64_t M, int64_t N, int64_t K, const uint16_t* Aop, int64_t lda_, const uint16_t* Bop, int64_t ldb_,
+               FT* C, int64_t ldc, int sub) {
+        if constexpr (kBf16)
+            return launch_gemm_bf16_c16(M, N, K, Aop, lda_, Bop, ldb_, (uint16_t*)C, ldc, sub, w.err, o.timeout_ns, 0,
+                                        s);
+        else
+            return launch_gemm_bf16(M, N, K, Aop, lda_, Bop, ldb_, C, ldc, sub, w.err, o.timeout_ns, 0, s);
+    }
 
     // r = b - op(A) x (b != NULL, scaled residual into sr if given) or r = op(A) x
     int resid(const double* x, const double* b, double* r, double* sr) {
@@ -754,15 +809,16 @@ struct Mxp {
         return st;
     }
 
-    // y (= or -=) P x for an FP32 column-major panel (rows x cols, ldp)
-    int gemv(int64_t rows, int64_t cols, const float* P, int64_t ldp, const float* x, float* y, int sub) {
+    // y (= or -=) P x for an FP32 or BF16 column-major panel (rows x cols, ldp)
+    template <typename PT>
+    int gemv(int64_t rows, int64_t cols, const PT* P, int64_t ldp, const float* x, float* y, int sub) {
         if (rows <= 0) return HPL_OK;
         const int64_t rb = (rows + 127) / 128;
         int64_t nsplit = std::min<int64_t>(kGemvSplitMax, std::max<int64_t>(1, (1216 + rb - 1) / rb));
         nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, cols / 64));
         const int64_t chunk = (cols + nsplit - 1) / nsplit;
         nsplit = (cols + chunk - 1) / chunk;
-        const int vec = (ldp % 4 == 0) && (((uintptr_t)P & 15) == 0);
+        const int vec = (ldp % 4 == 0) && (((uintptr_t)P & (4 * sizeof(PT) - 1)) == 0);
         k_gemv_part<<<dim3((unsigned)rb, (unsigned)nsplit), 256, 0, s>>>(rows, cols, P, ldp, x, chunk, w.gpart, n, vec);
         HPL_LAUNCH_CHECK();
         k_gemv_combine<<<grid_for(rows), 256, 0, s>>>(rows, (int)nsplit, w.gpart, n, y, sub);
@@ -784,13 +840,21 @@ struct Mxp {
         HPL_CUDA_TRY(cudaMemsetAsync(w.err, 0, sizeof(int) * 4, s));
         int cslot = phase_begin(s);
         if (A) {
-            k_f64_to_f32_mat<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(n, A, lda, w.F, ldf,
-                                                                                            kGemvSplitMax, w.gpart);
+            bool paired = false;
+            if constexpr (kBf16) {
+                paired = n % 2 == 0 && lda % 2 == 0 && ((uintptr_t)A & 15) == 0;
+                if (paired)
+                    k_f64_to_bf16_mat2<<<dim3((unsigned)((n + 511) / 512), kGemvSplitMax), 256, 0, s>>>(
+                        n, A, lda, F(), ldf, kGemvSplitMax, w.gpart);
+            }
+            if (!paired)
+                k_f64_to_f32_mat<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(
+                    n, A, lda, F(), ldf, kGemvSplitMax, w.gpart);
             HPL_LAUNCH_CHECK();
         } else {
             // one pass: the FP32 entries, the exact diagonal and the norm's row sums
-            int st = launch_generate_dominant_f32(seed, n, w.F, ldf, w.gdiag, &key, kGemvSplitMax, w.glo, w.ghi,
-                                                  w.gpart, s);
+            int st = launch_generate_dominant_f32(seed, n, F(), ldf, kBf16 ? 1 : 0, w.gdiag, &key, kGemvSplitMax,
+                                                  w.glo, w.ghi, w.gpart, s);
             if (st) return st;
         }
         HPL_CUDA_TRY(cudaMemsetAsync(w.scal + 6, 0, sizeof(double), s));
@@ -800,15 +864,28 @@ struct Mxp {
         phase_end(cslot, s, PH_CONVERT, A ? 12.0 * n * n : 8.0 * n * n);
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
-            float* D = w.F + k0 * ldf + k0;
             int slot = phase_begin(s);
-            k_zero_diag_flag<<<1, 256, 0, s>>>(D, ldf, (int)kb, k0, info);
+            // the diagonal block as FP32: in place, or (BF16 storage) widened into
+            // R, which the first Newton-Schulz product overwrites only after D
+            // has been split into its operand
+            const float* D;
+            int64_t ldd;
+            if constexpr (kBf16) {
+                k_copy_block32<<<grid_for(kb * kb), 256, 0, s>>>(F() + k0 * ldf + k0, ldf, kb, kb, w.R, kb);
+                HPL_LAUNCH_CHECK();
+                D = w.R;
+                ldd = kb;
+            } else {
+                D = F() + k0 * ldf + k0;
+                ldd = ldf;
+            }
+            k_zero_diag_flag<<<1, 256, 0, s>>>(D, ldd, (int)kb, k0, info);
             HPL_LAUNCH_CHECK();
-            k_ns_init<<<grid_for(kb * kb), 256, 0, s>>>(D, ldf, (int)kb, w.X);
+            k_ns_init<<<grid_for(kb * kb), 256, 0, s>>>(D, ldd, (int)kb, w.X);
             HPL_LAUNCH_CHECK();
             int st;
             // split D as the A operand: [hi | hi | lo]
-            if ((st = to_bf16_split3(D, ldf, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
+            if ((st = to_bf16_split3(D, ldd, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
             for (int it = 0; it < o.ns_iters; it++) {
                 // R = D X: B operand from X, [hi | lo | hi]
                 if ((st = to_bf16_split3(w.X, kb, kb, 0, 1, 2, 1, 0, w.nsB, kb8, s))) return st;
@@ -823,28 +900,35 @@ struct Mxp {
             k_copy_block32<<<grid_for(kb * kb), 256, 0, s>>>(w.X, kb, kb, kb, w.Dinv + k0, n);
             HPL_LAUNCH_CHECK();
             if (m2 > 0) {
-                float* A21 = w.F + k0 * ldf + k0 + kb;
-                float* A12 = w.F + (k0 + kb) * ldf + k0;
-                float* A22 = w.F + (k0 + kb) * ldf + k0 + kb;
-                // L21 = A21 D^-1 (FP16 operands with scales for FP16, else BF16)
-                if (o.prec == HPL_PREC_FP16) {
-                    k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa);
-                    HPL_LAUNCH_CHECK();
-                    k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb);
-                    HPL_LAUNCH_CHECK();
-                    if ((st = launch_gemm_f16(m2, kb, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A21, ldf, 0, w.err,
-                                              o.timeout_ns, 0, s)))
-                        return st;
-                } else {
+                FT* A21 = F() + k0 * ldf + k0 + kb;
+                FT* A12 = F() + (k0 + kb) * ldf + k0;
+                FT* A22 = F() + (k0 + kb) * ldf + k0 + kb;
+                // L21 = A21 D^-1 (FP16 operands with scales for FP16, else BF16;
+                // a BF16-stored working matrix is always BF16)
+                bool done = false;
+                if constexpr (!kBf16) {
+                    if (o.prec == HPL_PREC_FP16) {
+                        k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8,
+                                                                                   w.sa);
+                        HPL_LAUNCH_CHECK();
+                        k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb);
+                        HPL_LAUNCH_CHECK();
+                        if ((st = launch_gemm_f16(m2, kb, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A21, ldf, 0, w.err,
+                                                  o.timeout_ns, 0, s)))
+                            return st;
+                        done = true;
+                    }
+                }
+                if (!done) {
                     if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
                     if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
-                    if ((st = launch_gemm_bf16(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0, w.err, o.timeout_ns, 0,
-                                               s)))
-                        return st;
+                    if ((st = gemm_c(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0))) return st;
                 }
                 phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
                 // A22 -= L21 A12
                 slot = phase_begin(s);
+                done = false;
+                if constexpr (!kBf16) {
                 if (o.prec == HPL_PREC_FP8_E4M3) {
                     const int64_t kb16 = (kb + 15) / 16 * 16;
                     uint8_t* qa = (uint8_t*)w.opA;
@@ -864,12 +948,13 @@ struct Mxp {
                     if ((st = launch_gemm_f16(m2, m2, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A22, ldf, 1, w.err,
                                               o.timeout_ns, 0, s)))
                         return st;
-                } else {
+                }
+                done = o.prec == HPL_PREC_FP8_E4M3 || o.prec == HPL_PREC_FP16;
+                }
+                if (!done) {
                     if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
                     if ((st = to_bf16(A12, ldf, kb, m2, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
-                    if ((st = launch_gemm_bf16(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1, w.err, o.timeout_ns, 0,
-                                               s)))
-                        return st;
+                    if ((st = gemm_c(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1))) return st;
                 }
                 phase_end(slot, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
             } else {
@@ -897,7 +982,7 @@ struct Mxp {
             k_copy32<<<grid_for(kb), 256, 0, s>>>(kb, t, y + k0);
             HPL_LAUNCH_CHECK();
             if (m2 > 0) {
-                k_gemvT32<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(kb, m2, w.F + (k0 + kb) * ldf + k0, ldf, y + k0,
+                k_gemvT32<<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(kb, m2, F() + (k0 + kb) * ldf + k0, ldf, y + k0,
                                                                   y + k0 + kb, 1);
                 HPL_LAUNCH_CHECK();
             }
@@ -906,7 +991,7 @@ struct Mxp {
         for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
             if (m2 > 0) {
-                k_gemvT32<<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0 + kb,
+                k_gemvT32<<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(m2, kb, F() + k0 * ldf + k0 + kb, ldf, y + k0 + kb,
                                                                   y + k0, 1);
                 HPL_LAUNCH_CHECK();
             }
@@ -929,7 +1014,7 @@ struct Mxp {
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
             if (m2 > 0) {
-                int st = gemv(m2, kb, w.F + k0 * ldf + k0 + kb, ldf, y + k0, y + k0 + kb, 1);
+                int st = gemv(m2, kb, F() + k0 * ldf + k0 + kb, ldf, y + k0, y + k0 + kb, 1);
                 if (st) return st;
             }
         }
@@ -941,7 +1026,7 @@ struct Mxp {
             k_copy32<<<grid_for(kb), 256, 0, s>>>(kb, t, y + k0);
             HPL_LAUNCH_CHECK();
             if (k0 > 0) {
-                st = gemv(k0, kb, w.F + k0 * ldf, ldf, y + k0, y, 1);
+                st = gemv(k0, kb, F() + k0 * ldf, ldf, y + k0, y, 1);
                 if (st) return st;
             }
         }
@@ -1071,12 +1156,13 @@ struct Mxp {
     dim3 grid_blk(int64_t rows, int64_t cols) const { return dim3((unsigned)((rows + 255) / 256), (unsigned)cols); }
 
     // C (rows x k) -= or = op(P) (rows x kk) Y (kk x k), FP32
-    int sgemm(bool ta, int64_t rows, int64_t kk, const float* P, int64_t ldp, const float* Y, int64_t ldy, float* C,
+    template <typename PT>
+    int sgemm(bool ta, int64_t rows, int64_t kk, const PT* P, int64_t ldp, const float* Y, int64_t ldy, float* C,
               int64_t ldc, int64_t k, int sub) {
         if (rows <= 0 || kk <= 0 || k <= 0) return HPL_OK;
         dim3 g((unsigned)((rows + 63) / 64), (unsigned)((k + 63) / 64));
-        if (ta) k_sgemm<true><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
-        else k_sgemm<false><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
+        if (ta) k_sgemm<true, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
+        else k_sgemm<false, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
         HPL_LAUNCH_CHECK();
         return HPL_OK;
     }
@@ -1093,7 +1179,7 @@ struct Mxp {
         if (!trans) {
             for (int64_t k0 = 0; k0 < n; k0 += nb) {
                 const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
-                if ((st = sgemm(false, m2, kb, w.F + k0 * ldf + k0 + kb, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
+                if ((st = sgemm(false, m2, kb, F() + k0 * ldf + k0 + kb, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
                     return st;
             }
             for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
@@ -1101,7 +1187,7 @@ struct Mxp {
                 if ((st = sgemm(false, kb, kb, w.Dinv + k0, n, Y + k0, n, T, nb, k, 0))) return st;
                 k_copy32_blk<<<grid_blk(kb, k), 256, 0, s>>>(kb, k, T, nb, Y + k0, n);
                 HPL_LAUNCH_CHECK();
-                if ((st = sgemm(false, k0, kb, w.F + k0 * ldf, ldf, Y + k0, n, Y, n, k, 1))) return st;
+                if ((st = sgemm(false, k0, kb, F() + k0 * ldf, ldf, Y + k0, n, Y, n, k, 1))) return st;
             }
         } else {
             for (int64_t k0 = 0; k0 < n; k0 += nb) {
@@ -1109,12 +1195,12 @@ struct Mxp {
                 if ((st = sgemm(true, kb, kb, w.Dinv + k0, n, Y + k0, n, T, nb, k, 0))) return st;
                 k_copy32_blk<<<grid_blk(kb, k), 256, 0, s>>>(kb, k, T, nb, Y + k0, n);
                 HPL_LAUNCH_CHECK();
-                if ((st = sgemm(true, m2, kb, w.F + (k0 + kb) * ldf + k0, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
+                if ((st = sgemm(true, m2, kb, F() + (k0 + kb) * ldf + k0, ldf, Y + k0, n, Y + k0 + kb, n, k, 1)))
                     return st;
             }
             for (int64_t k0 = last; k0 >= 0; k0 -= nb) {
                 const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb;
-                if ((st = sgemm(true, kb, m2, w.F + k0 * ldf + k0 + kb, ldf, Y + k0 + kb, n, Y + k0, n, k, 1)))
+                if ((st = sgemm(true, kb, m2, F() + k0 * ldf + k0 + kb, ldf, Y + k0 + kb, n, Y + k0, n, k, 1)))
                     return st;
             }
         }
@@ -1195,23 +1281,28 @@ using namespace hplgb;
 // Right-hand sides refined as one block: several, with classic refinement.
 static int64_t block_rhs(int64_t nrhs, const Opts& o) { return (nrhs > 1 && o.refine == HPL_REFINE_IR) ? nrhs : 0; }
 
+static int fbytes_of(const Opts& o) { return o.storage == HPL_STORAGE_BF16 ? 2 : 4; }
+
+// Option checks shared by the solve and its adjoint: the precision, and BF16
+// storage only with BF16 operands.
+static bool mxp_opts_ok(const Opts& o) {
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return false;
+    if (o.storage != HPL_STORAGE_FP32 && o.storage != HPL_STORAGE_BF16) return false;
+    if (o.storage == HPL_STORAGE_BF16 && o.prec != HPL_PREC_BF16) return false;
+    return true;
+}
+
 extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts) {
     Opts o = resolve_opts(opts, kMxpDefaultNb);
     int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
-    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o));
+    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o), fbytes_of(o));
 }
 
-extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
-                         int64_t ldb, double* X, int64_t ldx, const hpl_opts* opts, void* ws, size_t ws_bytes,
-                         hpl_info* info, void* stream) {
-    if (n <= 0 || nrhs < 0 || (A && lda < n) || !info) return HPL_ERR_INVALID;
-    if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
-    if (n > 0x7fffffff) return HPL_ERR_INVALID;
-    Opts o = resolve_opts(opts, kMxpDefaultNb);
-    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return HPL_ERR_INVALID;
-    if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
-    if (o.ns_iters > 8) return HPL_ERR_INVALID;
-    Mxp mx;
+template <typename FT>
+static int mxp_solve_t(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
+                       int64_t ldb, double* X, int64_t ldx, const Opts& o, void* ws, size_t ws_bytes, hpl_info* info,
+                       void* stream) {
+    Mxp<FT> mx;
     mx.n = n;
     mx.nb = std::min<int64_t>(o.nb, n);
     mx.m = o.gmres_m;
@@ -1221,10 +1312,10 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     mx.lda = lda;
     mx.seed = seed;
     mx.nblk = A ? block_rhs(nrhs, o) : 0;       // the block residual reads a stored A
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk);
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o));
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk);
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o));
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     int st = mx.factor(info);
@@ -1260,20 +1351,29 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     return HPL_OK;
 }
 
+extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, uint64_t seed, const double* B,
+                         int64_t ldb, double* X, int64_t ldx, const hpl_opts* opts, void* ws, size_t ws_bytes,
+                         hpl_info* info, void* stream) {
+    if (n <= 0 || nrhs < 0 || (A && lda < n) || !info) return HPL_ERR_INVALID;
+    if (nrhs > 0 && (!B || !X || ldb < n || ldx < n)) return HPL_ERR_INVALID;
+    if (n > 0x7fffffff) return HPL_ERR_INVALID;
+    Opts o = resolve_opts(opts, kMxpDefaultNb);
+    if (!mxp_opts_ok(o)) return HPL_ERR_INVALID;
+    if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
+    if (o.ns_iters > 8) return HPL_ERR_INVALID;
+    if (o.storage == HPL_STORAGE_BF16)
+        return mxp_solve_t<__nv_bfloat16>(n, nrhs, A, lda, seed, B, ldb, X, ldx, o, ws, ws_bytes, info, stream);
+    return mxp_solve_t<float>(n, nrhs, A, lda, seed, B, ldb, X, ldx, o, ws, ws_bytes, info, stream);
+}
+
 // Adjoint of X = A^-1 B: grad_B = A^-T G by the same refinement with the
 // transposed system (M^-T from the saved block factor as preconditioner, FP64
 // residuals with A^T), then grad_A = -grad_B X^T (FP64 outer product).
-extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
-                                 const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA,
-                                 int64_t ldga, const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* info,
-                                 void* stream) {
-    if (n <= 0 || nrhs < 0 || !A || lda < n || !info || !ws) return HPL_ERR_INVALID;
-    if (nrhs > 0 && (!G || !gradB || ldg < n || ldgb < n)) return HPL_ERR_INVALID;
-    if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
-    if (n > 0x7fffffff) return HPL_ERR_INVALID;
-    Opts o = resolve_opts(opts, kMxpDefaultNb);
-    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return HPL_ERR_INVALID;
-    Mxp mx;
+template <typename FT>
+static int lu_solve_backward_t(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
+                               const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA, int64_t ldga,
+                               const Opts& o, void* ws, size_t ws_bytes, hpl_info* info, void* stream) {
+    Mxp<FT> mx;
     mx.n = n;
     mx.nb = std::min<int64_t>(o.nb, n);
     mx.m = o.gmres_m;
@@ -1283,10 +1383,10 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     mx.lda = lda;
     mx.trans = true;
     mx.nblk = block_rhs(nrhs, o);
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk);
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o));
     if (ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk);
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o));
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     HPL_CUDA_TRY(cudaMemsetAsync(mx.w.err, 0, sizeof(int) * 4, s));
@@ -1324,4 +1424,21 @@ extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64
     HPL_CUDA_TRY(cudaMemcpyAsync(info, &h, sizeof(h), cudaMemcpyHostToDevice, s));
     HPL_CUDA_TRY(cudaStreamSynchronize(s));
     return HPL_OK;
+}
+
+extern "C" int lu_solve_backward(int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* X, int64_t ldx,
+                                 const double* G, int64_t ldg, double* gradB, int64_t ldgb, double* gradA,
+                                 int64_t ldga, const hpl_opts* opts, void* ws, size_t ws_bytes, hpl_info* info,
+                                 void* stream) {
+    if (n <= 0 || nrhs < 0 || !A || lda < n || !info || !ws) return HPL_ERR_INVALID;
+    if (nrhs > 0 && (!G || !gradB || ldg < n || ldgb < n)) return HPL_ERR_INVALID;
+    if (gradA && (!X || ldx < n || ldga < n)) return HPL_ERR_INVALID;
+    if (n > 0x7fffffff) return HPL_ERR_INVALID;
+    Opts o = resolve_opts(opts, kMxpDefaultNb);
+    if (!mxp_opts_ok(o)) return HPL_ERR_INVALID;
+    if (o.storage == HPL_STORAGE_BF16)
+        return lu_solve_backward_t<__nv_bfloat16>(n, nrhs, A, lda, X, ldx, G, ldg, gradB, ldgb, gradA, ldga, o, ws,
+                                                  ws_bytes, info, stream);
+    return lu_solve_backward_t<float>(n, nrhs, A, lda, X, ldx, G, ldg, gradB, ldgb, gradA, ldga, o, ws, ws_bytes,
+                                      info, stream);
 }

@@ -115,17 +115,18 @@ def test_mxp_rejects_invalid(hpl):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("prec,stored", [(0, True), (1, True), (2, True), (0, False)])
-def test_mxp_full_size_n98304(hpl, orc, prec, stored):
-    """n = 98304, NB = 3072 (the benchmark's launch configuration), BF16 and
-    FP8 updates, A stored or regenerated by the library: the oracle cannot
+@pytest.mark.parametrize("prec,stored,storage", [(0, True, 0), (1, True, 0), (2, True, 0), (0, False, 0), (0, True, 1),
+                                                (0, False, 1)])
+def test_mxp_full_size_n98304(hpl, orc, prec, stored, storage):
+    """n = 98304, NB = 3072 (the benchmark's launch configuration), BF16, FP8
+    and FP16 updates, FP32 or BF16 storage, A stored or regenerated by the library: the oracle cannot
     factor this size; it checks the GPU solution through the scaled residual
     computed on the CPU with A regenerated from the seed."""
     import torch
     n, nb, seed = 98304, 3072, 1
     A = hpl.generate(seed, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT) if stored else None
     b = hpl.generate(seed, hpl.STREAM_B, n, 1)[:, 0].contiguous()
-    x, info, ws = hpl.mxp_solve(A, b, nb=nb, prec=prec, seed=seed)
+    x, info, ws = hpl.mxp_solve(A, b, nb=nb, prec=prec, seed=seed, storage=storage)
     torch.cuda.synchronize()
     rec = info.read()
     assert rec["status"] == 0 and rec["scaled_residual"] < 16, rec
@@ -259,3 +260,68 @@ def test_mxp_fp16_variant(hpl, orc, n, nb):
     assert berr(F) < berr(Fb) / 4
     emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_FP16, refine=1)
     assert abs(rec["iters"] - emu["iters"]) <= 2
+
+
+@pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256), (2560, 256), (300, 100)])
+def test_mxp_bf16_storage(hpl, orc, n, nb):
+    """BF16 storage of the working matrix: the factor (BF16 values) against the
+    oracle's BF16-storage emulation, the FP64 solution, iteration counts; the
+    regenerated-A factor is bit-identical to the stored-A one."""
+    import torch
+    A, b = _system(hpl, n, 21)
+    A0, b0 = _np(A).copy(order="F"), _np(b).copy()
+    x, info, ws = hpl.mxp_solve(A, b, nb=nb, storage=hpl.STORAGE_BF16)
+    torch.cuda.synchronize()
+    rec = info.read()
+    assert rec["status"] == 0, rec
+    xg = _np(x)[:, 0]
+    assert orc.scaled_residual(A0, xg, b0) < 16
+    x64, _ = orc.solve(A0, b0)
+    assert np.abs(xg - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A0, np.inf)
+    F, Dinv = hpl.mxp_factor_views(ws, n, nb, storage=hpl.STORAGE_BF16)
+    assert F.dtype == torch.bfloat16
+    Fg = F.float().cpu().numpy().astype(np.float64)
+    Fo, Do, _ = orc.mxp_factor(A0, nb, orc.PREC_BF16, storage=orc.STORAGE_BF16)
+    off = ~np.eye(n, dtype=bool)
+    # BF16 rounding of values whose FP32 computations differ in their last bits
+    assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -7 * np.abs(Fo[off]).max()
+    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 2.0 ** -7 * np.abs(np.diag(Fo)).max()
+    # the first block is the BF16 rounding of A itself (one rounding from FP64)
+    k = min(nb, n)
+    first = np.array([orc.round_bf16_d(v) for v in A0[:k, 0]])
+    assert np.array_equal(Fg[:k, 0], first)
+    emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_BF16, refine=1, storage=orc.STORAGE_BF16)
+    assert abs(rec["iters"] - emu["iters"]) <= 2
+    # regenerated A, BF16 storage: the same factor bit for bit
+    x2, i2, ws2 = hpl.mxp_solve(None, b, nb=nb, seed=21, storage=hpl.STORAGE_BF16)
+    torch.cuda.synchronize()
+    F2, D2 = hpl.mxp_factor_views(ws2, n, nb, storage=hpl.STORAGE_BF16)
+    assert torch.equal(F2, F)
+    for k0 in range(0, n, k):              # only the kb x kb part of each inverse slot is defined
+        kb = min(k, n - k0)
+        assert torch.equal(D2[k0:k0 + kb, :kb], Dinv[k0:k0 + kb, :kb])
+    assert i2.read()["status"] == 0
+
+
+def test_mxp_bf16_storage_adjoint_and_rejects(hpl, orc):
+    """The adjoint from a BF16-stored factor against the oracle's FP64
+    adjoint; BF16 storage with FP8 or FP16 operands is refused."""
+    import ctypes
+    import torch
+    n, nb = 700, 128
+    A, b = _system(hpl, n, 22)
+    x, info, ws = hpl.mxp_solve(A, b, nb=nb, storage=hpl.STORAGE_BF16)
+    g = torch.from_numpy(np.random.default_rng(3).standard_normal(n)).cuda()
+    gB, gA, inf2 = hpl.lu_solve_backward(A, x, g, ws, nb=nb, storage=hpl.STORAGE_BF16)
+    torch.cuda.synchronize()
+    assert inf2.read()["status"] == 0
+    want_b, want_a = orc.adjoint(_np(A), _np(x).reshape(n, 1), _np(g).reshape(n, 1))
+    gb = _np(gB)[:, 0]
+    assert np.abs(gb - want_b[:, 0]).max() <= 1e-9 * np.abs(want_b).max()
+    lib = hpl.load()
+    for prec in (hpl.PREC_FP8_E4M3, hpl.PREC_FP16):
+        opts = hpl.make_opts(nb=nb, prec=prec, storage=hpl.STORAGE_BF16)
+        X = hpl.colmajor(n, 1)
+        st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, X.data_ptr(), n, ctypes.byref(opts),
+                           ws.data_ptr(), ws.numel(), hpl.Info().ptr(), torch.cuda.current_stream().cuda_stream)
+        assert st == 1
