@@ -90,3 +90,22 @@ def test_autotune_table_lookup():
     got = autotune.variants([40, 100, 300, 40, 200], [0, 0, 0, 1, 1], table, "GPU-X")
     assert list(got) == [1, 0, 0, 0, 1]
     assert list(autotune.variants([40, 300], [0, 1], {}, "GPU-X")) == [0, 0]
+
+
+def test_workspace_sizes_follow_the_options():
+    """Workspace queries are host code: BF16 storage halves the working matrix
+    of the mixed-precision solve; the tensor-core FP64 emulation adds its
+    slice buffers to the LU workspace; the pfact option does not change it."""
+    import ctypes as C
+    import paper_2604_09517_gb300 as hpl
+    lib = hpl.load()
+    n = 4096
+    o32 = hpl.make_opts(nb=512)
+    o16 = hpl.make_opts(nb=512, storage=hpl.STORAGE_BF16)
+    s32 = lib.mxp_workspace_size(n, 1, C.byref(o32))
+    s16 = lib.mxp_workspace_size(n, 1, C.byref(o16))
+    assert s32 - s16 >= 2 * n * n - 256 and s32 - s16 <= 2 * n * n + 256
+    base = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256)))
+    emu = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, fp64_emulation=1)))
+    coop = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, pfact=1)))
+    assert emu > base + 40 * n * n // 2 and coop == base
