@@ -471,7 +471,7 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, float* scr
     float* W = S.W;
     for (int e = threadIdx.x; e < n * n; e += THREADS) {
         int j = e / n, i = e % n;
-        W[(long long)j * n + i] = (float)S.A[(long long)j * S.lda + i];
+        W[(long long)j * n + i] = f64_to_f32_rn(S.A[(long long)j * S.lda + i]);   // integer pipe, not FP64
     }
     __syncthreads();
     int first_zero = 0;
@@ -485,9 +485,11 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, float* scr
         if (threadIdx.x == 0)
             for (int i = 0; i < kb; i++)
                 if (D[(long long)i * n + i] == 0.0f && !first_zero) first_zero = k0 + i + 1;
+        float* Ds = scratch;                  // D staged in shared memory for the products
+        for (int e = threadIdx.x; e < kb * kb; e += THREADS) Ds[e] = D[(long long)(e / kb) * n + e % kb];
         __syncthreads();
         for (int it = 0; it < 3; it++) {     // 3 steps: systems this small are only weakly dominant
-            gemm32(kb, kb, kb, D, n, X, NB, R, NB, 0, 1);               // R = D X
+            gemm32(kb, kb, kb, Ds, kb, X, NB, R, NB, 0, 1);             // R = D X
             __syncthreads();
             for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
                 int j = e / kb, i = e % kb;
@@ -507,14 +509,27 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, float* scr
             float* A21 = W + (long long)k0 * n + k0 + kb;
             float* A12 = W + (long long)(k0 + kb) * n + k0;
             float* A22 = W + (long long)(k0 + kb) * n + k0 + kb;
-            // L21 = A21 D^-1: read all of A21's rows before overwriting them
-            for (int r0 = 0; r0 < m; r0 += NB) {
-                const int rm = min(NB, m - r0);
-                gemm32(rm, kb, kb, A21 + r0, n, X, NB, T, NB, 0, 0);
+            // L21 = bf16(A21) bf16(D^-1), FP32 accumulation in increasing k (the
+            // order of gemm32): both operands rounded once into shared memory,
+            // then every entry from there (A21 is read entirely before it is
+            // overwritten, and no product waits on an L2 load)
+            {
+                float* Ar = scratch;              // Ar[q * m + i] = bf16(A21(i, q))
+                float* Xr = scratch + m * kb;     // Xr[j * kb + q] = bf16(D^-1(q, j))
+                for (int e = threadIdx.x; e < m * kb; e += THREADS) {
+                    const int q = e / m, i = e - q * m;
+                    Ar[e] = bfr(A21[(long long)q * n + i]);
+                }
+                for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
+                    const int j = e / kb, q = e - j * kb;
+                    Xr[e] = bfr(X[j * NB + q]);
+                }
                 __syncthreads();
-                for (int e = threadIdx.x; e < rm * kb; e += THREADS) {
-                    int j = e / rm, i = e % rm;
-                    A21[(long long)j * n + r0 + i] = T[j * NB + i];
+                for (int e = threadIdx.x; e < m * kb; e += THREADS) {
+                    const int j = e / m, i = e - j * m;
+                    float acc = 0.0f;
+                    for (int q = 0; q < kb; q++) acc = fmaf(Ar[q * m + i], Xr[j * kb + q], acc);
+                    A21[(long long)j * n + i] = acc;
                 }
                 __syncthreads();
             }
@@ -574,11 +589,18 @@ __device__ double resid64(const Sys& S, const double* x, const double* b, double
     for (int i = threadIdx.x; i < n; i += THREADS) {
         double s = 0.0, a = 0.0;
         if (sum_norm) {
+            // row sums of |a_ij| in FP32 from the truncated magnitudes (integer
+            // operations; the stopping test's norm, as in the large solve)
+            float af = 0.0f;
             for (int j = 0; j < n; j++) {
                 double v = S.A[(long long)j * S.lda + i];
                 s = fma(v, x[j], s);
-                a += fabs(v);
+                const unsigned long long u = (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffull;
+                const int ex = (int)(u >> 52) - 1023 + 127;
+                af += ex <= 0 ? 0.0f : ex >= 255 ? __int_as_float(0x7f800000) :
+                      __int_as_float((ex << 23) | (int)((u >> 29) & 0x7fffff));
             }
+            a = (double)af;
         } else {
             for (int j = 0; j < n; j++) s = fma(S.A[(long long)j * S.lda + i], x[j], s);
         }

@@ -195,6 +195,23 @@ __device__ __forceinline__ __nv_bfloat16 f64_to_bf16_rn(double x) {
     if (nan) h = (unsigned short)(sgn | 0x7fc0u);
     return __ushort_as_bfloat16(h);
 }
+// FP64 -> FP32, round to nearest even, by integer operations (as
+// f64_to_bf16_rn, 23 fraction bits kept); values below FP32's normal range
+// flush to a signed zero.
+__device__ __forceinline__ float f64_to_f32_rn(double x) {
+    const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+    const unsigned sgn = (unsigned)(u >> 63) << 31;
+    unsigned long long a = u & 0x7fffffffffffffffull;
+    const bool nan = a > 0x7ff0000000000000ull;
+    a += (1ull << 28) - 1 + ((a >> 29) & 1);
+    const int e = (int)(a >> 52) - 1023 + 127;
+    unsigned h = sgn | ((unsigned)e << 23) | (unsigned)((a >> 29) & 0x7fffff);
+    if (e >= 255) h = sgn | 0x7f800000u;
+    if (e <= 0) h = sgn;
+    if (nan) h = sgn | 0x7fc00000u;
+    return __uint_as_float(h);
+}
+
 __device__ __forceinline__ float st_f64(float* p, double a) {
     const float v = (float)a;
     *p = v;
