@@ -262,7 +262,7 @@ def test_mxp_fp16_variant(hpl, orc, n, nb):
     assert abs(rec["iters"] - emu["iters"]) <= 2
 
 
-@pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256), (2560, 256), (300, 100)])
+@pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256), (2560, 256), (300, 100), (301, 64)])
 def test_mxp_bf16_storage(hpl, orc, n, nb):
     """BF16 storage of the working matrix: the factor (BF16 values) against the
     oracle's BF16-storage emulation, the FP64 solution, iteration counts; the
