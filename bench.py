@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--mxp-n", type=int, default=98304)
     ap.add_argument("--mxp-nb", type=int, default=3072)
     ap.add_argument("--mxp-fp8-nb", type=int, default=4096)
+    ap.add_argument("--mxp-ns-iters", type=int, default=1,
+                    help="Newton-Schulz steps per diagonal block in the n = 98304 solves (library default 2)")
     ap.add_argument("--mxp-large-n", type=int, default=0,
                     help="also time one regenerated-A, BF16-storage solve of this size (0: skip)")
     return ap.parse_args()
@@ -573,7 +575,8 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
     info = hpl.Info(dev)
     ws = None
     for _ in range(n_warm):
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage,
+                                        ns_iters=a.mxp_ns_iters)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
     hpl.set_phase_timing(True)
@@ -585,7 +588,8 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
         e1 = torch.cuda.Event(enable_timing=True)
         l0 = hpl.launch_count()
         e0.record(stream)
-        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage)
+        X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage,
+                                        ns_iters=a.mxp_ns_iters)
         e1.record(stream)
         launches += hpl.launch_count() - l0
         torch.cuda.synchronize(dev)
@@ -617,7 +621,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
         extra["cpu_oracle_basis"] = f"oracle FP64 getrf+getrs at n={sn} x (n/{sn})^3"
     return {**extra, "workload": f"hpl_mxp_{tag}{stag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
             "ms_per_step": total_ms / len(step_ms), "steps": n_steps, "warmup": n_warm,
-            "storage": "bf16" if storage else "fp32",
+            "storage": "bf16" if storage else "fp32", "ns_iters": a.mxp_ns_iters,
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
             "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,

@@ -148,9 +148,11 @@ def colmajor(m: int, n: int, dtype=torch.float64, device="cuda", ld: int | None 
 
 def make_opts(nb: int = 0, lookahead: int = 1, prec: int = PREC_BF16, refine: int = REFINE_GMRES,
               max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0, timeout_ns: int = 0,
-              fp64_emulation: int = 0, pfact: int = 0, storage: int = STORAGE_FP32) -> Opts:
+              fp64_emulation: int = 0, pfact: int = 0, storage: int = STORAGE_FP32, ns_iters: int = 0) -> Opts:
     o = Opts()
     load().hpl_default_opts(ctypes.byref(o))
+    if ns_iters:
+        o.ns_iters = ns_iters
     o.nb, o.lookahead, o.prec, o.refine = nb, lookahead, prec, refine
     o.fp64_emulation, o.pfact, o.storage = fp64_emulation, pfact, storage
     o.max_iter, o.gmres_m, o.tol = max_iter, gmres_m, tol
@@ -242,7 +244,8 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
 
 def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
-              info: Info | None = None, prec: int = PREC_BF16, seed: int = 0, storage: int = STORAGE_FP32):
+              info: Info | None = None, prec: int = PREC_BF16, seed: int = 0, storage: int = STORAGE_FP32,
+              ns_iters: int = 0):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
 
     A = None solves with the dominant generated matrix of `seed` without storing
@@ -260,7 +263,8 @@ def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: i
         Bc.copy_(Bm)
         Bm = Bc
     nrhs = Bm.shape[1]
-    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec, storage=storage)
+    opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec, storage=storage,
+                     ns_iters=ns_iters)
     if X is None:
         X = colmajor(n, nrhs, device=dev)
     Xm = X.view(n, 1) if X.dim() == 1 else X
