@@ -15,6 +15,9 @@
 namespace hplgb {
 
 constexpr int kResChunks = 16;
+#ifndef HPLGB_REGEN_I2F
+#define HPLGB_REGEN_I2F 1
+#endif
 
 __host__ __device__ __forceinline__ uint64_t res_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -126,6 +129,26 @@ __global__ void __launch_bounds__(256) k_res_partial(int64_t n, const double* __
             }
             r += r1;
         }
+    } else if (dominant && diag && want_norm == 0 && HPLGB_REGEN_I2F) {
+        // the plain product with the integer t = a * 2^53 converted by the
+        // hardware (exact, |t| <= 2^52): sum t_ij x_j, then one exact scaling by
+        // 2^-53 per row; every intermediate is the a_ij version times 2^53, so
+        // the rounding is the same
+        const uint64_t step = (uint64_t)n * 0x9E3779B97F4A7C15ull;
+        uint64_t z = key + ((uint64_t)j0 * (uint64_t)n + (uint64_t)i + 1) * 0x9E3779B97F4A7C15ull;
+        double r1 = 0.0;
+        int64_t j = j0;
+        for (; j + 1 < j1; j += 2, z += 2 * step) {
+            const long long t0 = (long long)(res_mix(z) >> 11) - (1LL << 52);
+            const long long t1 = (long long)(res_mix(z + step) >> 11) - (1LL << 52);
+            r = fma(j == i ? 0.0 : (double)t0, x[j], r);
+            r1 = fma(j + 1 == i ? 0.0 : (double)t1, x[j + 1], r1);
+        }
+        if (j < j1) {
+            const long long t0 = (long long)(res_mix(z) >> 11) - (1LL << 52);
+            r = fma(j == i ? 0.0 : (double)t0, x[j], r);
+        }
+        r = (r + r1) * 0x1p-53;
     } else if (dominant && diag && want_norm != 2) {
         // diagonal known: plain regenerated product over the off-diagonal
         // entries, one FP64 instruction (the FMA) per entry
