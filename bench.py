@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-emulation", action="store_true", help="skip the tensor-core FP64 emulation line")
     ap.add_argument("--batched-count", type=int, default=4096)
     ap.add_argument("--mxp-n", type=int, default=98304)
-    ap.add_argument("--mxp-nb", type=int, default=3072)
+    ap.add_argument("--mxp-nb", type=int, default=4096)
     ap.add_argument("--mxp-fp8-nb", type=int, default=4096)
     ap.add_argument("--mxp-ns-iters", type=int, default=1,
                     help="Newton-Schulz steps per diagonal block in the n = 98304 solves (library default 2)")
