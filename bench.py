@@ -1,6 +1,6 @@
 #!/usr/bin/env python
 """Benchmark: HPL FP64 LU solve (n=32768, NB=256, depth-1 look-ahead) on GB300,
-with the HPL-MxP mixed-precision solve (n=98304, NB=3072) reported beside it.
+with the HPL-MxP mixed-precision solve (n=98304, NB=4096) reported beside it.
 
 One step = one full solve of a fresh seeded system: lu_factor (PFACT, SWAP,
 DTRSM, DGEMM update, look-ahead) + lu_solve, all in the library's CUDA
@@ -555,7 +555,7 @@ def run_small(a, d: Dist, dev):
 
 def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=0, n=None, steps=None,
             warmup=None):
-    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 3072):
+    """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 4096):
     block-LU factor on the tcgen05 tensor cores (BF16 update; FP8 E4M3 with
     prec = 1, NB = 4096; scaled FP16 with prec = 2) + FP64 GMRES refinement.
     regen: the library regenerates A from the seed instead of reading a
