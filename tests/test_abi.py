@@ -70,6 +70,15 @@ def test_invalid_arguments_rejected_before_any_launch(lib):
     assert lib.lu_factor(-1, 8, 1, 8, None, 8, 1 << 20, 8, None) == 1
     assert lib.lu_factor(10, 8, 5, 8, None, 8, 1 << 20, 8, None) == 1
     assert lib.lu_factor(10, 8, 10, 8, None, 8, 16, 8, None) == 6          # workspace too small
+    import paper_2604_09517_gb300 as hpl
+    bad_pfact = hpl.make_opts(nb=64, pfact=2)
+    assert lib.lu_factor(10, 8, 10, 8, ctypes.byref(bad_pfact), 8, 1 << 20, 8, None) == 1
+    lib.mxp_solve.argtypes = [ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64,
+                              ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p,
+                              ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p]
+    for o in (hpl.make_opts(nb=64, storage=2), hpl.make_opts(nb=64, prec=hpl.PREC_FP8_E4M3, storage=1),
+              hpl.make_opts(nb=64, prec=hpl.PREC_FP16, storage=1), hpl.make_opts(nb=64, prec=3)):
+        assert lib.mxp_solve(10, 1, 8, 10, 0, 8, 10, 8, 10, ctypes.byref(o), 8, 1 << 30, 8, None) == 1
 
 
 def test_batch_sizes_host_function_matches_oracle(lib, orc):
