@@ -39,10 +39,14 @@ MAX_SM_MHZ = 2070.0
 # traffic of an update launch scales with its C tile, i.e. with flops at fixed k.
 DGEMM_DRAM_BYTES_PER_FLOP = 959.8e6 / 31.21e9
 # Same for the tcgen05 trailing update of the mixed-precision solve, from one
-# ncu capture each of a step-0 update at n = 24576 (BF16: m = 21504, k = 3072,
-# 5.264 GB for 2.841 TFLOP; FP8: m = 20480, k = 4096, 3.820 GB for 3.436 TFLOP).
-# FP16 (the BF16 kernel with F16 inputs): not captured, reported as null.
-MXP_DRAM_BYTES_PER_FLOP = {0: 5.264e9 / 2.841e12, 1: 3.820e9 / 3.436e12, 2: None}
+# ncu capture each of the step-0 update at n = 24576, NB = 4096 (m = 20480,
+# k = 4096, 3.436 TFLOP): key (prec, storage); BF16 5.199 GB, FP8 3.820 GB,
+# FP16 5.193 GB, BF16 operands with BF16 storage 3.512 GB. At fixed k a
+# launch's traffic scales with its C tile, i.e. with its flops; captured at
+# the bench's panel width only, so another width reports null.
+MXP_DRAM_BYTES_PER_FLOP = {(0, 0): 5.199e9 / 3.436e12, (1, 0): 3.820e9 / 3.436e12, (2, 0): 5.193e9 / 3.436e12,
+                           (0, 1): 3.512e9 / 3.436e12}
+MXP_TRAFFIC_NB = 4096
 
 
 def flops(n: int) -> float:
@@ -631,8 +635,9 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
                       + ("; regenerated from the seed, never stored" if regen else "; stored FP64"),
             "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak if achieved else None,
-                         "traffic": (MXP_DRAM_BYTES_PER_FLOP[prec] * upd_flops / upd_cnt
-                                     if upd_cnt and MXP_DRAM_BYTES_PER_FLOP[prec] else None),
+                         "traffic": (MXP_DRAM_BYTES_PER_FLOP[(prec, storage)] * upd_flops / upd_cnt
+                                     if upd_cnt and nb == MXP_TRAFFIC_NB and (prec, storage) in MXP_DRAM_BYTES_PER_FLOP
+                                     else None),
                          "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
                          "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec == 1 else ""),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
