@@ -35,9 +35,10 @@ FP64_FLOP_PER_CLK_PER_SM = 4.0      # 2 DFMA/clk/SM: nominal 1.25 TF/s / (152 SM
 NUM_SMS = 152
 MAX_SM_MHZ = 2070.0
 # DRAM bytes (read + write) per flop of the DFMA update kernel, from one ncu
-# capture of an m=7936, n=7680, k=256 launch (959.8 MB for 31.21 GFLOP); the
-# traffic of an update launch scales with its C tile, i.e. with flops at fixed k.
-DGEMM_DRAM_BYTES_PER_FLOP = 959.8e6 / 31.21e9
+# capture of an m=7936, n=7680, k=256 launch of k_dgemm_sub<64> (956.9 MB for
+# 31.21 GFLOP); the traffic of an update launch scales with its C tile, i.e.
+# with flops at fixed k.
+DGEMM_DRAM_BYTES_PER_FLOP = 956.9e6 / 31.21e9
 # Same for the tcgen05 trailing update of the mixed-precision solve, from one
 # ncu capture each of the step-0 update at n = 24576, NB = 4096 (m = 20480,
 # k = 4096, 3.436 TFLOP): key (prec, storage); BF16 5.199 GB, FP8 3.820 GB,
