@@ -413,7 +413,7 @@ def test_mxp_factor_diagonal_matrix_exact(orc):
 
 
 @pytest.mark.parametrize("refine", [0, 1])
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_mxp_solve_reaches_fp64_solution(orc, refine, prec):
     n, nb = 256, 64
     A = orc.generate(6, orc.STREAM_A, n, n, dominant=True)
@@ -593,3 +593,16 @@ def test_mxp_factor_bf16_storage(orc):
     assert out["status"] == 0 and orc.scaled_residual(A, out["x"], b) < 16
     x64, _ = orc.solve(A, b)
     assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 2 * 16 * n * 2.0 ** -53 * np.linalg.cond(A, np.inf)
+
+
+def test_fp16_factor_needs_no_more_corrections_than_bf16(orc):
+    """Classic refinement contracts the error by about the factorization's
+    relative accuracy per step, so the more accurate FP16 factor (8x smaller
+    error, pinned above) never needs more corrections than the BF16 one."""
+    n, nb = 384, 64
+    A = orc.generate(8, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(8, orc.STREAM_B, n, 1)[:, 0]
+    it16 = orc.mxp_solve(A, b, nb, prec=orc.PREC_FP16, refine=0)
+    itbf = orc.mxp_solve(A, b, nb, prec=orc.PREC_BF16, refine=0)
+    assert it16["status"] == 0 and itbf["status"] == 0
+    assert it16["iters"] <= itbf["iters"]
