@@ -123,29 +123,6 @@ __device__ __forceinline__ double gen_value(uint64_t h) {
         ((unsigned long long)(t < 0) << 63) | ((unsigned long long)(p - 53 + 1023) << 52) | mant;
     return __longlong_as_double((long long)bits);
 }
-// The same value rounded to the nearest FP32 (ties to even), again by integer
-// operations: identical to rounding the FP64 value once.
-__device__ __forceinline__ float gen_value_f32(uint64_t h) {
-    const long long t = (long long)(h >> 11) - (1LL << 52);
-    if (t == 0) return 0.0f;
-    const unsigned long long u = t < 0 ? (unsigned long long)(-t) : (unsigned long long)t;
-    int p = 63 - __clzll((long long)u);
-    unsigned long long q;
-    if (p <= 23) {
-        q = u << (23 - p);
-    } else {
-        const int sh = p - 23;
-        q = u >> sh;
-        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        q += (rem > half || (rem == half && (q & 1))) ? 1 : 0;
-        if (q == (1ull << 24)) {
-            q >>= 1;
-            p++;
-        }
-    }
-    const unsigned bits = ((unsigned)(t < 0) << 31) | ((unsigned)(p - 53 + 127) << 23) | ((unsigned)q & 0x7fffffu);
-    return __uint_as_float(bits);
-}
 
 // Magnitude key of a double for the pivot search: for |v| not NaN the IEEE
 // bit pattern orders like the value, so the comparison runs on the integer

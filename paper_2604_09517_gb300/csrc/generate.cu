@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) k_dominant_diag(int64_t n, double* __rest
 __device__ __forceinline__ float gen_store(float* p, uint64_t h) {
     // t = (h >> 11) - 2^52 converted by the hardware (one rounding to nearest
     // even of the integer), then the exact scaling by 2^-53: the FP32 rounding
-    // of the FP64 value, like gen_value_f32, in fewer instructions
+    // of the FP64 value (t 2^-53) in one step
     const long long t = (long long)(h >> 11) - (1LL << 52);
     const float v = __ll2float_rn(t) * 0x1p-53f;
     *p = v;
