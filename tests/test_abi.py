@@ -118,3 +118,16 @@ def test_workspace_sizes_follow_the_options():
     emu = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, fp64_emulation=1)))
     coop = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, pfact=1)))
     assert emu > base + 40 * n * n // 2 and coop == base
+
+
+def test_profiles_are_short_text_with_their_command():
+    """profiles/ holds short text summaries, each naming the command that made
+    it and running only committed files (no scratch paths)."""
+    names = sorted(glob.glob(os.path.join(ROOT, "profiles", "*")))
+    assert names
+    for p in names:
+        assert p.endswith((".txt", ".md")), p
+        text = open(p).read()
+        assert len(text) < 16384, p
+        assert "Command" in text and "ncu" in text, p
+        assert "_work" not in text and "gpurun" not in text, p
