@@ -241,7 +241,9 @@ def time_oracle_batched(seed: int, count: int, sample: int):
 def run_reference(a, d: Dist):
     if d.rank != 0:
         return
-    n = 4096
+    # the same bounded sample as cpu_baseline: one n = 8192 system per step
+    # (about 12 s on 16 Grace cores), so both report the oracle at one rate
+    n = a.cpu_sample_n
     for _ in range(a.warmup):
         time_oracle(n, a.seed)
     times = []
@@ -252,11 +254,12 @@ def run_reference(a, d: Dist):
         times.append(dt)
     total = sum(times)
     value = flops(n) * len(times) / total / 1e12
-    sample = f"oracle getrf+getrs (unblocked, OpenMP over columns) at n={n} per step"
+    sample = (f"oracle getrf+getrs (unblocked FP64, OpenMP over columns) of one n={n} system per step, "
+              f"standing in for the n={a.n} workload of config (rate in TFLOP/s at the sample size)")
     line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": a.gpus, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": 1e3 * total / len(times), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(a), "impl": "reference",
+            "config": {**workload_config(a), "reference_sample_n": n}, "impl": "reference",
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "scaled_residual": sr}

@@ -149,8 +149,11 @@ int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* 
  * scratch lu_factor needs comes from one fixed device array inside the
  * library (lu_factor_noalloc_max_scratch() bytes, 320 KiB, enough for any
  * NB <= 512), held by every GPU that loads the library until the process
- * exits. A panel width whose scratch would exceed it returns HPL_ERR_NOMEM
- * (with a message in hplgb_last_error). The first call on a device looks up
+ * exits. opts.fp64_emulation is not available here (its scratch grows with
+ * n): it returns HPL_ERR_INVALID with a message naming the option. Options
+ * lu_factor refuses return HPL_ERR_INVALID before any size test;
+ * HPL_ERR_NOMEM is kept for valid options whose scratch would exceed the
+ * array (none with NB <= 512 today). Messages are in hplgb_last_error. The first call on a device looks up
  * the array's device address (cudaGetSymbolAddress) and caches it: make that
  * first call before any stream capture. The array is shared by all calls on a
  * device and cleared by each call on its stream; calls whose GPU work

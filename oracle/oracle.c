@@ -28,9 +28,15 @@
  *   orc_getrf / orc_getrs : exact rational elimination (n <= 6), Cramer's rule,
  *       LAPACK getrf via scipy, closed forms, ||PA-LU|| invariant.
  *   orc_scaled_residual(_gen) : closed forms and a hand-computed case.
- *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine).
+ *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine),
+ *       normals, ties, FP32 subnormals and the overflow threshold.
  *   orc_round_fp16 : NumPy's float16 cast (library routine).
  *   orc_mxp_factor : FP32 mode equals unpivoted LU; BF16 mode error bound.
+ *   orc_mxp_lu_plain : a hand-worked 4 x 4 case in exact rationals for every
+ *       operand precision (tests/golden/mxp_2step_by_hand.txt); FP32 mode
+ *       against exact rational unpivoted elimination within FP32's bound and
+ *       against LAPACK's LU (no interchanges on dominant matrices); the
+ *       factor's independence of the panel width in FP32 mode.
  *   orc_mxp_solve : converged x equals the FP64 LU solution; iteration
  *       behaviour with an exact preconditioner (one step).
  *   orc_adjoint : central finite differences and torch.linalg.solve autograd.
@@ -348,28 +354,31 @@ void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU
  *     prec = 3: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
  *     mode.                                                                  */
 
-/* BF16 round-to-nearest-even of a float: keep 8 significant bits. Written from
- * the format definition (1 sign, 8 exponent, 7 stored fraction bits). */
-float orc_round_bf16(float x) {
-    if (x == 0.0f || !isfinite(x)) return x;
-    int e;
-    double f = frexp((double)x, &e);            /* x = f * 2^e, 0.5 <= |f| < 1 */
-    double q = nearbyint(ldexp(f, 8));          /* 8 significant bits, RNE */
-    double r = ldexp(q, e - 8);
-    if (fabs(r) > 3.3895313892515355e38) r = copysign(INFINITY, r); /* overflow */
-    return (float)r;
+/* BF16 round-to-nearest-even, written from the format definition (1 sign,
+ * 8 exponent, 7 stored fraction bits; the exponent range is FP32's). Normal
+ * values keep 8 significant bits. Below 2^-126 (BF16's smallest normal) the
+ * grid is the fixed subnormal spacing 2^-133, so fewer bits survive there.
+ * Results above the largest finite BF16 (0x1.FEp127) overflow to infinity.
+ * Applied to a double, this is one rounding (no intermediate FP32 rounding). */
+static double orc_bf16_rne(double x) {
+    if (x == 0.0 || !isfinite(x)) return x;
+    double r;
+    if (fabs(x) < 0x1p-126) {
+        r = ldexp(nearbyint(ldexp(x, 133)), -133);  /* multiples of 2^-133, RNE */
+    } else {
+        int e;
+        double f = frexp(x, &e);                    /* x = f * 2^e, 0.5 <= |f| < 1 */
+        r = ldexp(nearbyint(ldexp(f, 8)), e - 8);   /* 8 significant bits, RNE */
+    }
+    if (fabs(r) > 0x1.FEp127) r = copysign(INFINITY, r);
+    return r;
 }
 
-/* The same rounding applied once to a double (no intermediate FP32 rounding;
- * the working copy of a BF16-stored factorization is taken from FP64 A). The
- * inputs here are far inside FP32's exponent range. */
-float orc_round_bf16_d(double x) {
-    if (x == 0.0 || !isfinite(x)) return (float)x;
-    int e;
-    double f = frexp(x, &e);
-    double q = nearbyint(ldexp(f, 8));
-    return (float)ldexp(q, e - 8);
-}
+float orc_round_bf16(float x) { return (float)orc_bf16_rne((double)x); }
+
+/* The same rounding applied once to a double (the working copy of a
+ * BF16-stored factorization is taken from FP64 A). */
+float orc_round_bf16_d(double x) { return (float)orc_bf16_rne(x); }
 
 /* BF16 working copy of an FP64 matrix (values stored as float). */
 void orc_to_bf16_storage(int64_t m, int64_t n, const double* A, int64_t lda, float* F, int64_t ldf) {
@@ -594,6 +603,83 @@ int64_t orc_mxp_factor(int64_t n, int64_t nb, int prec, int ns_iters, int storag
     return info;
 }
 
+/* HPL-MxP factor as a plain right-looking LU without pivoting, in the order
+ * the paper states it (Sec. III-A.2: factorization and trailing updates in
+ * low precision, no pivoting; Table I: BF16 + FP32 on Aurora). This is the
+ * independent reference for the GPU's block factor: it shares nothing with
+ * that design (no block inverse, no Newton-Schulz). Per step k0 of width kb:
+ *   1. panel: FP32 unpivoted elimination of columns k0..k0+kb over rows
+ *      k0..n-1 (true division by the pivot, rank-1 updates inside the panel);
+ *   2. U12 = L11^-1 A12 by FP32 forward substitution with the unit lower L11;
+ *   3. A22 -= L21 U12 with L21 and U12 rounded to the low precision as
+ *      operands (prec as in orc_round_operand: 0 BF16, 1 FP8 E4M3 and 2 FP16
+ *      with their power-of-two row / column scales, 3 none), products summed
+ *      in FP32 in increasing k, the sum subtracted from the FP32 A22.
+ * A (n x n, FP32 working copy) is overwritten by L (unit lower, strictly
+ * below the diagonal) and U (on and above it); U12 is stored as computed in
+ * FP32 (only the update's operands are rounded). A zero pivot records
+ * info = its 1-based index (first occurrence); its column is left unscaled. */
+int64_t orc_mxp_lu_plain(int64_t n, int64_t nb, int prec, float* A, int64_t lda) {
+    int64_t info = 0;
+    for (int64_t k0 = 0; k0 < n; k0 += nb) {
+        int64_t kb = n - k0 < nb ? n - k0 : nb;
+        int64_t k1 = k0 + kb;
+        /* 1. panel */
+        for (int64_t c = k0; c < k1; c++) {
+            float* colc = A + c * lda;
+            float piv = colc[c];
+            if (piv == 0.0f) {
+                if (!info) info = c + 1;
+                continue;
+            }
+            for (int64_t i = c + 1; i < n; i++) colc[i] = colc[i] / piv;
+            for (int64_t j = c + 1; j < k1; j++) {
+                float* colj = A + j * lda;
+                float ucj = colj[c];
+                for (int64_t i = c + 1; i < n; i++) colj[i] = colj[i] - colc[i] * ucj;
+            }
+        }
+        int64_t m = n - k1;
+        if (m == 0) break;
+        /* 2. U12 = L11^-1 A12 */
+#pragma omp parallel for schedule(static) if (m > 256)
+        for (int64_t j = k1; j < n; j++) {
+            float* colj = A + j * lda;
+            for (int64_t c = k0; c < k1; c++) {
+                float ucj = colj[c];
+                for (int64_t i = c + 1; i < k1; i++) colj[i] = colj[i] - A[c * lda + i] * ucj;
+            }
+        }
+        /* 3. A22 -= round(L21) round(U12) */
+        float* t21 = (float*)malloc(sizeof(float) * m * kb);
+        float* t12 = (float*)malloc(sizeof(float) * kb * m);
+        for (int64_t j = 0; j < kb; j++) memcpy(t21 + j * m, A + (k0 + j) * lda + k1, sizeof(float) * m);
+        for (int64_t j = 0; j < m; j++) memcpy(t12 + j * kb, A + (k1 + j) * lda + k0, sizeof(float) * kb);
+        orc_round_operand(prec, t21, m, kb, m, 0);      /* A operand: k along columns */
+        orc_round_operand(prec, t12, kb, m, kb, 1);     /* B operand: k along rows    */
+        orc_gemm32(m, m, kb, t21, m, t12, kb, A + k1 * lda + k1, lda, 1);
+        free(t21);
+        free(t12);
+    }
+    return info;
+}
+
+/* Preconditioner M^-1 v with M = L U the plain factor above, in FP32:
+ * y = fl32(v); forward substitution by columns with the unit lower L (for
+ * j = 0, 1, ...: y_i -= L_ij y_j for i > j), backward substitution by columns
+ * with U (for j = n-1 down to 0: y_j /= U_jj, then y_i -= U_ij y_j for i < j).
+ * Widened to FP64. */
+static void orc_precond_plain(int64_t n, const float* F, int64_t ldf, const double* v, double* out, float* y) {
+    for (int64_t i = 0; i < n; i++) y[i] = (float)v[i];
+    for (int64_t j = 0; j < n; j++)
+        for (int64_t i = j + 1; i < n; i++) y[i] = y[i] - F[j * ldf + i] * y[j];
+    for (int64_t j = n - 1; j >= 0; j--) {
+        y[j] = y[j] / F[j * ldf + j];
+        for (int64_t i = 0; i < j; i++) y[i] = y[i] - F[j * ldf + i] * y[j];
+    }
+    for (int64_t i = 0; i < n; i++) out[i] = (double)y[i];
+}
+
 /* Preconditioner M^-1 v with M = L U the block factor, in FP32: y = fl32(v);
  * forward with the block unit lower L (y_i -= sum_j L_ij y_j over each block
  * column, in order); backward over the block rows from the last: x_k =
@@ -656,10 +742,42 @@ static double orc_dot(int64_t n, const double* a, const double* b) {
  * iters = corrections applied, inner = preconditioner applications inside
  * GMRES (equal to iters for refine = 0). hist (optional, max_iter+1) receives
  * the scaled residual before each correction. */
+/* The preconditioner in use: the block factor (Dinv != NULL) or the plain one. */
+typedef struct {
+    int64_t n, nb;
+    const float* F;
+    int64_t ldf;
+    const float* Dinv;
+} orc_prec_t;
+
+static void orc_apply_prec(const orc_prec_t* P, const double* v, double* out, float* tmp) {
+    if (P->Dinv) orc_precond(P->n, P->nb, P->F, P->ldf, P->Dinv, v, out, tmp);
+    else orc_precond_plain(P->n, P->F, P->ldf, v, out, tmp);
+}
+
+static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_prec_t* P,
+                           const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
+                           int* iters, int* inner, double* final_sr, double* hist);
+
 int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const float* F, int64_t ldf,
                    const float* Dinv,
                    const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
                    int* iters, int* inner, double* final_sr, double* hist) {
+    orc_prec_t P = {n, nb, F, ldf, Dinv};
+    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, tol, iters, inner, final_sr, hist);
+}
+
+/* The same refinement with the plain factor of orc_mxp_lu_plain as M. */
+int orc_mxp_refine_plain(int64_t n, const double* A, int64_t lda, const float* F, int64_t ldf,
+                         const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
+                         int* iters, int* inner, double* final_sr, double* hist) {
+    orc_prec_t P = {n, n, F, ldf, NULL};
+    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, tol, iters, inner, final_sr, hist);
+}
+
+static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_prec_t* P,
+                           const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
+                           int* iters, int* inner, double* final_sr, double* hist) {
     double eps = 0x1p-53;
     double anorm = 0.0;
     for (int64_t i = 0; i < n; i++) {
@@ -679,7 +797,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const fl
     double* sn = (double*)malloc(sizeof(double) * m);
     double* g = (double*)malloc(sizeof(double) * (m + 1));
     double* y = (double*)malloc(sizeof(double) * m);
-    orc_precond(n, nb, F, ldf, Dinv, b, x, tmp);
+    orc_apply_prec(P, b, x, tmp);
     int it = 0, inn = 0, status = 4;
     double sr = INFINITY;
     for (;;) {
@@ -690,7 +808,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const fl
         if (sr < tol) { status = 0; break; }
         if (it >= max_iter) break;
         if (refine == 0) {
-            orc_precond(n, nb, F, ldf, Dinv, r, d, tmp);
+            orc_apply_prec(P, r, d, tmp);
             inn++;
         } else {
             double beta = sqrt(orc_dot(n, r, r));
@@ -702,7 +820,7 @@ int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const fl
                 double* vj = V + (int64_t)j * n;
                 double* zj = Z + (int64_t)j * n;
                 double* w = V + (int64_t)(j + 1) * n;
-                orc_precond(n, nb, F, ldf, Dinv, vj, zj, tmp);
+                orc_apply_prec(P, vj, zj, tmp);
                 inn++;
                 orc_matvec(n, A, lda, zj, w);
                 for (int i = 0; i <= j; i++) {

@@ -899,6 +899,9 @@ struct Mxp {
             }
             k_copy_block32<<<grid_for(kb * kb), 256, 0, s>>>(w.X, kb, kb, kb, w.Dinv + k0, n);
             HPL_LAUNCH_CHECK();
+            if (kb < nb)   // a short last block: the rest of its slot holds zeros, not stale memory
+                HPL_CUDA_TRY(cudaMemset2DAsync(w.Dinv + kb * n + k0, sizeof(float) * n, 0,
+                                               sizeof(float) * (size_t)(n - k0), (size_t)(nb - kb), s));
             if (m2 > 0) {
                 FT* A21 = F() + k0 * ldf + k0 + kb;
                 FT* A12 = F() + (k0 + kb) * ldf + k0;

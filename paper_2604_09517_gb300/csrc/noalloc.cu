@@ -20,7 +20,7 @@
 
 #include "common.cuh"
 
-static constexpr size_t kNoAllocScratchBytes = 320 * 1024;   // enough for any NB <= 512
+static constexpr size_t kNoAllocScratchBytes = 320 * 1024;   // enough for any NB <= 512 (FP64 update)
 
 static __device__ __align__(256) unsigned char g_lu_scratch[kNoAllocScratchBytes];
 
@@ -49,10 +49,25 @@ extern "C" size_t lu_factor_noalloc_max_scratch(void) { return kNoAllocScratchBy
 
 extern "C" int lu_factor_noalloc(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hpl_opts* opts,
                                  hpl_info* info, void* stream) {
+    // Options lu_factor itself refuses get its HPL_ERR_INVALID here too, before
+    // any size test, so HPL_ERR_NOMEM only ever means "valid options whose
+    // scratch does not fit the array".
+    hplgb::Opts o = hplgb::resolve_opts(opts, 256);
+    if (o.nb < 1 || o.nb > 512 || o.pfact < 0 || o.pfact > 1 || o.fp64_emulation < 0 || o.fp64_emulation > 1) {
+        hplgb_internal_set_message("lu_factor_noalloc: invalid options (NB must be 1..512, pfact 0 or 1)");
+        return HPL_ERR_INVALID;
+    }
+    // The FP64-emulated update keeps sliced copies of L21 and U12 whose size
+    // grows with n, which no fixed array can hold for every n: refused.
+    if (o.fp64_emulation) {
+        hplgb_internal_set_message("lu_factor_noalloc: opts.fp64_emulation is not available without a "
+                                   "workspace (its scratch grows with n); use lu_factor");
+        return HPL_ERR_INVALID;
+    }
     size_t need = lu_factor_workspace_size(n, opts);
     if (need > kNoAllocScratchBytes) {
-        hplgb_internal_set_message("lu_factor_noalloc: the panel width needs more scratch than the fixed "
-                                   "device array holds (NB must be <= 512)");
+        hplgb_internal_set_message("lu_factor_noalloc: these options need more scratch than the fixed "
+                                   "device array holds");
         return HPL_ERR_NOMEM;
     }
     void* scratch = nullptr;

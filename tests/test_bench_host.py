@@ -62,7 +62,7 @@ def test_step_model_recovers_rates_and_predicts_the_model():
 def test_reference_arm_prints_the_contract_line():
     env = dict(os.environ, CUDA_VISIBLE_DEVICES="")
     r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
-                        "--warmup", "0"], capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
+                        "--warmup", "0", "--cpu-sample-n", "1024"], capture_output=True, text=True, timeout=600, cwd=ROOT, env=env)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
     sys.path.insert(0, ROOT)
@@ -73,3 +73,4 @@ def test_reference_arm_prints_the_contract_line():
     assert line["cpu_baseline"]["value"] == line["value"]
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["steps"] == 1 and line["warmup"] == 0 and line["config"]["workload"]
+    assert line["config"]["reference_sample_n"] == 1024 and "n=1024" in line["cpu_baseline"]["sample"]

@@ -11,38 +11,29 @@ def _np(t):
     return t.detach().cpu().numpy()
 
 
-def test_adjoint_matches_finite_differences_n64(hpl, orc):
+@pytest.mark.parametrize("nrhs", [3, 1])
+def test_adjoint_matches_finite_differences_n64(hpl, orc, nrhs):
+    """The differentiable-solve check at n = 64: every entry of the GPU's
+    grad_A and grad_B (through the autograd layer) within 1e-6 relative of
+    central finite differences in FP64 (numpy's LAPACK solve on the CPU), with
+    no absolute floor."""
     import torch
-    n, nrhs, nb = 64, 3, 32
+    from _parity import fd_gradients, max_rel_err
+    n, nb = 64, 32
     A = hpl.generate(21, hpl.STREAM_A, n, n, hpl.GEN_DIAG_DOMINANT)
     B = hpl.generate(21, hpl.STREAM_B, n, nrhs)
-    G = torch.from_numpy(np.random.default_rng(5).standard_normal((n, nrhs))).cuda()
+    Gn = np.random.default_rng(5).standard_normal((n, nrhs))
+    G = torch.from_numpy(Gn).cuda()
     A_ = A.clone().requires_grad_(True)
     B_ = B.clone().requires_grad_(True)
     X = hpl.solve(A_, B_, nb=nb)
     (X * G).sum().backward()
+    torch.cuda.synchronize()
     gA, gB = _np(A_.grad), _np(B_.grad)
-
-    def f(Am, Bm):
-        Xm = hpl.solve(torch.from_numpy(np.asfortranarray(Am)).cuda().t().contiguous().t(),
-                       torch.from_numpy(Bm).cuda(), nb=nb)
-        return float((Xm * G).sum())
-
-    A0, B0 = _np(A).copy(), _np(B).copy()
-    for (i, j) in [(0, 0), (5, 40), (63, 2), (17, 17)]:
-        h = 1e-6 * max(1.0, abs(A0[i, j]))
-        Ap, Am = A0.copy(), A0.copy()
-        Ap[i, j] += h
-        Am[i, j] -= h
-        fd = (f(Ap, B0) - f(Am, B0)) / (2 * h)
-        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j])) + 1e-9, (i, j, fd, gA[i, j])
-    for (i, c) in [(0, 0), (33, 2)]:
-        h = 1e-6
-        Bp, Bm = B0.copy(), B0.copy()
-        Bp[i, c] += h
-        Bm[i, c] -= h
-        fd = (f(A0, Bp) - f(A0, Bm)) / (2 * h)
-        assert abs(fd - gB[i, c]) <= 1e-6 * max(1.0, abs(gB[i, c])), (i, c, fd, gB[i, c])
+    fdA, fdB = fd_gradients(_np(A), _np(B), Gn)
+    ea, eb = max_rel_err(gA, fdA), max_rel_err(gB, fdB)
+    assert ea <= 1e-6, ea
+    assert eb <= 1e-6, eb
 
 
 @pytest.mark.parametrize("refine", [1, 0])     # GMRES per column; classic refinement on the block

@@ -31,8 +31,8 @@ def _check_system(orc, bt, s, A0, b0, emulate=True):
     kappa = np.linalg.cond(A0, np.inf)
     if bt.kind[s] == 0:
         LUo, ipo, _, gap = orc.getrf(A0)
-        if gap > 1e-12:
-            assert np.array_equal(_np(bt.pivots(s)), ipo), s
+        assert gap > 1e-12, ("near-tie pivot column: pick another seed", s, gap)
+        assert np.array_equal(_np(bt.pivots(s)), ipo), s
         assert np.abs(x - x64).max() / np.abs(x64).max() <= 100 * n * EPS * kappa
     else:
         assert np.abs(x - x64).max() / np.abs(x64).max() <= 2 * 16 * n * EPS * kappa

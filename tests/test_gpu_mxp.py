@@ -3,9 +3,32 @@ through the C ABI: the block factor (D_k^-1, L21, updated blocks), the
 refined solution, the scaled residual and the refinement iteration counts."""
 import numpy as np
 import pytest
+from _parity import (BLOCK_VS_PLAIN_BERR, assert_blocks_close, block_lu_backward_error,
+                     plain_lu_backward_error)
 
 pytestmark = pytest.mark.gpu
 EPS = 2.0 ** -53
+# Per-part tolerances of the GPU block factor against the oracle's block
+# emulation, each relative to the largest entry of the same part of the same
+# step (L21, U12, the off-diagonal and the diagonal of D_k). Operands are
+# rounded to the low precision on both sides, and a rounding decision may flip
+# on values that differ in their last FP32 bits: one flip moves an entry by
+# one unit in the last place of the operand format, relative to that entry.
+TOL_BF16 = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=1e-5)
+TOL_FP8 = dict(l21=2.0 ** -7, u12=2.0 ** -3, doff=2.0 ** -3, ddiag=1e-4)    # L21 keeps BF16 operands
+TOL_FP16 = dict(l21=2.0 ** -10, u12=2.0 ** -10, doff=2.0 ** -10, ddiag=1e-5)
+TOL_BF16_STORAGE = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=2.0 ** -7)
+
+
+def _check_against_plain(orc, A0, Fg, nb, prec):
+    """The GPU block factor against the plain LU of the paper's order (FP32
+    panel and U12 solve, rounded update operands, FP32 accumulation): its
+    backward error within the stated factor of the plain factor's, and not
+    below a quarter of it (the low precision really is used)."""
+    Fp, _ = orc.mxp_lu_plain(A0, nb, prec)
+    ep = plain_lu_backward_error(A0, Fp)
+    eg = block_lu_backward_error(A0, Fg, nb)
+    assert ep / 4 <= eg <= BLOCK_VS_PLAIN_BERR[prec] * ep, (eg, ep)
 
 
 def _np(t):
@@ -37,12 +60,10 @@ def test_mxp_factor_matches_oracle(hpl, orc, n, nb):
         kb = min(nbe, n - k0)
         dg, do = Dg[k0:k0 + kb, :kb], Do[k0:k0 + kb, :kb]
         assert np.abs(dg - do).max() <= 5e-5 * np.abs(do).max(), k0
-    # L21 / updated blocks: operands rounded to BF16 on both sides; a rounding
-    # decision may flip on values that differ in their last FP32 bits
-    off = ~np.eye(n, dtype=bool)
-    if n > 1:
-        assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -7 * np.abs(Fo[off]).max()
-    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 1e-5 * np.abs(np.diag(Fo)).max()
+    # L21, U12 and D_k, each against its own scale
+    assert_blocks_close(Fg, Fo, nbe, **TOL_BF16)
+    if n > nbe:                      # one block: no low-precision product at all
+        _check_against_plain(orc, _np(A), Fg, nbe, 0)
 
 
 @pytest.mark.parametrize("refine", [0, 1])
@@ -63,6 +84,9 @@ def test_mxp_solution_matches_fp64(hpl, orc, n, nb, refine):
     assert np.abs(xg - x64).max() / np.abs(x64).max() < bound
     emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_BF16, refine=refine)
     assert abs(rec["iters"] - emu["iters"]) <= 2, (rec, emu["iters"])
+    plain = orc.mxp_solve_plain(A0, b0, nb, prec=orc.PREC_BF16, refine=refine)
+    assert plain["status"] == 0
+    assert abs(rec["iters"] - plain["iters"]) <= 2, (rec, plain["iters"])
 
 
 def test_mxp_multiple_rhs(hpl, orc):
@@ -217,12 +241,12 @@ def test_mxp_fp8_variant(hpl, orc, n, nb):
     F, _ = hpl.mxp_factor_views(ws, n, nb)
     Fo, _, _ = orc.mxp_factor(A0, nb, orc.PREC_FP8)
     Fg = _np(F).astype(np.float64)
-    off = ~np.eye(n, dtype=bool)
-    # updated entries: FP8 rounding decisions may differ on nearly equal inputs
-    assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -3 * np.abs(Fo[off]).max()
-    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 1e-4 * np.abs(np.diag(Fo)).max()
+    assert_blocks_close(Fg, Fo, nb, **TOL_FP8)
+    _check_against_plain(orc, A0, Fg, nb, 1)
     emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_FP8, refine=1)
     assert abs(rec["iters"] - emu["iters"]) <= 2
+    plain = orc.mxp_solve_plain(A0, b0, nb, prec=orc.PREC_FP8, refine=1)
+    assert abs(rec["iters"] - plain["iters"]) <= 2
 
 
 @pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256), (2560, 256), (300, 100)])
@@ -244,11 +268,8 @@ def test_mxp_fp16_variant(hpl, orc, n, nb):
     F, _ = hpl.mxp_factor_views(ws, n, nb)
     Fg = _np(F).astype(np.float64)
     Fo, _, _ = orc.mxp_factor(A0, nb, orc.PREC_FP16)
-    off = ~np.eye(n, dtype=bool)
-    # operands rounded to FP16 on both sides: a rounding decision may flip on
-    # values that differ in their last FP32 bits
-    assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -10 * np.abs(Fo[off]).max()
-    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 1e-5 * np.abs(np.diag(Fo)).max()
+    assert_blocks_close(Fg, Fo, nb, **TOL_FP16)
+    _check_against_plain(orc, A0, Fg, nb, 2)
     # backward error of the GPU factor against the BF16 factor's
     _, _, wsb = hpl.mxp_solve(A, b, nb=nb, prec=hpl.PREC_BF16)
     torch.cuda.synchronize()
@@ -282,10 +303,8 @@ def test_mxp_bf16_storage(hpl, orc, n, nb):
     assert F.dtype == torch.bfloat16
     Fg = F.float().cpu().numpy().astype(np.float64)
     Fo, Do, _ = orc.mxp_factor(A0, nb, orc.PREC_BF16, storage=orc.STORAGE_BF16)
-    off = ~np.eye(n, dtype=bool)
     # BF16 rounding of values whose FP32 computations differ in their last bits
-    assert np.abs(Fg - Fo)[off].max() <= 2.0 ** -7 * np.abs(Fo[off]).max()
-    assert np.abs(np.diag(Fg) - np.diag(Fo)).max() <= 2.0 ** -7 * np.abs(np.diag(Fo)).max()
+    assert_blocks_close(Fg, Fo, nb, **TOL_BF16_STORAGE)
     # the first block is the BF16 rounding of A itself (one rounding from FP64)
     k = min(nb, n)
     first = np.array([orc.round_bf16_d(v) for v in A0[:k, 0]])

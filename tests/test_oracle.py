@@ -163,8 +163,8 @@ def test_getrf_pivots_match_lapack(orc, n, seed):
     LU, ipiv, info, gap = orc.getrf(A)
     lu, piv = sl.lu_factor(A)
     assert info == 0
-    if gap > 1e-12:
-        assert np.array_equal(ipiv, piv.astype(np.int32))
+    assert gap > 1e-12, ("near-tie pivot column: pick another seed", gap)
+    assert np.array_equal(ipiv, piv.astype(np.int32))
     assert np.max(np.abs(LU - lu)) < 1e-9 * n
 
 
@@ -284,14 +284,51 @@ def _tie_cases_bf16():
     return np.array(out, dtype=np.uint32).view(np.float32)
 
 
+def _subnormal_cases_bf16():
+    """FP32 values at and below BF16's smallest normal 2^-126, where the BF16
+    grid is the fixed spacing 2^-133: every FP32 subnormal bit pattern class
+    (smallest, ties at 2^-134 multiples, just off ties, the normal boundary)."""
+    bits = [0x00000001, 0x00000002, 0x0000FFFF, 0x00008000, 0x00018000, 0x00010000, 0x00007FFF,
+            0x00008001, 0x007FFFFF, 0x007F8000, 0x007F7FFF, 0x00800000, 0x00808000, 0x00818000,
+            0x0017F3E0, 0x00123456, 0x00400000, 0x003FFFFF]
+    out = []
+    for b in bits:
+        out.append(np.uint32(b))
+        out.append(np.uint32(b | 0x80000000))
+    rng = np.random.default_rng(11)
+    out.extend(rng.integers(1, 0x00800000, 3000, dtype=np.uint32))
+    return np.array(out, dtype=np.uint32).view(np.float32)
+
+
+def _overflow_cases_bf16():
+    """Around the largest finite BF16, 0x7F7F: below, at and past the midpoint
+    to 2^128 (which rounds to infinity)."""
+    bits = [0x7F7F0000, 0x7F7F7FFF, 0x7F7F8000, 0x7F7F8001, 0x7F7FFFFF, 0x7F7E8000, 0x7F7F4000]
+    return np.array(bits + [b | 0x80000000 for b in bits], dtype=np.uint32).view(np.float32)
+
+
 def test_round_bf16_matches_torch(orc):
     torch = pytest.importorskip("torch")
     rng = np.random.default_rng(1)
     vals = np.concatenate([rng.standard_normal(2000).astype(np.float32) * 10.0 ** rng.integers(-20, 20, 2000),
-                           _tie_cases_bf16()]).astype(np.float32)
+                           _tie_cases_bf16(), _subnormal_cases_bf16(), _overflow_cases_bf16(),
+                           np.array([2.0 ** -149, 3 * 2.0 ** -140, 1.7e-39], dtype=np.float32)]).astype(np.float32)
     want = torch.from_numpy(vals).to(torch.bfloat16).float().numpy()
     got = np.array([orc.round_bf16(v) for v in vals], dtype=np.float32)
-    assert np.array_equal(got, want)
+    assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+def test_round_bf16_subnormal_grid(orc):
+    """Below 2^-126 every result is a multiple of 2^-133 (BF16's subnormal
+    spacing) and the nearest one, ties to an even multiple; 2^-149 (FP32's
+    smallest subnormal) rounds to zero."""
+    for k in (0, 1, 2, 3, 5, 127):
+        for frac in (0.25, 0.5, 0.75):
+            x = np.float32((k + frac) * 2.0 ** -133)
+            got = orc.round_bf16(float(x))
+            q = k + (1 if frac > 0.5 or (frac == 0.5 and k % 2 == 1) else 0)
+            assert got == q * 2.0 ** -133, (k, frac, got)
+    assert orc.round_bf16(2.0 ** -149) == 0.0
 
 
 def test_round_e4m3_matches_torch(orc):
@@ -468,33 +505,227 @@ def test_mxp_refine_not_converged_status(orc):
     assert out["status"] == 4 and out["iters"] == 2
 
 
+# --- HPL-MxP plain LU emulation (paper order, independent of the block design) -------
+
+def _golden_kv(name):
+    out = {}
+    for line in _read_golden(name):
+        k, *v = line.split()
+        out[k] = v
+    return out
+
+
+def _frac_matrix(vals, n):
+    return np.array([float(Fraction(v)) for v in vals]).reshape(n, n)
+
+
+def test_mxp_lu_plain_by_hand(orc):
+    """Two panel steps of a 4 x 4 case worked by hand in exact rationals, for
+    every operand precision: the BF16 rounding of one U12 entry (up), the FP8
+    rounding of the same entry (down), FP16 and FP32 exact."""
+    g = _golden_kv("mxp_2step_by_hand.txt")
+    nb = int(g["nb"][0])
+    A = _frac_matrix(g["A"], 4)
+    for prec in (3, 0, 2, 1):
+        F, info = orc.mxp_lu_plain(A, nb, prec)
+        assert info == 0
+        want = _frac_matrix(g[f"F_prec{prec}"], 4)
+        assert np.array_equal(F.astype(np.float64), want), (prec, F)
+    for prec in (3, 0, 2, 1):
+        F, _ = orc.mxp_lu_plain(A, 4, prec)
+        assert np.array_equal(F.astype(np.float64), _frac_matrix(g["F_nb4"], 4)), prec
+
+
+def _exact_unpivoted_lu(A):
+    n = A.shape[0]
+    M = [[Fraction(float(A[i, j])) for j in range(n)] for i in range(n)]
+    for k in range(n):
+        for i in range(k + 1, n):
+            M[i][k] = M[i][k] / M[k][k]
+            for j in range(k + 1, n):
+                M[i][j] -= M[i][k] * M[k][j]
+    return M
+
+
+def test_mxp_lu_plain_fp32_within_error_bound_of_exact(orc):
+    """FP32 mode on a ragged panel split (n = 10, NB = 3): the computed L, U
+    satisfy the componentwise backward-error bound of Gaussian elimination,
+    |A - L U| <= gamma_n |L| |U| with gamma_n = n u / (1 - n u), u = 2^-24
+    (evaluated in exact rationals), and are close to the exact unpivoted LU
+    of the same (FP32) matrix."""
+    n, nb = 10, 3
+    A = orc.generate(41, orc.STREAM_A, n, n, dominant=True).astype(np.float32).astype(np.float64)
+    F, info = orc.mxp_lu_plain(A, nb, orc.PREC_FP32)
+    assert info == 0
+    Fq = [[Fraction(float(F[i, j])) for j in range(n)] for i in range(n)]
+    u = Fraction(1, 2 ** 24)
+    gamma = n * u / (1 - n * u)
+    for i in range(n):
+        for j in range(n):
+            lu = sum((Fq[i][k] if k < i else Fraction(1)) * Fq[k][j] for k in range(min(i, j) + 1) if k <= j)
+            absl = sum(abs(Fq[i][k] if k < i else Fraction(1)) * abs(Fq[k][j]) for k in range(min(i, j) + 1))
+            assert abs(Fraction(float(A[i, j])) - lu) <= gamma * absl, (i, j)
+    E = _exact_unpivoted_lu(A)
+    scale = np.abs(A).max()
+    err = max(abs(float(Fq[i][j] - E[i][j])) for i in range(n) for j in range(n))
+    assert err <= 8 * n * 2.0 ** -24 * scale
+
+
+def test_mxp_lu_plain_fp32_matches_lapack(orc):
+    """FP32 mode against LAPACK's LU of the same matrix (scipy): on a
+    diagonally dominant matrix partial pivoting makes no interchange, so the
+    two are the same factorization, FP32 against FP64 arithmetic."""
+    sl = pytest.importorskip("scipy.linalg")
+    n, nb = 300, 64
+    A = orc.generate(42, orc.STREAM_A, n, n, dominant=True)
+    P, L, U = sl.lu(A.astype(np.float32).astype(np.float64))
+    assert np.array_equal(P, np.eye(n))
+    F, _ = orc.mxp_lu_plain(A, nb, orc.PREC_FP32)
+    F = F.astype(np.float64)
+    assert np.abs(np.tril(F, -1) - np.tril(L, -1)).max() <= 1e-5 * np.abs(np.tril(L, -1)).max()
+    assert np.abs(np.triu(F) - U).max() <= 1e-5 * np.abs(U).max()
+
+
+def test_mxp_lu_plain_panel_width_independent_in_fp32(orc):
+    """Without operand rounding the panel width only reorders FP32 operations:
+    every NB gives the factor of the unblocked elimination to FP32 accuracy;
+    with BF16 operands the width matters (the updates are rounded)."""
+    n = 200
+    A = orc.generate(43, orc.STREAM_A, n, n, dominant=True)
+    ref, _ = orc.mxp_lu_plain(A, n, orc.PREC_FP32)
+    for nb in (1, 7, 64, 199):
+        F, _ = orc.mxp_lu_plain(A, nb, orc.PREC_FP32)
+        assert np.abs(F.astype(np.float64) - ref).max() <= 1e-5 * np.abs(ref).max(), nb
+    Fb, _ = orc.mxp_lu_plain(A, 64, orc.PREC_BF16)
+    assert np.abs(Fb.astype(np.float64) - ref).max() > 1e-6 * np.abs(ref).max()
+
+
+def test_mxp_lu_plain_error_levels(orc):
+    """Backward error ||A - LU||_inf / ||A||_inf by operand precision: FP32 <
+    FP16 < BF16 < FP8 (BF16 keeps 8 significant bits, FP16 11, E4M3 4): the
+    rounded operands really enter the update, and FP16 is at least 4x better
+    than BF16."""
+    from _parity import plain_lu_backward_error
+    n, nb = 384, 128
+    A = orc.generate(44, orc.STREAM_A, n, n, dominant=True)
+    e = {p: plain_lu_backward_error(A, orc.mxp_lu_plain(A, nb, p)[0]) for p in (3, 2, 0, 1)}
+    assert e[3] < 1e-6
+    assert e[3] < e[2] < e[0] < e[1]
+    assert 16 * e[3] < e[0] < 2.0 ** -9
+    assert e[2] < e[0] / 4
+    assert e[1] < 2.0 ** -6
+
+
+@pytest.mark.parametrize("refine", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_mxp_solve_plain_reaches_fp64_solution(orc, refine, prec):
+    n, nb = 256, 64
+    A = orc.generate(6, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(6, orc.STREAM_B, n, 1)[:, 0]
+    out = orc.mxp_solve_plain(A, b, nb, prec=prec, refine=refine)
+    assert out["status"] == 0 and out["sr"] < 16
+    x64, _ = orc.solve(A, b)
+    bound = 2 * 16 * n * EPS * np.linalg.cond(A, np.inf)
+    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < bound
+    assert 1 <= out["iters"] <= 20
+
+
+def test_mxp_plain_preconditioner_solves_lu(orc):
+    """One application of the plain preconditioner solves L U x = b (numpy's
+    solve of the assembled FP32 factors) to FP32 accuracy."""
+    n, nb = 128, 32
+    A = orc.generate(15, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(15, orc.STREAM_B, n, 1)[:, 0].astype(np.float32).astype(np.float64)
+    F, _ = orc.mxp_lu_plain(A, nb, orc.PREC_BF16)
+    out = orc.mxp_refine_plain(A, F, b, refine=0, max_iter=0)
+    Fd = F.astype(np.float64)
+    x_ref = np.linalg.solve((np.tril(Fd, -1) + np.eye(n)) @ np.triu(Fd), b)
+    assert np.abs(out["x"] - x_ref).max() / np.abs(x_ref).max() < 1e-5
+
+
+def test_block_and_plain_emulations_agree_on_iterations(orc):
+    """The two readings of the low-precision factorization (the block LU with a
+    Newton-Schulz diagonal inverse, and the plain LU in the paper's order)
+    need the same number of GMRES-IR corrections on the same system, and the
+    block factor's backward error stays within the factor stated for the GPU
+    parity tests (the block LU rounds A21 itself to BF16 inside L21 = A21 D^-1;
+    the plain LU rounds only the update operands L21 ~ 1/n and U12)."""
+    from _parity import block_lu_backward_error, plain_lu_backward_error, BLOCK_VS_PLAIN_BERR
+    for n, nb, prec in ((512, 128, 0), (300, 100, 0), (512, 128, 1), (512, 128, 2)):
+        A = orc.generate(3, orc.STREAM_A, n, n, dominant=True)
+        b = orc.generate(3, orc.STREAM_B, n, 1)[:, 0]
+        Fp, _ = orc.mxp_lu_plain(A, nb, prec)
+        Fb, Db, _ = orc.mxp_factor(A, nb, prec)
+        ep, eb = plain_lu_backward_error(A, Fp), block_lu_backward_error(A, Fb, nb)
+        assert ep / 4 <= eb <= BLOCK_VS_PLAIN_BERR[prec] * ep, (n, nb, prec, ep, eb)
+        sp, sb = orc.mxp_refine_plain(A, Fp, b), orc.mxp_refine(A, Fb, Db, nb, b)
+        assert abs(sp["iters"] - sb["iters"]) <= 2
+
+
+def test_block_tolerances_catch_planted_mistakes(orc):
+    """The per-part tolerances of the GPU factor tests fail on a CPU copy of the
+    oracle's factor with one mistake planted (L21 of one step scaled by 2, one
+    U12 entry's sign flipped, a diagonal of D perturbed), and pass on the
+    unmodified copy. A single tolerance over all off-diagonal entries relative
+    to their overall maximum (an entry of U, ~1/2) would let the scaled L21
+    (entries ~2/n) through."""
+    from _parity import assert_blocks_close
+    n, nb = 1000, 256
+    A = orc.generate(3, orc.STREAM_A, n, n, dominant=True)
+    Fo, _, _ = orc.mxp_factor(A, nb, orc.PREC_BF16)
+    Fo = Fo.astype(np.float64)
+    tol = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=1e-5)
+    assert_blocks_close(Fo.copy(), Fo, nb, **tol)
+    bad = Fo.copy()
+    bad[512:, 256:512] *= 2.0
+    off = ~np.eye(n, dtype=bool)
+    assert np.abs(bad - Fo)[off].max() <= 2.0 ** -7 * np.abs(Fo[off]).max()   # the old global test passes it
+    with pytest.raises(AssertionError):
+        assert_blocks_close(bad, Fo, nb, **tol)
+    bad = Fo.copy()
+    bad[300, 700] = -bad[300, 700]
+    with pytest.raises(AssertionError):
+        assert_blocks_close(bad, Fo, nb, **tol)
+    bad = Fo.copy()
+    bad[600, 600] *= 1 + 1e-4
+    with pytest.raises(AssertionError):
+        assert_blocks_close(bad, Fo, nb, **tol)
+
+
 # --- adjoint ---------------------------------------------------------------------
 
 def test_adjoint_matches_finite_differences(orc):
-    n, nrhs = 8, 2
-    A = orc.generate(12, orc.STREAM_A, n, n, dominant=True)
-    B = orc.generate(12, orc.STREAM_B, n, nrhs)
-    G = np.random.default_rng(3).standard_normal((n, nrhs))
+    """The differentiable-solve check at n = 64: every entry of grad_A and
+    grad_B against central differences of sum(G * A^-1 B) in FP64, within
+    1e-6 relative per entry (no absolute floor)."""
+    from _parity import fd_gradients, max_rel_err
+    n, nrhs = 64, 3
+    A = orc.generate(21, orc.STREAM_A, n, n, dominant=True)
+    B = orc.generate(21, orc.STREAM_B, n, nrhs)
+    G = np.random.default_rng(5).standard_normal((n, nrhs))
     X = np.linalg.solve(A, B)
     gB, gA = orc.adjoint(A, X, G)
+    fdA, fdB = fd_gradients(A, B, G)
+    assert max_rel_err(gA, fdA) <= 1e-6
+    assert max_rel_err(gB, fdB) <= 1e-6
 
-    def f(Am, Bm):
-        return float(np.sum(G * np.linalg.solve(Am, Bm)))
 
-    for (i, j) in [(0, 0), (3, 5), (7, 1)]:
-        h = 1e-6 * max(1.0, abs(A[i, j]))
-        Ap, Am = A.copy(), A.copy()
-        Ap[i, j] += h
-        Am[i, j] -= h
-        fd = (f(Ap, B) - f(Am, B)) / (2 * h)
-        assert abs(fd - gA[i, j]) <= 1e-6 * max(1.0, abs(gA[i, j]))
-    for (i, c) in [(0, 0), (5, 1)]:
-        h = 1e-6
-        Bp, Bm = B.copy(), B.copy()
-        Bp[i, c] += h
-        Bm[i, c] -= h
-        fd = (f(A, Bp) - f(A, Bm)) / (2 * h)
-        assert abs(fd - gB[i, c]) <= 1e-6 * max(1.0, abs(gB[i, c]))
+def test_fd_yardstick_catches_wrong_gradients(orc):
+    """The finite-difference yardstick flags a gradient with one wrong sign or
+    a transposed grad_A (planted in a CPU copy of the oracle's result)."""
+    from _parity import fd_gradients, max_rel_err
+    n, nrhs = 12, 2
+    A = orc.generate(31, orc.STREAM_A, n, n, dominant=True)
+    B = orc.generate(31, orc.STREAM_B, n, nrhs)
+    G = np.random.default_rng(9).standard_normal((n, nrhs))
+    gB, gA = orc.adjoint(A, np.linalg.solve(A, B), G)
+    fdA, fdB = fd_gradients(A, B, G)
+    assert max_rel_err(gA, fdA) <= 1e-6 and max_rel_err(gB, fdB) <= 1e-6
+    bad = gA.copy()
+    bad[3, 7] = -bad[3, 7]
+    assert max_rel_err(bad, fdA) > 1e-6
+    assert max_rel_err(gA.T, fdA) > 1e-6
+    assert max_rel_err(gB * (1 + 1e-5), fdB) > 1e-6
 
 
 def test_adjoint_matches_torch_autograd(orc):
