@@ -17,7 +17,11 @@ EPS = 2.0 ** -53
 TOL_BF16 = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=1e-5)
 TOL_FP8 = dict(l21=2.0 ** -7, u12=2.0 ** -3, doff=2.0 ** -3, ddiag=1e-4)    # L21 keeps BF16 operands
 TOL_FP16 = dict(l21=2.0 ** -10, u12=2.0 ** -10, doff=2.0 ** -10, ddiag=1e-5)
-TOL_BF16_STORAGE = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=2.0 ** -7)
+# BF16 storage rounds every stored value (L21 and the updated trailing matrix)
+# to BF16 after each step, so a rounding flip in an earlier step carries into
+# the inputs of later ones: a few units of BF16's 2^-8 relative spacing
+# (measured: 1.35 x 2^-7 on L21 of the third step at n = 1000, NB = 256).
+TOL_BF16_STORAGE = dict(l21=2.0 ** -6, u12=2.0 ** -6, doff=2.0 ** -6, ddiag=2.0 ** -7)
 
 
 def _check_against_plain(orc, A0, Fg, nb, prec):
