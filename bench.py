@@ -76,6 +76,9 @@ def parse():
     ap.add_argument("--mxp-fp8-nb", type=int, default=4096)
     ap.add_argument("--mxp-ns-iters", type=int, default=1,
                     help="Newton-Schulz steps per diagonal block in the n = 98304 solves (library default 2)")
+    ap.add_argument("--mxp-inner", default="fp32", choices=["fp32", "fp64"],
+                    help="GMRES inner matrix-vector products of the mixed-precision solves: on an FP32 copy of A "
+                         "(default) or on the FP64 A; residuals and the acceptance test are FP64 either way")
     ap.add_argument("--mxp-large-n", type=int, default=0,
                     help="also time one regenerated-A, BF16-storage solve of this size (0: skip)")
     return ap.parse_args()
@@ -582,12 +585,21 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
     X = hpl.colmajor(n, 1, device=dev)
     info = hpl.Info(dev)
     ws = None
+    # FP32 inner products with FP32 storage only: the BF16-stored factor is
+    # coarse enough that an FP32-accurate correction needs a second outer step
+    # (measured: 2 corrections and 8 preconditioner applications against 1 and
+    # 4). The larger regenerated solve keeps FP64 ones too: an FP32 copy of A
+    # at n = 262144 would need 275 GB.
+    use_f32 = a.mxp_inner == "fp32" and n == a.mxp_n and storage == 0
+    inner = hpl.INNER_FP32 if use_f32 else hpl.INNER_FP64
     for _ in range(n_warm):
         X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage,
-                                        ns_iters=a.mxp_ns_iters)
+                                        ns_iters=a.mxp_ns_iters, inner=inner)
     stream = torch.cuda.current_stream(dev)
     torch.cuda.synchronize(dev)
     hpl.set_phase_timing(True)
+    clocks = ClockSampler(d.local)
+    clocks.start()
     step_ms, launches = [], 0
     for _ in range(n_steps):
         d.barrier()
@@ -597,7 +609,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
         l0 = hpl.launch_count()
         e0.record(stream)
         X, info, ws = hpl.mxp_solve(A, b, nb=nb, X=X, ws=ws, info=info, prec=prec, seed=seed, storage=storage,
-                                        ns_iters=a.mxp_ns_iters)
+                                        ns_iters=a.mxp_ns_iters, inner=inner)
         e1.record(stream)
         launches += hpl.launch_count() - l0
         torch.cuda.synchronize(dev)
@@ -605,6 +617,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
         step_ms.append(e0.elapsed_time(e1))
     phases = hpl.phase_times()
     hpl.set_phase_timing(False)
+    clk = clocks.stop()
     rec = info.read()
     total_ms = d.max(sum(step_ms))
     value = d.sum(flops(n) * len(step_ms)) / (total_ms * 1e-3) / 1e12
@@ -630,6 +643,8 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
     return {**extra, "workload": f"hpl_mxp_{tag}{stag}_n{n}_nb{nb}_gmres" + ("_regenerated_a" if regen else ""), "n": n, "nb": nb, "value": value, "unit": "TFLOP/s",
             "ms_per_step": total_ms / len(step_ms), "steps": n_steps, "warmup": n_warm,
             "storage": "bf16" if storage else "fp32", "ns_iters": a.mxp_ns_iters,
+            "gmres_inner_products": "fp32 (FP32 copy of A)" if use_f32 else "fp64 (FP64 A)",
+            "clocks": clk,
             "status": rec["status_name"], "scaled_residual": rec["scaled_residual"], "refine_iters": rec["iters"],
             "preconditioner_applications": rec["inner_iters"],
             "speedup_vs_fp64_lu_rate": value / fp64_value if fp64_value else None,

@@ -78,8 +78,15 @@ typedef struct {
                             factors either way. */
     int32_t storage;     /* mxp_solve / lu_solve_backward: HPL_STORAGE_FP32 (default) or HPL_STORAGE_BF16, the
                             element type of the working matrix / factor (BF16: with HPL_PREC_BF16 only) */
-    int32_t reserved;
+    int32_t inner;       /* mxp_solve with GMRES refinement: HPL_INNER_FP64 (default) computes the matrix-vector
+                            products inside GMRES with the FP64 A; HPL_INNER_FP32 with an FP32 copy of A that
+                            the factorization's conversion pass also writes (4 n^2 more workspace bytes). The
+                            residual of every refinement step and the acceptance test stay FP64. Ignored by
+                            classic refinement and by lu_solve_backward. */
 } hpl_opts;
+
+/* Precision of GMRES's inner matrix-vector products (opts.inner). */
+enum { HPL_INNER_FP64 = 0, HPL_INNER_FP32 = 1 };
 
 /* Working-matrix storage of the mixed-precision factorization. */
 enum { HPL_STORAGE_FP32 = 0, HPL_STORAGE_BF16 = 1 };
@@ -336,6 +343,30 @@ int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t ld
  */
 int hplgb_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int32_t* err, void* stream);
+
+/*
+ * hplgb_gemm_config — tuning switches of the tensor-core product, for
+ * measurement (not in the paper). what = 0: epilogue (value 0, the default:
+ * an FP32 C that is 16-byte aligned with a leading dimension divisible by 4
+ * is updated by bulk tensor reductions from shared memory, C += -(A B^T), so
+ * the SMs never read C; 1: every C read and written by the epilogue threads).
+ * what = 1: rows-of-tiles per band of the tile walk (0 = the default per
+ * operand kind). what = 2: largest M x N given to the two-SM pair kernel
+ * (0 = the default, negative = never). Process-wide, not thread-safe; results
+ * are bit-identical for every setting except where FP32 subnormals occur (the
+ * bulk reduction flushes them to zero). Returns HPL_ERR_INVALID for an unknown
+ * switch or value.
+ */
+int hplgb_gemm_config(int what, long long value);
+
+/*
+ * hplgb_batched_config — residency switch of the batched solver, for
+ * measurement (not in the paper). what = 0: value 0 (default) runs a plan
+ * whose systems all use 16-wide panels with two CTAs per SM (its shared
+ * memory fits twice), value 1 always one CTA per SM. Same results either way.
+ * Process-wide; HPL_ERR_INVALID for an unknown switch or value.
+ */
+int hplgb_batched_config(int what, long long value);
 
 /*
  * Diagnostics.

@@ -89,10 +89,11 @@ def _load():
             "orc_to_bf16_storage": (None, [i64, i64, dp, i64, fp, i64]),
             "orc_round_bf16_d": (ctypes.c_float, [ctypes.c_double]),
             "orc_mxp_refine": (ctypes.c_int, [i64, dp, i64, i64, fp, i64, fp, dp, dp, ctypes.c_int, ctypes.c_int,
-                                              ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
+                                              ctypes.c_int, ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
             "orc_mxp_lu_plain": (i64, [i64, i64, ctypes.c_int, fp, i64]),
             "orc_mxp_refine_plain": (ctypes.c_int, [i64, dp, i64, fp, i64, dp, dp, ctypes.c_int, ctypes.c_int,
-                                                    ctypes.c_int, ctypes.c_double, intp, intp, dp, dp]),
+                                                    ctypes.c_int, ctypes.c_int, ctypes.c_double, intp, intp, dp,
+                                                    dp]),
             "orc_adjoint": (i64, [i64, i64, dp, i64, dp, i64, dp, i64, dp, i64, dp, i64]),
             "orc_batch_sizes": (None, [u64, i64, i64p]),
             "orc_num_threads": (ctypes.c_int, []),
@@ -306,29 +307,36 @@ def block_lu_parts(F, nb: int):
     return L, U
 
 
+INNER_FP64 = 0
+INNER_FP32 = 1
+
+
 def mxp_refine(A, F, Dinv, nb: int, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30,
-               tol: float = 16.0):
-    """Refine with the block factor (F, Dinv). Returns dict(x, status, iters, inner, sr, hist)."""
+               tol: float = 16.0, inner: int = INNER_FP64):
+    """Refine with the block factor (F, Dinv). inner = INNER_FP32 takes GMRES's
+    inner products from the FP32 rounding of A and of the vector. Returns
+    dict(x, status, iters, inner, sr, hist)."""
     A = _fortran(A, np.float64)
     F = np.asfortranarray(F, dtype=np.float32)
     Dinv = np.asfortranarray(Dinv, dtype=np.float32)
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = A.shape[0]
     x = np.zeros(n, dtype=np.float64)
-    it, inner = ctypes.c_int(0), ctypes.c_int(0)
+    it, inn = ctypes.c_int(0), ctypes.c_int(0)
     sr = ctypes.c_double(0.0)
     hist = np.full(max_iter + 1, np.nan)
     st = _load().orc_mxp_refine(n, _dp(A), max(n, 1), nb, _fp(F), max(n, 1), _fp(Dinv), _dp(b), _dp(x),
-                                int(refine), int(max_iter), int(gmres_m), float(tol), ctypes.byref(it),
-                                ctypes.byref(inner), ctypes.byref(sr), _dp(hist))
-    return dict(x=x, status=int(st), iters=int(it.value), inner=int(inner.value), sr=float(sr.value),
+                                int(refine), int(max_iter), int(gmres_m), int(inner), float(tol), ctypes.byref(it),
+                                ctypes.byref(inn), ctypes.byref(sr), _dp(hist))
+    return dict(x=x, status=int(st), iters=int(it.value), inner=int(inn.value), sr=float(sr.value),
                 hist=hist[: it.value + 1])
 
 
 def mxp_solve(A, b, nb: int, prec: int = PREC_BF16, refine: int = 1, max_iter: int = 50,
-              gmres_m: int = 30, tol: float = 16.0, ns_iters: int = NS_ITERS, storage: int = STORAGE_FP32):
+              gmres_m: int = 30, tol: float = 16.0, ns_iters: int = NS_ITERS, storage: int = STORAGE_FP32,
+              inner: int = INNER_FP64):
     F, Dinv, info = mxp_factor(A, nb, prec, ns_iters, storage)
-    out = mxp_refine(A, F, Dinv, nb, b, refine, max_iter, gmres_m, tol)
+    out = mxp_refine(A, F, Dinv, nb, b, refine, max_iter, gmres_m, tol, inner)
     out["F"] = F
     out["Dinv"] = Dinv
     out["info"] = info
@@ -347,7 +355,8 @@ def mxp_lu_plain(A, nb: int, prec: int = PREC_BF16):
     return F, int(info)
 
 
-def mxp_refine_plain(A, F, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0):
+def mxp_refine_plain(A, F, b, refine: int = 1, max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0,
+                     inner: int = INNER_FP64):
     """Refinement (classic or GMRES-IR) with the plain factor F as M = L U,
     applied in FP32. Returns dict(x, status, iters, inner, sr, hist)."""
     A = _fortran(A, np.float64)
@@ -355,20 +364,20 @@ def mxp_refine_plain(A, F, b, refine: int = 1, max_iter: int = 50, gmres_m: int 
     b = np.ascontiguousarray(b, dtype=np.float64)
     n = A.shape[0]
     x = np.zeros(n, dtype=np.float64)
-    it, inner = ctypes.c_int(0), ctypes.c_int(0)
+    it, inn = ctypes.c_int(0), ctypes.c_int(0)
     sr = ctypes.c_double(0.0)
     hist = np.full(max_iter + 1, np.nan)
     st = _load().orc_mxp_refine_plain(n, _dp(A), max(n, 1), _fp(F), max(n, 1), _dp(b), _dp(x), int(refine),
-                                      int(max_iter), int(gmres_m), float(tol), ctypes.byref(it), ctypes.byref(inner),
-                                      ctypes.byref(sr), _dp(hist))
-    return dict(x=x, status=int(st), iters=int(it.value), inner=int(inner.value), sr=float(sr.value),
+                                      int(max_iter), int(gmres_m), int(inner), float(tol), ctypes.byref(it),
+                                      ctypes.byref(inn), ctypes.byref(sr), _dp(hist))
+    return dict(x=x, status=int(st), iters=int(it.value), inner=int(inn.value), sr=float(sr.value),
                 hist=hist[: it.value + 1])
 
 
 def mxp_solve_plain(A, b, nb: int, prec: int = PREC_BF16, refine: int = 1, max_iter: int = 50,
-                    gmres_m: int = 30, tol: float = 16.0):
+                    gmres_m: int = 30, tol: float = 16.0, inner: int = INNER_FP64):
     F, info = mxp_lu_plain(A, nb, prec)
-    out = mxp_refine_plain(A, F, b, refine, max_iter, gmres_m, tol)
+    out = mxp_refine_plain(A, F, b, refine, max_iter, gmres_m, tol, inner)
     out["F"] = F
     out["info"] = info
     return out

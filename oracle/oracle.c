@@ -723,6 +723,18 @@ static void orc_matvec(int64_t n, const double* A, int64_t lda, const double* x,
     }
 }
 
+/* GMRES's inner product in FP32 data (inner = 1): y = fl32(A) fl32(x), the
+ * products of two FP32 values exact in FP64 and summed in FP64 in increasing
+ * j, so the only error is the FP32 rounding of A and x. */
+static void orc_matvec_f32data(int64_t n, const double* A, int64_t lda, const double* x, double* y) {
+#pragma omp parallel for schedule(static)
+    for (int64_t i = 0; i < n; i++) {
+        double s = 0.0;
+        for (int64_t j = 0; j < n; j++) s += (double)(float)A[j * lda + i] * (double)(float)x[j];
+        y[i] = s;
+    }
+}
+
 static double orc_dot(int64_t n, const double* a, const double* b) {
     double s = 0.0;
     for (int64_t i = 0; i < n; i++) s += a[i] * b[i];
@@ -737,7 +749,11 @@ static double orc_dot(int64_t n, const double* a, const double* b) {
  * Arnoldi steps, right-preconditioned by M^-1, modified Gram-Schmidt and
  * Givens rotations in FP64, stopping early once the estimated residual is
  * below 1e-10 of ||r||_2 (refine = 1, GMRES-IR after Carson & Higham, SIAM J.
- * Sci. Comput. 2018, with the preconditioner on the right). Then x += d.
+ * Sci. Comput. 2018, with the preconditioner on the right). inner_f32 = 1
+ * computes GMRES's inner matrix-vector products from the FP32 rounding of A
+ * and of the vector (the lower "matrix-vector precision" of the
+ * five-precision GMRES-IR analysis of Amestoy, Buttari, Higham, L'Excellent,
+ * Mary & Vieuble, 2024); the residual of every outer step stays FP64. Then x += d.
  * Returns 0 when converged, 4 when max_iter corrections did not get there.
  * iters = corrections applied, inner = preconditioner applications inside
  * GMRES (equal to iters for refine = 0). hist (optional, max_iter+1) receives
@@ -756,28 +772,30 @@ static void orc_apply_prec(const orc_prec_t* P, const double* v, double* out, fl
 }
 
 static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_prec_t* P,
-                           const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
-                           int* iters, int* inner, double* final_sr, double* hist);
+                           const double* b, double* x, int refine, int max_iter, int gmres_m, int inner_f32,
+                           double tol, int* iters, int* inner, double* final_sr, double* hist);
 
 int orc_mxp_refine(int64_t n, const double* A, int64_t lda, int64_t nb, const float* F, int64_t ldf,
                    const float* Dinv,
-                   const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
+                   const double* b, double* x, int refine, int max_iter, int gmres_m, int inner_f32, double tol,
                    int* iters, int* inner, double* final_sr, double* hist) {
     orc_prec_t P = {n, nb, F, ldf, Dinv};
-    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, tol, iters, inner, final_sr, hist);
+    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, inner_f32, tol, iters, inner, final_sr,
+                           hist);
 }
 
 /* The same refinement with the plain factor of orc_mxp_lu_plain as M. */
 int orc_mxp_refine_plain(int64_t n, const double* A, int64_t lda, const float* F, int64_t ldf,
-                         const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
-                         int* iters, int* inner, double* final_sr, double* hist) {
+                         const double* b, double* x, int refine, int max_iter, int gmres_m, int inner_f32,
+                         double tol, int* iters, int* inner, double* final_sr, double* hist) {
     orc_prec_t P = {n, n, F, ldf, NULL};
-    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, tol, iters, inner, final_sr, hist);
+    return orc_refine_impl(n, A, lda, &P, b, x, refine, max_iter, gmres_m, inner_f32, tol, iters, inner, final_sr,
+                           hist);
 }
 
 static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_prec_t* P,
-                           const double* b, double* x, int refine, int max_iter, int gmres_m, double tol,
-                           int* iters, int* inner, double* final_sr, double* hist) {
+                           const double* b, double* x, int refine, int max_iter, int gmres_m, int inner_f32,
+                           double tol, int* iters, int* inner, double* final_sr, double* hist) {
     double eps = 0x1p-53;
     double anorm = 0.0;
     for (int64_t i = 0; i < n; i++) {
@@ -822,7 +840,8 @@ static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_pr
                 double* w = V + (int64_t)(j + 1) * n;
                 orc_apply_prec(P, vj, zj, tmp);
                 inn++;
-                orc_matvec(n, A, lda, zj, w);
+                if (inner_f32) orc_matvec_f32data(n, A, lda, zj, w);
+                else orc_matvec(n, A, lda, zj, w);
                 for (int i = 0; i <= j; i++) {
                     double h = orc_dot(n, w, V + (int64_t)i * n);
                     H[j * (m + 1) + i] = h;

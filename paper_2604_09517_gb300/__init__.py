@@ -32,6 +32,8 @@ PREC_FP8_E4M3 = 1
 PREC_FP16 = 2
 STORAGE_FP32 = 0
 STORAGE_BF16 = 1
+INNER_FP64 = 0          # GMRES inner matrix-vector products with the FP64 A
+INNER_FP32 = 1          # ... with an FP32 copy of A kept in the workspace
 REFINE_IR = 0
 REFINE_GMRES = 1
 STREAM_A = 0
@@ -58,7 +60,7 @@ class Opts(ctypes.Structure):
                 ("refine", ctypes.c_int32), ("max_iter", ctypes.c_int32), ("gmres_m", ctypes.c_int32),
                 ("ns_iters", ctypes.c_int32), ("tol", ctypes.c_double), ("timeout_ns", ctypes.c_int64),
                 ("fp64_emulation", ctypes.c_int32), ("pfact", ctypes.c_int32),
-                ("storage", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("storage", ctypes.c_int32), ("inner", ctypes.c_int32)]
 
 
 def library_path() -> str:
@@ -108,6 +110,8 @@ def load():
             "mxp_solve": (i32, [i64, i64, vp, i64, u64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
+            "hplgb_gemm_config": (i32, [i32, ctypes.c_longlong]),
+            "hplgb_batched_config": (i32, [i32, ctypes.c_longlong]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
             "hplgb_phase_records": (i32, [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]),
         }
@@ -148,13 +152,14 @@ def colmajor(m: int, n: int, dtype=torch.float64, device="cuda", ld: int | None 
 
 def make_opts(nb: int = 0, lookahead: int = 1, prec: int = PREC_BF16, refine: int = REFINE_GMRES,
               max_iter: int = 50, gmres_m: int = 30, tol: float = 16.0, timeout_ns: int = 0,
-              fp64_emulation: int = 0, pfact: int = 0, storage: int = STORAGE_FP32, ns_iters: int = 0) -> Opts:
+              fp64_emulation: int = 0, pfact: int = 0, storage: int = STORAGE_FP32, ns_iters: int = 0,
+              inner: int = 0) -> Opts:
     o = Opts()
     load().hpl_default_opts(ctypes.byref(o))
     if ns_iters:
         o.ns_iters = ns_iters
     o.nb, o.lookahead, o.prec, o.refine = nb, lookahead, prec, refine
-    o.fp64_emulation, o.pfact, o.storage = fp64_emulation, pfact, storage
+    o.fp64_emulation, o.pfact, o.storage, o.inner = fp64_emulation, pfact, storage, inner
     o.max_iter, o.gmres_m, o.tol = max_iter, gmres_m, tol
     if timeout_ns:
         o.timeout_ns = timeout_ns
@@ -245,13 +250,14 @@ def scaled_residual(A: torch.Tensor | None, x: torch.Tensor, b: torch.Tensor, se
 def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: int = REFINE_GMRES, max_iter: int = 50,
               gmres_m: int = 30, tol: float = 16.0, X: torch.Tensor | None = None, ws: torch.Tensor | None = None,
               info: Info | None = None, prec: int = PREC_BF16, seed: int = 0, storage: int = STORAGE_FP32,
-              ns_iters: int = 0):
+              ns_iters: int = 0, inner: int = INNER_FP64):
     """Mixed-precision solve of A X = B (A FP64 n x n column-major, diagonally dominant).
 
     A = None solves with the dominant generated matrix of `seed` without storing
     it (the library regenerates its entries). storage = STORAGE_BF16 keeps the
-    working matrix in BF16. Returns (X, info, ws); ws holds the block factor
-    afterwards (see mxp_factor_views).
+    working matrix in BF16. inner = INNER_FP32 runs GMRES's inner
+    matrix-vector products on an FP32 copy of A. Returns (X, info, ws); ws
+    holds the block factor afterwards (see mxp_factor_views).
     """
     lib = load()
     n = B.shape[0]
@@ -264,7 +270,7 @@ def mxp_solve(A: torch.Tensor | None, B: torch.Tensor, nb: int = 3072, refine: i
         Bm = Bc
     nrhs = Bm.shape[1]
     opts = make_opts(nb=nb, refine=refine, max_iter=max_iter, gmres_m=gmres_m, tol=tol, prec=prec, storage=storage,
-                     ns_iters=ns_iters)
+                     ns_iters=ns_iters, inner=inner)
     if X is None:
         X = colmajor(n, nrhs, device=dev)
     Xm = X.view(n, 1) if X.dim() == 1 else X
@@ -517,6 +523,21 @@ PHASES = ("pfact", "swap", "trsm", "update", "other", "convert", "resid", "refin
 
 def launch_count() -> int:
     return int(load().hplgb_launch_count())
+
+
+GEMM_EPILOGUE = 0        # hplgb_gemm_config switches
+GEMM_GROUP_M = 1
+GEMM_PAIR_MAX_MN = 2
+
+
+def gemm_config(what: int, value: int) -> None:
+    """Tuning switch of the tensor-core product (see include/hplgb.h)."""
+    _check(load().hplgb_gemm_config(int(what), int(value)), "hplgb_gemm_config")
+
+
+def batched_config(what: int, value: int) -> None:
+    """Residency switch of the batched solver (see include/hplgb.h)."""
+    _check(load().hplgb_batched_config(int(what), int(value)), "hplgb_batched_config")
 
 
 def set_phase_timing(on: bool) -> None:

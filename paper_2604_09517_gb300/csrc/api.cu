@@ -71,6 +71,7 @@ Opts resolve_opts(const hpl_opts* o, int64_t default_nb) {
     r.fp64_emulation = o->fp64_emulation;
     r.pfact = o->pfact;
     r.storage = o->storage;
+    r.inner = o->inner;
     return r;
 }
 

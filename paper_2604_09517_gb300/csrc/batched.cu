@@ -22,8 +22,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <mutex>
 #include <cmath>
 #include <numeric>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -34,7 +36,10 @@ namespace bt {
 constexpr int NBMAX = 32;          // widest panel (storage); variants use 32 or 16
 constexpr int NMAX = 512;          // largest system handled
 constexpr int THREADS = 256;
-constexpr int PS = NBMAX + 1;      // SMEM panel row stride (doubles)
+// SMEM panel row stride (doubles) of a panel NB wide: NB + 1, so that the
+// rows of one column fall in different banks.
+template <int NB>
+constexpr int panel_stride() { return NB + 1; }
 
 struct Sys {
     long long n, lda;
@@ -55,7 +60,7 @@ struct Header {
     unsigned int counter;
     int count;
     int max_iter;
-    int pad;
+    int nb_max;       // widest panel of the plan (16 or 32)
     double tol;
 };
 
@@ -114,7 +119,7 @@ __device__ void upd64(double* A, long long lda, const double* P, int prow, int m
 #pragma unroll
                 for (int i = 0; i < 4; i++) {
                     int r = ti + tx + 16 * i;
-                    a[i] = r < m ? P[(prow + r) * PS + kq] : 0.0;
+                    a[i] = r < m ? P[(prow + r) * panel_stride<NB>() + kq] : 0.0;
                 }
 #pragma unroll
                 for (int j = 0; j < 4; j++) bb[j] = Us[kq * 65 + ty + 16 * j];
@@ -149,7 +154,7 @@ __device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long 
         __syncthreads();
         for (int e = threadIdx.x; e < pm * kb; e += THREADS) {
             int c = e / pm, r = e % pm;
-            P[r * PS + c] = A[(long long)(k0 + c) * lda + k0 + r];
+            P[r * panel_stride<NB>() + c] = A[(long long)(k0 + c) * lda + k0 + r];
         }
         __syncthreads();
         for (int j = 0; j < kb; j++) {
@@ -157,7 +162,7 @@ __device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long 
             // (mag_key: no FP64 compares, which issue at the FP64 rate)
             long long bk = -1, br = 0x7fffffffffffffffLL;
             for (int r = j + threadIdx.x; r < pm; r += THREADS) {
-                const long long k = mag_key(P[r * PS + j]);
+                const long long k = mag_key(P[r * panel_stride<NB>() + j]);
                 if (key_better(k, r, bk, br)) { bk = k; br = r; }
             }
             warp_best(bk, br);
@@ -176,26 +181,26 @@ __device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long 
             if (threadIdx.x == 0) S.ipiv[k0 + j] = k0 + p;
             if (p != j)
                 for (int c = threadIdx.x; c < kb; c += THREADS) {
-                    double t = P[j * PS + c];
-                    P[j * PS + c] = P[p * PS + c];
-                    P[p * PS + c] = t;
+                    double t = P[j * panel_stride<NB>() + c];
+                    P[j * panel_stride<NB>() + c] = P[p * panel_stride<NB>() + c];
+                    P[p * panel_stride<NB>() + c] = t;
                 }
             __syncthreads();
-            const double piv = P[j * PS + j];
+            const double piv = P[j * panel_stride<NB>() + j];
             if (piv == 0.0) {
                 if (!first_zero) first_zero = k0 + j + 1;
                 continue;
             }
             for (int r = j + 1 + threadIdx.x; r < pm; r += THREADS) {
-                double l = P[r * PS + j] / piv;
-                P[r * PS + j] = l;
-                for (int c = j + 1; c < kb; c++) P[r * PS + c] = fma(-l, P[j * PS + c], P[r * PS + c]);
+                double l = P[r * panel_stride<NB>() + j] / piv;
+                P[r * panel_stride<NB>() + j] = l;
+                for (int c = j + 1; c < kb; c++) P[r * panel_stride<NB>() + c] = fma(-l, P[j * panel_stride<NB>() + c], P[r * panel_stride<NB>() + c]);
             }
             __syncthreads();
         }
         for (int e = threadIdx.x; e < pm * kb; e += THREADS) {
             int c = e / pm, r = e % pm;
-            A[(long long)(k0 + c) * lda + k0 + r] = P[r * PS + c];
+            A[(long long)(k0 + c) * lda + k0 + r] = P[r * panel_stride<NB>() + c];
         }
         __syncthreads();
         // interchanges on the other columns. Panels of 16: warp 0 replays the kb
@@ -290,7 +295,7 @@ __device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long 
                     double* col = A + (long long)c * lda + k0;
                     for (int i = 1; i < kb; i++) {
                         double s = col[i];
-                        for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], col[q], s);
+                        for (int q = 0; q < i; q++) s = fma(-P[i * panel_stride<NB>() + q], col[q], s);
                         col[i] = s;
                     }
                 }
@@ -305,7 +310,7 @@ __device__ void lu64(const Sys& S, double* P, double* Us, long long* redk, long 
                     if (i < kb) {
                         double s = x[i];
 #pragma unroll
-                        for (int q = 0; q < i; q++) s = fma(-P[i * PS + q], x[q], s);
+                        for (int q = 0; q < i; q++) s = fma(-P[i * panel_stride<NB>() + q], x[q], s);
                         x[i] = s;
                     }
                 }
@@ -650,7 +655,12 @@ __device__ void mxp_one(const Sys& S, const Header* H, float* X, float* R, float
     }
 }
 
-constexpr size_t SMEM = sizeof(double) * (NMAX * PS + NBMAX * 65) + sizeof(float) * 3 * NBMAX * NBMAX;
+// Dynamic shared memory of a run whose widest panel is NBR: the FP64 panel
+// (NMAX x (NBR + 1)), the U block (NBR x 65), three NBR x NBR FP32 blocks.
+template <int NBR>
+constexpr size_t smem_bytes() {
+    return sizeof(double) * (NMAX * panel_stride<NBR>() + NBR * 65) + sizeof(float) * 3 * NBR * NBR;
+}
 
 }  // namespace bt
 
@@ -706,6 +716,12 @@ extern "C" int hpl_batch_shard(int64_t count, const int64_t* n, const uint8_t* k
     }
     return HPL_OK;
 }
+
+namespace hplgb {
+namespace bt {
+void remember_plan(const void* ws, int nb_max);
+}  // namespace bt
+}  // namespace hplgb
 
 extern "C" size_t solve_batched_workspace_size(int64_t count, const int64_t* n, const uint8_t* kind) {
     if (count <= 0 || !n || !kind) return 256;
@@ -763,6 +779,10 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
     h.count = (int)count;
     h.max_iter = o.max_iter;
     h.tol = o.tol;
+    h.nb_max = 16;
+    for (int64_t s = 0; s < count; s++)
+        if (!variant || variant[s] == 0) h.nb_max = bt::NBMAX;
+    bt::remember_plan(ws, h.nb_max);
     HPL_CUDA_TRY(cudaMemcpy(base, &h, sizeof(h), cudaMemcpyHostToDevice));
     HPL_CUDA_TRY(cudaMemcpy(base + align_up(sizeof(bt::Header), 256), table.data(), sizeof(bt::Sys) * count,
                             cudaMemcpyHostToDevice));
@@ -772,8 +792,33 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
 namespace hplgb {
 namespace bt {
 // Table entries carry the caller's index in `pad`; the kernel writes infos there.
-__global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restrict__ table, Header* H,
-                                                            hpl_info* infos);
+// NBR is the widest panel the launch handles; MINB CTAs share an SM.
+template <int NBR, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_batched_run(const Sys* __restrict__ table, Header* H,
+                                                               hpl_info* infos);
+
+// The widest panel of each planned workspace (host side), so that the run
+// launch picks its kernel without reading the device: a plan whose systems all
+// use 16-wide panels runs two CTAs per SM (79 KB of shared memory each),
+// otherwise one (the 32-wide panel takes 164 KB). A workspace that was not
+// planned in this process gets the one-per-SM kernel, which handles both.
+std::mutex g_plan_mu;
+std::vector<std::pair<const void*, int>> g_plan_nb;
+int g_residency_mode = 0;           // hplgb_batched_config: 0 auto, 1 always one CTA per SM
+
+void remember_plan(const void* ws, int nb_max) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto& e : g_plan_nb)
+        if (e.first == ws) { e.second = nb_max; return; }
+    if (g_plan_nb.size() >= 64) g_plan_nb.erase(g_plan_nb.begin());
+    g_plan_nb.emplace_back(ws, nb_max);
+}
+int planned_nb(const void* ws) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    for (auto& e : g_plan_nb)
+        if (e.first == ws) return e.second;
+    return NBMAX;
+}
 }  // namespace bt
 }  // namespace hplgb
 
@@ -785,16 +830,24 @@ extern "C" int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* 
     const bt::Sys* table = (const bt::Sys*)(base + align_up(sizeof(bt::Header), 256));
     static bool attr = false;
     if (!attr) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt::SMEM));
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run<bt::NBMAX, 1>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)bt::smem_bytes<bt::NBMAX>()));
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run<16, 2>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt::smem_bytes<16>()));
         attr = true;
     }
     int dev = 0, sms = kNumSMsGB300;
     HPL_CUDA_TRY(cudaGetDevice(&dev));
     HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    int grid = max_ctas > 0 ? std::min(max_ctas, sms) : sms;
+    const bool narrow = bt::planned_nb(ws) == 16 && bt::g_residency_mode == 0;
+    const int per_sm = narrow ? 2 : 1;
+    int grid = max_ctas > 0 ? std::min(max_ctas, per_sm * sms) : per_sm * sms;
     HPL_CUDA_TRY(cudaMemsetAsync(&H->counter, 0, sizeof(unsigned int), s));
-    bt::k_batched_run<<<grid, bt::THREADS, bt::SMEM, s>>>(table, H, infos);
+    if (narrow)
+        bt::k_batched_run<16, 2><<<grid, bt::THREADS, bt::smem_bytes<16>(), s>>>(table, H, infos);
+    else
+        bt::k_batched_run<bt::NBMAX, 1><<<grid, bt::THREADS, bt::smem_bytes<bt::NBMAX>(), s>>>(table, H, infos);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
@@ -809,18 +862,19 @@ extern "C" int solve_batched(int64_t count, const int64_t* n, double* const* A, 
 
 namespace hplgb {
 namespace bt {
-__global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restrict__ table, Header* H,
-                                                            hpl_info* infos) {
+template <int NBR, int MINB>
+__global__ void __launch_bounds__(THREADS, MINB) k_batched_run(const Sys* __restrict__ table, Header* H,
+                                                               hpl_info* infos) {
     extern __shared__ double bsm[];
     __shared__ double red[THREADS / 32 + 1];
     __shared__ long long redk[THREADS / 32 + 1];
     __shared__ long long redi[THREADS / 32 + 1];
     __shared__ int s_idx;
     double* P = bsm;
-    double* Us = bsm + NMAX * PS;
-    float* X = (float*)(Us + NBMAX * 65);
-    float* R = X + NBMAX * NBMAX;
-    float* T = R + NBMAX * NBMAX;
+    double* Us = bsm + NMAX * panel_stride<NBR>();
+    float* X = (float*)(Us + NBR * 65);
+    float* R = X + NBR * NBR;
+    float* T = R + NBR * NBR;
     for (;;) {
         if (threadIdx.x == 0) s_idx = (int)atomicAdd(&H->counter, 1u);
         __syncthreads();
@@ -838,15 +892,31 @@ __global__ void __launch_bounds__(THREADS, 1) k_batched_run(const Sys* __restric
         }
         __syncthreads();
         if (S.kind == 0) {
-            if (S.variant) lu64<16>(S, P, Us, redk, redi, info);
-            else lu64<32>(S, P, Us, redk, redi, info);
+            if constexpr (NBR == 16) {
+                lu64<16>(S, P, Us, redk, redi, info);
+            } else {
+                if (S.variant) lu64<16>(S, P, Us, redk, redi, info);
+                else lu64<32>(S, P, Us, redk, redi, info);
+            }
         } else {
             // the FP64 panel area is free in this path: bf16 operand copies
-            if (S.variant) mxp_one<16>(S, H, X, R, T, (float*)P, red, info);
-            else mxp_one<32>(S, H, X, R, T, (float*)P, red, info);
+            if constexpr (NBR == 16) {
+                mxp_one<16>(S, H, X, R, T, (float*)P, red, info);
+            } else {
+                if (S.variant) mxp_one<16>(S, H, X, R, T, (float*)P, red, info);
+                else mxp_one<32>(S, H, X, R, T, (float*)P, red, info);
+            }
         }
         __syncthreads();
     }
 }
+template __global__ void k_batched_run<NBMAX, 1>(const Sys* __restrict__, Header*, hpl_info*);
+template __global__ void k_batched_run<16, 2>(const Sys* __restrict__, Header*, hpl_info*);
 }  // namespace bt
 }  // namespace hplgb
+
+extern "C" int hplgb_batched_config(int what, long long value) {
+    if (what != 0 || value < 0 || value > 1) return HPL_ERR_INVALID;
+    hplgb::bt::g_residency_mode = (int)value;
+    return HPL_OK;
+}

@@ -44,6 +44,7 @@ struct Opts {
     int fp64_emulation;
     int pfact;
     int storage;
+    int inner;
 };
 Opts resolve_opts(const hpl_opts* o, int64_t default_nb);
 

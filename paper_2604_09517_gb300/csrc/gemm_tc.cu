@@ -10,7 +10,12 @@
 // Blackwell design: persistent, warp-specialised kernels, one CTA per SM.
 //   warp 0      : TMA producer (cp.async.bulk.tensor, 128B swizzle)
 //   warp 1      : TMEM allocator and single-thread tcgen05.mma issuer
-//   warps 2..9  : epilogue (tcgen05.ld from TMEM, FP32 read-modify-write of C)
+//   warps 2..9  : epilogue (tcgen05.ld from TMEM, then C updated in FP32)
+// With an FP32 C whose address and leading dimension suit the tensor memory
+// accelerator, the epilogue stages each 32 x 32 chunk of the result in shared
+// memory and hands it to a bulk tensor reduction (C += -(A B^T)) or store, so
+// the SM never reads C: the read-modify-write happens in L2. Otherwise (BF16
+// C, unaligned C) each thread reads and writes its row of C directly.
 // The accumulator lives in TMEM, double buffered, so the epilogue of one tile
 // overlaps the MMAs of the next; K advances 128 bytes per stage (one swizzle
 // row). Tiles are walked in bands of row tiles so the A band stays in L2
@@ -27,6 +32,9 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <climits>
+#include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -61,6 +69,13 @@ struct Tile {
     static constexpr int TMEM_COLS = 2 * BN;            // two accumulators
     static constexpr int DYN_SMEM = STAGES * STAGE_BYTES + 1024;
 };
+// Shared memory of the bulk-tensor epilogue: one 32 x 32 FP32 chunk per
+// epilogue warp (column-major, 128 bytes per column).
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_CHUNK_FLOATS = 32 * 32;
+constexpr int EPI_SMEM = EPI_WARPS * EPI_CHUNK_FLOATS * 4;
+template <int BN, bool TMA_EPI>
+constexpr int dyn_smem() { return Tile<BN>::DYN_SMEM + (TMA_EPI ? EPI_SMEM : 0); }
 
 // Operand kinds: 0 = BF16 (kind::f16, 2 bytes, 64 K per stage), 1 = FP8 E4M3
 // (kind::f8f6f4, 1 byte, 128 K per stage), 2 = FP16 (kind::f16, 2 bytes).
@@ -149,6 +164,55 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
         : "memory");
 }
 
+// Bulk tensor operations from shared memory to global memory (the epilogue):
+// an element-wise add into the tensor (performed in L2), or a plain store.
+// Completion is tracked per thread with bulk async-groups.
+__device__ __forceinline__ void bulk_reduce_add_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.reduce.async.bulk.tensor.2d.global.shared::cta.add.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     (uint64_t)map),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"((uint64_t)map),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// the source shared memory of every committed group has been read
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// every committed group has completed (its global writes are done)
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy writes to shared memory become visible to the async proxy (TMA)
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// One 32-row x 32-column chunk of the product, held by a warp as r[j] =
+// column j of the lane's row, scaled (row scale rs, optional column scales
+// sb over the chunk's columns) and handed to the bulk-tensor epilogue:
+// C += -value (sub) or C = value, at tensor coordinates (x = first row,
+// y = first column). `stage` is the warp's 4 KB chunk of shared memory. The
+// tensor map clips rows and columns outside C, so no masking is needed; only
+// the scale reads are guarded.
+__device__ __forceinline__ void epi_chunk_tma(const CUtensorMap* tmC, float* stage, const uint32_t (&r)[32], float rs,
+                                              const float* sb, int col0, int ncol_left, int sub, int x, int y,
+                                              int lane) {
+    if (lane == 0) bulk_wait_read_all();      // the warp's previous chunk has left the stage
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        float v = __uint_as_float(r[j]) * rs;
+        if (sb) v *= j < ncol_left ? sb[col0 + j] : 0.0f;
+        stage[j * 32 + lane] = sub ? -v : v;
+    }
+    fence_async_smem();
+    __syncwarp();
+    if (lane == 0) {
+        if (sub) bulk_reduce_add_2d(tmC, stage, x, y);
+        else bulk_store_2d(tmC, stage, x, y);
+        bulk_commit();
+    }
+}
+
 // Shared-memory matrix descriptor for a K-major tile stored with the 128-byte
 // swizzle (8 rows x 128 B atoms, 1024-byte aligned): start address >> 4 in
 // bits 0-13, leading byte offset (unused for swizzled K-major; 1) in bits
@@ -215,9 +279,10 @@ __device__ __forceinline__ void tile_coords(int t, int mt_count, int nt_count, i
 
 // C is FP32, or BF16 for a working matrix stored in BF16 (ld_f / st_f: read
 // widened to FP32, the FP32 result rounded to nearest even when stored).
-template <int KIND, int BN, typename CT>
+template <int KIND, int BN, typename CT, bool TMA_EPI>
 __global__ void __launch_bounds__(THREADS, 1)
-    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              const __grid_constant__ CUtensorMap tmC, Params p) {
     constexpr int BK = BKB / Kind<KIND>::ELEM;     // K elements per stage
     constexpr int STAGES = Tile<BN>::STAGES, STAGE_BYTES = Tile<BN>::STAGE_BYTES, TMEM_COLS = Tile<BN>::TMEM_COLS;
     extern __shared__ __align__(1024) unsigned char dsm[];
@@ -311,6 +376,44 @@ __global__ void __launch_bounds__(THREADS, 1)
             umma_commit(&drain_bar);
             mbar_wait(&drain_bar, 0, deadline + 1000000000ull, &s_abort, p.err);
         }
+    } else if constexpr (TMA_EPI) {
+        // ---------------- epilogue: warps 2..9, through shared memory to a bulk tensor reduce ----------------
+        // warp w reads TMEM lane quarter (w & 3) and the column half (w - 2) / 4
+        // of the tile; the accumulator is released as soon as its last chunk
+        // is in registers, so the next tile's MMAs start before the writes end.
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int CHUNKS = BN / 2 / 32;
+        float* stage = (float*)(tiles + STAGES * STAGE_BYTES) + (warp - 2) * EPI_CHUNK_FLOATS;
+        uint32_t tcount = 0;
+        for (int t = blockIdx.x; t < ntiles; t += gridDim.x, tcount++) {
+            int mt, nt;
+            tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
+            const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+            const int row0 = mt * BM + quarter * 32;
+            const int row = row0 + lane;
+            const int cbase = nt * BN + half * (BN / 2);
+            const int ncol = min(BN / 2, p.N - cbase);
+            const float rs = (p.sa && row < p.M) ? p.sa[row] : 1.0f;
+            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < CHUNKS; c++) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * BN + half * (BN / 2) + c * 32, r);
+                tmem_wait_ld();
+                if (c == CHUNKS - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(&tempty_bar[acc]);
+                }
+                if (c * 32 < ncol)
+                    epi_chunk_tma(&tmC, stage, r, rs, p.sb, cbase + c * 32, ncol - c * 32, p.sub, row0,
+                                  cbase + c * 32, lane);
+            }
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     } else {
         // ---------------- epilogue: warps 2..9 ----------------
         // warp w reads TMEM lane quarter (w & 3) and the column half (w - 2) / 4
@@ -401,7 +504,11 @@ __global__ void __launch_bounds__(THREADS, 1)
 constexpr int PAIR_ROWS = 128;                 // rows of A and of B staged by each CTA
 constexpr int PAIR_STAGE_BYTES = 2 * PAIR_ROWS * BKB;
 constexpr int PAIR_STAGES = 7;
-constexpr int PAIR_DYN_SMEM = PAIR_STAGES * PAIR_STAGE_BYTES + 1024;
+constexpr int PAIR_STAGES_TMA_EPI = 6;         // the bulk-tensor epilogue's 32 KB take one stage
+template <bool TMA_EPI>
+constexpr int pair_stages() { return TMA_EPI ? PAIR_STAGES_TMA_EPI : PAIR_STAGES; }
+template <bool TMA_EPI>
+constexpr int pair_dyn_smem() { return pair_stages<TMA_EPI>() * PAIR_STAGE_BYTES + 1024 + (TMA_EPI ? EPI_SMEM : 0); }
 
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc_pair() {
@@ -463,10 +570,12 @@ __device__ __forceinline__ void umma_commit_pair_own(uint64_t* bar) {
                  : "memory");
 }
 
-template <int KIND, typename CT>
+template <int KIND, typename CT, bool TMA_EPI>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
-    k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, Params p) {
+    k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const __grid_constant__ CUtensorMap tmC, Params p) {
     constexpr int BK = BKB / Kind<KIND>::ELEM;
+    constexpr int PAIR_STAGES = pair_stages<TMA_EPI>();
     constexpr int HALF = PAIR_ROWS * BKB;       // bytes of one operand half per stage
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t full_bar[PAIR_STAGES], empty_bar[PAIR_STAGES];
@@ -562,6 +671,42 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
             umma_commit_pair_own(&drain_bar);
             mbar_wait(&drain_bar, 0, deadline + 1000000000ull, &s_abort, p.err);
         }
+    } else if constexpr (TMA_EPI) {
+        // ---------------- epilogue: warps 2..9 of each CTA, its own 128 rows, bulk tensor reduce ----------------
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        constexpr int CHUNKS = 128 / 32;
+        const uint32_t tempty_leader[2] = {cluster_addr(&tempty_bar[0], 0), cluster_addr(&tempty_bar[1], 0)};
+        float* stage = (float*)(tiles + PAIR_STAGES * PAIR_STAGE_BYTES) + (warp - 2) * EPI_CHUNK_FLOATS;
+        uint32_t tcount = 0;
+        for (int t = pair; t < ntiles; t += npairs, tcount++) {
+            int mt, nt;
+            tile_coords(t, mt_count, nt_count, p.group_m, mt, nt);
+            const uint32_t acc = tcount & 1, aph = (tcount >> 1) & 1;
+            const int row0 = mt * 256 + (int)rank * PAIR_ROWS + quarter * 32;
+            const int row = row0 + lane;
+            const int cbase = nt * 256 + half * 128;
+            const int ncol = min(128, p.N - cbase);
+            const float rs = (p.sa && row < p.M) ? p.sa[row] : 1.0f;
+            if (!mbar_wait(&tfull_bar[acc], aph, deadline, &s_abort, p.err)) break;
+            tc_fence_after();
+#pragma unroll 1
+            for (int c = 0; c < CHUNKS; c++) {
+                uint32_t r[32];
+                tmem_ld32(tmem_base + ((uint32_t)(quarter * 32) << 16) + acc * 256 + half * 128 + c * 32, r);
+                tmem_wait_ld();
+                if (c == CHUNKS - 1) {
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_remote(tempty_leader[acc]);
+                }
+                if (c * 32 < ncol)
+                    epi_chunk_tma(&tmC, stage, r, rs, p.sb, cbase + c * 32, ncol - c * 32, p.sub, row0,
+                                  cbase + c * 32, lane);
+            }
+        }
+        if (lane == 0) bulk_wait_all();
+        __syncwarp();
     } else {
         // ---------------- epilogue: warps 2..9 of each CTA, its own 128 rows ----------------
         const int quarter = warp & 3;
@@ -664,6 +809,56 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, i
     return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
 }
 
+// C (FP32, column-major): rows x cols, leading dimension ld; box of 32 x 32
+// (the epilogue's chunk), no swizzle.
+static int make_map_c(CUtensorMap* m, const float* base, int64_t rows, int64_t cols, int64_t ld) {
+    EncodeTiledFn enc = get_encode();
+    if (!enc) return HPL_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, 32};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
+}
+
+// Tuning and diagnostics (hplgb_gemm_config): the epilogue kind (0: the
+// bulk-tensor epilogue wherever C allows it, 1: always the per-thread one),
+// an override of the band height of the tile walk (0: the per-kind default),
+// and of the largest product (M x N) given to the pair kernel (0: default,
+// < 0: never).
+static int g_epilogue_mode = 0;
+static int g_group_m_override = 0;
+static long long g_pair_max_mn = 0;
+
+// The bulk-tensor epilogue: FP32 C at a 16-byte aligned address with a
+// leading dimension that is a multiple of 4 (TMA strides are multiples of 16
+// bytes), and rows / columns within the tensor map's 32-bit extents.
+template <typename CT>
+static bool tma_epilogue_ok(const CT* C, int64_t ldc) {
+    if constexpr (!std::is_same<CT, float>::value) {
+        return false;
+    } else {
+        return g_epilogue_mode == 0 && ((uintptr_t)C & 15) == 0 && ldc % 4 == 0;
+    }
+}
+
+template <int KIND, int BN, typename CT, bool TMA_EPI>
+static int launch_kind_epi(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, const Params& p,
+                           int grid, cudaStream_t s) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN, CT, TMA_EPI>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem<BN, TMA_EPI>()));
+        attr_set = true;
+    }
+    k_gemm_tc<KIND, BN, CT, TMA_EPI><<<grid, THREADS, dyn_smem<BN, TMA_EPI>(), s>>>(ma, mb, mc, p);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
 template <int KIND, int BN, typename CT = float>
 static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                        const float* sa, const float* sb, CT* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
@@ -675,16 +870,15 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     // TMA: 16-byte aligned base addresses and row strides
     if (lda < K || ldb < K || ldc < M || (lda * elem) % 16 || (ldb * elem) % 16) return HPL_ERR_INVALID;
     if (((uintptr_t)A | (uintptr_t)B) & 15) return HPL_ERR_INVALID;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mc;
     int st = make_map(&ma, A, M, K, lda, BM, elem);
     if (st) return st;
     st = make_map(&mb, B, N, K, ldb, BN, elem);
     if (st) return st;
-    static bool attr_set = false;
-    if (!attr_set) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN, CT>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, Tile<BN>::DYN_SMEM));
-        attr_set = true;
+    const bool tma_epi = tma_epilogue_ok(C, ldc);
+    memset(&mc, 0, sizeof(mc));
+    if constexpr (std::is_same<CT, float>::value) {
+        if (tma_epi && (st = make_map_c(&mc, C, M, N, ldc))) return st;
     }
     int dev = 0, sms = kNumSMsGB300;
     HPL_CUDA_TRY(cudaGetDevice(&dev));
@@ -702,10 +896,34 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
-    p.group_m = group_m<KIND>();
-    k_gemm_tc<KIND, BN, CT><<<grid, THREADS, Tile<BN>::DYN_SMEM, s>>>(ma, mb, p);
-    HPL_LAUNCH_CHECK();
-    return HPL_OK;
+    p.group_m = g_group_m_override > 0 ? g_group_m_override : group_m<KIND>();
+    if (tma_epi) return launch_kind_epi<KIND, BN, CT, true>(ma, mb, mc, p, grid, s);
+    return launch_kind_epi<KIND, BN, CT, false>(ma, mb, mc, p, grid, s);
+}
+
+// Clusters of the pair kernel that fit on the GPU at once (set-up once per
+// instantiation; -1 on a CUDA error).
+template <int KIND, typename CT, bool TMA_EPI>
+static int pair_capacity() {
+    static int max_pairs = 0;
+    if (!max_pairs) {
+        const void* f = (const void*)k_gemm_tc_pair<KIND, CT, TMA_EPI>;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_dyn_smem<TMA_EPI>()) !=
+            cudaSuccess)
+            return -1;
+        int dev = 0, sms = kNumSMsGB300;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return -1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3((unsigned)(sms & ~1));
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = pair_dyn_smem<TMA_EPI>();
+        int nc = 0;
+        if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) != cudaSuccess) return -1;
+        max_pairs = nc > 0 ? nc : sms / 2;
+    }
+    return max_pairs;
 }
 
 // The pair kernel: grid = 2 x min(tiles, clusters that fit at once).
@@ -719,26 +937,18 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if (M > 0x7fffffff || N > 0x7fffffff || K > 0x7fffffff) return HPL_ERR_INVALID;
     if (lda < K || ldb < K || ldc < M || (lda * elem) % 16 || (ldb * elem) % 16) return HPL_ERR_INVALID;
     if (((uintptr_t)A | (uintptr_t)B) & 15) return HPL_ERR_INVALID;
-    CUtensorMap ma, mb;
+    CUtensorMap ma, mb, mc;
     int st = make_map(&ma, A, M, K, lda, PAIR_ROWS, elem);
     if (st) return st;
     st = make_map(&mb, B, N, K, ldb, PAIR_ROWS, elem);
     if (st) return st;
-    static int max_pairs = 0;
-    if (!max_pairs) {
-        HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc_pair<KIND, CT>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, PAIR_DYN_SMEM));
-        int dev = 0, sms = kNumSMsGB300;
-        HPL_CUDA_TRY(cudaGetDevice(&dev));
-        HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3((unsigned)(sms & ~1));
-        cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = PAIR_DYN_SMEM;
-        int nc = 0;
-        HPL_CUDA_TRY(cudaOccupancyMaxActiveClusters(&nc, (const void*)k_gemm_tc_pair<KIND, CT>, &cfg));
-        max_pairs = nc > 0 ? nc : sms / 2;
+    const bool tma_epi = tma_epilogue_ok(C, ldc);
+    memset(&mc, 0, sizeof(mc));
+    if constexpr (std::is_same<CT, float>::value) {
+        if (tma_epi && (st = make_map_c(&mc, C, M, N, ldc))) return st;
     }
+    const int max_pairs = tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>();
+    if (max_pairs < 0) return HPL_ERR_CUDA;
     const int64_t ntiles = ((M + 255) / 256) * ((N + 255) / 256);
     int pairs = (int)std::min<int64_t>(ntiles, max_pairs);
     if (max_ctas > 0) pairs = std::max(1, std::min(pairs, max_ctas / 2));
@@ -753,15 +963,23 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
-    p.group_m = GROUP_M_PAIR;
-    k_gemm_tc_pair<KIND, CT><<<2 * pairs, THREADS, PAIR_DYN_SMEM, s>>>(ma, mb, p);
+    p.group_m = g_group_m_override > 0 ? g_group_m_override : GROUP_M_PAIR;
+    if (tma_epi)
+        k_gemm_tc_pair<KIND, CT, true><<<2 * pairs, THREADS, pair_dyn_smem<true>(), s>>>(ma, mb, mc, p);
+    else
+        k_gemm_tc_pair<KIND, CT, false><<<2 * pairs, THREADS, pair_dyn_smem<false>(), s>>>(ma, mb, mc, p);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
 
-// A product of moderate size with a 256 x 256 tile for every SM pair: the pair kernel.
-static bool pair_tiles(int64_t M, int64_t N) {
-    return M * N <= HPLGB_PAIR_MAX_MN && ((M + 255) / 256) * ((N + 255) / 256) >= kNumSMsGB300 / 2;
+// A product with a 256 x 256 tile for every SM pair goes to the pair kernel:
+// any size when its epilogue is the bulk-tensor one (measured faster than the
+// single-CTA kernel at every size: M = N = 20480 and 49152, K = 4096, BF16 +9
+// and +4 %, FP8 +8 and +7 %), otherwise only up to HPLGB_PAIR_MAX_MN (with the
+// per-thread epilogue the single-CTA kernel is as fast on large updates).
+static bool pair_tiles(int64_t M, int64_t N, bool tma_epi) {
+    const long long max_mn = g_pair_max_mn != 0 ? g_pair_max_mn : (tma_epi ? LLONG_MAX : HPLGB_PAIR_MAX_MN);
+    return M * N <= max_mn && ((M + 255) / 256) * ((N + 255) / 256) >= kNumSMsGB300 / 2;
 }
 
 // Fewer 128 x 256 tiles than SMs: use 128 x 128 tiles.
@@ -775,7 +993,7 @@ static bool narrow_tiles(int64_t M, int64_t N) {
 // one CTA per SM. err: device int that receives HPL_ERR_TIMEOUT on a timeout.
 int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                      float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
-    if (tc::pair_tiles(M, N))
+    if (tc::pair_tiles(M, N, tc::tma_epilogue_ok(C, ldc)))
         return tc::launch_pair<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns,
@@ -789,7 +1007,7 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s) {
-    if (tc::pair_tiles(M, N))
+    if (tc::pair_tiles(M, N, tc::tma_epilogue_ok(C, ldc)))
         return tc::launch_pair<1>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<1, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
@@ -802,7 +1020,7 @@ int launch_gemm_bf16_c16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int
                          int64_t ldb, uint16_t* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas,
                          cudaStream_t s) {
     __nv_bfloat16* Cb = reinterpret_cast<__nv_bfloat16*>(C);
-    if (tc::pair_tiles(M, N))
+    if (tc::pair_tiles(M, N, tc::tma_epilogue_ok(Cb, ldc)))
         return tc::launch_pair<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, Cb, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, Cb, ldc, sub, err, timeout_ns,
@@ -815,7 +1033,7 @@ int launch_gemm_bf16_c16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int
 int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s) {
-    if (tc::pair_tiles(M, N))
+    if (tc::pair_tiles(M, N, tc::tma_epilogue_ok(C, ldc)))
         return tc::launch_pair<2>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
     if (tc::narrow_tiles(M, N))
         return tc::launch_kind<2, 128>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
@@ -825,6 +1043,24 @@ int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t 
 }  // namespace hplgb
 
 using namespace hplgb;
+
+extern "C" int hplgb_gemm_config(int what, long long value) {
+    switch (what) {
+        case 0:
+            if (value < 0 || value > 1) return HPL_ERR_INVALID;
+            tc::g_epilogue_mode = (int)value;
+            return HPL_OK;
+        case 1:
+            if (value < 0 || value > 4096) return HPL_ERR_INVALID;
+            tc::g_group_m_override = (int)value;
+            return HPL_OK;
+        case 2:
+            tc::g_pair_max_mn = value;
+            return HPL_OK;
+        default:
+            return HPL_ERR_INVALID;
+    }
+}
 
 extern "C" int hplgb_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
                                int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream) {

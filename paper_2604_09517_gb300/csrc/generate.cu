@@ -9,6 +9,8 @@
 // generator (Sec. II-B); this definition is the library's own.
 #include <algorithm>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace hplgb {
@@ -109,10 +111,13 @@ __device__ __forceinline__ float gen_store(__nv_bfloat16* p, uint64_t h) {
     return __bfloat162float(v);
 }
 
+// A32 (optional, n x n, ld n) receives the FP32 rounding of each entry as
+// well (GMRES's inner products in FP32 data).
 template <typename FT>
 __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, FT* __restrict__ F, int64_t ldf,
                                                       int chunks, uint64_t* __restrict__ plo,
-                                                      uint64_t* __restrict__ phi, float* __restrict__ pf) {
+                                                      uint64_t* __restrict__ phi, float* __restrict__ pf,
+                                                      float* __restrict__ A32) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const int64_t cw = (n + chunks - 1) / chunks;
@@ -124,6 +129,13 @@ __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, F
     for (int64_t j = j0; j < j1; j++, z += step) {
         const uint64_t h = sm64_mix(z);
         const float v = gen_store(F + j * ldf + i, h);
+        if (A32) {
+            if constexpr (std::is_same<FT, float>::value) {
+                A32[j * n + i] = v;
+            } else {
+                A32[j * n + i] = __ll2float_rn((long long)(h >> 11) - (1LL << 52)) * 0x1p-53f;
+            }
+        }
         const uint64_t m = h >> 11, u = m >= (1ull << 52) ? m - (1ull << 52) : (1ull << 52) - m;
         const uint64_t nl = lo + u;
         hi += (nl < lo);
@@ -141,7 +153,8 @@ __global__ void __launch_bounds__(256) k_generate_f32(uint64_t key, int64_t n, F
 template <typename FT>
 __global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks, const uint64_t* __restrict__ plo,
                                                            const uint64_t* __restrict__ phi, double* __restrict__ diag,
-                                                           FT* __restrict__ F, int64_t ldf, float* __restrict__ pf) {
+                                                           FT* __restrict__ F, int64_t ldf, float* __restrict__ pf,
+                                                           float* __restrict__ A32) {
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     uint64_t lo = 0, hi = 0;
@@ -153,6 +166,7 @@ __global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks
     const double d = u128_to_double_rn(hi, lo) * 0x1p-53;
     diag[i] = d;
     const float f = st_f64(F + i * ldf + i, d);
+    if (A32) A32[i * n + i] = f64_to_f32_rn(d);
     const int64_t cw = (n + chunks - 1) / chunks;
     pf[(i / cw) * n + i] += fabsf(f);
 }
@@ -164,21 +178,21 @@ __global__ void __launch_bounds__(256) k_dominant_diag_fin(int64_t n, int chunks
 // receives the row sums of |F| split by column chunk.
 int launch_generate_dominant_f32(uint64_t seed, int64_t n, void* F, int64_t ldf, int bf16, double* diag,
                                  uint64_t* key_out, int chunks, uint64_t* plo, uint64_t* phi, float* pf,
-                                 cudaStream_t s) {
+                                 float* A32, cudaStream_t s) {
     const uint64_t key = sm64_host_mix(seed + 1 * kGamma);
     if (key_out) *key_out = key;
     if (n <= 0) return HPL_OK;
     const dim3 g1((unsigned)((n + 255) / 256), (unsigned)chunks), g2((unsigned)((n + 255) / 256));
     if (bf16) {
         __nv_bfloat16* Fb = (__nv_bfloat16*)F;
-        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Fb, ldf, chunks, plo, phi, pf);
+        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Fb, ldf, chunks, plo, phi, pf, A32);
         HPL_LAUNCH_CHECK();
-        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Fb, ldf, pf);
+        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Fb, ldf, pf, A32);
     } else {
         float* Ff = (float*)F;
-        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Ff, ldf, chunks, plo, phi, pf);
+        k_generate_f32<<<g1, 256, 0, s>>>(key, n, Ff, ldf, chunks, plo, phi, pf, A32);
         HPL_LAUNCH_CHECK();
-        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Ff, ldf, pf);
+        k_dominant_diag_fin<<<g2, 256, 0, s>>>(n, chunks, plo, phi, diag, Ff, ldf, pf, A32);
     }
     HPL_LAUNCH_CHECK();
     return HPL_OK;

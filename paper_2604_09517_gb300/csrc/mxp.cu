@@ -49,7 +49,7 @@ int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, c
                         cudaStream_t s);
 int launch_generate_dominant_f32(uint64_t seed, int64_t n, void* F, int64_t ldf, int bf16, double* diag,
                                  uint64_t* key_out, int chunks, uint64_t* plo, uint64_t* phi, float* pf,
-                                 cudaStream_t s);
+                                 float* A32, cudaStream_t s);
 int launch_residual_vec_t(int64_t n, const double* A, int64_t lda, double* anorm, int norm_mode, const double* x,
                           const double* b, double* r, double* sr, void* ws, cudaStream_t s);
 
@@ -274,10 +274,17 @@ __global__ void __launch_bounds__(256) k_abs_rowsum_max(int64_t n, int chunks, c
 // FP32 working copy F of A; on the way, the row sums of |F| over `stripes`
 // column stripes into part[stripe][row] (the refinement's ||A||_inf, reduced
 // by k_abs_rowsum_max), so the norm costs no extra pass over the matrix.
+// A32 (optional, n x n, ld n): the FP32 rounding of A as well, for GMRES's
+// inner matrix-vector products.
+__device__ __forceinline__ void st_a32(float* A32, int64_t idx, double d, float stored, bool fp32_stored) {
+    if (A32) A32[idx] = fp32_stored ? stored : f64_to_f32_rn(d);
+}
+
 template <typename FT>
 __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double* __restrict__ A, int64_t lda,
                                                         FT* __restrict__ F, int64_t ldf, int stripes,
-                                                        float* __restrict__ part) {
+                                                        float* __restrict__ part, float* __restrict__ A32) {
+    constexpr bool kF32 = std::is_same<FT, float>::value;
     const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x;
     if (i >= n) return;
     const int64_t cw = (n + stripes - 1) / stripes;
@@ -287,11 +294,17 @@ __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double*
 #pragma unroll 4
     for (; j + 1 < j1; j += 2) {
         const double d0 = A[j * lda + i], d1 = A[(j + 1) * lda + i];
-        s0 += fabsf(st_f64(F + j * ldf + i, d0));
-        s1 += fabsf(st_f64(F + (j + 1) * ldf + i, d1));
+        const float v0 = st_f64(F + j * ldf + i, d0), v1 = st_f64(F + (j + 1) * ldf + i, d1);
+        st_a32(A32, j * n + i, d0, v0, kF32);
+        st_a32(A32, (j + 1) * n + i, d1, v1, kF32);
+        s0 += fabsf(v0);
+        s1 += fabsf(v1);
     }
     if (j < j1) {
-        s0 += fabsf(st_f64(F + j * ldf + i, A[j * lda + i]));
+        const double d0 = A[j * lda + i];
+        const float v0 = st_f64(F + j * ldf + i, d0);
+        st_a32(A32, j * n + i, d0, v0, kF32);
+        s0 += fabsf(v0);
     }
     part[(int64_t)blockIdx.y * n + i] = s0 + s1;
 }
@@ -301,7 +314,7 @@ __global__ void __launch_bounds__(256) k_f64_to_f32_mat(int64_t n, const double*
 // would leave every line half written by each warp). n and ldf even.
 __global__ void __launch_bounds__(256) k_f64_to_bf16_mat2(int64_t n, const double* __restrict__ A, int64_t lda,
                                                           __nv_bfloat16* __restrict__ F, int64_t ldf, int stripes,
-                                                          float* __restrict__ part) {
+                                                          float* __restrict__ part, float* __restrict__ A32) {
     const int64_t i = 2 * ((int64_t)blockIdx.x * 256 + threadIdx.x);
     if (i >= n) return;
     const int64_t cw = (n + stripes - 1) / stripes;
@@ -314,6 +327,7 @@ __global__ void __launch_bounds__(256) k_f64_to_bf16_mat2(int64_t n, const doubl
         v.x = f64_to_bf16_rn(a.x);
         v.y = f64_to_bf16_rn(a.y);
         *reinterpret_cast<__nv_bfloat162*>(F + j * ldf + i) = v;
+        if (A32) *reinterpret_cast<float2*>(A32 + j * n + i) = make_float2(f64_to_f32_rn(a.x), f64_to_f32_rn(a.y));
         s0 += fabsf(__bfloat162float(v.x));
         s1 += fabsf(__bfloat162float(v.y));
     }
@@ -381,6 +395,98 @@ __global__ void k_gemv_combine(int64_t rows, int nsplit, const float* __restrict
         float s = 0.f;
         for (int q = 0; q < nsplit; q++) s += part[q * ldpart + r];
         y[r] = sub ? y[r] - s : s;
+    }
+}
+
+// GMRES's inner product w = A32 z in FP32 data (opts.inner = FP32): A32 is
+// the FP32 copy of A (n x n, ld lda), z the FP32 rounding of the vector. Each
+// CTA takes 128 rows (4 per lane, float4 loads when aligned) and one column
+// chunk, its 8 warps split the chunk's columns; every thread sums blocks of 32
+// of its products in FP32 and adds each block into FP64 accumulators, so the
+// result carries about the FP32 rounding of A and z and little of the summation.
+// part[s][r] holds chunk s's FP64 sum; k_matvec32_combine adds the chunks in
+// order (the result does not depend on scheduling).
+__global__ void __launch_bounds__(256) k_matvec32_part(int64_t n, const float* __restrict__ A, int64_t lda,
+                                                       const float* __restrict__ z, int64_t chunk,
+                                                       double* __restrict__ part, int vec) {
+    __shared__ double red[8][129];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int64_t r = (int64_t)blockIdx.x * 128 + 4 * lane;
+    const int64_t c0 = (int64_t)blockIdx.y * chunk, c1 = min(n, c0 + chunk);
+    const bool v4 = vec && r + 3 < n;
+    double d0 = 0.0, d1 = 0.0, d2 = 0.0, d3 = 0.0;
+    int64_t c = c0 + warp;
+    // blocks of 32 of the warp's columns (a fixed trip count, so the loads
+    // pipeline): FP32 sums, then one FP64 add per row
+    for (; c + 8 * 31 < c1; c += 8 * 32) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        if (v4) {
+#pragma unroll 8
+            for (int q = 0; q < 32; q++) {
+                const float4 v = *reinterpret_cast<const float4*>(A + (c + 8 * q) * lda + r);
+                const float zc = __ldg(z + c + 8 * q);
+                a0 = fmaf(v.x, zc, a0);
+                a1 = fmaf(v.y, zc, a1);
+                a2 = fmaf(v.z, zc, a2);
+                a3 = fmaf(v.w, zc, a3);
+            }
+        } else {
+#pragma unroll 4
+            for (int q = 0; q < 32; q++) {
+                const float zc = __ldg(z + c + 8 * q);
+                const float* pc = A + (c + 8 * q) * lda;
+                if (r < n) a0 = fmaf(pc[r], zc, a0);
+                if (r + 1 < n) a1 = fmaf(pc[r + 1], zc, a1);
+                if (r + 2 < n) a2 = fmaf(pc[r + 2], zc, a2);
+                if (r + 3 < n) a3 = fmaf(pc[r + 3], zc, a3);
+            }
+        }
+        d0 += a0;
+        d1 += a1;
+        d2 += a2;
+        d3 += a3;
+    }
+    {   // the rest: fewer than 32 of the warp's columns
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        for (; c < c1; c += 8) {
+            const float zc = __ldg(z + c);
+            const float* pc = A + c * lda;
+            if (v4) {
+                const float4 v = *reinterpret_cast<const float4*>(pc + r);
+                a0 = fmaf(v.x, zc, a0);
+                a1 = fmaf(v.y, zc, a1);
+                a2 = fmaf(v.z, zc, a2);
+                a3 = fmaf(v.w, zc, a3);
+            } else {
+                if (r < n) a0 = fmaf(pc[r], zc, a0);
+                if (r + 1 < n) a1 = fmaf(pc[r + 1], zc, a1);
+                if (r + 2 < n) a2 = fmaf(pc[r + 2], zc, a2);
+                if (r + 3 < n) a3 = fmaf(pc[r + 3], zc, a3);
+            }
+        }
+        d0 += a0;
+        d1 += a1;
+        d2 += a2;
+        d3 += a3;
+    }
+    red[warp][4 * lane] = d0;
+    red[warp][4 * lane + 1] = d1;
+    red[warp][4 * lane + 2] = d2;
+    red[warp][4 * lane + 3] = d3;
+    __syncthreads();
+    if (threadIdx.x < 128) {
+        const int64_t rr = (int64_t)blockIdx.x * 128 + threadIdx.x;
+        double t = 0.0;
+        for (int w = 0; w < 8; w++) t += red[w][threadIdx.x];
+        if (rr < n) part[blockIdx.y * n + rr] = t;
+    }
+}
+
+__global__ void k_matvec32_combine(int64_t n, int nsplit, const double* __restrict__ part, double* __restrict__ w) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        double t = 0.0;
+        for (int q = 0; q < nsplit; q++) t += part[q * n + r];
+        w[r] = t;
     }
 }
 
@@ -720,10 +826,13 @@ struct MxpWs {
     double* Rb;        // n x nrhs_blk FP64 residuals / corrections
     double* partb;     // kBlkSplit x n x nrhs_blk FP64 K slices of the residual
     unsigned long long* cmax;   // 3 x nrhs_blk column maxima
+    // GMRES's inner products in FP32 data (opts.inner = FP32; absent otherwise)
+    float* A32;        // n x n FP32 copy of A
+    double* mvpart;    // kGemvSplitMax x n FP64 chunk sums of A32 z
 };
 
 static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, int64_t nrhs_blk = 0,
-                            int fbytes = 4) {
+                            int fbytes = 4, int a32 = 0) {
     const int64_t nb8 = round8(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -763,6 +872,9 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, 
     t.Rb = (double*)take(sizeof(double) * n * nrhs_blk);
     t.partb = (double*)take(sizeof(double) * kBlkSplit * n * nrhs_blk);
     t.cmax = (unsigned long long*)take(sizeof(unsigned long long) * 3 * nrhs_blk);
+    // last, so that every offset above (the factor's included) is the same with or without it
+    t.A32 = a32 ? (float*)take(sizeof(float) * n * n) : nullptr;
+    t.mvpart = a32 ? (double*)take(sizeof(double) * kGemvSplitMax * n) : nullptr;
     if (w) *w = t;
     return off;
 }
@@ -845,23 +957,23 @@ struct Mxp {
                 paired = n % 2 == 0 && lda % 2 == 0 && ((uintptr_t)A & 15) == 0;
                 if (paired)
                     k_f64_to_bf16_mat2<<<dim3((unsigned)((n + 511) / 512), kGemvSplitMax), 256, 0, s>>>(
-                        n, A, lda, F(), ldf, kGemvSplitMax, w.gpart);
+                        n, A, lda, F(), ldf, kGemvSplitMax, w.gpart, w.A32);
             }
             if (!paired)
                 k_f64_to_f32_mat<<<dim3((unsigned)((n + 255) / 256), kGemvSplitMax), 256, 0, s>>>(
-                    n, A, lda, F(), ldf, kGemvSplitMax, w.gpart);
+                    n, A, lda, F(), ldf, kGemvSplitMax, w.gpart, w.A32);
             HPL_LAUNCH_CHECK();
         } else {
             // one pass: the FP32 entries, the exact diagonal and the norm's row sums
             int st = launch_generate_dominant_f32(seed, n, F(), ldf, kBf16 ? 1 : 0, w.gdiag, &key, kGemvSplitMax,
-                                                  w.glo, w.ghi, w.gpart, s);
+                                                  w.glo, w.ghi, w.gpart, w.A32, s);
             if (st) return st;
         }
         HPL_CUDA_TRY(cudaMemsetAsync(w.scal + 6, 0, sizeof(double), s));
         k_abs_rowsum_max<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, kGemvSplitMax, w.gpart,
                                                                      (unsigned long long*)(w.scal + 6));
         HPL_LAUNCH_CHECK();
-        phase_end(cslot, s, PH_CONVERT, A ? 12.0 * n * n : 8.0 * n * n);
+        phase_end(cslot, s, PH_CONVERT, (A ? 12.0 * n * n : 8.0 * n * n) + (w.A32 ? 4.0 * n * n : 0.0));
         for (int64_t k0 = 0; k0 < n; k0 += nb) {
             const int64_t kb = std::min(nb, n - k0), m2 = n - k0 - kb, kb8 = round8(kb), K3 = 3 * kb8;
             int slot = phase_begin(s);
@@ -1053,6 +1165,26 @@ struct Mxp {
         return HPL_OK;
     }
 
+    // out = A32 fl32(z) (FP64 out): GMRES's inner product in FP32 data.
+    int matvec32(const double* z, double* out) {
+        int slot = phase_begin(s);
+        float* z32 = w.y32;
+        k_f64_to_f32<<<grid_for(n), 256, 0, s>>>(n, z, z32);
+        HPL_LAUNCH_CHECK();
+        const int64_t rb = (n + 127) / 128;
+        int64_t nsplit = std::min<int64_t>(kGemvSplitMax, std::max<int64_t>(1, (1216 + rb - 1) / rb));
+        nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, n / 64));
+        const int64_t chunk = (n + nsplit - 1) / nsplit;
+        nsplit = (n + chunk - 1) / chunk;
+        const int vec = n % 4 == 0;
+        k_matvec32_part<<<dim3((unsigned)rb, (unsigned)nsplit), 256, 0, s>>>(n, w.A32, n, z32, chunk, w.mvpart, vec);
+        HPL_LAUNCH_CHECK();
+        k_matvec32_combine<<<grid_for(n), 256, 0, s>>>(n, (int)nsplit, w.mvpart, out);
+        HPL_LAUNCH_CHECK();
+        phase_end(slot, s, PH_RESID, 4.0 * n * n);
+        return HPL_OK;
+    }
+
     // GMRES correction: d solves A d = r approximately (right preconditioning).
     int gmres(const double* r, double* d, int* inner) {
         const int64_t ldv = n;
@@ -1075,7 +1207,7 @@ struct Mxp {
             double* wv = w.V + (int64_t)(j + 1) * ldv;
             if ((st = precond(vj, zj))) return st;
             (*inner)++;
-            if ((st = resid(zj, nullptr, wv, nullptr))) return st;
+            if ((st = (w.A32 && !trans) ? matvec32(zj, wv) : resid(zj, nullptr, wv, nullptr))) return st;
             for (int i = 0; i <= j; i++) {
                 double* hij = w.h + (int64_t)j * (m + 1) + i;
                 if ((st = dot(wv, w.V + (int64_t)i * ldv, hij, 0))) return st;
@@ -1286,6 +1418,9 @@ static int64_t block_rhs(int64_t nrhs, const Opts& o) { return (nrhs > 1 && o.re
 
 static int fbytes_of(const Opts& o) { return o.storage == HPL_STORAGE_BF16 ? 2 : 4; }
 
+// The FP32 copy of A for GMRES's inner products (opts.inner = FP32, GMRES only).
+static int a32_of(const Opts& o) { return o.inner == HPL_INNER_FP32 && o.refine == HPL_REFINE_GMRES ? 1 : 0; }
+
 // Option checks shared by the solve and its adjoint: the precision, and BF16
 // storage only with BF16 operands.
 static bool mxp_opts_ok(const Opts& o) {
@@ -1298,7 +1433,8 @@ static bool mxp_opts_ok(const Opts& o) {
 extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* opts) {
     Opts o = resolve_opts(opts, kMxpDefaultNb);
     int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
-    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o), fbytes_of(o));
+    return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o), fbytes_of(o),
+                         a32_of(o));
 }
 
 template <typename FT>
@@ -1315,10 +1451,10 @@ static int mxp_solve_t(int64_t n, int64_t nrhs, const double* A, int64_t lda, ui
     mx.lda = lda;
     mx.seed = seed;
     mx.nblk = A ? block_rhs(nrhs, o) : 0;       // the block residual reads a stored A
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o));
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o), a32_of(o));
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o));
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o), a32_of(o));
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     int st = mx.factor(info);
@@ -1364,6 +1500,7 @@ extern "C" int mxp_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, 
     if (!mxp_opts_ok(o)) return HPL_ERR_INVALID;
     if (o.refine != HPL_REFINE_IR && o.refine != HPL_REFINE_GMRES) return HPL_ERR_INVALID;
     if (o.ns_iters > 8) return HPL_ERR_INVALID;
+    if (o.inner != HPL_INNER_FP64 && o.inner != HPL_INNER_FP32) return HPL_ERR_INVALID;
     if (o.storage == HPL_STORAGE_BF16)
         return mxp_solve_t<__nv_bfloat16>(n, nrhs, A, lda, seed, B, ldb, X, ldx, o, ws, ws_bytes, info, stream);
     return mxp_solve_t<float>(n, nrhs, A, lda, seed, B, ldb, X, ldx, o, ws, ws_bytes, info, stream);

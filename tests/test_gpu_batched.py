@@ -164,3 +164,34 @@ def test_batched_share_matches_whole_batch(hpl):
             if kind[g] == 0:
                 assert torch.equal(part.pivots(j), whole.pivots(int(g)))
                 assert torch.equal(part.matrix(j), whole.matrix(int(g)))
+
+
+def test_batched_two_ctas_per_sm_same_results(hpl, orc):
+    """A plan whose systems all use 16-wide panels runs two CTAs per SM; the
+    one-per-SM kernel gives the same pivots and solutions bit for bit (the same
+    per-system code), and both meet the oracle's checks."""
+    import torch
+    n = np.array([32, 33, 64, 100, 127, 200, 256, 300, 511, 512] * 4, dtype=np.int64)
+    kind = np.array([0, 1] * 20, dtype=np.uint8)
+    out = []
+    try:
+        for mode in (0, 1):
+            hpl.batched_config(0, mode)
+            bt = hpl.Batch(n, kind)
+            bt.generate(17)
+            if mode == 0:
+                A0 = [_np(bt.matrix(s)).copy(order="F") for s in range(bt.count)]
+                b0 = [_np(bt.rhs(s)).copy() for s in range(bt.count)]
+            bt.plan(variant=1)
+            bt.run()
+            torch.cuda.synchronize()
+            out.append((bt.B.clone(), bt.ipiv.clone(), [r["status"] for r in bt.info()]))
+            if mode == 0:
+                for s in range(bt.count):
+                    _check_system(orc, bt, s, A0[s], b0[s], emulate=False)
+    finally:
+        hpl.batched_config(0, 0)
+    assert torch.equal(out[0][0], out[1][0]) and torch.equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+    with pytest.raises(hpl.HplError):
+        hpl.batched_config(1, 0)

@@ -123,3 +123,53 @@ def test_gemm_bf16_small_integer_products_are_exact(hpl, M, N, K):
     exact = Ai[:, :K].double() @ Bi[:, :K].double().t()     # integers below 2^53: exact in FP64
     assert exact.abs().max().item() < 2 ** 24
     assert torch.equal(C.double(), exact)
+
+
+@pytest.mark.parametrize("kind", ["bf16", "fp8", "f16"])
+@pytest.mark.parametrize("M,N,K,sub", [(300, 500, 208, True), (2404, 2300, 208, True), (1540, 1030, 96, False),
+                                       (2304, 2560, 256, True), (64, 4096, 128, True)])
+def test_gemm_epilogues_bit_identical(hpl, kind, M, N, K, sub):
+    """The bulk-tensor epilogue (C += -(A B^T) reduced in L2 from shared
+    memory, or stored) against the per-thread one (each thread reads and
+    writes its row of C): the same bits, for every operand kind, with scales,
+    ragged tile edges and both kernels (sizes with >= 76 tiles of 256 x 256 go
+    to the pair kernel)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M * 7 + N + K)
+    ld = (K + 15) // 16 * 16
+    if kind == "bf16":
+        A = torch.randn(M, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+        B = torch.randn(N, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+    elif kind == "fp8":
+        A = (torch.randn(M, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+        B = (torch.randn(N, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+    else:
+        A = torch.randn(M, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
+        B = torch.randn(N, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
+    sa = torch.pow(2.0, torch.randint(-4, 4, (M,), device="cuda", generator=g).float())
+    sb = torch.pow(2.0, torch.randint(-4, 4, (N,), device="cuda", generator=g).float())
+    C0 = hpl.colmajor(M, N, dtype=torch.float32)
+    C0.copy_(torch.randn(M, N, device="cuda", generator=g))
+    out = []
+    try:
+        for mode in (0, 1):
+            hpl.gemm_config(hpl.GEMM_EPILOGUE, mode)
+            C = C0.clone()
+            if kind == "bf16":
+                hpl.gemm_bf16(A, B, C, sub=sub)
+            elif kind == "fp8":
+                hpl.gemm_fp8(A, B, C, sa, sb, sub=sub)
+            else:
+                hpl.gemm_f16(A, B, C, sa, sb, sub=sub)
+            torch.cuda.synchronize()
+            out.append(C)
+    finally:
+        hpl.gemm_config(hpl.GEMM_EPILOGUE, 0)
+    assert torch.equal(out[0], out[1])
+
+
+def test_gemm_config_rejects_unknown(hpl):
+    with pytest.raises(hpl.HplError):
+        hpl.gemm_config(9, 0)
+    with pytest.raises(hpl.HplError):
+        hpl.gemm_config(hpl.GEMM_EPILOGUE, 5)

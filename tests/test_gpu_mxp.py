@@ -348,3 +348,64 @@ def test_mxp_bf16_storage_adjoint_and_rejects(hpl, orc):
         st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, X.data_ptr(), n, ctypes.byref(opts),
                            ws.data_ptr(), ws.numel(), hpl.Info().ptr(), torch.cuda.current_stream().cuda_stream)
         assert st == 1
+
+
+def _a32_view(ws, n, need):
+    """The FP32 copy of A that opts.inner = FP32 keeps at the end of the
+    workspace (followed by 16 x n FP64 chunk sums), as an n x n view."""
+    al = lambda x: (x + 255) // 256 * 256
+    off = need - al(8 * 16 * n) - al(4 * n * n)
+    return ws[off:off + 4 * n * n].view(__import__("torch").float32).view(n, n).t()
+
+
+@pytest.mark.parametrize("n,nb,prec,stored,storage", [(1000, 256, 0, True, 0), (777, 128, 1, True, 0),
+                                                      (900, 128, 2, True, 0), (1000, 256, 0, False, 0),
+                                                      (1000, 256, 0, True, 1), (301, 64, 0, False, 1),
+                                                      (2048, 512, 0, True, 0)])
+def test_mxp_inner_fp32(hpl, orc, n, nb, prec, stored, storage):
+    """GMRES's inner products on the FP32 copy of A (opts.inner = FP32): the
+    copy is the FP32 rounding of A (stored or regenerated), the factor is the
+    same as with FP64 inner products, x meets the FP64 bounds recomputed by the
+    oracle, and the iteration counts are within 2 of the oracle's emulation of
+    the same option."""
+    import ctypes
+    import torch
+    seed = 31
+    A, b = _system(hpl, n, seed)
+    A0, b0 = _np(A).copy(order="F"), _np(b).copy()
+    x1, i1, ws1 = hpl.mxp_solve(A if stored else None, b, nb=nb, prec=prec, seed=seed, storage=storage,
+                                inner=hpl.INNER_FP32)
+    x0, i0, ws0 = hpl.mxp_solve(A if stored else None, b, nb=nb, prec=prec, seed=seed, storage=storage)
+    torch.cuda.synchronize()
+    r1 = i1.read()
+    assert r1["status"] == 0 and r1["scaled_residual"] < 16, r1
+    opts = hpl.make_opts(nb=nb, prec=prec, storage=storage, inner=hpl.INNER_FP32)
+    need = hpl.load().mxp_workspace_size(n, 1, ctypes.byref(opts))
+    assert torch.equal(_a32_view(ws1, n, need), A.float())
+    F1, _ = hpl.mxp_factor_views(ws1, n, nb, storage=storage)
+    F0, _ = hpl.mxp_factor_views(ws0, n, nb, storage=storage)
+    assert torch.equal(F1, F0)
+    xg = _np(x1)[:, 0]
+    assert orc.scaled_residual(A0, xg, b0) < 16
+    x64, _ = orc.solve(A0, b0)
+    assert np.abs(xg - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A0, np.inf)
+    emu = orc.mxp_solve(A0, b0, nb, prec=prec, refine=1, storage=storage, inner=orc.INNER_FP32)
+    assert emu["status"] == 0
+    assert abs(r1["iters"] - emu["iters"]) <= 2, (r1, emu["iters"])
+
+
+def test_mxp_inner_rejects_unknown(hpl):
+    import ctypes
+    import torch
+    lib = hpl.load()
+    n = 64
+    A, b = _system(hpl, n, 2)
+    x = hpl.colmajor(n, 1)
+    info = hpl.Info()
+    opts = hpl.make_opts(nb=64)
+    need = lib.mxp_workspace_size(n, 1, ctypes.byref(opts))
+    ws = hpl.workspace(need + 512, A.device)
+    bad = hpl.make_opts(nb=64, inner=2)
+    st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, x.data_ptr(), n, ctypes.byref(bad), ws.data_ptr(),
+                       need, info.ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == 1

@@ -837,3 +837,24 @@ def test_fp16_factor_needs_no_more_corrections_than_bf16(orc):
     itbf = orc.mxp_solve(A, b, nb, prec=orc.PREC_BF16, refine=0)
     assert it16["status"] == 0 and itbf["status"] == 0
     assert it16["iters"] <= itbf["iters"]
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_mxp_inner_fp32_reaches_fp64_solution(orc, prec):
+    """GMRES with inner products from the FP32 rounding of A and the vector
+    still reaches the FP64 solution (the residual of each outer step is FP64),
+    in at most a few more outer steps than with FP64 inner products; with FP32
+    operands the inner products really differ (a correction is less exact)."""
+    n, nb = 512, 128
+    A = orc.generate(7, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(7, orc.STREAM_B, n, 1)[:, 0]
+    r64 = orc.mxp_solve(A, b, nb, prec=prec, inner=orc.INNER_FP64)
+    r32 = orc.mxp_solve(A, b, nb, prec=prec, inner=orc.INNER_FP32)
+    assert r32["status"] == 0 and r32["sr"] < 16
+    x64, _ = orc.solve(A, b)
+    bound = 2 * 16 * n * EPS * np.linalg.cond(A, np.inf)
+    assert np.abs(r32["x"] - x64).max() / np.abs(x64).max() < bound
+    assert r64["iters"] <= r32["iters"] <= r64["iters"] + 3
+    # after the first correction the FP32 inner products leave a larger residual
+    assert r32["hist"][1] > r64["hist"][1]
+
