@@ -41,12 +41,14 @@ MAX_SM_MHZ = 2070.0
 DGEMM_DRAM_BYTES_PER_FLOP = 956.9e6 / 31.21e9
 # Same for the tcgen05 trailing update of the mixed-precision solve, from one
 # ncu capture each of the step-0 update at n = 24576, NB = 4096 (m = 20480,
-# k = 4096, 3.436 TFLOP): key (prec, storage); BF16 5.199 GB, FP8 3.820 GB,
-# FP16 5.193 GB, BF16 operands with BF16 storage 3.512 GB. At fixed k a
-# launch's traffic scales with its C tile, i.e. with its flops; captured at
-# the bench's panel width only, so another width reports null.
-MXP_DRAM_BYTES_PER_FLOP = {(0, 0): 5.199e9 / 3.436e12, (1, 0): 3.820e9 / 3.436e12, (2, 0): 5.193e9 / 3.436e12,
-                           (0, 1): 3.512e9 / 3.436e12}
+# k = 4096, 3.436 TFLOP): key (prec, storage). BF16 and FP8 with FP32 storage
+# on the pair kernel with the bulk-tensor epilogue (4.715 GB and 3.808 GB,
+# profiles/k_gemm_tc_pair_update_tma_epilogue_n24576.txt); BF16 operands with
+# BF16 storage on the per-thread epilogue (3.512 GB). At fixed k a launch's
+# traffic scales with its C tile, i.e. with its flops; captured at the bench's
+# panel width only, so another width reports null, as does FP16 (not captured
+# on the current kernel).
+MXP_DRAM_BYTES_PER_FLOP = {(0, 0): 4.715e9 / 3.436e12, (1, 0): 3.808e9 / 3.436e12, (0, 1): 3.512e9 / 3.436e12}
 MXP_TRAFFIC_NB = 4096
 
 
@@ -657,7 +659,9 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
                          "traffic": (MXP_DRAM_BYTES_PER_FLOP[(prec, storage)] * upd_flops / upd_cnt
                                      if upd_cnt and nb == MXP_TRAFFIC_NB and (prec, storage) in MXP_DRAM_BYTES_PER_FLOP
                                      else None),
-                         "kernel": f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C)",
+                         "kernel": (f"k_gemm_tc_pair<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C, "
+                                    "bulk-tensor epilogue)" if not storage else
+                                    f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, BF16 C)"),
                          "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec == 1 else ""),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
             "phases": {k: {"ms_per_step": v[0] / len(step_ms), "intervals": v[2]} for k, v in phases.items() if v[2]}}

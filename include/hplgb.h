@@ -379,9 +379,10 @@ int hplgb_batched_config(int what, long long value);
  * (0 PFACT or the mixed-precision diagonal inverse + L21, 1 SWAP, 2 DTRSM,
  * 3 trailing update, 4 preconditioner / outer product, 5 FP64 -> FP32 copy,
  * 6 FP64 residuals and matrix-vector products, 7 whole refinement, which
- * contains 4 and 6), the summed milliseconds, the algorithmic work (flops;
- * bytes moved for 1, 5 and 6) and the number of timed intervals, then clears
- * the record. ms, work, count: host arrays of 8, any may be NULL. Returns
+ * contains 4 and 6, 8 low-precision operand copies of the mixed-precision
+ * products), the summed milliseconds, the algorithmic work (flops; bytes
+ * moved for 1, 5, 6 and 8) and the number of timed intervals, then clears
+ * the record. ms, work, count: host arrays of 9, any may be NULL. Returns
  * HPL_ERR_CUDA if an event query fails.
  * hplgb_phase_records returns the same intervals one by one, in the order
  * they were opened, without clearing them (call it before hplgb_phase_times):

@@ -518,7 +518,7 @@ def gemm_f16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None
     return C
 
 
-PHASES = ("pfact", "swap", "trsm", "update", "other", "convert", "resid", "refine")
+PHASES = ("pfact", "swap", "trsm", "update", "other", "convert", "resid", "refine", "opconv")
 
 
 def launch_count() -> int:

@@ -70,7 +70,8 @@ enum Phase {
     PH_CONVERT = 5,   // FP64 -> FP32 copy of the matrix (mixed precision)
     PH_RESID = 6,     // FP64 residuals and matrix-vector products (refinement)
     PH_REFINE = 7,    // the whole refinement of one right-hand side (contains 4 and 6)
-    PH_COUNT = 8
+    PH_OPCONV = 8,    // low-precision operand copies of the mixed-precision products (L21, U12, D^-1)
+    PH_COUNT = 9
 };
 int phase_begin(cudaStream_t s);                                   // -1 when timing is off
 void phase_end(int slot, cudaStream_t s, int phase, double work, int step = -1);  // work: flops or bytes

@@ -86,57 +86,120 @@ struct Seg {
     int64_t seg_off, seg_stride, kpad;
 };
 
+__device__ __forceinline__ float eye2_of(float v, int64_t r, int64_t c) { return (r == c ? 2.0f : 0.0f) - v; }
+
+// trans = 1: a transpose through a 64 (K) x 32 (operand rows) shared tile, one per CTA.
+// Each warp reads 128 contiguous bytes of one column of X per instruction and
+// writes 128 contiguous bytes (64 BF16 values, two per lane) of one operand
+// row per instruction.
 template <typename XT>
 __global__ void __launch_bounds__(256) k_to_bf16_t(const XT* __restrict__ X, int64_t ldx, int64_t rows,
                                                    int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
                                                    Seg g) {
-    __shared__ float tile[32][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 32, r0 = (int64_t)blockIdx.y * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;
-    for (int i = ty; i < 32; i += 8) {
-        int64_t c = c0 + i, r = r0 + tx;
+    __shared__ float tile[64][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int cc = warp + 8 * j;
+        const int64_t c = c0 + cc, r = r0 + lane;
         float v = (c < cols && r < rows) ? ld_f(X + c * ldx + r) : 0.0f;
-        if (g.eye2 && c < cols && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
-        tile[i][tx] = v;
+        if (g.eye2 && c < cols && r < rows) v = eye2_of(v, r, c);
+        tile[cc][lane] = v;
     }
     __syncthreads();
-    for (int i = ty; i < 32; i += 8) {
-        int64_t r = r0 + i, c = c0 + tx;
-        if (r < rows && c < g.kpad)
-            for (int q = 0; q < g.nseg; q++)
-                out[r * ldo + g.seg_off + q * g.seg_stride + c] =
-                    __float2bfloat16_rn(bf16_part(tile[tx][i], (g.parts >> (2 * q)) & 3));
+    const int64_t c = c0 + 2 * lane;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int rr = warp * 4 + i;
+        const int64_t r = r0 + rr;
+        if (r >= rows) continue;
+        const float v0 = tile[2 * lane][rr], v1 = tile[2 * lane + 1][rr];
+        for (int q = 0; q < g.nseg; q++) {
+            const int part = (g.parts >> (2 * q)) & 3;
+            __nv_bfloat16* o = out + r * ldo + g.seg_off + q * g.seg_stride + c;
+            if (c + 1 < g.kpad) {
+                __nv_bfloat162 h;
+                h.x = __float2bfloat16_rn(bf16_part(v0, part));
+                h.y = __float2bfloat16_rn(bf16_part(v1, part));
+                *reinterpret_cast<__nv_bfloat162*>(o) = h;
+            } else if (c < g.kpad) {
+                *o = __float2bfloat16_rn(bf16_part(v0, part));
+            }
+        }
     }
 }
 
+// trans = 0: a straight conversion along the contraction index; each thread
+// converts 8 consecutive values (two 16-byte loads, one 16-byte store when
+// aligned), a grid-stride loop over (operand row, group of 8).
 template <typename XT>
 __global__ void __launch_bounds__(256) k_to_bf16_n(const XT* __restrict__ X, int64_t ldx, int64_t rows,
                                                    int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
-                                                   Seg g) {
-    const int64_t r = (int64_t)blockIdx.x * 256 + threadIdx.x;   // K index
-    const int64_t c = blockIdx.y;                                  // operand row
-    if (r >= g.kpad || c >= cols) return;
-    float v = r < rows ? ld_f(X + c * ldx + r) : 0.0f;
-    if (g.eye2 && r < rows) v = (r == c ? 2.0f : 0.0f) - v;
-    for (int q = 0; q < g.nseg; q++)
-        out[c * ldo + g.seg_off + q * g.seg_stride + r] = __float2bfloat16_rn(bf16_part(v, (g.parts >> (2 * q)) & 3));
+                                                   Seg g, int vec) {
+    const int64_t groups = (g.kpad + 7) / 8;
+    const int64_t total = groups * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t / groups;
+        const int64_t r = (t - c * groups) * 8;
+        float v[8];
+        const XT* xc = X + c * ldx;
+        if (vec && r + 7 < rows) {
+            if constexpr (std::is_same<XT, float>::value) {
+                const float4 a = *reinterpret_cast<const float4*>(xc + r);
+                const float4 b = *reinterpret_cast<const float4*>(xc + r + 4);
+                v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+                v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+            } else {
+#pragma unroll
+                for (int e = 0; e < 8; e++) v[e] = ld_f(xc + r + e);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; e++) v[e] = r + e < rows ? ld_f(xc + r + e) : 0.0f;
+        }
+        if (g.eye2) {
+#pragma unroll
+            for (int e = 0; e < 8; e++)
+                if (r + e < rows) v[e] = eye2_of(v[e], r + e, c);
+        }
+        for (int q = 0; q < g.nseg; q++) {
+            const int part = (g.parts >> (2 * q)) & 3;
+            __nv_bfloat16* o = out + c * ldo + g.seg_off + q * g.seg_stride + r;
+            if (vec && r + 7 < g.kpad) {
+                __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(bf16_part(v[e], part));
+                *reinterpret_cast<uint4*>(o) = *reinterpret_cast<const uint4*>(h);
+            } else {
+                for (int e = 0; e < 8 && r + e < g.kpad; e++) o[e] = __float2bfloat16_rn(bf16_part(v[e], part));
+            }
+        }
+    }
 }
 
 template <typename XT>
 static int to_bf16_seg(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int trans, uint16_t* out, int64_t ldo,
                        Seg g, cudaStream_t s) {
     if (trans) {
-        dim3 grid((unsigned)((g.kpad + 31) / 32), (unsigned)((rows + 31) / 32));
-        k_to_bf16_t<<<grid, dim3(32, 8), 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g);
+        // BF16 pairs are stored 4-byte aligned: even strides and offsets
+        if ((ldo | g.seg_off | g.seg_stride) & 1 || ((uintptr_t)out & 3)) return HPL_ERR_INVALID;
+        // one 64 x 32 tile per CTA (a grid-stride loop over tiles measured slower)
+        if ((g.kpad + 63) / 64 > 0x7fffffff || (rows + 31) / 32 > 65535) return HPL_ERR_INVALID;
+        dim3 grid((unsigned)((g.kpad + 63) / 64), (unsigned)((rows + 31) / 32));
+        k_to_bf16_t<<<grid, 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g);
         HPL_LAUNCH_CHECK();
         return HPL_OK;
     }
-    for (int64_t c0 = 0; c0 < cols; c0 += 65535) {           // grid.y limit
-        int64_t cc = std::min<int64_t>(65535, cols - c0);
-        dim3 grid((unsigned)((g.kpad + 255) / 256), (unsigned)cc);
-        k_to_bf16_n<<<grid, 256, 0, s>>>(X + c0 * ldx, ldx, rows, cc, (__nv_bfloat16*)(out + c0 * ldo), ldo, g);
-        HPL_LAUNCH_CHECK();
-    }
+    // 16-byte accesses: X column starts and out row starts / segment offsets aligned
+    const int vec = std::is_same<XT, float>::value && ((uintptr_t)X & 15) == 0 && ldx % 4 == 0 &&
+                    ((uintptr_t)out & 15) == 0 && ldo % 8 == 0 && g.seg_off % 8 == 0 && g.seg_stride % 8 == 0;
+    const int64_t items = ((g.kpad + 7) / 8) * cols;
+    const int64_t blocks = std::min<int64_t>((items + 255) / 256, 152 * 32);
+    k_to_bf16_n<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g,
+                                                                       vec);
+    HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
 
@@ -197,15 +260,31 @@ struct LowFmt<2> {
     static __device__ __forceinline__ T cvt(float x) { return __half_as_ushort(__float2half_rn(x)); }
 };
 
+// Float4 loads along a column-major matrix's columns: 16-byte aligned columns.
+static inline int vec4_ok(const float* X, int64_t ldx) { return ((uintptr_t)X & 15) == 0 && ldx % 4 == 0; }
+
+// Four consecutive low-precision values in one store (the callers keep the
+// address aligned to four values: operand rows of kpad values, kpad a multiple
+// of 16 for FP8 and of 8 for FP16, and column offsets that are multiples of 4).
+__device__ __forceinline__ void store4(unsigned char* o, const unsigned char (&q)[4]) {
+    *reinterpret_cast<uint32_t*>(o) = (uint32_t)q[0] | ((uint32_t)q[1] << 8) | ((uint32_t)q[2] << 16) |
+                                      ((uint32_t)q[3] << 24);
+}
+__device__ __forceinline__ void store4(uint16_t* o, const uint16_t (&q)[4]) {
+    *reinterpret_cast<uint2*>(o) = make_uint2((uint32_t)q[0] | ((uint32_t)q[1] << 16),
+                                              (uint32_t)q[2] | ((uint32_t)q[3] << 16));
+}
+
 // A operand: X (rows x cols, column-major) -> out row r = X(r, :) (K = cols),
 // sa[r] = 2^e. 32 rows per CTA, the 8 warps split the columns.
 template <int FMT>
 __global__ void __launch_bounds__(256) k_quant_rows(const float* __restrict__ X, int64_t ldx, int64_t rows,
                                                     int64_t cols, typename LowFmt<FMT>::T* __restrict__ out,
                                                     int64_t ldo, int64_t kpad, float* __restrict__ sa) {
+    using T = typename LowFmt<FMT>::T;
     __shared__ float part[8][33];
     __shared__ float inv[32];
-    __shared__ float tile[32][33];
+    __shared__ float tile[128][33];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int64_t r0 = (int64_t)blockIdx.x * 32;
     const int64_t r = r0 + lane;
@@ -222,15 +301,32 @@ __global__ void __launch_bounds__(256) k_quant_rows(const float* __restrict__ X,
         if (r < rows) sa[r] = ldexpf(1.0f, e);
     }
     __syncthreads();
-    for (int64_t c0 = 0; c0 < kpad; c0 += 32) {
-        for (int i = warp; i < 32; i += 8) {
+    // 32 rows x 128 columns per pass: each warp reads 128 contiguous bytes of
+    // one column per instruction and writes four converted values per lane
+    // (128 bytes of FP8 or 256 of FP16 per row and instruction)
+    for (int64_t c0 = 0; c0 < kpad; c0 += 128) {
+#pragma unroll 4
+        for (int i = warp; i < 128; i += 8) {
             const int64_t c = c0 + i;
-            tile[lane][i] = (r < rows && c < cols) ? X[c * ldx + r] : 0.0f;
+            tile[i][lane] = (r < rows && c < cols) ? X[c * ldx + r] : 0.0f;
         }
         __syncthreads();
-        for (int i = warp; i < 32; i += 8) {
-            const int64_t rr = r0 + i, c = c0 + lane;
-            if (rr < rows && c < kpad) out[rr * ldo + c] = LowFmt<FMT>::cvt(tile[i][lane] * inv[i]);
+        const int64_t c = c0 + 4 * lane;
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            const int rr = warp * 4 + i;
+            const int64_t row = r0 + rr;
+            if (row >= rows) continue;
+            const float sc = inv[rr];
+            T* o = out + row * ldo + c;
+            if (c + 3 < kpad) {
+                T q[4];
+#pragma unroll
+                for (int e = 0; e < 4; e++) q[e] = LowFmt<FMT>::cvt(tile[4 * lane + e][rr] * sc);
+                store4(o, q);
+            } else {
+                for (int e = 0; e < 4 && c + e < kpad; e++) o[e] = LowFmt<FMT>::cvt(tile[4 * lane + e][rr] * sc);
+            }
         }
         __syncthreads();
     }
@@ -241,18 +337,48 @@ __global__ void __launch_bounds__(256) k_quant_rows(const float* __restrict__ X,
 template <int FMT>
 __global__ void __launch_bounds__(256) k_quant_cols(const float* __restrict__ X, int64_t ldx, int64_t rows,
                                                     int64_t cols, typename LowFmt<FMT>::T* __restrict__ out,
-                                                    int64_t ldo, int64_t kpad, float* __restrict__ sb) {
+                                                    int64_t ldo, int64_t kpad, float* __restrict__ sb, int vec) {
+    using T = typename LowFmt<FMT>::T;
     const int lane = threadIdx.x & 31;
     const int64_t c = (int64_t)blockIdx.x * 8 + (threadIdx.x >> 5);
     if (c >= cols) return;
     const float* col = X + c * ldx;
     float amax = 0.0f;
-    for (int64_t r = lane; r < rows; r += 32) amax = fmaxf(amax, fabsf(col[r]));
+    if (vec) {      // four values per lane and load: 512 contiguous bytes per warp instruction
+        int64_t r = 4 * lane;
+        for (; r + 3 < rows; r += 128) {
+            const float4 v = *reinterpret_cast<const float4*>(col + r);
+            amax = fmaxf(amax, fmaxf(fmaxf(fabsf(v.x), fabsf(v.y)), fmaxf(fabsf(v.z), fabsf(v.w))));
+        }
+        for (; r < rows; r++) amax = fmaxf(amax, fabsf(col[r]));
+    } else {
+        for (int64_t r = lane; r < rows; r += 32) amax = fmaxf(amax, fabsf(col[r]));
+    }
     for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
     const int e = LowFmt<FMT>::scale_exp(amax);
     const float inv = ldexpf(1.0f, -e);
     if (lane == 0) sb[c] = ldexpf(1.0f, e);
-    for (int64_t r = lane; r < kpad; r += 32) out[c * ldo + r] = LowFmt<FMT>::cvt(r < rows ? col[r] * inv : 0.0f);
+    T* o = out + c * ldo;
+    if (vec) {
+        for (int64_t r = 4 * lane; r < kpad; r += 128) {
+            T q[4];
+            if (r + 3 < rows) {
+                const float4 v = *reinterpret_cast<const float4*>(col + r);
+                q[0] = LowFmt<FMT>::cvt(v.x * inv);
+                q[1] = LowFmt<FMT>::cvt(v.y * inv);
+                q[2] = LowFmt<FMT>::cvt(v.z * inv);
+                q[3] = LowFmt<FMT>::cvt(v.w * inv);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; k++) q[k] = LowFmt<FMT>::cvt(r + k < rows ? col[r + k] * inv : 0.0f);
+            }
+            if (r + 3 < kpad) store4(o + r, q);
+            else
+                for (int k = 0; k < 4 && r + k < kpad; k++) o[r + k] = q[k];
+        }
+    } else {
+        for (int64_t r = lane; r < kpad; r += 32) o[r] = LowFmt<FMT>::cvt(r < rows ? col[r] * inv : 0.0f);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1026,7 +1152,8 @@ struct Mxp {
                         k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8,
                                                                                    w.sa);
                         HPL_LAUNCH_CHECK();
-                        k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb);
+                        k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb,
+                                                                          vec4_ok(w.X, kb));
                         HPL_LAUNCH_CHECK();
                         if ((st = launch_gemm_f16(m2, kb, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A21, ldf, 0, w.err,
                                                   o.timeout_ns, 0, s)))
@@ -1035,43 +1162,57 @@ struct Mxp {
                     }
                 }
                 if (!done) {
+                    const int cv = phase_begin(s);
                     if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
                     if ((st = to_bf16(w.X, kb, kb, kb, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                    phase_end(cv, s, PH_OPCONV, (double)(m2 + kb) * kb * (sizeof(FT) + 2));
                     if ((st = gemm_c(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0))) return st;
                 }
                 phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
-                // A22 -= L21 A12
-                slot = phase_begin(s);
+                // A22 -= L21 A12 (the operand copies timed as PH_OPCONV, the product as PH_UPDATE)
                 done = false;
                 if constexpr (!kBf16) {
                 if (o.prec == HPL_PREC_FP8_E4M3) {
                     const int64_t kb16 = (kb + 15) / 16 * 16;
                     uint8_t* qa = (uint8_t*)w.opA;
                     uint8_t* qb = (uint8_t*)w.opB;
+                    const int cv = phase_begin(s);
                     k_quant_rows<1><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa);
                     HPL_LAUNCH_CHECK();
-                    k_quant_cols<1><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb);
+                    k_quant_cols<1><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb,
+                                                                           vec4_ok(A12, ldf));
                     HPL_LAUNCH_CHECK();
+                    phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * (4 + 1));
+                    const int ug = phase_begin(s);
                     if ((st = launch_gemm_fp8(m2, m2, kb, qa, kb16, qb, kb16, w.sa, w.sb, A22, ldf, 1, w.err,
                                               o.timeout_ns, 0, s)))
                         return st;
+                    phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 } else if (o.prec == HPL_PREC_FP16) {
+                    const int cv = phase_begin(s);
                     k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa);
                     HPL_LAUNCH_CHECK();
-                    k_quant_cols<2><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, w.opB, kb8, kb8, w.sb);
+                    k_quant_cols<2><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, w.opB, kb8, kb8, w.sb,
+                                                                           vec4_ok(A12, ldf));
                     HPL_LAUNCH_CHECK();
+                    phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * (4 + 2));
+                    const int ug = phase_begin(s);
                     if ((st = launch_gemm_f16(m2, m2, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A22, ldf, 1, w.err,
                                               o.timeout_ns, 0, s)))
                         return st;
+                    phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 }
                 done = o.prec == HPL_PREC_FP8_E4M3 || o.prec == HPL_PREC_FP16;
                 }
                 if (!done) {
+                    const int cv = phase_begin(s);
                     if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
                     if ((st = to_bf16(A12, ldf, kb, m2, 0, 0, w.opB, kb8, 0, kb8, s))) return st;
+                    phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * (sizeof(FT) + 2));
+                    const int ug = phase_begin(s);
                     if ((st = gemm_c(m2, m2, kb, w.opA, kb8, w.opB, kb8, A22, ldf, 1))) return st;
+                    phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 }
-                phase_end(slot, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
             } else {
                 phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb);
             }

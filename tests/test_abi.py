@@ -99,6 +99,12 @@ def test_autotune_table_lookup():
     got = autotune.variants([40, 100, 300, 40, 200], [0, 0, 0, 1, 1], table, "GPU-X")
     assert list(got) == [1, 0, 0, 0, 1]
     assert list(autotune.variants([40, 300], [0, 1], {}, "GPU-X")) == [0, 0]
+    # the whole-batch policy "narrow" (16-wide panels everywhere, two CTAs per
+    # SM) overrides the per-bucket widths; "per_bucket" keeps them
+    table["GPU-X"]["policy"] = "narrow"
+    assert list(autotune.variants([40, 100, 300], [0, 0, 1], table, "GPU-X")) == [1, 1, 1]
+    table["GPU-X"]["policy"] = "per_bucket"
+    assert list(autotune.variants([40, 100, 300], [0, 0, 1], table, "GPU-X")) == [1, 0, 0]
 
 
 def test_workspace_sizes_follow_the_options():
