@@ -84,6 +84,7 @@ def _load():
             "orc_round_bf16": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_e4m3": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_fp16": (ctypes.c_float, [ctypes.c_float]),
+            "orc_round_tf32": (ctypes.c_float, [ctypes.c_float]),
             "orc_round_operand_ext": (None, [ctypes.c_int, fp, i64, i64, i64, ctypes.c_int]),
             "orc_mxp_factor": (i64, [i64, i64, ctypes.c_int, ctypes.c_int, ctypes.c_int, fp, i64, fp]),
             "orc_to_bf16_storage": (None, [i64, i64, dp, i64, fp, i64]),
@@ -238,6 +239,7 @@ PREC_BF16 = 0
 PREC_FP8 = 1
 PREC_FP16 = 2
 PREC_FP32 = 3
+PREC_TF32 = 4
 
 
 def round_bf16_d(x: float) -> float:
@@ -255,6 +257,10 @@ def round_e4m3(x: float) -> float:
 
 def round_fp16(x: float) -> float:
     return float(_load().orc_round_fp16(float(x)))
+
+
+def round_tf32(x: float) -> float:
+    return float(_load().orc_round_tf32(float(x)))
 
 
 def round_operand(prec: int, X, kdim_is_rows: bool) -> np.ndarray:

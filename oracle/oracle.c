@@ -31,6 +31,8 @@
  *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine),
  *       normals, ties, FP32 subnormals and the overflow threshold.
  *   orc_round_fp16 : NumPy's float16 cast (library routine).
+ *   orc_round_tf32 : brute-force nearest search over exact rationals, ties,
+ *       subnormals and the overflow threshold.
  *   orc_mxp_factor : FP32 mode equals unpivoted LU; BF16 mode error bound.
  *   orc_mxp_lu_plain : a hand-worked 4 x 4 case in exact rationals for every
  *       operand precision (tests/golden/mxp_2step_by_hand.txt); FP32 mode
@@ -352,7 +354,10 @@ void orc_lu_sample_diff(uint64_t seed, int64_t n, int dominant, const double* LU
  *     as well as in the trailing update (its 3 extra fraction bits over BF16
  *     are lost if L21 is formed from BF16 operands);
  *     prec = 3: no rounding (FP32 operands, FP32 Newton-Schulz), a reference
- *     mode.                                                                  */
+ *     mode;
+ *     prec = 4: TF32 (FP32 exponent range, 10 fraction bits), round to nearest
+ *     even, no scales (the range is FP32's), in the panel product and the
+ *     trailing update like FP16.                                             */
 
 /* BF16 round-to-nearest-even, written from the format definition (1 sign,
  * 8 exponent, 7 stored fraction bits; the exponent range is FP32's). Normal
@@ -421,6 +426,26 @@ float orc_round_fp16(float x) {
     return (float)copysign(q, (double)x);
 }
 
+/* TF32 (the tensor cores' 19-bit format: FP32's sign and 8-bit exponent, 10
+ * stored fraction bits) round-to-nearest-even of a float, written from the
+ * format definition: normal values keep 11 significant bits; below 2^-126 the
+ * grid is the fixed spacing 2^-136; results beyond the largest finite TF32
+ * value (2 - 2^-10) 2^127 overflow to infinity. The result is an FP32 value
+ * whose 13 low fraction bits are zero. */
+float orc_round_tf32(float x) {
+    if (x == 0.0f || !isfinite(x)) return x;
+    double a = (double)x, r;
+    if (fabs(a) < 0x1p-126) {
+        r = ldexp(nearbyint(ldexp(a, 136)), -136);
+    } else {
+        int e;
+        double f = frexp(a, &e);                       /* a = f 2^e, 0.5 <= |f| < 1 */
+        r = ldexp(nearbyint(ldexp(f, 11)), e - 11);    /* 11 significant bits, RNE */
+    }
+    if (fabs(r) > 0x1.FFCp127) r = copysign(INFINITY, r);
+    return (float)r;
+}
+
 /* Scale exponent for a block with max magnitude amax: smallest e with
  * amax * 2^-e <= bound (448 for E4M3, 65504 for FP16). Returns 0 for an
  * all-zero block. */
@@ -438,9 +463,10 @@ static int orc_block_exp(double amax, double bound) {
  * is the dequantised value, stored as float. */
 static void orc_round_operand(int prec, float* X, int64_t r, int64_t c, int64_t ld, int kdim_is_rows) {
     if (prec == 3) return;
-    if (prec == 0) {
+    if (prec == 0 || prec == 4) {
+        float (*rnd)(float) = prec == 0 ? orc_round_bf16 : orc_round_tf32;
         for (int64_t j = 0; j < c; j++)
-            for (int64_t i = 0; i < r; i++) X[j * ld + i] = orc_round_bf16(X[j * ld + i]);
+            for (int64_t i = 0; i < r; i++) X[j * ld + i] = rnd(X[j * ld + i]);
         return;
     }
     /* FP8 or FP16 with one scale per operand row (A) or column (B), i.e. per
@@ -512,8 +538,11 @@ static void orc_split_bf16(const float* X, int64_t r, int64_t c, int64_t ld, flo
 }
 
 /* Newton-Schulz inverse of the kb x kb FP32 block D (ld ldd) into X (ld kb):
- * X = diag(D)^-1, then ns_iters times R = D X, T = 2I - R, X = X T. With
- * split != 0 the products use split BF16 operands, else plain FP32. */
+ * X = diag(D)^-1, then ns_iters times R = D X, T = 2I - R, X = X T. The
+ * first step starts from a diagonal X, so its two products are scalings,
+ * X_ij = x_i (2 delta_ij - D_ij x_j) with x_i = 1 / D_ii, computed directly in
+ * FP32 (a multiply, a subtraction, a multiply, each rounded once). Later steps
+ * use split BF16 operands in their products when split != 0, else plain FP32. */
 static void orc_newton_schulz(int64_t kb, const float* D, int64_t ldd, int ns_iters, int split, float* X) {
     size_t sz = sizeof(float) * kb * kb;
     float *R = (float*)malloc(sz), *Dh = (float*)malloc(sz), *Dl = (float*)malloc(sz);
@@ -526,6 +555,16 @@ static void orc_newton_schulz(int64_t kb, const float* D, int64_t ldd, int ns_it
         }
     if (split) orc_split_bf16(Dc, kb, kb, kb, Dh, Dl);
     for (int it = 0; it < ns_iters; it++) {
+        if (it == 0) {                                   /* X is diag(D)^-1: scalings */
+            for (int64_t j = 0; j < kb; j++)
+                for (int64_t i = 0; i < kb; i++) {
+                    float xi = 1.0f / Dc[i * kb + i], xj = 1.0f / Dc[j * kb + j];
+                    float r = Dc[j * kb + i] * xj;
+                    float t = ((i == j) ? 2.0f : 0.0f) - r;
+                    X[j * kb + i] = xi * t;
+                }
+            continue;
+        }
         if (split) {
             orc_split_bf16(X, kb, kb, kb, Xh, Xl);
             orc_gemm32_split(kb, kb, kb, Dh, Dl, kb, Xh, Xl, kb, R, kb);          /* R = D X */

@@ -493,7 +493,14 @@ __device__ void blocklu32(const Sys& S, float* X, float* R, float* T, float* scr
         float* Ds = scratch;                  // D staged in shared memory for the products
         for (int e = threadIdx.x; e < kb * kb; e += THREADS) Ds[e] = D[(long long)(e / kb) * n + e % kb];
         __syncthreads();
-        for (int it = 0; it < 3; it++) {     // 3 steps: systems this small are only weakly dominant
+        // first step from X0 = diag(D)^-1: diagonal scalings, each operation rounded once
+        for (int e = threadIdx.x; e < kb * kb; e += THREADS) {
+            const int j = e / kb, i = e % kb;
+            const float xi = 1.0f / Ds[i * kb + i], xj = 1.0f / Ds[j * kb + j];
+            X[j * NB + i] = __fmul_rn(xi, __fsub_rn(i == j ? 2.0f : 0.0f, __fmul_rn(Ds[j * kb + i], xj)));
+        }
+        __syncthreads();
+        for (int it = 1; it < 3; it++) {     // 3 steps: systems this small are only weakly dominant
             gemm32(kb, kb, kb, Ds, kb, X, NB, R, NB, 0, 1);             // R = D X
             __syncthreads();
             for (int e = threadIdx.x; e < kb * kb; e += THREADS) {

@@ -616,11 +616,16 @@ __global__ void k_matvec32_combine(int64_t n, int nsplit, const double* __restri
     }
 }
 
-__global__ void k_ns_init(const float* __restrict__ D, int64_t ldd, int kb, float* __restrict__ X) {
+// The first Newton-Schulz step from X0 = diag(D)^-1: its products are
+// diagonal scalings, X1_ij = x_i (2 delta_ij - D_ij x_j), x_i = 1 / D_ii, each
+// operation rounded once in FP32 (explicit _rn operations: no contraction).
+__global__ void k_ns_first(const float* __restrict__ D, int64_t ldd, int kb, float* __restrict__ X) {
     const int64_t total = (int64_t)kb * kb;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        int64_t j = t / kb, i = t - j * kb;
-        X[t] = (i == j) ? 1.0f / D[j * ldd + j] : 0.0f;
+        const int64_t j = t / kb, i = t - j * kb;
+        const float xi = 1.0f / D[i * ldd + i], xj = 1.0f / D[j * ldd + j];
+        const float r = __fmul_rn(D[j * ldd + i], xj);
+        X[t] = __fmul_rn(xi, __fsub_rn(i == j ? 2.0f : 0.0f, r));
     }
 }
 
@@ -1119,12 +1124,13 @@ struct Mxp {
             }
             k_zero_diag_flag<<<1, 256, 0, s>>>(D, ldd, (int)kb, k0, info);
             HPL_LAUNCH_CHECK();
-            k_ns_init<<<grid_for(kb * kb), 256, 0, s>>>(D, ldd, (int)kb, w.X);
-            HPL_LAUNCH_CHECK();
             int st;
-            // split D as the A operand: [hi | hi | lo]
-            if ((st = to_bf16_split3(D, ldd, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
-            for (int it = 0; it < o.ns_iters; it++) {
+            // split D as the A operand of the later steps' products: [hi | hi | lo]
+            // (before k_ns_first: with BF16 storage D lives in R, which those products overwrite)
+            if (o.ns_iters > 1 && (st = to_bf16_split3(D, ldd, kb, 1, 1, 1, 2, 0, w.nsD, kb8, s))) return st;
+            k_ns_first<<<grid_for(kb * kb), 256, 0, s>>>(D, ldd, (int)kb, w.X);
+            HPL_LAUNCH_CHECK();
+            for (int it = 1; it < o.ns_iters; it++) {
                 // R = D X: B operand from X, [hi | lo | hi]
                 if ((st = to_bf16_split3(w.X, kb, kb, 0, 1, 2, 1, 0, w.nsB, kb8, s))) return st;
                 if ((st = launch_gemm_bf16(kb, kb, K3, w.nsD, K3, w.nsB, K3, w.R, kb, 0, w.err, o.timeout_ns, 0, s)))
@@ -1168,7 +1174,7 @@ struct Mxp {
                     phase_end(cv, s, PH_OPCONV, (double)(m2 + kb) * kb * (sizeof(FT) + 2));
                     if ((st = gemm_c(m2, kb, kb, w.opA, kb8, w.opB, kb8, A21, ldf, 0))) return st;
                 }
-                phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
+                phase_end(slot, s, PH_PANEL, 2.0 * (o.ns_iters - 1) * 2.0 * 3.0 * kb * kb * kb + 2.0 * m2 * kb * kb);
                 // A22 -= L21 A12 (the operand copies timed as PH_OPCONV, the product as PH_UPDATE)
                 done = false;
                 if constexpr (!kBf16) {
@@ -1214,7 +1220,7 @@ struct Mxp {
                     phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 }
             } else {
-                phase_end(slot, s, PH_PANEL, 2.0 * o.ns_iters * 2.0 * 3.0 * kb * kb * kb);
+                phase_end(slot, s, PH_PANEL, 2.0 * (o.ns_iters - 1) * 2.0 * 3.0 * kb * kb * kb);
             }
         }
         return HPL_OK;

@@ -858,3 +858,95 @@ def test_mxp_inner_fp32_reaches_fp64_solution(orc, prec):
     # after the first correction the FP32 inner products leave a larger residual
     assert r32["hist"][1] > r64["hist"][1]
 
+
+
+def test_newton_schulz_first_step_closed_form(orc):
+    """One Newton-Schulz step from X0 = diag(D)^-1 is X1 = 2 X0 - X0 D X0 (the
+    two products of a diagonal X0 are scalings): the oracle's one-step inverse
+    equals that closed form, evaluated in FP64 from the same FP32 diagonal
+    blocks, to within three FP32 roundings per entry; a second step moves it
+    (the later steps really are products)."""
+    n, nb = 300, 100
+    A = orc.generate(16, orc.STREAM_A, n, n, dominant=True)
+    F1, D1, _ = orc.mxp_factor(A, nb, orc.PREC_BF16, ns_iters=1)
+    F2, D2, _ = orc.mxp_factor(A, nb, orc.PREC_BF16, ns_iters=2)
+    for k0 in range(0, n, nb):
+        D = F1[k0:k0 + nb, k0:k0 + nb].astype(np.float64)
+        x0 = np.diag(1.0 / np.diag(D).astype(np.float32).astype(np.float64))
+        want = 2 * x0 - x0 @ D @ x0
+        got = D1[k0:k0 + nb, :].astype(np.float64)
+        assert np.all(np.abs(got - want) <= 4 * 2.0 ** -24 * (np.abs(x0) @ (np.abs(D) @ np.abs(x0)) + 2 * np.abs(x0)))
+    assert not np.array_equal(D1[:nb], D2[:nb])
+
+
+def _nearest_tf32_bruteforce(x: float) -> float:
+    """The TF32 value nearest to x (FP32's exponent range, 11 significant bits
+    for normals, the fixed spacing 2^-136 below 2^-126; ties to an even last
+    fraction bit), by exact comparison of every grid point around x."""
+    if x == 0.0:
+        return 0.0
+    X = Fraction(abs(x))
+    cands = set()
+    # normal grid points k 2^(ee-10), 2^10 <= k < 2^11, around x
+    e = int(np.frexp(abs(x))[1]) - 1             # 2^e <= |x| < 2^(e+1)
+    for ee in (e - 1, e, e + 1):
+        if ee < -126:
+            continue
+        q = Fraction(2) ** (ee - 10)
+        base = int(X / q)
+        for k in range(base - 2, base + 3):
+            if 1024 <= k < 2048:
+                cands.add((Fraction(k) * q, k))
+        if ee == 127:
+            cands.add((Fraction(2) ** 128, 2))  # the overflow point (even)
+    # subnormal grid points k 2^-136, 0 <= k < 2^10
+    q = Fraction(2) ** -136
+    base = int(X / q)
+    for k in range(base - 2, base + 3):
+        if 0 <= k < 1024:
+            cands.add((Fraction(k) * q, k))
+    best = min(cands, key=lambda c: (abs(c[0] - X), c[1] & 1))
+    v = float(best[0]) if best[0] < Fraction(2) ** 128 else float("inf")
+    return float(np.copysign(v, x))
+
+
+def test_round_tf32_matches_bruteforce(orc):
+    """TF32 rounding against the nearest-grid-point search: random values over
+    the whole exponent range, exact ties and values one FP32 unit off a tie,
+    subnormals, and the overflow threshold."""
+    rng = np.random.default_rng(21)
+    vals = list((rng.standard_normal(1500) * 10.0 ** rng.integers(-35, 35, 1500)).astype(np.float32))
+    bits = rng.integers(0x00800000, 0x7f000000, 300, dtype=np.uint32)
+    for b in bits:                                 # ties (low 13 bits 0x1000) and their neighbours
+        hi = int(b) & ~0x1FFF
+        for low in (0x1000, 0x0FFF, 0x1001, 0x0000, 0x1FFF):
+            vals.append(np.array([hi | low], dtype=np.uint32).view(np.float32)[0])
+    vals += list(np.array([0x00000001, 0x00001000, 0x00003000, 0x007FFFFF, 0x007FF000, 0x00800000,
+                           0x7F7FF000, 0x7F7FEFFF, 0x7F7FF001, 0x7F7FFFFF], dtype=np.uint32).view(np.float32))
+    for v in vals:
+        for sgn in (1.0, -1.0):
+            x = float(np.float32(sgn * v))
+            got = orc.round_tf32(x)
+            want = _nearest_tf32_bruteforce(x)
+            assert got == want or (np.isinf(got) and np.isinf(want) and np.sign(got) == np.sign(want)), (x, got, want)
+            assert np.isinf(got) or (np.array([got], dtype=np.float32).view(np.uint32)[0] & 0x1FFF) == 0
+
+
+def test_mxp_tf32_operands(orc):
+    """TF32 operands (no scales) in the panel product and the update: the
+    factor's backward error sits between FP32 and BF16 and near FP16's (the
+    same 11 significant bits), for both readings of the factorization, and
+    the refinement reaches the FP64 solution."""
+    from _parity import block_lu_backward_error, plain_lu_backward_error
+    n, nb = 384, 128
+    A = orc.generate(44, orc.STREAM_A, n, n, dominant=True)
+    b = orc.generate(44, orc.STREAM_B, n, 1)[:, 0]
+    eb = {p: block_lu_backward_error(A, orc.mxp_factor(A, nb, p)[0], nb) for p in (3, 4, 2, 0)}
+    ep = {p: plain_lu_backward_error(A, orc.mxp_lu_plain(A, nb, p)[0]) for p in (3, 4, 2, 0)}
+    for e in (eb, ep):
+        assert e[3] < e[4] < e[0]
+        assert e[4] < 4 * e[2] and e[2] < 4 * e[4]
+    out = orc.mxp_solve(A, b, nb, prec=orc.PREC_TF32)
+    assert out["status"] == 0 and out["sr"] < 16
+    x64, _ = orc.solve(A, b)
+    assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A, np.inf)
