@@ -570,7 +570,7 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
             warmup=None):
     """HPL-MxP solve of the diagonally dominant system (n = 98304, NB = 4096):
     block-LU factor on the tcgen05 tensor cores (BF16 update; FP8 E4M3 with
-    prec = 1, NB = 4096; scaled FP16 with prec = 2) + FP64 GMRES refinement.
+    prec = 1, NB = 4096; scaled FP16 with prec = 2; TF32 with prec = 3) + FP64 GMRES refinement.
     regen: the library regenerates A from the seed instead of reading a
     stored FP64 copy. storage = 1 keeps the working matrix in BF16. n, steps,
     warmup override the defaults (a one-off larger solve)."""
@@ -626,11 +626,13 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
     peaks = measured_peaks()
     upd_ms, upd_flops, upd_cnt = phases["update"]
     achieved = upd_flops / (upd_ms * 1e-3) / 1e12 if upd_ms > 0 else None
-    # FP8 dense peak: the measured BF16 peak times the nominal FP8/BF16 ratio (4.5 / 2.25)
-    peak = peaks["bf16_tflops_sustained"] * (2.0 if prec == 1 else 1.0)
+    # FP8 and TF32 dense peaks: the measured BF16 peak times the nominal ratio
+    # to BF16 (FP8 4.5 / 2.25, TF32 1.1 / 2.25 PFLOP/s)
+    ratio = {1: 2.0, 3: 1.1 / 2.25}.get(prec, 1.0)
+    peak = peaks["bf16_tflops_sustained"] * ratio
     del A, X, ws
     torch.cuda.empty_cache()
-    tag = {0: "bf16", 1: "fp8e4m3", 2: "fp16"}[prec]
+    tag = {0: "bf16", 1: "fp8e4m3", 2: "fp16", 3: "tf32"}[prec]
     stag = "_bf16storage" if storage else ""
     # the factorization alone: the step minus its refinement phase
     refine_ms = phases["refine"][0] / len(step_ms) if phases["refine"][2] else 0.0
@@ -662,7 +664,8 @@ def run_mxp(a, d: Dist, dev, fp64_value, prec=0, regen=False, cpu=None, storage=
                          "kernel": (f"k_gemm_tc_pair<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, FP32 C, "
                                     "bulk-tensor epilogue)" if not storage else
                                     f"k_gemm_tc<{prec}> (tcgen05 {tag} trailing update A22 -= L21 A12, BF16 C)"),
-                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (" x 2 (FP8/BF16 nominal)" if prec == 1 else ""),
+                         "peak_basis": f"bf16_tflops_sustained ({peaks['source']})" + (
+                             {1: " x 2 (FP8/BF16 nominal)", 3: " x 1.1/2.25 (TF32/BF16 nominal)"}.get(prec, "")),
                          "algorithmic_flops_per_launch": upd_flops / upd_cnt if upd_cnt else None},
             "phases": {k: {"ms_per_step": v[0] / len(step_ms), "intervals": v[2]} for k, v in phases.items() if v[2]}}
 
@@ -802,6 +805,7 @@ def run_ours(a, d: Dist):
     mxp = None if a.no_mxp else run_mxp(a, d, dev, value, cpu=cpu)
     mxp_fp8 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=1, cpu=cpu)
     mxp_fp16 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=2, cpu=cpu)
+    mxp_tf32 = None if a.no_mxp else run_mxp(a, d, dev, value, prec=3, cpu=cpu)
     mxp_regen = None if a.no_mxp else run_mxp(a, d, dev, value, regen=True)
     mxp_bf16s = None if a.no_mxp else run_mxp(a, d, dev, value, storage=1)
     # optional: one larger solve that only BF16 storage and a regenerated A fit
@@ -822,7 +826,7 @@ def run_ours(a, d: Dist):
                              "peak_basis": "152 SMs x 4 FP64 flop/clk x 2070 MHz"},
                 "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches), "clocks": clk,
                 "scaled_residual": sr, "status": rec["status_name"], "phases": phase_report, "step_model": model,
-                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_fp16": mxp_fp16, "mxp_regenerated": mxp_regen, "mxp_bf16_storage": mxp_bf16s, "mxp_large": mxp_large, "batched": batched, "adjoint": adjoint}
+                "fraction_of_fp64_peak": value / peak, "fp64_emulated": emu, "small": small, "mxp": mxp, "mxp_fp8": mxp_fp8, "mxp_fp16": mxp_fp16, "mxp_tf32": mxp_tf32, "mxp_regenerated": mxp_regen, "mxp_bf16_storage": mxp_bf16s, "mxp_large": mxp_large, "batched": batched, "adjoint": adjoint}
         print(json.dumps(line), flush=True)
 
 

@@ -54,7 +54,7 @@ enum {
 };
 
 /* Low-precision operand formats of the mixed-precision factorization. */
-enum { HPL_PREC_BF16 = 0, HPL_PREC_FP8_E4M3 = 1, HPL_PREC_FP16 = 2 };
+enum { HPL_PREC_BF16 = 0, HPL_PREC_FP8_E4M3 = 1, HPL_PREC_FP16 = 2, HPL_PREC_TF32 = 3 };
 
 /* Refinement methods of the mixed-precision solve. */
 enum { HPL_REFINE_IR = 0, HPL_REFINE_GMRES = 1 };
@@ -231,7 +231,10 @@ int hpl_scaled_residual(int64_t n, const double* A, int64_t lda, uint64_t seed, 
  * panel product L21 = A21 D^-1 keeps BF16). opts->prec = HPL_PREC_FP16 uses
  * IEEE FP16 operands, scaled the same way (bound 65504), in both the panel
  * product and the trailing update: about 8x less factorization error than
- * BF16 at the same tensor-core rate.
+ * BF16 at the same tensor-core rate. opts->prec = HPL_PREC_TF32 uses TF32
+ * operands (FP32's exponent range, 10 fraction bits, round to nearest even,
+ * no scales) in both products: FP16's accuracy at half the tensor-core rate.
+ * FP8, FP16 and TF32 operands need FP32 storage.
  * With nrhs > 1 and opts->refine == HPL_REFINE_IR (and A stored) the columns
  * are refined together: each step forms R = B - A X for all of them as one
  * FP64 product and applies the factor to all of them at once (FP32 block
@@ -343,6 +346,16 @@ int hplgb_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t ld
  */
 int hplgb_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B, int64_t ldb,
                    const float* sa, const float* sb, float* C, int64_t ldc, int sub, int32_t* err, void* stream);
+
+/*
+ * hplgb_gemm_tf32 — the TF32 variant (tcgen05 kind::tf32): A (M x K) and B
+ * (N x K) are FP32 words with K contiguous (row strides lda, ldb multiples of
+ * 4 elements, 16-byte aligned), already rounded to TF32 (the MMA reads only
+ * the sign, exponent and top 10 fraction bits); no scales. C, err as
+ * hplgb_gemm_bf16.
+ */
+int hplgb_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                    float* C, int64_t ldc, int sub, int32_t* err, void* stream);
 
 /*
  * hplgb_gemm_config — tuning switches of the tensor-core product, for

@@ -30,6 +30,7 @@ GEN_DIAG_DOMINANT = 1
 PREC_BF16 = 0
 PREC_FP8_E4M3 = 1
 PREC_FP16 = 2
+PREC_TF32 = 3
 STORAGE_FP32 = 0
 STORAGE_BF16 = 1
 INNER_FP64 = 0          # GMRES inner matrix-vector products with the FP64 A
@@ -100,6 +101,7 @@ def load():
             "hplgb_gemm_bf16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
             "hplgb_gemm_fp8": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, vp, vp, i64, i32, vp, vp]),
             "hplgb_gemm_f16": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, vp, vp, i64, i32, vp, vp]),
+            "hplgb_gemm_tf32": (i32, [i64, i64, i64, vp, i64, vp, i64, vp, i64, i32, vp, vp]),
             "mxp_workspace_size": (sz, [i64, i64, op]),
             "lu_solve_backward": (i32, [i64, i64, vp, i64, vp, i64, vp, i64, vp, i64, vp, i64, op, vp, sz, vp, vp]),
             "hpl_batch_sizes": (i32, [u64, i64, vp]),
@@ -515,6 +517,24 @@ def gemm_f16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None
     e = int(err.item())
     if e:
         raise HplError(e, "hplgb_gemm_f16 (device)")
+    return C
+
+
+def gemm_tf32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sub: bool = True) -> torch.Tensor:
+    """C = C - A B^T (sub) or A B^T, A and B float32 words already rounded to
+    TF32 (K contiguous), on the tensor cores' TF32 path."""
+    lib = load()
+    assert A.dtype == torch.float32 and B.dtype == torch.float32 and C.dtype == torch.float32
+    assert A.stride(1) == 1 and B.stride(1) == 1 and C.stride(0) == 1
+    M, K = A.shape
+    N = B.shape[0]
+    err = torch.zeros(1, dtype=torch.int32, device=C.device)
+    _check(lib.hplgb_gemm_tf32(M, N, K, _ptr(A), A.stride(0), _ptr(B), B.stride(0), _ptr(C), _ld(C), int(sub),
+                               _ptr(err), _stream(C.device)), "hplgb_gemm_tf32")
+    torch.cuda.current_stream(C.device).synchronize()
+    e = int(err.item())
+    if e:
+        raise HplError(e, "hplgb_gemm_tf32 (device)")
     return C
 
 

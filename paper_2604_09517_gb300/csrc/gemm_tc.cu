@@ -78,12 +78,16 @@ template <int BN, bool TMA_EPI>
 constexpr int dyn_smem() { return Tile<BN>::DYN_SMEM + (TMA_EPI ? EPI_SMEM : 0); }
 
 // Operand kinds: 0 = BF16 (kind::f16, 2 bytes, 64 K per stage), 1 = FP8 E4M3
-// (kind::f8f6f4, 1 byte, 128 K per stage), 2 = FP16 (kind::f16, 2 bytes).
-// Either way one MMA consumes 32 bytes of K (16 BF16 / FP16 or 32 E4M3
-// values); A and B always have the same type.
+// (kind::f8f6f4, 1 byte, 128 K per stage), 2 = FP16 (kind::f16, 2 bytes),
+// 3 = TF32 (kind::tf32, 4-byte FP32 words of which the MMA uses the sign,
+// exponent and top 10 fraction bits; the operand copies are rounded to TF32
+// beforehand, so the ignored bits are zero; 32 K per stage).
+// Either way one MMA consumes 32 bytes of K (16 BF16 / FP16, 32 E4M3 or 8
+// TF32 values); A and B always have the same type.
 // Instruction descriptor: D = F32 (bits 4-5 = 1); A and B formats in bits
-// 7-9 and 10-12 (kind::f16: F16 = 0, BF16 = 1; kind::f8f6f4: E4M3 = 0); both
-// K-major (bits 15, 16 = 0); N >> 3 at bits 17-22; M >> 4 at bits 24-28.
+// 7-9 and 10-12 (kind::f16: F16 = 0, BF16 = 1; kind::tf32: TF32 = 2;
+// kind::f8f6f4: E4M3 = 0); both K-major (bits 15, 16 = 0); N >> 3 at bits
+// 17-22; M >> 4 at bits 24-28.
 template <int KIND>
 struct Kind;
 template <>
@@ -100,6 +104,11 @@ template <>
 struct Kind<2> {
     static constexpr int ELEM = 2;
     static constexpr uint32_t FORMATS = (1u << 4);
+};
+template <>
+struct Kind<3> {
+    static constexpr int ELEM = 4;
+    static constexpr uint32_t FORMATS = (1u << 4) | (2u << 7) | (2u << 10);
 };
 template <int KIND, int BN>
 __host__ __device__ constexpr uint32_t idesc() {
@@ -229,7 +238,14 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 
 template <int KIND, int BN>
 __device__ __forceinline__ void umma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    if constexpr (KIND == 0 || KIND == 2) {
+    if constexpr (KIND == 3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc<3, BN>()), "r"(accumulate)
+            : "memory");
+    } else if constexpr (KIND == 0 || KIND == 2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -541,7 +557,14 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
 
 template <int KIND>
 __device__ __forceinline__ void umma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    if constexpr (KIND == 0 || KIND == 2) {
+    if constexpr (KIND == 3) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::2.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+            "l"(adesc), "l"(bdesc), "r"(idesc_pair<3>()), "r"(accumulate)
+            : "memory");
+    } else if constexpr (KIND == 0 || KIND == 2) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.b32 p, %4, 0;\n\t"
@@ -803,7 +826,9 @@ static int make_map(CUtensorMap* m, const void* base, int64_t rows, int64_t K, i
     cuuint64_t strides[1] = {(cuuint64_t)ld * elem};
     cuuint32_t box[2] = {(cuuint32_t)(BKB / elem), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(m, elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8, 2,
+    const CUtensorMapDataType dt = elem == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : elem == 2 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+    CUresult r = enc(m, dt, 2,
                      const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                      CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? HPL_OK : HPL_ERR_INVALID;
@@ -1040,9 +1065,27 @@ int launch_gemm_f16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t 
     return tc::launch_kind<2, 256>(M, N, K, A, lda, B, ldb, sa, sb, C, ldc, sub, err, timeout_ns, max_ctas, s);
 }
 
+// TF32 operands (FP32 words already rounded to TF32, K contiguous), no scales.
+int launch_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s) {
+    if (tc::pair_tiles(M, N, tc::tma_epilogue_ok(C, ldc)))
+        return tc::launch_pair<3>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas, s);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<3, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns,
+                                       max_ctas, s);
+    return tc::launch_kind<3, 256>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas,
+                                   s);
+}
+
 }  // namespace hplgb
 
 using namespace hplgb;
+
+extern "C" int hplgb_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B,
+                               int64_t ldb, float* C, int64_t ldc, int sub, int32_t* err, void* stream) {
+    if (!err || !C || !A || !B) return HPL_ERR_INVALID;
+    return launch_gemm_tf32(M, N, K, A, lda, B, ldb, C, ldc, sub, (int*)err, 0, 0, (cudaStream_t)stream);
+}
 
 extern "C" int hplgb_gemm_config(int what, long long value) {
     switch (what) {

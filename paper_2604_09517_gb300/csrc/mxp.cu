@@ -43,6 +43,8 @@ int launch_gemm_bf16_c16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int
 int launch_gemm_fp8(int64_t M, int64_t N, int64_t K, const uint8_t* A, int64_t lda, const uint8_t* B, int64_t ldb,
                     const float* sa, const float* sb, float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
                     int max_ctas, cudaStream_t s);
+int launch_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda, const float* B, int64_t ldb,
+                     float* C, int64_t ldc, int sub, int* err, int64_t timeout_ns, int max_ctas, cudaStream_t s);
 size_t residual_ws_bytes(int64_t n);
 int launch_residual_vec(int64_t n, const double* A, int64_t lda, uint64_t key, const double* diag,
                         const double* anorm, const double* x, const double* b, double* r, double* sr, void* ws,
@@ -199,6 +201,91 @@ static int to_bf16_seg(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int
     const int64_t blocks = std::min<int64_t>((items + 255) / 256, 152 * 32);
     k_to_bf16_n<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g,
                                                                        vec);
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// TF32 operands: FP32 words rounded to TF32 (round to nearest even at
+// fraction bit 13, on the bit pattern: the carry moves into the exponent and
+// past the largest finite value to infinity; subnormals on their fixed grid;
+// NaN and infinity unchanged), so the 13 bits the MMA ignores are zero.
+__device__ __forceinline__ float round_tf32(float x) {
+    uint32_t u = __float_as_uint(x);
+    if ((u & 0x7f800000u) != 0x7f800000u) {
+        u += 0x0FFFu + ((u >> 13) & 1u);
+        u &= 0xFFFFE000u;
+    }
+    return __uint_as_float(u);
+}
+
+// trans = 1 (operand row r holds X(r, 0..cols)): 64 x 32 shared tiles, two
+// values (8 bytes) per lane and store, 256 contiguous bytes per warp.
+__global__ void __launch_bounds__(256) k_to_tf32_t(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                   int64_t cols, float* __restrict__ out, int64_t ldo, int64_t kpad) {
+    __shared__ float tile[64][33];
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const int cc = warp + 8 * j;
+        const int64_t c = c0 + cc, r = r0 + lane;
+        tile[cc][lane] = (c < cols && r < rows) ? X[c * ldx + r] : 0.0f;
+    }
+    __syncthreads();
+    const int64_t c = c0 + 2 * lane;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        const int rr = warp * 4 + i;
+        const int64_t r = r0 + rr;
+        if (r >= rows) continue;
+        float* o = out + r * ldo + c;
+        if (c + 1 < kpad)
+            *reinterpret_cast<float2*>(o) = make_float2(round_tf32(tile[2 * lane][rr]), round_tf32(tile[2 * lane + 1][rr]));
+        else if (c < kpad)
+            *o = round_tf32(tile[2 * lane][rr]);
+    }
+}
+
+// trans = 0 (operand row c holds X(0..rows, c)): 8 values per thread, 16-byte
+// loads and stores when aligned, a grid-stride loop.
+__global__ void __launch_bounds__(256) k_to_tf32_n(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                   int64_t cols, float* __restrict__ out, int64_t ldo, int64_t kpad,
+                                                   int vec) {
+    const int64_t groups = (kpad + 7) / 8;
+    const int64_t total = groups * cols;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = t / groups;
+        const int64_t r = (t - c * groups) * 8;
+        const float* xc = X + c * ldx;
+        float* o = out + c * ldo + r;
+        if (vec && r + 7 < rows && r + 7 < kpad) {
+            const float4 a = *reinterpret_cast<const float4*>(xc + r);
+            const float4 b = *reinterpret_cast<const float4*>(xc + r + 4);
+            *reinterpret_cast<float4*>(o) = make_float4(round_tf32(a.x), round_tf32(a.y), round_tf32(a.z), round_tf32(a.w));
+            *reinterpret_cast<float4*>(o + 4) =
+                make_float4(round_tf32(b.x), round_tf32(b.y), round_tf32(b.z), round_tf32(b.w));
+        } else {
+            for (int e = 0; e < 8 && r + e < kpad; e++) o[e] = r + e < rows ? round_tf32(xc[r + e]) : 0.0f;
+        }
+    }
+}
+
+static int to_tf32(const float* X, int64_t ldx, int64_t rows, int64_t cols, int trans, float* out, int64_t ldo,
+                   int64_t kpad, cudaStream_t s) {
+    if (trans) {
+        if ((ldo & 1) || ((uintptr_t)out & 7)) return HPL_ERR_INVALID;
+        if ((kpad + 63) / 64 > 0x7fffffff || (rows + 31) / 32 > 65535) return HPL_ERR_INVALID;
+        dim3 grid((unsigned)((kpad + 63) / 64), (unsigned)((rows + 31) / 32));
+        k_to_tf32_t<<<grid, 256, 0, s>>>(X, ldx, rows, cols, out, ldo, kpad);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
+    }
+    const int vec = ((uintptr_t)X & 15) == 0 && ldx % 4 == 0 && ((uintptr_t)out & 15) == 0 && ldo % 4 == 0;
+    const int64_t items = ((kpad + 7) / 8) * cols;
+    const int64_t blocks = std::min<int64_t>((items + 255) / 256, 152 * 32);
+    k_to_tf32_n<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(X, ldx, rows, cols, out, ldo, kpad, vec);
     HPL_LAUNCH_CHECK();
     return HPL_OK;
 }
@@ -963,7 +1050,7 @@ struct MxpWs {
 };
 
 static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, int64_t nrhs_blk = 0,
-                            int fbytes = 4, int a32 = 0) {
+                            int fbytes = 4, int a32 = 0, int opbytes = 2) {
     const int64_t nb8 = round8(nb);
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -974,8 +1061,8 @@ static size_t mxp_ws_layout(int64_t n, int64_t nb, int m, MxpWs* w, char* base, 
     MxpWs t;
     t.F = take((size_t)fbytes * n * n);
     t.Dinv = (float*)take(sizeof(float) * n * nb);
-    t.opA = (uint16_t*)take(2 * n * nb8);
-    t.opB = (uint16_t*)take(2 * n * nb8);
+    t.opA = (uint16_t*)take((size_t)opbytes * n * nb8);      // BF16 / FP16 / FP8, or TF32 words
+    t.opB = (uint16_t*)take((size_t)opbytes * n * nb8);
     t.nsD = (uint16_t*)take(2 * nb * 3 * nb8);
     t.nsX = (uint16_t*)take(2 * nb * 3 * nb8);
     t.nsB = (uint16_t*)take(2 * nb * 3 * nb8);
@@ -1165,6 +1252,17 @@ struct Mxp {
                                                   o.timeout_ns, 0, s)))
                             return st;
                         done = true;
+                    } else if (o.prec == HPL_PREC_TF32) {
+                        float* ta = (float*)w.opA;
+                        float* tb = (float*)w.opB;
+                        const int cv = phase_begin(s);
+                        if ((st = to_tf32((const float*)A21, ldf, m2, kb, 1, ta, kb8, kb8, s))) return st;
+                        if ((st = to_tf32(w.X, kb, kb, kb, 0, tb, kb8, kb8, s))) return st;
+                        phase_end(cv, s, PH_OPCONV, (double)(m2 + kb) * kb * 8.0);
+                        if ((st = launch_gemm_tf32(m2, kb, kb, ta, kb8, tb, kb8, (float*)A21, ldf, 0, w.err, o.timeout_ns,
+                                                   0, s)))
+                            return st;
+                        done = true;
                     }
                 }
                 if (!done) {
@@ -1207,8 +1305,20 @@ struct Mxp {
                                               o.timeout_ns, 0, s)))
                         return st;
                     phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
+                } else if (o.prec == HPL_PREC_TF32) {
+                    float* ta = (float*)w.opA;
+                    float* tb = (float*)w.opB;
+                    const int cv = phase_begin(s);
+                    if ((st = to_tf32((const float*)A21, ldf, m2, kb, 1, ta, kb8, kb8, s))) return st;
+                    if ((st = to_tf32((const float*)A12, ldf, kb, m2, 0, tb, kb8, kb8, s))) return st;
+                    phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * 8.0);
+                    const int ug = phase_begin(s);
+                    if ((st = launch_gemm_tf32(m2, m2, kb, ta, kb8, tb, kb8, (float*)A22, ldf, 1, w.err, o.timeout_ns, 0,
+                                               s)))
+                        return st;
+                    phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 }
-                done = o.prec == HPL_PREC_FP8_E4M3 || o.prec == HPL_PREC_FP16;
+                done = o.prec == HPL_PREC_FP8_E4M3 || o.prec == HPL_PREC_FP16 || o.prec == HPL_PREC_TF32;
                 }
                 if (!done) {
                     const int cv = phase_begin(s);
@@ -1568,10 +1678,15 @@ static int fbytes_of(const Opts& o) { return o.storage == HPL_STORAGE_BF16 ? 2 :
 // The FP32 copy of A for GMRES's inner products (opts.inner = FP32, GMRES only).
 static int a32_of(const Opts& o) { return o.inner == HPL_INNER_FP32 && o.refine == HPL_REFINE_GMRES ? 1 : 0; }
 
+// Bytes per element of the low-precision operand copies (TF32 keeps FP32 words).
+static int opbytes_of(const Opts& o) { return o.prec == HPL_PREC_TF32 ? 4 : 2; }
+
 // Option checks shared by the solve and its adjoint: the precision, and BF16
 // storage only with BF16 operands.
 static bool mxp_opts_ok(const Opts& o) {
-    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16)) return false;
+    if (o.nb < 8 || (o.prec != HPL_PREC_BF16 && o.prec != HPL_PREC_FP8_E4M3 && o.prec != HPL_PREC_FP16 &&
+                     o.prec != HPL_PREC_TF32))
+        return false;
     if (o.storage != HPL_STORAGE_FP32 && o.storage != HPL_STORAGE_BF16) return false;
     if (o.storage == HPL_STORAGE_BF16 && o.prec != HPL_PREC_BF16) return false;
     return true;
@@ -1581,7 +1696,7 @@ extern "C" size_t mxp_workspace_size(int64_t n, int64_t nrhs, const hpl_opts* op
     Opts o = resolve_opts(opts, kMxpDefaultNb);
     int64_t nb = std::min<int64_t>(o.nb, std::max<int64_t>(n, 1));
     return mxp_ws_layout(std::max<int64_t>(n, 1), nb, o.gmres_m, nullptr, nullptr, block_rhs(nrhs, o), fbytes_of(o),
-                         a32_of(o));
+                         a32_of(o), opbytes_of(o));
 }
 
 template <typename FT>
@@ -1598,10 +1713,10 @@ static int mxp_solve_t(int64_t n, int64_t nrhs, const double* A, int64_t lda, ui
     mx.lda = lda;
     mx.seed = seed;
     mx.nblk = A ? block_rhs(nrhs, o) : 0;       // the block residual reads a stored A
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o), a32_of(o));
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o), a32_of(o), opbytes_of(o));
     if (!ws || ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o), a32_of(o));
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o), a32_of(o), opbytes_of(o));
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     int st = mx.factor(info);
@@ -1670,10 +1785,10 @@ static int lu_solve_backward_t(int64_t n, int64_t nrhs, const double* A, int64_t
     mx.lda = lda;
     mx.trans = true;
     mx.nblk = block_rhs(nrhs, o);
-    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o));
+    size_t need = mxp_ws_layout(n, mx.nb, mx.m, nullptr, nullptr, mx.nblk, fbytes_of(o), 0, opbytes_of(o));
     if (ws_bytes < need) return HPL_ERR_NOMEM;
     if (((uintptr_t)ws & 255) || ((uintptr_t)info & 7)) return HPL_ERR_INVALID;
-    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o));
+    mxp_ws_layout(n, mx.nb, mx.m, &mx.w, (char*)ws, mx.nblk, fbytes_of(o), 0, opbytes_of(o));
     cudaStream_t s = mx.s;
     HPL_CUDA_TRY(cudaMemsetAsync(info, 0, sizeof(hpl_info), s));
     HPL_CUDA_TRY(cudaMemsetAsync(mx.w.err, 0, sizeof(int) * 4, s));

@@ -125,7 +125,7 @@ def test_gemm_bf16_small_integer_products_are_exact(hpl, M, N, K):
     assert torch.equal(C.double(), exact)
 
 
-@pytest.mark.parametrize("kind", ["bf16", "fp8", "f16"])
+@pytest.mark.parametrize("kind", ["bf16", "fp8", "f16", "tf32"])
 @pytest.mark.parametrize("M,N,K,sub", [(300, 500, 208, True), (2404, 2300, 208, True), (1540, 1030, 96, False),
                                        (2304, 2560, 256, True), (64, 4096, 128, True)])
 def test_gemm_epilogues_bit_identical(hpl, kind, M, N, K, sub):
@@ -143,9 +143,12 @@ def test_gemm_epilogues_bit_identical(hpl, kind, M, N, K, sub):
     elif kind == "fp8":
         A = (torch.randn(M, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
         B = (torch.randn(N, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
-    else:
+    elif kind == "f16":
         A = torch.randn(M, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
         B = torch.randn(N, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
+    else:
+        A = _tf32(torch.randn(M, ld, device="cuda", generator=g))[:, :K]
+        B = _tf32(torch.randn(N, ld, device="cuda", generator=g))[:, :K]
     sa = torch.pow(2.0, torch.randint(-4, 4, (M,), device="cuda", generator=g).float())
     sb = torch.pow(2.0, torch.randint(-4, 4, (N,), device="cuda", generator=g).float())
     C0 = hpl.colmajor(M, N, dtype=torch.float32)
@@ -159,8 +162,10 @@ def test_gemm_epilogues_bit_identical(hpl, kind, M, N, K, sub):
                 hpl.gemm_bf16(A, B, C, sub=sub)
             elif kind == "fp8":
                 hpl.gemm_fp8(A, B, C, sa, sb, sub=sub)
-            else:
+            elif kind == "f16":
                 hpl.gemm_f16(A, B, C, sa, sb, sub=sub)
+            else:
+                hpl.gemm_tf32(A, B, C, sub=sub)
             torch.cuda.synchronize()
             out.append(C)
     finally:
@@ -173,3 +178,41 @@ def test_gemm_config_rejects_unknown(hpl):
         hpl.gemm_config(9, 0)
     with pytest.raises(hpl.HplError):
         hpl.gemm_config(hpl.GEMM_EPILOGUE, 5)
+
+
+def _tf32(x):
+    """Input preparation: round float32 values to TF32 (round to nearest even
+    at fraction bit 13) so that the MMA, which reads only the top 19 bits,
+    sees exactly these values."""
+    import torch
+    u = x.contiguous().view(torch.int32).to(torch.int64) & 0xFFFFFFFF
+    finite = (u & 0x7F800000) != 0x7F800000
+    r = (u + 0x0FFF + ((u >> 13) & 1)) & 0xFFFFE000
+    u = torch.where(finite, r, u)
+    u = torch.where(u >= 2 ** 31, u - 2 ** 32, u).to(torch.int32)
+    return u.view(torch.float32).view(x.shape)
+
+
+@pytest.mark.parametrize("M,N,K,sub", [(128, 256, 64, True), (300, 500, 200, True), (257, 129, 72, False),
+                                       (1536, 2048, 1536, True), (2304, 2560, 256, True), (2404, 2100, 200, True)])
+def test_gemm_tf32_matches_fp64(hpl, M, N, K, sub):
+    """kind::tf32 products of TF32-rounded FP32 operands against the FP64
+    product of the same operands, FP32 accumulation bound; single-CTA and
+    pair kernels, ragged edges and K tails."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + K)
+    ld = (K + 7) // 8 * 8
+    A = _tf32(torch.randn(M, ld, device="cuda", generator=g))[:, :K]
+    B = _tf32(torch.randn(N, ld, device="cuda", generator=g))[:, :K]
+    C = hpl.colmajor(M, N, dtype=torch.float32)
+    C.copy_(torch.randn(M, N, device="cuda", generator=g))
+    C0 = C.clone()
+    hpl.gemm_tf32(A, B, C, sub=sub)
+    prod = A.double() @ B.double().t()
+    ref = C0.double() - prod if sub else prod
+    bound = A.double().abs() @ B.double().abs().t()
+    err = (C.double() - ref).abs()
+    tol = (K * 2.0 ** -23 + 1e-6) * bound + 2.0 ** -23 * C0.double().abs()
+    assert (err > tol).sum().item() == 0, err.max().item()
+    # the operands really are TF32: a BF16 rounding of them would miss this bound
+    assert torch.equal(_tf32(A), A)

@@ -17,6 +17,7 @@ EPS = 2.0 ** -53
 TOL_BF16 = dict(l21=2.0 ** -7, u12=2.0 ** -7, doff=2.0 ** -7, ddiag=1e-5)
 TOL_FP8 = dict(l21=2.0 ** -7, u12=2.0 ** -3, doff=2.0 ** -3, ddiag=1e-4)    # L21 keeps BF16 operands
 TOL_FP16 = dict(l21=2.0 ** -10, u12=2.0 ** -10, doff=2.0 ** -10, ddiag=1e-5)
+TOL_TF32 = TOL_FP16                  # the same 10 fraction bits, FP32's exponent range
 # BF16 storage rounds every stored value (L21 and the updated trailing matrix)
 # to BF16 after each step, so a rounding flip in an earlier step carries into
 # the inputs of later ones: a few units of BF16's 2^-8 relative spacing
@@ -408,4 +409,45 @@ def test_mxp_inner_rejects_unknown(hpl):
     bad = hpl.make_opts(nb=64, inner=2)
     st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, x.data_ptr(), n, ctypes.byref(bad), ws.data_ptr(),
                        need, info.ptr(), torch.cuda.current_stream().cuda_stream)
+    assert st == 1
+
+
+@pytest.mark.parametrize("n,nb", [(512, 128), (1000, 256), (2560, 256), (300, 100)])
+def test_mxp_tf32_variant(hpl, orc, n, nb):
+    """TF32 operands (no scales) in the panel product and the trailing update:
+    factor parts against the oracle's TF32 emulation, backward error against
+    the plain emulation, the FP64 solution and iteration counts."""
+    import torch
+    A, b = _system(hpl, n, 14)
+    A0, b0 = _np(A).copy(order="F"), _np(b).copy()
+    x, info, ws = hpl.mxp_solve(A, b, nb=nb, prec=hpl.PREC_TF32)
+    torch.cuda.synchronize()
+    rec = info.read()
+    assert rec["status"] == 0, rec
+    xg = _np(x)[:, 0]
+    assert orc.scaled_residual(A0, xg, b0) < 16
+    x64, _ = orc.solve(A0, b0)
+    assert np.abs(xg - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A0, np.inf)
+    F, _ = hpl.mxp_factor_views(ws, n, nb)
+    Fg = _np(F).astype(np.float64)
+    Fo, _, _ = orc.mxp_factor(A0, nb, orc.PREC_TF32)
+    assert_blocks_close(Fg, Fo, nb, **TOL_TF32)
+    _check_against_plain(orc, A0, Fg, nb, orc.PREC_TF32)
+    emu = orc.mxp_solve(A0, b0, nb, prec=orc.PREC_TF32, refine=1)
+    assert abs(rec["iters"] - emu["iters"]) <= 2
+    plain = orc.mxp_solve_plain(A0, b0, nb, prec=orc.PREC_TF32, refine=1)
+    assert abs(rec["iters"] - plain["iters"]) <= 2
+
+
+def test_mxp_tf32_rejects_bf16_storage(hpl):
+    import ctypes
+    import torch
+    lib = hpl.load()
+    n = 64
+    A, b = _system(hpl, n, 2)
+    x = hpl.colmajor(n, 1)
+    opts = hpl.make_opts(nb=64, prec=hpl.PREC_TF32, storage=hpl.STORAGE_BF16)
+    ws = hpl.workspace(lib.mxp_workspace_size(n, 1, ctypes.byref(opts)) + 512, A.device)
+    st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, x.data_ptr(), n, ctypes.byref(opts), ws.data_ptr(),
+                       ws.numel(), hpl.Info().ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 1
