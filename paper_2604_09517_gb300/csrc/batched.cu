@@ -1,9 +1,10 @@
 // solve_batched: many independent small systems in one persistent launch.
 //
-// Each CTA takes the next system from an atomic work queue (the plan orders
-// the systems by decreasing estimated cost, longest first) and solves it
-// alone, its matrix in global memory (L2-resident) with one panel of NB
-// columns staged in shared memory:
+// Each CTA takes the next system from one of two atomic work lists (general
+// systems and dominant ones, each ordered by decreasing estimated cost,
+// longest first; the two CTAs that share an SM prefer different lists) and
+// solves it alone, its matrix in global memory (L2-resident) with one panel
+// of NB columns staged in shared memory:
 //   kind 0 (general): HPL's LU with partial pivoting in FP64 (Sec. III-A.1):
 //     blocked right-looking, panel factored in SMEM (block argmax with the
 //     first-index tie rule, row swaps, true division, rank-1), interchanges
@@ -56,12 +57,21 @@ struct Sys {
     int pad2;
 };
 
+// Two work lists, each ordered longest first: general systems (FP64-bound)
+// at table[0, count0), dominant ones (mostly FP32 work) at table[count0,
+// count). Each CTA prefers one list and takes from the other once its own is
+// empty; the two CTAs that share an SM prefer different lists (the first to
+// start on an SM takes the general list), so an FP64-bound system and a
+// mostly-FP32 one run side by side. The counters are cleared by every run.
+constexpr int kMaxSmSlots = 512;
 struct Header {
-    unsigned int counter;
+    unsigned int counter[2];    // next index in list 0 / list 1
+    int count0;                 // systems in list 0
     int count;
     int max_iter;
-    int nb_max;       // widest panel of the plan (16 or 32)
+    int nb_max;                 // widest panel of the plan (16 or 32)
     double tol;
+    unsigned int sm_slot[kMaxSmSlots];   // CTAs started per SM (role by arrival)
 };
 
 // ---- block-wide reductions -------------------------------------------------
@@ -750,11 +760,17 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
     if ((uintptr_t)ws & 255) return HPL_ERR_INVALID;
     Opts o = resolve_opts(opts, bt::NBMAX);
     // longest first
+    // general systems first, then dominant ones, each list longest first
     std::vector<double> cost((size_t)count);
     for (int64_t s = 0; s < count; s++) cost[s] = system_cost(n[s], kind[s]);
     std::vector<int64_t> order((size_t)count);
     std::iota(order.begin(), order.end(), 0);
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) { return cost[a] > cost[b]; });
+    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
+        if (kind[a] != kind[b]) return kind[a] < kind[b];
+        return cost[a] > cost[b];
+    });
+    int64_t count0 = 0;
+    for (int64_t s = 0; s < count; s++) count0 += kind[s] == 0;
     std::vector<bt::Sys> table((size_t)count);
     char* base = (char*)ws;
     for (int64_t q = 0; q < count; q++) {
@@ -784,6 +800,7 @@ extern "C" int solve_batched_plan(int64_t count, const int64_t* n, double* const
     bt::Header h;
     memset(&h, 0, sizeof(h));
     h.count = (int)count;
+    h.count0 = (int)count0;
     h.max_iter = o.max_iter;
     h.tol = o.tol;
     h.nb_max = 16;
@@ -850,7 +867,8 @@ extern "C" int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* 
     const bool narrow = bt::planned_nb(ws) == 16 && bt::g_residency_mode == 0;
     const int per_sm = narrow ? 2 : 1;
     int grid = max_ctas > 0 ? std::min(max_ctas, per_sm * sms) : per_sm * sms;
-    HPL_CUDA_TRY(cudaMemsetAsync(&H->counter, 0, sizeof(unsigned int), s));
+    HPL_CUDA_TRY(cudaMemsetAsync(H->counter, 0, sizeof(H->counter), s));
+    HPL_CUDA_TRY(cudaMemsetAsync(H->sm_slot, 0, sizeof(H->sm_slot), s));
     if (narrow)
         bt::k_batched_run<16, 2><<<grid, bt::THREADS, bt::smem_bytes<16>(), s>>>(table, H, infos);
     else
@@ -882,12 +900,31 @@ __global__ void __launch_bounds__(THREADS, MINB) k_batched_run(const Sys* __rest
     float* X = (float*)(Us + NBR * 65);
     float* R = X + NBR * NBR;
     float* T = R + NBR * NBR;
+    __shared__ int s_pref;
+    if (threadIdx.x == 0) {
+        unsigned smid;
+        asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+        s_pref = (int)(atomicAdd(&H->sm_slot[smid % kMaxSmSlots], 1u) & 1u);
+    }
+    __syncthreads();
+    const int pref = s_pref;
+    const int lo[2] = {0, H->count0}, sz[2] = {H->count0, H->count - H->count0};
     for (;;) {
-        if (threadIdx.x == 0) s_idx = (int)atomicAdd(&H->counter, 1u);
+        if (threadIdx.x == 0) {
+            int idx = -1;
+            for (int q = 0; q < 2 && idx < 0; q++) {
+                const int l = pref ^ q;
+                if (sz[l] > 0 && (int)*(volatile unsigned int*)&H->counter[l] < sz[l]) {
+                    const int t = (int)atomicAdd(&H->counter[l], 1u);
+                    if (t < sz[l]) idx = lo[l] + t;
+                }
+            }
+            s_idx = idx;
+        }
         __syncthreads();
         const int idx = s_idx;
         __syncthreads();
-        if (idx >= H->count) break;
+        if (idx < 0) break;
         const Sys S = table[idx];
         hpl_info* info = infos + S.pad;
         if (threadIdx.x == 0) {
