@@ -394,8 +394,9 @@ def run_adjoint(a, d: Dist, dev):
                  "cpu_oracle_cores": oracle.num_threads(),
                  "cpu_oracle_kind": "FP64 getrf+getrs; adjoint = its own FP64 LU, transposed solves, outer product"}
     return {**extra, "workload": "diff_solve_n4096_nrhs64", "refinement": "classic, all 64 columns as one block",
-            "forward_ms": sum(fwd) / len(fwd),
-            "backward_ms": sum(bwd) / len(bwd), "forward_status": fi["status_name"],
+            "forward_ms": statistics.median(fwd), "backward_ms": statistics.median(bwd),
+            "forward_ms_mean": sum(fwd) / len(fwd), "backward_ms_mean": sum(bwd) / len(bwd),
+            "forward_status": fi["status_name"],
             "backward_status": binfo.read()["status_name"], "forward_scaled_residual": fi["scaled_residual"],
             "backward_scaled_residual": bi["scaled_residual"], "forward_iters": fi["iters"],
             "backward_iters": bi["iters"],
@@ -763,11 +764,10 @@ def run_ours(a, d: Dist):
         A_h.copy_(A)
         b_h = b0.cpu().pin_memory()
         x_h = torch.empty(n, dtype=torch.float64, pin_memory=True)
-        # untimed warm-up copies: the first transfers from a fresh 8.6 GB pinned
-        # buffer run several times slower than later ones (measured 0.2-1.5 s
-        # against 41 ms)
-        for _ in range(2):
-            A.copy_(A_h, non_blocking=True)
+        # the library's kernel copy from the pinned buffer (hpl_upload): the copy
+        # engine's cudaMemcpyAsync of 8.6 GB took 41 ms back to back but 0.3-0.8 s
+        # after the GPU had been busy or idle, the kernel copy 41-49 ms every time
+        hpl.upload(A, A_h)
         torch.cuda.synchronize(dev)
         e2e_ms = []
         for _ in range(a.steps):
@@ -776,8 +776,8 @@ def run_ours(a, d: Dist):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            A.copy_(A_h, non_blocking=True)
-            b.copy_(b_h, non_blocking=True)
+            hpl.upload(A, A_h)
+            hpl.upload(b, b_h)
             solve()
             x_h.copy_(b, non_blocking=True)
             e1.record(stream)

@@ -314,6 +314,22 @@ int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64
                   size_t ws_bytes, hpl_info* infos, void* stream);
 
 /*
+ * hpl_upload — copy an FP64 column-major m x n matrix from host memory the
+ * device can address (src, leading dimension lds: page-locked memory from
+ * cudaHostAlloc / cudaHostRegister or a torch pinned tensor, or any host
+ * memory on platforms that give the GPU access to pageable memory, such as
+ * Grace) into device memory (dst, ldd), asynchronously on
+ * `stream`, by a kernel that reads the host buffer through its mapped device
+ * address rather than by the copy engine (on GB300 the copy engine's large
+ * host-to-device copies were measured to stall for hundreds of ms after the
+ * GPU had been busy or idle; the kernel copy ran at the link's 210 GB/s every
+ * time). Not in the paper: the data staging of a solve whose inputs start on
+ * the host. HPL_ERR_INVALID for bad sizes or a host buffer the device cannot
+ * address (message in hplgb_last_error); nothing is launched then.
+ */
+int hpl_upload(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd, void* stream);
+
+/*
  * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path
  * (Sec. III-A.2: the factorization and trailing updates run in low precision;
  * Table I: BF16 + FP32 + FP64): C = C - A B^T (sub = 1) or C = A B^T (sub = 0),

@@ -113,6 +113,7 @@ def load():
             "hplgb_launch_count": (ctypes.c_longlong, []),
             "hplgb_set_phase_timing": (None, [i32]),
             "hplgb_gemm_config": (i32, [i32, ctypes.c_longlong]),
+            "hpl_upload": (i32, [i64, i64, vp, i64, vp, i64, vp]),
             "hplgb_batched_config": (i32, [i32, ctypes.c_longlong]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
             "hplgb_phase_records": (i32, [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]),
@@ -518,6 +519,19 @@ def gemm_f16(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sa=None, sb=None
     if e:
         raise HplError(e, "hplgb_gemm_f16 (device)")
     return C
+
+
+def upload(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """Copy the host FP64 matrix src (page-locked, or any host memory where the
+    GPU can address pageable memory) into the device matrix dst (both
+    column-major, stride(0) == 1) with the library's kernel copy (hpl_upload)."""
+    assert src.dtype == torch.float64 and dst.dtype == torch.float64 and dst.is_cuda and not src.is_cuda
+    if src.dim() == 1:
+        src, dst = src.view(-1, 1), dst.view(-1, 1)
+    assert src.shape == dst.shape and src.stride(0) == 1 and dst.stride(0) == 1
+    m, n = src.shape
+    _check(load().hpl_upload(m, n, _ptr(src), _ld(src), _ptr(dst), _ld(dst), _stream(dst.device)), "hpl_upload")
+    return dst
 
 
 def gemm_tf32(A: torch.Tensor, B: torch.Tensor, C: torch.Tensor, sub: bool = True) -> torch.Tensor:

@@ -90,30 +90,50 @@ struct Seg {
 
 __device__ __forceinline__ float eye2_of(float v, int64_t r, int64_t c) { return (r == c ? 2.0f : 0.0f) - v; }
 
-// trans = 1: a transpose through a 64 (K) x 32 (operand rows) shared tile, one per CTA.
-// Each warp reads 128 contiguous bytes of one column of X per instruction and
-// writes 128 contiguous bytes (64 BF16 values, two per lane) of one operand
-// row per instruction.
+// trans = 1: a transpose through a 64 (K) x 64 (operand rows) shared tile, one
+// per CTA. Each warp reads 256 contiguous bytes of one column of X per
+// instruction (two FP32 values per lane when aligned) and writes 128 contiguous
+// bytes (64 BF16 values, two per lane) of one operand row per instruction.
 template <typename XT>
 __global__ void __launch_bounds__(256) k_to_bf16_t(const XT* __restrict__ X, int64_t ldx, int64_t rows,
                                                    int64_t cols, __nv_bfloat16* __restrict__ out, int64_t ldo,
-                                                   Seg g) {
-    __shared__ float tile[64][33];
-    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 32;
+                                                   Seg g, int vec2) {
+    __shared__ float tile[64][65];
+    const int64_t c0 = (int64_t)blockIdx.x * 64, r0 = (int64_t)blockIdx.y * 64;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < 8; j++) {
         const int cc = warp + 8 * j;
-        const int64_t c = c0 + cc, r = r0 + lane;
-        float v = (c < cols && r < rows) ? ld_f(X + c * ldx + r) : 0.0f;
-        if (g.eye2 && c < cols && r < rows) v = eye2_of(v, r, c);
-        tile[cc][lane] = v;
+        const int64_t c = c0 + cc, r = r0 + 2 * lane;
+        float v0 = 0.0f, v1 = 0.0f;
+        if (c < cols) {
+            const XT* xc = X + c * ldx;
+            if constexpr (std::is_same<XT, float>::value) {
+                if (vec2 && r + 1 < rows) {
+                    const float2 t = *reinterpret_cast<const float2*>(xc + r);
+                    v0 = t.x;
+                    v1 = t.y;
+                } else {
+                    if (r < rows) v0 = xc[r];
+                    if (r + 1 < rows) v1 = xc[r + 1];
+                }
+            } else {
+                if (r < rows) v0 = ld_f(xc + r);
+                if (r + 1 < rows) v1 = ld_f(xc + r + 1);
+            }
+            if (g.eye2) {
+                if (r < rows) v0 = eye2_of(v0, r, c);
+                if (r + 1 < rows) v1 = eye2_of(v1, r + 1, c);
+            }
+        }
+        tile[cc][2 * lane] = v0;
+        tile[cc][2 * lane + 1] = v1;
     }
     __syncthreads();
     const int64_t c = c0 + 2 * lane;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const int rr = warp * 4 + i;
+    for (int i = 0; i < 8; i++) {
+        const int rr = warp * 8 + i;
         const int64_t r = r0 + rr;
         if (r >= rows) continue;
         const float v0 = tile[2 * lane][rr], v1 = tile[2 * lane + 1][rr];
@@ -187,10 +207,11 @@ static int to_bf16_seg(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int
     if (trans) {
         // BF16 pairs are stored 4-byte aligned: even strides and offsets
         if ((ldo | g.seg_off | g.seg_stride) & 1 || ((uintptr_t)out & 3)) return HPL_ERR_INVALID;
-        // one 64 x 32 tile per CTA (a grid-stride loop over tiles measured slower)
-        if ((g.kpad + 63) / 64 > 0x7fffffff || (rows + 31) / 32 > 65535) return HPL_ERR_INVALID;
-        dim3 grid((unsigned)((g.kpad + 63) / 64), (unsigned)((rows + 31) / 32));
-        k_to_bf16_t<<<grid, 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g);
+        // one 64 x 64 tile per CTA (a grid-stride loop over tiles measured slower)
+        if ((g.kpad + 63) / 64 > 0x7fffffff || (rows + 63) / 64 > 65535) return HPL_ERR_INVALID;
+        dim3 grid((unsigned)((g.kpad + 63) / 64), (unsigned)((rows + 63) / 64));
+        const int vec2 = ((uintptr_t)X & 7) == 0 && ldx % 2 == 0;
+        k_to_bf16_t<<<grid, 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g, vec2);
         HPL_LAUNCH_CHECK();
         return HPL_OK;
     }

@@ -1,0 +1,57 @@
+"""hpl_upload: FP64 column-major matrices from page-locked host memory into
+device memory by the library's copy kernel (the end-to-end path's data
+staging), through the C ABI."""
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+def test_upload_contiguous_and_strided(hpl):
+    import torch
+    g = torch.Generator().manual_seed(5)
+    # contiguous (the 16-byte flat path)
+    n = 1024
+    src = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    src.copy_(torch.randn(n, n, generator=g, dtype=torch.float64))
+    dst = hpl.colmajor(n, n)
+    hpl.upload(dst, src)
+    torch.cuda.synchronize()
+    assert torch.equal(dst.cpu(), src)
+    # leading dimensions larger than the rows, odd rows (the column path)
+    m, k, lds, ldd = 777, 301, 800, 779
+    big = torch.empty((k, lds), dtype=torch.float64, pin_memory=True)
+    big.copy_(torch.randn(k, lds, generator=g, dtype=torch.float64))
+    src = big.t()[:m]                               # m x k view, stride(1) = lds
+    dbuf = torch.full((k, ldd), -7.0, dtype=torch.float64, device="cuda")
+    dst = dbuf.t()[:m]
+    hpl.upload(dst, src)
+    torch.cuda.synchronize()
+    assert torch.equal(dst.cpu(), src)
+    assert bool((dbuf.t()[m:] == -7.0).all())        # rows beyond m untouched
+    # a vector
+    v = torch.randn(333, generator=g, dtype=torch.float64).pin_memory()
+    dv = torch.empty(333, dtype=torch.float64, device="cuda")
+    hpl.upload(dv, v)
+    torch.cuda.synchronize()
+    assert torch.equal(dv.cpu(), v)
+
+
+def test_upload_pageable_memory_copied_or_refused(hpl):
+    """Pageable host memory: where the platform lets the GPU address it (Grace:
+    the runtime maps every host address) the copy must be exact; elsewhere it
+    is refused with HPL_ERR_INVALID and nothing is written."""
+    import torch
+    src = torch.randn(64, 64, dtype=torch.float64).t()    # not page-locked
+    dst = hpl.colmajor(64, 64)
+    dst.zero_()
+    try:
+        hpl.upload(dst, src)
+        refused = False
+    except hpl.HplError as e:
+        refused = True
+        assert e.status == 1
+    torch.cuda.synchronize()
+    if refused:
+        assert bool((dst == 0).all())
+    else:
+        assert torch.equal(dst.cpu(), src)
