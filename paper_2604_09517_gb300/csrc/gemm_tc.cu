@@ -125,6 +125,8 @@ struct Params {
     const float* sa;       // optional per-row scale of the product (M)
     const float* sb;       // optional per-column scale of the product (N)
     int group_m;           // row tiles per band of the tile walk
+    uint16_t* C16;         // optional BF16 copy of a stored product (sub = 0), row-major, ld16 a multiple of 8
+    long long ld16;
 };
 
 
@@ -201,10 +203,13 @@ __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.a
 // C += -value (sub) or C = value, at tensor coordinates (x = first row,
 // y = first column). `stage` is the warp's 4 KB chunk of shared memory. The
 // tensor map clips rows and columns outside C, so no masking is needed; only
-// the scale reads are guarded.
+// the scale reads are guarded. With a stored product (sub = 0) and C16, the
+// lane also writes its row's 32 values rounded to BF16 to C16 (row-major,
+// columns below ld16; the accumulator is zero past the product's last column,
+// so the padding of each C16 row up to ld16 is written as zeros).
 __device__ __forceinline__ void epi_chunk_tma(const CUtensorMap* tmC, float* stage, const uint32_t (&r)[32], float rs,
                                               const float* sb, int col0, int ncol_left, int sub, int x, int y,
-                                              int lane) {
+                                              int lane, uint16_t* C16 = nullptr, long long ld16 = 0, int M = 0) {
     if (lane == 0) bulk_wait_read_all();      // the warp's previous chunk has left the stage
     __syncwarp();
 #pragma unroll
@@ -212,6 +217,18 @@ __device__ __forceinline__ void epi_chunk_tma(const CUtensorMap* tmC, float* sta
         float v = __uint_as_float(r[j]) * rs;
         if (sb) v *= j < ncol_left ? sb[col0 + j] : 0.0f;
         stage[j * 32 + lane] = sub ? -v : v;
+    }
+    if (C16 && !sub && x + lane < M) {
+        uint16_t* dst = C16 + (long long)(x + lane) * ld16 + y;
+#pragma unroll
+        for (int q = 0; q < 4; q++) {
+            if (y + 8 * q + 8 <= ld16) {
+                __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+                for (int e = 0; e < 8; e++) h[e] = __float2bfloat16_rn(stage[(8 * q + e) * 32 + lane]);
+                *reinterpret_cast<uint4*>(dst + 8 * q) = *reinterpret_cast<const uint4*>(h);
+            }
+        }
     }
     fence_async_smem();
     __syncwarp();
@@ -425,7 +442,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 }
                 if (c * 32 < ncol)
                     epi_chunk_tma(&tmC, stage, r, rs, p.sb, cbase + c * 32, ncol - c * 32, p.sub, row0,
-                                  cbase + c * 32, lane);
+                                  cbase + c * 32, lane, p.C16, p.ld16, p.M);
             }
         }
         if (lane == 0) bulk_wait_all();
@@ -725,7 +742,7 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                 }
                 if (c * 32 < ncol)
                     epi_chunk_tma(&tmC, stage, r, rs, p.sb, cbase + c * 32, ncol - c * 32, p.sub, row0,
-                                  cbase + c * 32, lane);
+                                  cbase + c * 32, lane, p.C16, p.ld16, p.M);
             }
         }
         if (lane == 0) bulk_wait_all();
@@ -887,7 +904,7 @@ static int launch_kind_epi(const CUtensorMap& ma, const CUtensorMap& mb, const C
 template <int KIND, int BN, typename CT = float>
 static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                        const float* sa, const float* sb, CT* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
-                       int max_ctas, cudaStream_t s) {
+                       int max_ctas, cudaStream_t s, uint16_t* C16 = nullptr, int64_t ld16 = 0) {
     constexpr int elem = Kind<KIND>::ELEM;
     if (M <= 0 || N <= 0) return HPL_OK;
     if (K <= 0) return HPL_ERR_INVALID;
@@ -921,6 +938,8 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
+    p.C16 = C16;
+    p.ld16 = ld16;
     p.group_m = g_group_m_override > 0 ? g_group_m_override : group_m<KIND>();
     if (tma_epi) return launch_kind_epi<KIND, BN, CT, true>(ma, mb, mc, p, grid, s);
     return launch_kind_epi<KIND, BN, CT, false>(ma, mb, mc, p, grid, s);
@@ -955,7 +974,7 @@ static int pair_capacity() {
 template <int KIND, typename CT = float>
 static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t lda, const void* B, int64_t ldb,
                        const float* sa, const float* sb, CT* C, int64_t ldc, int sub, int* err, int64_t timeout_ns,
-                       int max_ctas, cudaStream_t s) {
+                       int max_ctas, cudaStream_t s, uint16_t* C16 = nullptr, int64_t ld16 = 0) {
     constexpr int elem = Kind<KIND>::ELEM;
     if (M <= 0 || N <= 0) return HPL_OK;
     if (K <= 0) return HPL_ERR_INVALID;
@@ -988,6 +1007,8 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.timeout_ns = timeout_ns > 0 ? timeout_ns : kDefaultTimeoutNs;
     p.sa = sa;
     p.sb = sb;
+    p.C16 = C16;
+    p.ld16 = ld16;
     p.group_m = g_group_m_override > 0 ? g_group_m_override : GROUP_M_PAIR;
     if (tma_epi)
         k_gemm_tc_pair<KIND, CT, true><<<2 * pairs, THREADS, pair_dyn_smem<true>(), s>>>(ma, mb, mc, p);
@@ -1025,6 +1046,31 @@ int launch_gemm_bf16(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t
                                        max_ctas, s);
     return tc::launch_kind<0, 256>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, sub, err, timeout_ns, max_ctas,
                                    s);
+}
+
+// A stored BF16 product C = A B^T (FP32 C) that also writes C rounded to BF16,
+// row-major, into C16 (ld16 >= N, a multiple of 8; columns N .. ld16-1 of each
+// row written as zeros): the operand copy of the next product without a
+// separate pass. Only where the bulk-tensor epilogue serves C
+// (gemm_bf16_copy_ok); HPL_ERR_INVALID otherwise.
+bool gemm_bf16_copy_ok(const float* C, int64_t ldc, const uint16_t* C16, int64_t N, int64_t ld16) {
+    // columns N .. ld16-1 must lie in the last 32-column chunk that holds product columns
+    return tc::tma_epilogue_ok(C, ldc) && C16 && ((uintptr_t)C16 & 15) == 0 && ld16 % 8 == 0 && ld16 >= N &&
+           ld16 <= (N + 31) / 32 * 32;
+}
+
+int launch_gemm_bf16_copy(int64_t M, int64_t N, int64_t K, const uint16_t* A, int64_t lda, const uint16_t* B,
+                          int64_t ldb, float* C, int64_t ldc, uint16_t* C16, int64_t ld16, int* err, int64_t timeout_ns,
+                          cudaStream_t s) {
+    if (!gemm_bf16_copy_ok(C, ldc, C16, N, ld16)) return HPL_ERR_INVALID;
+    if (tc::pair_tiles(M, N, true))
+        return tc::launch_pair<0>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, 0, err, timeout_ns, 0, s, C16,
+                                  ld16);
+    if (tc::narrow_tiles(M, N))
+        return tc::launch_kind<0, 128>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, 0, err, timeout_ns, 0, s,
+                                       C16, ld16);
+    return tc::launch_kind<0, 256>(M, N, K, A, lda, B, ldb, nullptr, nullptr, C, ldc, 0, err, timeout_ns, 0, s, C16,
+                                   ld16);
 }
 
 // FP8 E4M3 operands (bytes, K contiguous); the product of row i and column j

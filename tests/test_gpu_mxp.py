@@ -451,3 +451,26 @@ def test_mxp_tf32_rejects_bf16_storage(hpl):
     st = lib.mxp_solve(n, 1, A.data_ptr(), n, 0, b.data_ptr(), n, x.data_ptr(), n, ctypes.byref(opts), ws.data_ptr(),
                        ws.numel(), hpl.Info().ptr(), torch.cuda.current_stream().cuda_stream)
     assert st == 1
+
+
+@pytest.mark.parametrize("n,nb", [(1000, 256), (2600, 512), (777, 128), (5000, 1024)])
+def test_mxp_l21_copy_from_the_product_epilogue(hpl, n, nb):
+    """With the bulk-tensor epilogue the L21 product also writes L21's BF16
+    operand copy for the trailing update (no separate transposing pass); with
+    the per-thread epilogue that copy is made by the conversion kernel. Both
+    factorizations must be bit-identical (ragged last blocks included: the
+    copy's padding columns are zeros)."""
+    import torch
+    A, b = _system(hpl, n, 7)
+    x0, i0, ws0 = hpl.mxp_solve(A, b, nb=nb, prec=0)
+    hpl.gemm_config(hpl.GEMM_EPILOGUE, 1)
+    try:
+        x1, i1, ws1 = hpl.mxp_solve(A, b, nb=nb, prec=0)
+    finally:
+        hpl.gemm_config(hpl.GEMM_EPILOGUE, 0)
+    torch.cuda.synchronize()
+    F0, D0 = hpl.mxp_factor_views(ws0, n, nb)
+    F1, D1 = hpl.mxp_factor_views(ws1, n, nb)
+    assert torch.equal(F0, F1) and torch.equal(D0, D1)
+    assert torch.equal(x0, x1)
+    assert i0.read()["status"] == 0
