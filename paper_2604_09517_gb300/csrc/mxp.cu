@@ -419,59 +419,160 @@ __device__ __forceinline__ void store4(uint16_t* o, const uint16_t (&q)[4]) {
 }
 
 // A operand: X (rows x cols, column-major) -> out row r = X(r, :) (K = cols),
-// sa[r] = 2^e. 32 rows per CTA, the 8 warps split the columns.
+// sa[r] = 2^e. 128 rows per CTA. Pass 1 takes each row's largest |x|, every
+// warp reading 512 contiguous bytes of a column per instruction; pass 2 moves
+// 32-column tiles through shared memory and writes 32 consecutive values of
+// each row (the first version, 32 rows per CTA, read 128 bytes per column and
+// instruction and ran at under half the HBM bandwidth).
 template <int FMT>
 __global__ void __launch_bounds__(256) k_quant_rows(const float* __restrict__ X, int64_t ldx, int64_t rows,
                                                     int64_t cols, typename LowFmt<FMT>::T* __restrict__ out,
-                                                    int64_t ldo, int64_t kpad, float* __restrict__ sa) {
+                                                    int64_t ldo, int64_t kpad, float* __restrict__ sa, int vec4) {
     using T = typename LowFmt<FMT>::T;
-    __shared__ float part[8][33];
-    __shared__ float inv[32];
-    __shared__ float tile[128][33];
+    __shared__ float part[8][129];
+    __shared__ float inv[128];
+    __shared__ float tile[32][129];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int64_t r0 = (int64_t)blockIdx.x * 32;
-    const int64_t r = r0 + lane;
-    float amax = 0.0f;
-    if (r < rows)
-        for (int64_t c = warp; c < cols; c += 8) amax = fmaxf(amax, fabsf(X[c * ldx + r]));
-    part[warp][lane] = amax;
+    const int64_t r0 = (int64_t)blockIdx.x * 128;
+    const int64_t r = r0 + 4 * lane;
+    auto load4 = [&](int64_t c, float (&v)[4]) {
+        v[0] = v[1] = v[2] = v[3] = 0.0f;
+        if (c >= cols) return;
+        const float* xc = X + c * ldx;
+        if (vec4 && r + 3 < rows) {
+            const float4 t = *reinterpret_cast<const float4*>(xc + r);
+            v[0] = t.x;
+            v[1] = t.y;
+            v[2] = t.z;
+            v[3] = t.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (r + e < rows) v[e] = xc[r + e];
+        }
+    };
+    // four column loads in flight per warp (a CTA stays resident for the
+    // whole row block, so the loads in flight per SM set the bandwidth)
+    float am[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    int64_t c1 = warp;
+    for (; c1 + 24 < cols; c1 += 32) {
+        float v0[4], v1[4], v2[4], v3[4];
+        load4(c1, v0);
+        load4(c1 + 8, v1);
+        load4(c1 + 16, v2);
+        load4(c1 + 24, v3);
+#pragma unroll
+        for (int e = 0; e < 4; e++)
+            am[e] = fmaxf(am[e], fmaxf(fmaxf(fabsf(v0[e]), fabsf(v1[e])), fmaxf(fabsf(v2[e]), fabsf(v3[e]))));
+    }
+    for (; c1 < cols; c1 += 8) {
+        float v[4];
+        load4(c1, v);
+#pragma unroll
+        for (int e = 0; e < 4; e++) am[e] = fmaxf(am[e], fabsf(v[e]));
+    }
+#pragma unroll
+    for (int e = 0; e < 4; e++) part[warp][4 * lane + e] = am[e];
     __syncthreads();
-    if (warp == 0) {
+    if (threadIdx.x < 128) {
         float m = 0.0f;
-        for (int w = 0; w < 8; w++) m = fmaxf(m, part[w][lane]);
+        for (int w = 0; w < 8; w++) m = fmaxf(m, part[w][threadIdx.x]);
         const int e = LowFmt<FMT>::scale_exp(m);
-        inv[lane] = ldexpf(1.0f, -e);
-        if (r < rows) sa[r] = ldexpf(1.0f, e);
+        inv[threadIdx.x] = ldexpf(1.0f, -e);
+        if (r0 + threadIdx.x < rows) sa[r0 + threadIdx.x] = ldexpf(1.0f, e);
     }
     __syncthreads();
-    // 32 rows x 128 columns per pass: each warp reads 128 contiguous bytes of
-    // one column per instruction and writes four converted values per lane
-    // (128 bytes of FP8 or 256 of FP16 per row and instruction)
-    for (int64_t c0 = 0; c0 < kpad; c0 += 128) {
-#pragma unroll 4
-        for (int i = warp; i < 128; i += 8) {
-            const int64_t c = c0 + i;
-            tile[i][lane] = (r < rows && c < cols) ? X[c * ldx + r] : 0.0f;
+    // 8 lanes per row, four values each; four rows per warp instruction. The
+    // next tile's columns are loaded into registers while this one is written.
+    const int sub = lane >> 3, l = lane & 7;
+    float nv[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) load4(warp + 8 * j, nv[j]);
+    for (int64_t c0 = 0; c0 < kpad; c0 += 32) {
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const int cc = warp + 8 * j;
+#pragma unroll
+            for (int e = 0; e < 4; e++) tile[cc][4 * lane + e] = nv[j][e];
         }
         __syncthreads();
-        const int64_t c = c0 + 4 * lane;
+        if (c0 + 32 < kpad) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) load4(c0 + 32 + warp + 8 * j, nv[j]);
+        }
+        const int64_t c = c0 + 4 * l;
 #pragma unroll
         for (int i = 0; i < 4; i++) {
-            const int rr = warp * 4 + i;
+            const int rr = warp * 16 + 4 * i + sub;
             const int64_t row = r0 + rr;
-            if (row >= rows) continue;
+            if (row >= rows || c >= kpad) continue;
             const float sc = inv[rr];
             T* o = out + row * ldo + c;
-            if (c + 3 < kpad) {
-                T q[4];
+            T q[4];
 #pragma unroll
-                for (int e = 0; e < 4; e++) q[e] = LowFmt<FMT>::cvt(tile[4 * lane + e][rr] * sc);
+            for (int e = 0; e < 4; e++) q[e] = LowFmt<FMT>::cvt(tile[4 * l + e][rr] * sc);
+            if (c + 3 < kpad) {
                 store4(o, q);
             } else {
-                for (int e = 0; e < 4 && c + e < kpad; e++) o[e] = LowFmt<FMT>::cvt(tile[4 * lane + e][rr] * sc);
+                for (int e = 0; e < 4 && c + e < kpad; e++) o[e] = q[e];
             }
         }
         __syncthreads();
+    }
+}
+
+// B operand, K <= 4096: one CTA per column, read once into registers (16
+// values per thread), the column's largest |x| reduced in the CTA, then the
+// scaled values converted and written.
+template <int FMT>
+__global__ void __launch_bounds__(256) k_quant_col_cta(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                                       typename LowFmt<FMT>::T* __restrict__ out, int64_t ldo,
+                                                       int64_t kpad, float* __restrict__ sb) {
+    using T = typename LowFmt<FMT>::T;
+    __shared__ float red[8];
+    const int64_t c = blockIdx.x;
+    const float* col = X + c * ldx;
+    const int t = threadIdx.x;
+    float v[16];
+    float am = 0.0f;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t r = 1024 * k + 4 * t;
+        if (r + 3 < rows) {
+            const float4 q = *reinterpret_cast<const float4*>(col + r);
+            v[4 * k] = q.x;
+            v[4 * k + 1] = q.y;
+            v[4 * k + 2] = q.z;
+            v[4 * k + 3] = q.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 4; e++) v[4 * k + e] = r + e < rows ? col[r + e] : 0.0f;
+        }
+#pragma unroll
+        for (int e = 0; e < 4; e++) am = fmaxf(am, fabsf(v[4 * k + e]));
+    }
+    for (int off = 16; off > 0; off >>= 1) am = fmaxf(am, __shfl_xor_sync(0xffffffffu, am, off));
+    if ((t & 31) == 0) red[t >> 5] = am;
+    __syncthreads();
+    float m = red[0];
+#pragma unroll
+    for (int w = 1; w < 8; w++) m = fmaxf(m, red[w]);
+    const int e = LowFmt<FMT>::scale_exp(m);
+    const float inv = ldexpf(1.0f, -e);
+    if (t == 0) sb[c] = ldexpf(1.0f, e);
+    T* o = out + c * ldo;
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+        const int64_t r = 1024 * k + 4 * t;
+        if (r >= kpad) continue;
+        T q[4];
+#pragma unroll
+        for (int e2 = 0; e2 < 4; e2++) q[e2] = LowFmt<FMT>::cvt(v[4 * k + e2] * inv);
+        if (r + 3 < kpad) {
+            store4(o + r, q);
+        } else {
+            for (int e2 = 0; e2 < 4 && r + e2 < kpad; e2++) o[r + e2] = q[e2];
+        }
     }
 }
 
@@ -522,6 +623,31 @@ __global__ void __launch_bounds__(256) k_quant_cols(const float* __restrict__ X,
     } else {
         for (int64_t r = lane; r < kpad; r += 32) o[r] = LowFmt<FMT>::cvt(r < rows ? col[r] * inv : 0.0f);
     }
+}
+
+// Host side of the scaled operand copies.
+template <int FMT>
+static int quant_rows(const float* X, int64_t ldx, int64_t rows, int64_t cols, typename LowFmt<FMT>::T* out,
+                      int64_t ldo, int64_t kpad, float* sa, cudaStream_t s) {
+    if (rows <= 0) return HPL_OK;
+    k_quant_rows<FMT><<<(unsigned)((rows + 127) / 128), 256, 0, s>>>(X, ldx, rows, cols, out, ldo, kpad, sa,
+                                                                     vec4_ok(X, ldx));
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
+
+template <int FMT>
+static int quant_cols(const float* X, int64_t ldx, int64_t rows, int64_t cols, typename LowFmt<FMT>::T* out,
+                      int64_t ldo, int64_t kpad, float* sb, cudaStream_t s) {
+    if (cols <= 0) return HPL_OK;
+    const int vec = vec4_ok(X, ldx);
+    if (vec && kpad <= 4096 && cols <= 0x7fffffff) {
+        k_quant_col_cta<FMT><<<(unsigned)cols, 256, 0, s>>>(X, ldx, rows, out, ldo, kpad, sb);
+    } else {
+        k_quant_cols<FMT><<<(unsigned)((cols + 7) / 8), 256, 0, s>>>(X, ldx, rows, cols, out, ldo, kpad, sb, vec);
+    }
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1298,12 +1424,8 @@ struct Mxp {
                 bool done = false;
                 if constexpr (!kBf16) {
                     if (o.prec == HPL_PREC_FP16) {
-                        k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8,
-                                                                                   w.sa);
-                        HPL_LAUNCH_CHECK();
-                        k_quant_cols<2><<<(unsigned)((kb + 7) / 8), 256, 0, s>>>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb,
-                                                                          vec4_ok(w.X, kb));
-                        HPL_LAUNCH_CHECK();
+                        if ((st = quant_rows<2>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa, s))) return st;
+                        if ((st = quant_cols<2>(w.X, kb, kb, kb, w.opB, kb8, kb8, w.sb, s))) return st;
                         if ((st = launch_gemm_f16(m2, kb, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A21, ldf, 0, w.err,
                                                   o.timeout_ns, 0, s)))
                             return st;
@@ -1350,11 +1472,8 @@ struct Mxp {
                     uint8_t* qa = (uint8_t*)w.opA;
                     uint8_t* qb = (uint8_t*)w.opB;
                     const int cv = phase_begin(s);
-                    k_quant_rows<1><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa);
-                    HPL_LAUNCH_CHECK();
-                    k_quant_cols<1><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb,
-                                                                           vec4_ok(A12, ldf));
-                    HPL_LAUNCH_CHECK();
+                    if ((st = quant_rows<1>(A21, ldf, m2, kb, qa, kb16, kb16, w.sa, s))) return st;
+                    if ((st = quant_cols<1>(A12, ldf, kb, m2, qb, kb16, kb16, w.sb, s))) return st;
                     phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * (4 + 1));
                     const int ug = phase_begin(s);
                     if ((st = launch_gemm_fp8(m2, m2, kb, qa, kb16, qb, kb16, w.sa, w.sb, A22, ldf, 1, w.err,
@@ -1363,11 +1482,8 @@ struct Mxp {
                     phase_end(ug, s, PH_UPDATE, 2.0 * m2 * m2 * kb);
                 } else if (o.prec == HPL_PREC_FP16) {
                     const int cv = phase_begin(s);
-                    k_quant_rows<2><<<(unsigned)((m2 + 31) / 32), 256, 0, s>>>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa);
-                    HPL_LAUNCH_CHECK();
-                    k_quant_cols<2><<<(unsigned)((m2 + 7) / 8), 256, 0, s>>>(A12, ldf, kb, m2, w.opB, kb8, kb8, w.sb,
-                                                                           vec4_ok(A12, ldf));
-                    HPL_LAUNCH_CHECK();
+                    if ((st = quant_rows<2>(A21, ldf, m2, kb, w.opA, kb8, kb8, w.sa, s))) return st;
+                    if ((st = quant_cols<2>(A12, ldf, kb, m2, w.opB, kb8, kb8, w.sb, s))) return st;
                     phase_end(cv, s, PH_OPCONV, 2.0 * m2 * kb * (4 + 2));
                     const int ug = phase_begin(s);
                     if ((st = launch_gemm_f16(m2, m2, kb, w.opA, kb8, w.opB, kb8, w.sa, w.sb, A22, ldf, 1, w.err,
