@@ -767,27 +767,33 @@ def run_ours(a, d: Dist):
         # the library's kernel copy from the pinned buffer (hpl_upload): the copy
         # engine's cudaMemcpyAsync of 8.6 GB took 41 ms back to back but 0.3-0.8 s
         # after the GPU had been busy or idle, the kernel copy 41-49 ms every time
+        # x comes back the same way (hpl_download: a kernel writing the pinned
+        # buffer), not by a copy-engine read-back that can stall the same way
         hpl.upload(A, A_h)
         torch.cuda.synchronize(dev)
-        e2e_ms = []
+        e2e_ms, parts = [], []
         for _ in range(a.steps):
             d.barrier()
             torch.cuda.synchronize(dev)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+            ev[0].record(stream)
             hpl.upload(A, A_h)
             hpl.upload(b, b_h)
+            ev[1].record(stream)
             solve()
-            x_h.copy_(b, non_blocking=True)
-            e1.record(stream)
+            ev[2].record(stream)
+            hpl.download(x_h, b)
+            ev[3].record(stream)
             torch.cuda.synchronize(dev)
             d.barrier()
-            e2e_ms.append(e0.elapsed_time(e1))
+            e2e_ms.append(ev[0].elapsed_time(ev[3]))
+            parts.append([ev[i].elapsed_time(ev[i + 1]) for i in range(3)])
         e2e_total = d.max(sum(e2e_ms))
         e2e = {"value": d.sum(flops(n) * len(e2e_ms)) / (e2e_total * 1e-3) / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 8 * n * n + 8 * n, "d2h_bytes_per_step": 8 * n,
-               "ms_per_step": e2e_total / len(e2e_ms)}
+               "ms_per_step": e2e_total / len(e2e_ms),
+               "upload_ms": [round(p[0], 2) for p in parts], "solve_ms": [round(p[1], 2) for p in parts],
+               "download_ms": [round(p[2], 3) for p in parts]}
         del A_h
 
     cpu = None

@@ -330,6 +330,16 @@ int solve_batched(int64_t count, const int64_t* n, double* const* A, const int64
 int hpl_upload(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd, void* stream);
 
 /*
+ * hpl_download — the reverse copy: an FP64 column-major m x n matrix from
+ * device memory (src, lds) into host memory the device can address (dst,
+ * ldd; as for hpl_upload), asynchronously on `stream`, by a kernel that writes
+ * the host buffer through its mapped device address (the result read-back of
+ * a solve without the copy engine). The host sees the values once the stream
+ * has been synchronized. Not in the paper. Errors as hpl_upload.
+ */
+int hpl_download(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd, void* stream);
+
+/*
  * hplgb_gemm_bf16 — the tensor-core product of the mixed-precision path
  * (Sec. III-A.2: the factorization and trailing updates run in low precision;
  * Table I: BF16 + FP32 + FP64): C = C - A B^T (sub = 1) or C = A B^T (sub = 0),

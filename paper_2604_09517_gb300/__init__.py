@@ -114,6 +114,7 @@ def load():
             "hplgb_set_phase_timing": (None, [i32]),
             "hplgb_gemm_config": (i32, [i32, ctypes.c_longlong]),
             "hpl_upload": (i32, [i64, i64, vp, i64, vp, i64, vp]),
+            "hpl_download": (i32, [i64, i64, vp, i64, vp, i64, vp]),
             "hplgb_batched_config": (i32, [i32, ctypes.c_longlong]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
             "hplgb_phase_records": (i32, [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]),
@@ -531,6 +532,21 @@ def upload(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
     assert src.shape == dst.shape and src.stride(0) == 1 and dst.stride(0) == 1
     m, n = src.shape
     _check(load().hpl_upload(m, n, _ptr(src), _ld(src), _ptr(dst), _ld(dst), _stream(dst.device)), "hpl_upload")
+    return dst
+
+
+def download(dst: torch.Tensor, src: torch.Tensor) -> torch.Tensor:
+    """Copy the device FP64 matrix src into the host matrix dst (page-locked,
+    or any host memory the GPU can address; both column-major, stride(0) == 1)
+    with the library's kernel copy (hpl_download); asynchronous on the current
+    stream: synchronize before reading dst."""
+    assert src.dtype == torch.float64 and dst.dtype == torch.float64 and src.is_cuda and not dst.is_cuda
+    if src.dim() == 1:
+        src, dst = src.view(-1, 1), dst.view(-1, 1)
+    assert src.shape == dst.shape and src.stride(0) == 1 and dst.stride(0) == 1
+    m, n = src.shape
+    _check(load().hpl_download(m, n, _ptr(src), _ld(src), _ptr(dst), _ld(dst), _stream(src.device)),
+           "hpl_download")
     return dst
 
 

@@ -1,10 +1,11 @@
-// hpl_upload: an FP64 column-major matrix from page-locked host memory into
-// device memory, copied by a kernel that reads the host buffer through its
-// mapped device address (over the CPU-GPU link) instead of by the copy engine.
-// On GB300 the copy engine's host-to-device copies of a large buffer
-// sometimes stall for hundreds of milliseconds after the GPU has been busy
-// or idle for a while (measured: 8.6 GB in 41 ms back to back, 302 and 814 ms
-// after such stretches), while the kernel copy kept 41-49 ms every time.
+// hpl_upload / hpl_download: an FP64 column-major matrix between page-locked
+// host memory and device memory, copied by a kernel that reads (upload) or
+// writes (download) the host buffer through its mapped device address (over
+// the CPU-GPU link) instead of by the copy engine. On GB300 the copy engine's
+// host-to-device copies of a large buffer sometimes stall for hundreds of
+// milliseconds after the GPU has been busy or idle for a while (measured:
+// 8.6 GB in 41 ms back to back, 302 and 814 ms after such stretches), while
+// the kernel copy kept 41-49 ms every time.
 #include <algorithm>
 
 #include "common.cuh"
@@ -41,36 +42,61 @@ __global__ void __launch_bounds__(512) k_upload_cols(const double* __restrict__ 
     }
 }
 
-}  // namespace hplgb
+// The copy between two device-addressable matrices (both addresses already
+// device addresses).
+static int copy_kernel(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
+                       cudaStream_t s) {
+    int dev = 0, sms = kNumSMsGB300;
+    HPL_CUDA_TRY(cudaGetDevice(&dev));
+    HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const size_t bytes = (size_t)m * (size_t)n * sizeof(double);
+    const bool flat = lds == m && ldd == m && (((uintptr_t)src | (uintptr_t)dst) & 15) == 0 && bytes % 16 == 0;
+    if (flat) {
+        const size_t n16 = bytes / 16;
+        const unsigned blocks = (unsigned)std::max<size_t>(1, std::min<size_t>((n16 + 511) / 512, (size_t)sms * 8));
+        k_upload_flat<<<blocks, 512, 0, s>>>((const uint4*)src, (uint4*)dst, n16);
+    } else {
+        const int vec2 = (((uintptr_t)src | (uintptr_t)dst) & 15) == 0 && lds % 2 == 0 && ldd % 2 == 0;
+        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, 8));
+        const unsigned gy = (unsigned)std::min<int64_t>(n, 65535);
+        k_upload_cols<<<dim3(gx, gy), 512, 0, s>>>(src, lds, dst, ldd, m, n, vec2);
+    }
+    HPL_LAUNCH_CHECK();
+    return HPL_OK;
+}
 
-using namespace hplgb;
+// Device address of a host buffer, or nullptr (message set) when the device
+// cannot address it.
+static void* host_device_ptr(const double* p, const char* who) {
+    void* d = nullptr;
+    if (cudaHostGetDevicePointer(&d, const_cast<double*>(p), 0) != cudaSuccess || !d) {
+        cudaGetLastError();
+        hplgb_internal_set_message(who);
+        return nullptr;
+    }
+    return d;
+}
+
+}  // namespace hplgb
 
 extern "C" int hpl_upload(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
                           void* stream) {
     if (m < 0 || n < 0 || lds < (m > 1 ? m : 1) || ldd < (m > 1 ? m : 1)) return HPL_ERR_INVALID;
     if (m == 0 || n == 0) return HPL_OK;
     if (!src || !dst) return HPL_ERR_INVALID;
-    void* dsrc = nullptr;
-    if (cudaHostGetDevicePointer(&dsrc, const_cast<double*>(src), 0) != cudaSuccess || !dsrc) {
-        cudaGetLastError();
-        hplgb_internal_set_message("hpl_upload: the device cannot address this host buffer (page-lock it: "
-                                   "cudaHostAlloc or cudaHostRegister; torch pin_memory)");
-        return HPL_ERR_INVALID;
-    }
-    cudaStream_t s = (cudaStream_t)stream;
-    int dev = 0, sms = kNumSMsGB300;
-    HPL_CUDA_TRY(cudaGetDevice(&dev));
-    HPL_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const size_t bytes = (size_t)m * (size_t)n * sizeof(double);
-    const bool flat = lds == m && ldd == m && (((uintptr_t)dsrc | (uintptr_t)dst) & 15) == 0 && bytes % 16 == 0;
-    if (flat) {
-        k_upload_flat<<<(unsigned)(sms * 8), 512, 0, s>>>((const uint4*)dsrc, (uint4*)dst, bytes / 16);
-    } else {
-        const int vec2 = (((uintptr_t)dsrc | (uintptr_t)dst) & 15) == 0 && lds % 2 == 0 && ldd % 2 == 0;
-        const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>((m + 1023) / 1024, 8));
-        const unsigned gy = (unsigned)std::min<int64_t>(n, 65535);
-        k_upload_cols<<<dim3(gx, gy), 512, 0, s>>>((const double*)dsrc, lds, dst, ldd, m, n, vec2);
-    }
-    HPL_LAUNCH_CHECK();
-    return HPL_OK;
+    void* dsrc = hplgb::host_device_ptr(src, "hpl_upload: the device cannot address this host buffer (page-lock "
+                                             "it: cudaHostAlloc or cudaHostRegister; torch pin_memory)");
+    if (!dsrc) return HPL_ERR_INVALID;
+    return hplgb::copy_kernel(m, n, (const double*)dsrc, lds, dst, ldd, (cudaStream_t)stream);
+}
+
+extern "C" int hpl_download(int64_t m, int64_t n, const double* src, int64_t lds, double* dst, int64_t ldd,
+                            void* stream) {
+    if (m < 0 || n < 0 || lds < (m > 1 ? m : 1) || ldd < (m > 1 ? m : 1)) return HPL_ERR_INVALID;
+    if (m == 0 || n == 0) return HPL_OK;
+    if (!src || !dst) return HPL_ERR_INVALID;
+    void* ddst = hplgb::host_device_ptr(dst, "hpl_download: the device cannot address this host buffer (page-lock "
+                                             "it: cudaHostAlloc or cudaHostRegister; torch pin_memory)");
+    if (!ddst) return HPL_ERR_INVALID;
+    return hplgb::copy_kernel(m, n, src, lds, (double*)ddst, ldd, (cudaStream_t)stream);
 }

@@ -1,6 +1,6 @@
-"""hpl_upload: FP64 column-major matrices from page-locked host memory into
-device memory by the library's copy kernel (the end-to-end path's data
-staging), through the C ABI."""
+"""hpl_upload / hpl_download: FP64 column-major matrices between page-locked
+host memory and device memory by the library's copy kernel (the end-to-end
+path's data staging and result read-back), through the C ABI."""
 import pytest
 
 pytestmark = pytest.mark.gpu
@@ -55,3 +55,44 @@ def test_upload_pageable_memory_copied_or_refused(hpl):
         assert bool((dst == 0).all())
     else:
         assert torch.equal(dst.cpu(), src)
+
+
+def test_download_contiguous_strided_and_vector(hpl):
+    """The reverse copy writes the host buffer through its mapped address:
+    exact values, only the m rows of each column, visible after a sync."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(9)
+    n = 1000
+    src = hpl.colmajor(n, n)
+    src.copy_(torch.randn(n, n, generator=g, dtype=torch.float64, device="cuda"))
+    dst = torch.empty((n, n), dtype=torch.float64, pin_memory=True).t()
+    hpl.download(dst, src)
+    torch.cuda.synchronize()
+    assert torch.equal(dst, src.cpu())
+    m, k, lds, ldd = 513, 77, 520, 600
+    sbuf = torch.randn(k, lds, generator=g, dtype=torch.float64, device="cuda")
+    src = sbuf.t()[:m]
+    hbuf = torch.full((k, ldd), -3.0, dtype=torch.float64).pin_memory()
+    dst = hbuf.t()[:m]
+    hpl.download(dst, src)
+    torch.cuda.synchronize()
+    assert torch.equal(dst, src.cpu())
+    assert bool((hbuf.t()[m:] == -3.0).all())
+    v = torch.randn(4097, generator=g, dtype=torch.float64, device="cuda")
+    hv = torch.zeros(4097, dtype=torch.float64).pin_memory()
+    hpl.download(hv, v)
+    torch.cuda.synchronize()
+    assert torch.equal(hv, v.cpu())
+
+
+def test_download_rejects_bad_sizes(hpl):
+    import ctypes
+    import torch
+    lib = hpl.load()
+    d = torch.zeros(16, dtype=torch.float64, device="cuda")
+    h = torch.zeros(16, dtype=torch.float64).pin_memory()
+    assert lib.hpl_download(16, 1, d.data_ptr(), 8, h.data_ptr(), 16, None) == 1      # lds < m
+    assert lib.hpl_download(-1, 1, d.data_ptr(), 16, h.data_ptr(), 16, None) == 1
+    assert lib.hpl_download(0, 5, d.data_ptr(), 1, h.data_ptr(), 1, None) == 0        # empty: nothing to do
+    torch.cuda.synchronize()
+    assert bool((h == 0).all())
