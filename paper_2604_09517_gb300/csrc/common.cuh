@@ -105,6 +105,12 @@ __device__ __forceinline__ double ld_cluster_f64(uint32_t caddr) {
     asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(caddr) : "memory");
     return v;
 }
+__device__ __forceinline__ void st_cluster_f64(uint32_t caddr, double v) {
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(caddr), "d"(v) : "memory");
+}
+__device__ __forceinline__ void st_cluster_s64(uint32_t caddr, long long v) {
+    asm volatile("st.shared::cluster.s64 [%0], %1;" ::"r"(caddr), "l"(v) : "memory");
+}
 __device__ __forceinline__ long long ld_cluster_s64(uint32_t caddr) {
     long long v;
     asm volatile("ld.shared::cluster.s64 %0, [%1];" : "=l"(v) : "r"(caddr) : "memory");

@@ -31,6 +31,7 @@ struct PanelSync {
 constexpr int kLeafW = 32;          // widest leaf of the recursive panel
 constexpr int kLeafStride = 33;     // SMEM row stride (doubles) of the leaf
 constexpr int kLeafThreads = 256;
+constexpr int kMaxLeafCluster = 16;    // CTAs of the cluster panel leaf (the non-portable maximum)
 constexpr int kMaxPanelCtas = 512;
 // panels up to this many rows are factored by the cluster leaf when they fit
 #ifndef HPLGB_CLUSTER_LEAF_MAX_ROWS
@@ -312,12 +313,16 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf(
 //    column j + 1's new values.
 //  * The rank-1 update maps threads densely onto the active (row, column)
 //    pairs, so no FP64 instruction runs for finished columns.
-//  * Exchange: per column every CTA publishes its candidate (key, row, values)
-//    and, its owner, the diagonal row in its own shared memory; one cluster
-//    barrier; then warp 0 of every CTA reads the C candidates and the two rows
-//    from the publishers. Publications alternate between two buffers by
-//    column parity: a CTA rewrites buffer j & 1 only after the cluster barrier
-//    of column j + 1, which every reader of column j has passed.
+//  * Exchange: per column every CTA pushes its candidate (key, row, values)
+//    and, its owner, the diagonal row into the shared memory of every CTA of
+//    the cluster (distributed shared memory stores, the destinations split
+//    over the warps); one cluster barrier; then every CTA picks the winner
+//    from its own copies, with no remote read on the critical path (reading
+//    the candidates and then the winning row from their publishers after the
+//    barrier cost two dependent remote round trips per column). The buffers
+//    alternate by column parity: a CTA writes buffer j & 1 of another CTA
+//    again only after the cluster barrier of column j + 1, which that CTA
+//    passes after its reads of column j.
 // W: leaf width bound (32 or 64; w <= W columns are factored).
 template <int W>
 __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
@@ -326,8 +331,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
     constexpr int S = W + 1;
     constexpr int NW = kLeafThreads / 32;
     extern __shared__ double sm[];
-    __shared__ double pub_vals[2][W], pub_diag[2][W];
-    __shared__ long long pub_key[2], pub_row[2];
+    __shared__ double cand_vals[2][kMaxLeafCluster][W], pub_diag[2][W];
+    __shared__ long long cand_key[2][kMaxLeafCluster], cand_row[2][kMaxLeafCluster];
     __shared__ double s_piv[W], s_diag[W];
     __shared__ long long s_wk[NW], s_wr[NW];
     __shared__ long long s_p;
@@ -347,7 +352,8 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
     }
     const int64_t nother = pw - w;
     const int64_t gtid = (int64_t)me * kLeafThreads + tid;
-    __syncthreads();
+    // every CTA of the cluster runs before any pushes into its shared memory
+    cluster_sync_all();
     // this thread's candidate for column 0
     long long bk = -1, br = kNone;
     for (int r = tid; r < nloc; r += kLeafThreads) {
@@ -362,21 +368,31 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
         warp_best(bk, br);
         if (lane == 0) { s_wk[warp] = bk; s_wr[warp] = br; }
         __syncthreads();
-        if (warp == 0) {
+        {
+            // every warp forms the CTA's candidate and pushes it (and, in the
+            // diagonal row's owner, that row) to the CTAs q = warp, warp + NW, ...
             long long k = lane < NW ? s_wk[lane] : -1, r = lane < NW ? s_wr[lane] : kNone;
             warp_best(k, r);
-            if (lane == 0) { pub_key[par] = k; pub_row[par] = r; }
-            if (r != kNone)
-                for (int c = lane; c < w; c += 32) pub_vals[par][c] = sm[(int)(r - grow0) * S + c];
-        } else if (warp == 1 && rd >= 0 && rd < nloc) {
-            for (int c = lane; c < w; c += 32) pub_diag[par][c] = sm[rd * S + c];
+            const bool have = r != kNone, diag = rd >= 0 && rd < nloc;
+            const int lr = have ? (int)(r - grow0) : 0;
+            for (unsigned q = warp; q < C; q += NW) {
+                if (lane == 0) {
+                    st_cluster_s64(cluster_addr(&cand_key[par][me], q), k);
+                    st_cluster_s64(cluster_addr(&cand_row[par][me], q), r);
+                }
+                if (have)
+                    for (int c = lane; c < w; c += 32)
+                        st_cluster_f64(cluster_addr(&cand_vals[par][me][c], q), sm[lr * S + c]);
+                if (diag)
+                    for (int c = lane; c < w; c += 32)
+                        st_cluster_f64(cluster_addr(&pub_diag[par][c], q), sm[rd * S + c]);
+            }
         }
         cluster_sync_all();
         if (warp == 0) {
             long long gk = -1, gr = kNone, gw = -1;
             for (unsigned q = lane; q < C; q += 32) {
-                long long k = ld_cluster_s64(cluster_addr(&pub_key[par], q));
-                long long r = ld_cluster_s64(cluster_addr(&pub_row[par], q));
+                const long long k = cand_key[par][q], r = cand_row[par][q];
                 if (key_better(k, r, gk, gr)) { gk = k; gr = r; gw = (long long)q; }
             }
 #pragma unroll
@@ -387,11 +403,10 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
                 if (key_better(ok, orr, gk, gr)) { gk = ok; gr = orr; gw = ow; }
             }
             if (gr == kNone) { gr = rowj; gw = -1; }     // only NaN in the column: keep the diagonal row
-            const unsigned downer = (unsigned)(j / rows_per);
             for (int c = lane; c < w; c += 32) {
-                double dv = ld_cluster_f64(cluster_addr(&pub_diag[par][c], downer));
+                const double dv = pub_diag[par][c];
                 s_diag[c] = dv;
-                s_piv[c] = gw >= 0 ? ld_cluster_f64(cluster_addr(&pub_vals[par][c], (unsigned)gw)) : dv;
+                s_piv[c] = gw >= 0 ? cand_vals[par][gw][c] : dv;
             }
             if (lane == 0) s_p = gr;
         }
