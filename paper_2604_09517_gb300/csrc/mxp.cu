@@ -1021,25 +1021,30 @@ __global__ void __launch_bounds__(256) k_resid_blk_finish(int64_t m, int64_t nn,
 
 // C (m x nn, FP32) = or -= op(A) (m x kk) B (kk x nn), FP32 accumulation;
 // op(A)(i, q) = A[q * lda + i] (TA = false) or A[i * lda + q] (TA = true).
+// With P (split K): block z of the grid's z dimension takes the K slice
+// [z kslice, (z + 1) kslice) and stores its partial product in P (slice z at
+// P + z nn m, ld m) instead of touching C; k_sgemm_reduce adds the slices.
 template <bool TA, typename AT>
 __global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk, const AT* __restrict__ A,
                                                int64_t lda, const float* __restrict__ B, int64_t ldb,
-                                               float* __restrict__ C, int64_t ldc, int sub) {
+                                               float* __restrict__ C, int64_t ldc, int sub, int64_t kslice,
+                                               float* __restrict__ P) {
     __shared__ float As[16][65], Bs[16][65];
     const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
     const int64_t row0 = (int64_t)blockIdx.x * 64, col0 = (int64_t)blockIdx.y * 64;
+    const int64_t kb0 = (int64_t)blockIdx.z * kslice, kb1 = min(kk, kb0 + kslice);
     float acc[4][4] = {};
-    for (int64_t k0 = 0; k0 < kk; k0 += 16) {
+    for (int64_t k0 = kb0; k0 < kb1; k0 += 16) {
         for (int e = tid; e < 16 * 64; e += 256) {
             int kq, r;
             if (TA) { r = e >> 4; kq = e & 15; }
             else { kq = e >> 6; r = e & 63; }
-            const bool ok = k0 + kq < kk && row0 + r < m;
+            const bool ok = k0 + kq < kb1 && row0 + r < m;
             As[kq][r] = ok ? ld_f(TA ? A + (row0 + r) * lda + k0 + kq : A + (k0 + kq) * lda + row0 + r) : 0.0f;
         }
         for (int e = tid; e < 16 * 64; e += 256) {
             const int c = e >> 4, kq = e & 15;
-            const bool ok = k0 + kq < kk && col0 + c < nn;
+            const bool ok = k0 + kq < kb1 && col0 + c < nn;
             Bs[kq][c] = ok ? B[(col0 + c) * ldb + k0 + kq] : 0.0f;
         }
         __syncthreads();
@@ -1057,13 +1062,28 @@ __global__ void __launch_bounds__(256) k_sgemm(int64_t m, int64_t nn, int64_t kk
         }
         __syncthreads();
     }
+    float* Pz = P ? P + (int64_t)blockIdx.z * nn * m : nullptr;
 #pragma unroll
     for (int j = 0; j < 4; j++)
 #pragma unroll
         for (int i = 0; i < 4; i++) {
             const int64_t r = row0 + tx + 16 * i, c = col0 + ty + 16 * j;
-            if (r < m && c < nn) C[c * ldc + r] = sub ? C[c * ldc + r] - acc[i][j] : acc[i][j];
+            if (r < m && c < nn) {
+                if (Pz) Pz[c * m + r] = acc[i][j];
+                else C[c * ldc + r] = sub ? C[c * ldc + r] - acc[i][j] : acc[i][j];
+            }
         }
+}
+
+// C (m x nn) = or -= the sum of the S K-slice partial products in P, added in
+// slice order (the same bits on every run).
+__global__ void __launch_bounds__(256) k_sgemm_reduce(int64_t m, int64_t nn, int S, const float* __restrict__ P,
+                                                      float* __restrict__ C, int64_t ldc, int sub) {
+    const int64_t i = (int64_t)blockIdx.x * 256 + threadIdx.x, c = blockIdx.y;
+    if (i >= m) return;
+    float v = 0.0f;
+    for (int z = 0; z < S; z++) v += P[((int64_t)z * nn + c) * m + i];
+    C[c * ldc + i] = sub ? C[c * ldc + i] - v : v;
 }
 
 // Y (FP32, ld ldy) = X (FP64, ld ldx), m x nn; and back (add: Y += X).
@@ -1448,7 +1468,8 @@ struct Mxp {
                     // D^-1's copy in nsX (free after the Newton-Schulz steps), so that
                     // the product can write L21's BF16 copy for the update into opB
                     // as it stores L21 (FP32 working matrix, bulk-tensor epilogue)
-                    const bool fuse = !kBf16 && gemm_bf16_copy_ok((const float*)A21, ldf, w.opB, kb, kb8);
+                    const bool fuse = !kBf16 && o.prec == HPL_PREC_BF16 &&
+                                      gemm_bf16_copy_ok((const float*)A21, ldf, w.opB, kb, kb8);
                     uint16_t* dcopy = fuse ? w.nsX : w.opB;
                     const int cv = phase_begin(s);
                     if ((st = to_bf16(A21, ldf, m2, kb, 1, 0, w.opA, kb8, 0, kb8, s))) return st;
@@ -1740,15 +1761,35 @@ struct Mxp {
 
     dim3 grid_blk(int64_t rows, int64_t cols) const { return dim3((unsigned)((rows + 255) / 256), (unsigned)cols); }
 
-    // C (rows x k) -= or = op(P) (rows x kk) Y (kk x k), FP32
+    // C (rows x k) -= or = op(P) (rows x kk) Y (kk x k), FP32. A product with
+    // fewer 64 x 64 tiles than SMs and a long K is split along K into up to 8
+    // slices (partial products in the residual's scratch, free while the
+    // preconditioner runs), then the slices are added in order.
     template <typename PT>
     int sgemm(bool ta, int64_t rows, int64_t kk, const PT* P, int64_t ldp, const float* Y, int64_t ldy, float* C,
               int64_t ldc, int64_t k, int sub) {
         if (rows <= 0 || kk <= 0 || k <= 0) return HPL_OK;
         dim3 g((unsigned)((rows + 63) / 64), (unsigned)((k + 63) / 64));
-        if (ta) k_sgemm<true, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
-        else k_sgemm<false, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub);
+        const int64_t tiles = (int64_t)g.x * g.y;
+        int S = 1;
+        if (tiles < kNumSMsGB300 && kk >= 512)
+            S = (int)std::min<int64_t>({8, (kNumSMsGB300 + tiles - 1) / tiles, kk / 256});
+        int64_t kslice = kk;
+        float* part = nullptr;
+        const int64_t cap = (int64_t)(2 * kBlkSplit) * n * nblk;      // floats in w.partb
+        if (S > 1 && w.partb && (int64_t)S * rows * k <= cap) {
+            kslice = ((kk + S - 1) / S + 15) / 16 * 16;
+            S = (int)((kk + kslice - 1) / kslice);
+            g.z = (unsigned)S;
+            part = (float*)w.partb;
+        }
+        if (ta) k_sgemm<true, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub, kslice, part);
+        else k_sgemm<false, PT><<<g, 256, 0, s>>>(rows, k, kk, P, ldp, Y, ldy, C, ldc, sub, kslice, part);
         HPL_LAUNCH_CHECK();
+        if (part) {
+            k_sgemm_reduce<<<grid_blk(rows, k), 256, 0, s>>>(rows, k, S, part, C, ldc, sub);
+            HPL_LAUNCH_CHECK();
+        }
         return HPL_OK;
     }
 
