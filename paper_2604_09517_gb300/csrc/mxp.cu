@@ -127,6 +127,12 @@ __global__ void __launch_bounds__(256) k_to_bf16_t(const XT* __restrict__ X, int
                     for (int e = 0; e < 4; e++)
                         if (r + e < rows) v[e] = xc[r + e];
                 }
+            } else if (vec4 && r + 3 < rows) {          // BF16 source: four values in one 8-byte load
+                const uint2 t = *reinterpret_cast<const uint2*>(xc + r);
+                v[0] = __uint_as_float(t.x << 16);
+                v[1] = __uint_as_float(t.x & 0xffff0000u);
+                v[2] = __uint_as_float(t.y << 16);
+                v[3] = __uint_as_float(t.y & 0xffff0000u);
             } else {
 #pragma unroll
                 for (int e = 0; e < 4; e++)
@@ -187,9 +193,14 @@ __global__ void __launch_bounds__(256) k_to_bf16_n(const XT* __restrict__ X, int
                 const float4 b = *reinterpret_cast<const float4*>(xc + r + 4);
                 v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
                 v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
-            } else {
+            } else {                                   // BF16 source: eight values in one 16-byte load
+                const uint4 t = *reinterpret_cast<const uint4*>(xc + r);
+                const uint32_t w4[4] = {t.x, t.y, t.z, t.w};
 #pragma unroll
-                for (int e = 0; e < 8; e++) v[e] = ld_f(xc + r + e);
+                for (int e = 0; e < 4; e++) {
+                    v[2 * e] = __uint_as_float(w4[e] << 16);
+                    v[2 * e + 1] = __uint_as_float(w4[e] & 0xffff0000u);
+                }
             }
         } else {
 #pragma unroll
@@ -224,14 +235,16 @@ static int to_bf16_seg(const XT* X, int64_t ldx, int64_t rows, int64_t cols, int
         // one 32 x 128 tile per CTA (a grid-stride loop over tiles measured slower)
         if ((g.kpad + 31) / 32 > 0x7fffffff || (rows + 127) / 128 > 65535) return HPL_ERR_INVALID;
         dim3 grid((unsigned)((g.kpad + 31) / 32), (unsigned)((rows + 127) / 128));
-        const int vec4 = ((uintptr_t)X & 15) == 0 && ldx % 4 == 0;
+        // four-value loads: 16-byte aligned FP32 or 8-byte aligned BF16 columns
+        const int vec4 = ((uintptr_t)X & (4 * sizeof(XT) - 1)) == 0 && ldx % 4 == 0;
         k_to_bf16_t<<<grid, 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g, vec4);
         HPL_LAUNCH_CHECK();
         return HPL_OK;
     }
     // 16-byte accesses: X column starts and out row starts / segment offsets aligned
-    const int vec = std::is_same<XT, float>::value && ((uintptr_t)X & 15) == 0 && ldx % 4 == 0 &&
-                    ((uintptr_t)out & 15) == 0 && ldo % 8 == 0 && g.seg_off % 8 == 0 && g.seg_stride % 8 == 0;
+    // (a BF16 X: eight values per 16-byte load, so columns starting on 16 bytes: ldx % 8 == 0)
+    const int vec = ((uintptr_t)X & 15) == 0 && ldx % (16 / sizeof(XT)) == 0 && ((uintptr_t)out & 15) == 0 &&
+                    ldo % 8 == 0 && g.seg_off % 8 == 0 && g.seg_stride % 8 == 0;
     const int64_t items = ((g.kpad + 7) / 8) * cols;
     const int64_t blocks = std::min<int64_t>((items + 255) / 256, 152 * 32);
     k_to_bf16_n<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(X, ldx, rows, cols, (__nv_bfloat16*)out, ldo, g,
