@@ -76,12 +76,12 @@ Opts resolve_opts(const hpl_opts* o, int64_t default_nb) {
 }
 
 static std::mutex g_ctx_mu;
-static DeviceCtx* g_ctx[64];
+static DeviceCtx* g_ctx[kMaxDevices];
 
 int get_ctx(DeviceCtx** out) {
     int dev = 0;
     HPL_CUDA_TRY(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= 64) return HPL_ERR_INVALID;
+    if (dev < 0 || dev >= kMaxDevices) return HPL_ERR_INVALID;
     std::lock_guard<std::mutex> lk(g_ctx_mu);
     if (!g_ctx[dev]) {
         DeviceCtx* c = new DeviceCtx();

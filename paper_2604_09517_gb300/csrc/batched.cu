@@ -852,14 +852,16 @@ extern "C" int solve_batched_run(void* ws, hpl_info* infos, int max_ctas, void* 
     char* base = (char*)ws;
     bt::Header* H = (bt::Header*)base;
     const bt::Sys* table = (const bt::Sys*)(base + align_up(sizeof(bt::Header), 256));
-    static bool attr = false;
-    if (!attr) {
+    static std::atomic<bool> attr[kMaxDevices];
+    const int dv = device_slot();
+    if (dv < 0) return HPL_ERR_CUDA;
+    if (!attr[dv].load()) {
         HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run<bt::NBMAX, 1>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize,
                                           (int)bt::smem_bytes<bt::NBMAX>()));
         HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)bt::k_batched_run<16, 2>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bt::smem_bytes<16>()));
-        attr = true;
+        attr[dv].store(true);
     }
     int dev = 0, sms = kNumSMsGB300;
     HPL_CUDA_TRY(cudaGetDevice(&dev));

@@ -5,6 +5,8 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
+
 #include "../../include/hplgb.h"
 
 #define HPL_CUDA_TRY(expr)                                                       \
@@ -28,6 +30,14 @@ extern "C" void hplgb_internal_set_message(const char* msg);
 namespace hplgb {
 
 constexpr int kNumSMsGB300 = 152;
+// Per-device caches (function attributes set, occupancy results) are indexed
+// by the current device: a process that drives several GPUs prepares each.
+constexpr int kMaxDevices = 64;
+inline int device_slot() {
+    int d = -1;
+    if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kMaxDevices) return -1;
+    return d;
+}
 constexpr int64_t kDefaultTimeoutNs = 20LL * 1000 * 1000 * 1000;
 
 // Resolved options (defaults filled in).

@@ -890,11 +890,13 @@ static bool tma_epilogue_ok(const CT* C, int64_t ldc) {
 template <int KIND, int BN, typename CT, bool TMA_EPI>
 static int launch_kind_epi(const CUtensorMap& ma, const CUtensorMap& mb, const CUtensorMap& mc, const Params& p,
                            int grid, cudaStream_t s) {
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<bool> attr_set[kMaxDevices];
+    const int dv = device_slot();
+    if (dv < 0) return HPL_ERR_CUDA;
+    if (!attr_set[dv].load()) {
         HPL_CUDA_TRY(cudaFuncSetAttribute((const void*)k_gemm_tc<KIND, BN, CT, TMA_EPI>,
                                           cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_smem<BN, TMA_EPI>()));
-        attr_set = true;
+        attr_set[dv].store(true);
     }
     k_gemm_tc<KIND, BN, CT, TMA_EPI><<<grid, THREADS, dyn_smem<BN, TMA_EPI>(), s>>>(ma, mb, mc, p);
     HPL_LAUNCH_CHECK();
@@ -949,7 +951,10 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
 // instantiation; -1 on a CUDA error).
 template <int KIND, typename CT, bool TMA_EPI>
 static int pair_capacity() {
-    static int max_pairs = 0;
+    static std::atomic<int> cache[kMaxDevices];      // 0: not yet known
+    const int dv = device_slot();
+    if (dv < 0) return -1;
+    int max_pairs = cache[dv].load();
     if (!max_pairs) {
         const void* f = (const void*)k_gemm_tc_pair<KIND, CT, TMA_EPI>;
         if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_dyn_smem<TMA_EPI>()) !=
@@ -966,6 +971,7 @@ static int pair_capacity() {
         int nc = 0;
         if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) != cudaSuccess) return -1;
         max_pairs = nc > 0 ? nc : sms / 2;
+        cache[dv].store(max_pairs);
     }
     return max_pairs;
 }

@@ -1046,8 +1046,10 @@ static int panel_rec(int64_t n, double* A, int64_t lda, int64_t c0, int w, int64
 // Largest cluster (16, else the portable 8) on which the cluster leaf can run
 // with its largest shared-memory footprint; 0 when none can.
 static int max_leaf_cluster() {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+    static std::atomic<int> cache[kMaxDevices];      // cluster size + 1; 0: not yet known
+    const int dv = device_slot();
+    if (dv < 0) return 0;
+    if (const int c = cache[dv].load()) return c - 1;
     int best = 0;
     const void* fns[2] = {(const void*)k_panel_leaf_cl<32>, (const void*)k_panel_leaf_cl<64>};
     for (const void* f : fns) {
@@ -1074,7 +1076,7 @@ static int max_leaf_cluster() {
         cudaGetLastError();
         if (ok) { best = c; break; }
     }
-    cached = best;
+    cache[dv].store(best + 1);
     return best;
 }
 

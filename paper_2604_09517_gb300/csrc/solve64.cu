@@ -242,8 +242,10 @@ constexpr int kTrsvClusterBlocksPerCta = 8;
 
 // Cluster size for k_trsv_cluster (16, else the portable 8; 0 = unavailable).
 static int trsv_cluster_max() {
-    static int cached = -1;
-    if (cached >= 0) return cached;
+    static std::atomic<int> cache[kMaxDevices];      // cluster size + 1; 0: not yet known
+    const int dv = device_slot();
+    if (dv < 0) return 0;
+    if (const int c = cache[dv].load()) return c - 1;
     int best = 0;
     const void* f = (const void*)k_trsv_cluster;
     cudaFuncSetAttribute(f, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -266,7 +268,7 @@ static int trsv_cluster_max() {
         }
     }
     cudaGetLastError();
-    cached = best;
+    cache[dv].store(best + 1);
     return best;
 }
 
