@@ -96,3 +96,23 @@ def test_download_rejects_bad_sizes(hpl):
     assert lib.hpl_download(0, 5, d.data_ptr(), 1, h.data_ptr(), 1, None) == 0        # empty: nothing to do
     torch.cuda.synchronize()
     assert bool((h == 0).all())
+
+
+def test_download_pageable_memory_copied_or_refused(hpl):
+    """Pageable host memory as the destination: copied exactly where the
+    platform lets the GPU address it, else refused with HPL_ERR_INVALID and
+    the host buffer left as it was."""
+    import torch
+    src = torch.randn(64, 64, dtype=torch.float64, device="cuda").t()
+    dst = torch.zeros(64, 64, dtype=torch.float64).t()     # not page-locked
+    try:
+        hpl.download(dst, src)
+        refused = False
+    except hpl.HplError as e:
+        refused = True
+        assert e.status == 1
+    torch.cuda.synchronize()
+    if refused:
+        assert bool((dst == 0).all())
+    else:
+        assert torch.equal(dst, src.cpu())
