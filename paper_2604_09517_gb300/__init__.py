@@ -578,6 +578,7 @@ def launch_count() -> int:
 GEMM_EPILOGUE = 0        # hplgb_gemm_config switches
 GEMM_GROUP_M = 1
 GEMM_PAIR_MAX_MN = 2
+GEMM_PAIR_ATOMS = 3
 
 
 def gemm_config(what: int, value: int) -> None:

@@ -23,9 +23,10 @@
 //   k_gemm_tc      : one CTA per 128 x BN tile (BN 256, or 128 for products
 //                    with fewer tiles than SMs), 4 (6) stages.
 //   k_gemm_tc_pair : two CTAs of a cluster per 256 x 256 tile with
-//                    tcgen05.mma.cta_group::2, 7 stages of half the bytes;
-//                    used for products of moderate size that have a 256 x 256
-//                    tile for every pair of SMs.
+//                    tcgen05.mma.cta_group::2; with the bulk-tensor epilogue
+//                    3 stages of two swizzle atoms of K (64 KB per CTA), else
+//                    7 stages of one; used for every product that has a
+//                    256 x 256 tile for each pair of SMs.
 // Every wait is bounded by a %globaltimer deadline; on expiry the CTA raises
 // an error flag, drains what it has in flight, frees TMEM and returns.
 #include <cuda.h>
@@ -521,9 +522,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 // ---------------------------------------------------------------------------
 // Pair kernel: the two CTAs of a cluster (two SMs) compute one 256 x 256 tile
 // together with tcgen05.mma.cta_group::2. Each CTA stages only its own 128
-// rows of A and its own 128 rows of B per K step (32 KB for BF16), half the
-// bytes per SM of the 128 x 256 single-CTA tile for the same MMA work, so
-// seven stages fit in shared memory and the loads run further ahead.
+// rows of A and its own 128 rows of B per K step (32 KB per swizzle atom of
+// K), half the bytes per SM of the 128 x 256 single-CTA tile for the same MMA
+// work, so the loads run further ahead (192 KB in flight per CTA).
 //   leader (cluster rank 0): warp 0 TMA producer, warp 1 MMA issuer for the
 //     pair (reads the A and B halves from both CTAs' shared memory, writes
 //     rows 0..127 of the tile into its TMEM and rows 128..255 into the peer's)
@@ -535,13 +536,19 @@ __global__ void __launch_bounds__(THREADS, 1)
 // of both CTAs (multicast); both CTAs' epilogue warps arrive on the leader's
 // tempty barrier.
 constexpr int PAIR_ROWS = 128;                 // rows of A and of B staged by each CTA
-constexpr int PAIR_STAGE_BYTES = 2 * PAIR_ROWS * BKB;
-constexpr int PAIR_STAGES = 7;
-constexpr int PAIR_STAGES_TMA_EPI = 6;         // the bulk-tensor epilogue's 32 KB take one stage
-template <bool TMA_EPI>
-constexpr int pair_stages() { return TMA_EPI ? PAIR_STAGES_TMA_EPI : PAIR_STAGES; }
-template <bool TMA_EPI>
-constexpr int pair_dyn_smem() { return pair_stages<TMA_EPI>() * PAIR_STAGE_BYTES + 1024 + (TMA_EPI ? EPI_SMEM : 0); }
+// AT: 128-byte swizzle atoms of K per stage (1: 32 KB stages, 4 MMAs per
+// barrier round trip; 2, the default with the bulk-tensor epilogue: 64 KB
+// stages holding [A atom 0][A atom 1][B atom 0][B atom 1], 8 MMAs per round
+// trip, half the stages, the same bytes in flight)
+constexpr int PAIR_ATOM_BYTES = PAIR_ROWS * BKB;          // one operand half, one atom: 16 KB
+template <int AT>
+constexpr int pair_stage_bytes() { return 2 * AT * PAIR_ATOM_BYTES; }
+template <bool TMA_EPI, int AT = 1>
+constexpr int pair_stages() { return AT == 1 ? (TMA_EPI ? 6 : 7) : 3; }   // the bulk-tensor epilogue takes 32 KB
+template <bool TMA_EPI, int AT = 1>
+constexpr int pair_dyn_smem() {
+    return pair_stages<TMA_EPI, AT>() * pair_stage_bytes<AT>() + 1024 + (TMA_EPI ? EPI_SMEM : 0);
+}
 
 template <int KIND>
 __host__ __device__ constexpr uint32_t idesc_pair() {
@@ -610,13 +617,15 @@ __device__ __forceinline__ void umma_commit_pair_own(uint64_t* bar) {
                  : "memory");
 }
 
-template <int KIND, typename CT, bool TMA_EPI>
+template <int KIND, typename CT, bool TMA_EPI, int AT = 1>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
     k_gemm_tc_pair(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const __grid_constant__ CUtensorMap tmC, Params p) {
-    constexpr int BK = BKB / Kind<KIND>::ELEM;
-    constexpr int PAIR_STAGES = pair_stages<TMA_EPI>();
-    constexpr int HALF = PAIR_ROWS * BKB;       // bytes of one operand half per stage
+    constexpr int BKA = BKB / Kind<KIND>::ELEM;     // K values per atom
+    constexpr int BK = AT * BKA;                    // K values per stage
+    constexpr int PAIR_STAGES = pair_stages<TMA_EPI, AT>();
+    constexpr int PAIR_STAGE_BYTES = pair_stage_bytes<AT>();
+    constexpr int HALF = AT * PAIR_ATOM_BYTES;      // bytes of one operand half per stage
     extern __shared__ __align__(1024) unsigned char dsm[];
     __shared__ __align__(8) uint64_t full_bar[PAIR_STAGES], empty_bar[PAIR_STAGES];
     __shared__ __align__(8) uint64_t tfull_bar[2], tempty_bar[2], drain_bar;
@@ -673,8 +682,13 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     unsigned char* sa = tiles + s * PAIR_STAGE_BYTES;
                     if (rank == 0) mbar_expect_tx(&full_bar[s], 2 * PAIR_STAGE_BYTES);
                     const uint32_t fb = cluster_addr(&full_bar[s], 0);
-                    tma_load_2d_pair(sa, &tmA, fb, kb * BK, mt * 256 + (int)rank * PAIR_ROWS);
-                    tma_load_2d_pair(sa + HALF, &tmB, fb, kb * BK, nt * 256 + (int)rank * PAIR_ROWS);
+#pragma unroll
+                    for (int a = 0; a < AT; a++) {
+                        tma_load_2d_pair(sa + a * PAIR_ATOM_BYTES, &tmA, fb, kb * BK + a * BKA,
+                                         mt * 256 + (int)rank * PAIR_ROWS);
+                        tma_load_2d_pair(sa + HALF + a * PAIR_ATOM_BYTES, &tmB, fb, kb * BK + a * BKA,
+                                         nt * 256 + (int)rank * PAIR_ROWS);
+                    }
                 }
             }
             if (!ok) {
@@ -700,10 +714,14 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(THREADS, 1)
                     if (!mbar_wait(&full_bar[s], ph, deadline, &s_abort, p.err)) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t sa = smem_u32(tiles + s * PAIR_STAGE_BYTES);
-                    const uint64_t ad = desc_sw128(sa), bd = desc_sw128(sa + HALF);
 #pragma unroll
-                    for (int kk = 0; kk < BKB / 32; kk++)
-                        umma_pair<KIND>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | kk) != 0);
+                    for (int a = 0; a < AT; a++) {
+                        const uint64_t ad = desc_sw128(sa + a * PAIR_ATOM_BYTES);
+                        const uint64_t bd = desc_sw128(sa + HALF + a * PAIR_ATOM_BYTES);
+#pragma unroll
+                        for (int kk = 0; kk < BKB / 32; kk++)
+                            umma_pair<KIND>(d_tmem, ad + 2 * kk, bd + 2 * kk, (kb | a | kk) != 0);
+                    }
                     umma_commit_pair_both(&empty_bar[s]);
                 }
                 if (ok) umma_commit_pair_both(&tfull_bar[acc]);
@@ -874,6 +892,10 @@ static int make_map_c(CUtensorMap* m, const float* base, int64_t rows, int64_t c
 static int g_epilogue_mode = 0;
 static int g_group_m_override = 0;
 static long long g_pair_max_mn = 0;
+// two atoms per stage: measured on GB300, n = 98304 MxP solve 502 -> 484 ms
+// (BF16) and 343 -> 337 ms (FP8); BF16 products of 20480^2 x 4096 1391-1566
+// -> 1670-1678 TF/s
+static int g_pair_atoms = 2;
 
 // The bulk-tensor epilogue: FP32 C at a 16-byte aligned address with a
 // leading dimension that is a multiple of 4 (TMA strides are multiples of 16
@@ -949,15 +971,15 @@ static int launch_kind(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
 
 // Clusters of the pair kernel that fit on the GPU at once (set-up once per
 // instantiation; -1 on a CUDA error).
-template <int KIND, typename CT, bool TMA_EPI>
+template <int KIND, typename CT, bool TMA_EPI, int AT = 1>
 static int pair_capacity() {
     static std::atomic<int> cache[kMaxDevices];      // 0: not yet known
     const int dv = device_slot();
     if (dv < 0) return -1;
     int max_pairs = cache[dv].load();
     if (!max_pairs) {
-        const void* f = (const void*)k_gemm_tc_pair<KIND, CT, TMA_EPI>;
-        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_dyn_smem<TMA_EPI>()) !=
+        const void* f = (const void*)k_gemm_tc_pair<KIND, CT, TMA_EPI, AT>;
+        if (cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, pair_dyn_smem<TMA_EPI, AT>()) !=
             cudaSuccess)
             return -1;
         int dev = 0, sms = kNumSMsGB300;
@@ -967,7 +989,7 @@ static int pair_capacity() {
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3((unsigned)(sms & ~1));
         cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = pair_dyn_smem<TMA_EPI>();
+        cfg.dynamicSmemBytes = pair_dyn_smem<TMA_EPI, AT>();
         int nc = 0;
         if (cudaOccupancyMaxActiveClusters(&nc, f, &cfg) != cudaSuccess) return -1;
         max_pairs = nc > 0 ? nc : sms / 2;
@@ -997,7 +1019,14 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if constexpr (std::is_same<CT, float>::value) {
         if (tma_epi && (st = make_map_c(&mc, C, M, N, ldc))) return st;
     }
-    const int max_pairs = tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>();
+    // two swizzle atoms per stage (switch 3 of hplgb_gemm_config) for the bulk-tensor epilogue
+    const bool two_atoms = std::is_same<CT, float>::value && tma_epi && g_pair_atoms == 2;
+    int max_pairs;
+    if constexpr (std::is_same<CT, float>::value)
+        max_pairs = two_atoms ? pair_capacity<KIND, CT, true, 2>()
+                              : (tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>());
+    else
+        max_pairs = tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>();
     if (max_pairs < 0) return HPL_ERR_CUDA;
     const int64_t ntiles = ((M + 255) / 256) * ((N + 255) / 256);
     int pairs = (int)std::min<int64_t>(ntiles, max_pairs);
@@ -1016,6 +1045,13 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.C16 = C16;
     p.ld16 = ld16;
     p.group_m = g_group_m_override > 0 ? g_group_m_override : GROUP_M_PAIR;
+    if constexpr (std::is_same<CT, float>::value) {
+        if (two_atoms) {
+            k_gemm_tc_pair<KIND, CT, true, 2><<<2 * pairs, THREADS, pair_dyn_smem<true, 2>(), s>>>(ma, mb, mc, p);
+            HPL_LAUNCH_CHECK();
+            return HPL_OK;
+        }
+    }
     if (tma_epi)
         k_gemm_tc_pair<KIND, CT, true><<<2 * pairs, THREADS, pair_dyn_smem<true>(), s>>>(ma, mb, mc, p);
     else
@@ -1151,6 +1187,10 @@ extern "C" int hplgb_gemm_config(int what, long long value) {
             return HPL_OK;
         case 2:
             tc::g_pair_max_mn = value;
+            return HPL_OK;
+        case 3:
+            if (value != 1 && value != 2) return HPL_ERR_INVALID;
+            tc::g_pair_atoms = (int)value;
             return HPL_OK;
         default:
             return HPL_ERR_INVALID;

@@ -173,11 +173,59 @@ def test_gemm_epilogues_bit_identical(hpl, kind, M, N, K, sub):
     assert torch.equal(out[0], out[1])
 
 
+@pytest.mark.parametrize("kind", ["bf16", "fp8", "f16", "tf32"])
+@pytest.mark.parametrize("M,N,K,sub", [(2560, 2304, 4096, True), (2404, 2600, 200, True), (2560, 2560, 328, False)])
+def test_gemm_pair_two_atom_stages_bit_identical(hpl, kind, M, N, K, sub):
+    """The pair kernel with two 128-byte swizzle atoms of K per pipeline stage
+    (switch 3) issues the same MMAs in the same K order as with one, so C must
+    be bit-identical; a K that ends inside a stage (the second atom entirely
+    past K, zero-filled) included."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(M + 3 * N + K)
+    ld = (K + 15) // 16 * 16
+    if kind == "bf16":
+        A = torch.randn(M, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+        B = torch.randn(N, ld, device="cuda", generator=g).to(torch.bfloat16)[:, :K]
+    elif kind == "fp8":
+        A = (torch.randn(M, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+        B = (torch.randn(N, ld, device="cuda", generator=g) * 8).to(torch.float8_e4m3fn)[:, :K]
+    elif kind == "f16":
+        A = torch.randn(M, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
+        B = torch.randn(N, ld, device="cuda", generator=g).to(torch.float16)[:, :K]
+    else:
+        A = _tf32(torch.randn(M, ld, device="cuda", generator=g))[:, :K]
+        B = _tf32(torch.randn(N, ld, device="cuda", generator=g))[:, :K]
+    sa = torch.pow(2.0, torch.randint(-4, 4, (M,), device="cuda", generator=g).float())
+    sb = torch.pow(2.0, torch.randint(-4, 4, (N,), device="cuda", generator=g).float())
+    C0 = hpl.colmajor(M, N, dtype=torch.float32)
+    C0.copy_(torch.randn(M, N, device="cuda", generator=g))
+    out = []
+    try:
+        for atoms in (1, 2):
+            hpl.gemm_config(hpl.GEMM_PAIR_ATOMS, atoms)
+            C = C0.clone()
+            if kind == "bf16":
+                hpl.gemm_bf16(A, B, C, sub=sub)
+            elif kind == "fp8":
+                hpl.gemm_fp8(A, B, C, sa, sb, sub=sub)
+            elif kind == "f16":
+                hpl.gemm_f16(A, B, C, sa, sb, sub=sub)
+            else:
+                hpl.gemm_tf32(A, B, C, sub=sub)
+            torch.cuda.synchronize()
+            out.append(C)
+    finally:
+        hpl.gemm_config(hpl.GEMM_PAIR_ATOMS, 2)
+    assert torch.equal(out[0], out[1])
+
+
 def test_gemm_config_rejects_unknown(hpl):
     with pytest.raises(hpl.HplError):
         hpl.gemm_config(9, 0)
     with pytest.raises(hpl.HplError):
         hpl.gemm_config(hpl.GEMM_EPILOGUE, 5)
+    with pytest.raises(hpl.HplError):
+        hpl.gemm_config(hpl.GEMM_PAIR_ATOMS, 3)
 
 
 def _tf32(x):
