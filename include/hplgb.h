@@ -392,7 +392,7 @@ int hplgb_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
  * what = 1: rows-of-tiles per band of the tile walk (0 = the default per
  * operand kind). what = 2: largest M x N given to the two-SM pair kernel
  * (0 = the default, negative = never). what = 3: 128-byte swizzle atoms of K
- * per pipeline stage of the pair kernel with the bulk-tensor epilogue (1:
+ * per pipeline stage of the pair kernel (1:
  * 32 KB stages, four MMAs per barrier round trip; 2, the default: 64 KB
  * stages, eight; the same MMAs in the same order). Process-wide, not thread-safe; results
  * are bit-identical for every setting except where FP32 subnormals occur (the

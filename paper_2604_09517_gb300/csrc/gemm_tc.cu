@@ -1019,14 +1019,10 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     if constexpr (std::is_same<CT, float>::value) {
         if (tma_epi && (st = make_map_c(&mc, C, M, N, ldc))) return st;
     }
-    // two swizzle atoms per stage (switch 3 of hplgb_gemm_config) for the bulk-tensor epilogue
-    const bool two_atoms = std::is_same<CT, float>::value && tma_epi && g_pair_atoms == 2;
-    int max_pairs;
-    if constexpr (std::is_same<CT, float>::value)
-        max_pairs = two_atoms ? pair_capacity<KIND, CT, true, 2>()
-                              : (tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>());
-    else
-        max_pairs = tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>();
+    // two swizzle atoms per stage (switch 3 of hplgb_gemm_config)
+    const bool two_atoms = g_pair_atoms == 2;
+    const int max_pairs = two_atoms ? (tma_epi ? pair_capacity<KIND, CT, true, 2>() : pair_capacity<KIND, CT, false, 2>())
+                                    : (tma_epi ? pair_capacity<KIND, CT, true>() : pair_capacity<KIND, CT, false>());
     if (max_pairs < 0) return HPL_ERR_CUDA;
     const int64_t ntiles = ((M + 255) / 256) * ((N + 255) / 256);
     int pairs = (int)std::min<int64_t>(ntiles, max_pairs);
@@ -1045,12 +1041,13 @@ static int launch_pair(int64_t M, int64_t N, int64_t K, const void* A, int64_t l
     p.C16 = C16;
     p.ld16 = ld16;
     p.group_m = g_group_m_override > 0 ? g_group_m_override : GROUP_M_PAIR;
-    if constexpr (std::is_same<CT, float>::value) {
-        if (two_atoms) {
+    if (two_atoms) {
+        if (tma_epi)
             k_gemm_tc_pair<KIND, CT, true, 2><<<2 * pairs, THREADS, pair_dyn_smem<true, 2>(), s>>>(ma, mb, mc, p);
-            HPL_LAUNCH_CHECK();
-            return HPL_OK;
-        }
+        else
+            k_gemm_tc_pair<KIND, CT, false, 2><<<2 * pairs, THREADS, pair_dyn_smem<false, 2>(), s>>>(ma, mb, mc, p);
+        HPL_LAUNCH_CHECK();
+        return HPL_OK;
     }
     if (tma_epi)
         k_gemm_tc_pair<KIND, CT, true><<<2 * pairs, THREADS, pair_dyn_smem<true>(), s>>>(ma, mb, mc, p);

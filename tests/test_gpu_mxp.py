@@ -474,3 +474,25 @@ def test_mxp_l21_copy_from_the_product_epilogue(hpl, n, nb):
     assert torch.equal(F0, F1) and torch.equal(D0, D1)
     assert torch.equal(x0, x1)
     assert i0.read()["status"] == 0
+
+
+@pytest.mark.parametrize("storage", [0, 1])
+def test_mxp_factor_same_bits_with_one_or_two_atom_stages(hpl, storage):
+    """The pair kernel's pipeline stages of one or two swizzle atoms issue the
+    same MMAs in the same order: the factor must not change, for an FP32
+    working matrix (bulk-tensor epilogue) and a BF16 one (per-thread epilogue
+    on a BF16 C)."""
+    import torch
+    n, nb = 5000, 512
+    A, b = _system(hpl, n, 11)
+    F = []
+    try:
+        for atoms in (1, 2):
+            hpl.gemm_config(hpl.GEMM_PAIR_ATOMS, atoms)
+            x, i, ws = hpl.mxp_solve(A, b, nb=nb, prec=0, storage=storage)
+            torch.cuda.synchronize()
+            assert i.read()["status"] == 0
+            F.append(hpl.mxp_factor_views(ws, n, nb, storage=storage)[0].clone())
+    finally:
+        hpl.gemm_config(hpl.GEMM_PAIR_ATOMS, 2)
+    assert torch.equal(F[0], F[1])
