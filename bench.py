@@ -41,15 +41,16 @@ MAX_SM_MHZ = 2070.0
 DGEMM_DRAM_BYTES_PER_FLOP = 956.9e6 / 31.21e9
 # Same for the tcgen05 trailing update of the mixed-precision solve, from one
 # ncu capture each of the step-0 update at n = 24576, NB = 4096 (m = 20480,
-# k = 4096, 3.436 TFLOP): key (prec, storage). BF16 and FP8 with FP32 storage
-# on the pair kernel with the bulk-tensor epilogue (4.715 GB and 3.808 GB,
-# profiles/k_gemm_tc_pair_update_tma_epilogue_n24576.txt), FP16 and TF32
-# likewise (5.367 GB and 11.092 GB, k_gemm_tc_pair_update_fp16_tf32_n24576.txt);
-# BF16 operands with BF16 storage on the per-thread epilogue (3.512 GB). At
-# fixed k a launch's traffic scales with its C tile, i.e. with its flops;
-# captured at the bench's panel width only, so another width reports null.
-MXP_DRAM_BYTES_PER_FLOP = {(0, 0): 4.715e9 / 3.436e12, (1, 0): 3.808e9 / 3.436e12, (2, 0): 5.367e9 / 3.436e12,
-                           (3, 0): 11.092e9 / 3.436e12, (0, 1): 3.512e9 / 3.436e12}
+# k = 4096, 3.436 TFLOP): key (prec, storage). BF16, FP8, FP16 and TF32 with
+# FP32 storage on the pair kernel with the bulk-tensor epilogue and two-atom
+# stages (4.711, 3.807, 4.743 and 11.132 GB,
+# profiles/k_gemm_tc_pair_update_two_atom_stages_n24576.txt); BF16 operands
+# with BF16 storage on the single-CTA kernel's per-thread epilogue (3.512 GB,
+# k_gemm_tc_update_bf16_vs_fp32_storage_n24576.txt). At fixed k a launch's
+# traffic scales with its C tile, i.e. with its flops; captured at the
+# bench's panel width only, so another width reports null.
+MXP_DRAM_BYTES_PER_FLOP = {(0, 0): 4.711e9 / 3.436e12, (1, 0): 3.807e9 / 3.436e12, (2, 0): 4.743e9 / 3.436e12,
+                           (3, 0): 11.132e9 / 3.436e12, (0, 1): 3.512e9 / 3.436e12}
 MXP_TRAFFIC_NB = 4096
 
 
