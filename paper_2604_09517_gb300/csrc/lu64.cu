@@ -333,9 +333,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
     extern __shared__ double sm[];
     __shared__ double cand_vals[2][kMaxLeafCluster][W], pub_diag[2][W];
     __shared__ long long cand_key[2][kMaxLeafCluster], cand_row[2][kMaxLeafCluster];
-    __shared__ double s_piv[W], s_diag[W];
     __shared__ long long s_wk[NW], s_wr[NW];
-    __shared__ long long s_p;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned C = gridDim.x;                        // the launch is one cluster
@@ -389,30 +387,25 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
             }
         }
         cluster_sync_all();
-        if (warp == 0) {
-            long long gk = -1, gr = kNone, gw = -1;
-            for (unsigned q = lane; q < C; q += 32) {
-                const long long k = cand_key[par][q], r = cand_row[par][q];
-                if (key_better(k, r, gk, gr)) { gk = k; gr = r; gw = (long long)q; }
-            }
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                long long ok = __shfl_xor_sync(0xffffffffu, gk, off);
-                long long orr = __shfl_xor_sync(0xffffffffu, gr, off);
-                long long ow = __shfl_xor_sync(0xffffffffu, gw, off);
-                if (key_better(ok, orr, gk, gr)) { gk = ok; gr = orr; gw = ow; }
-            }
-            if (gr == kNone) { gr = rowj; gw = -1; }     // only NaN in the column: keep the diagonal row
-            for (int c = lane; c < w; c += 32) {
-                const double dv = pub_diag[par][c];
-                s_diag[c] = dv;
-                s_piv[c] = gw >= 0 ? cand_vals[par][gw][c] : dv;
-            }
-            if (lane == 0) s_p = gr;
+        // every warp picks the winner from the local copies (no CTA barrier):
+        // the pivot row and the diagonal row are read where they were pushed
+        long long gk = -1, gr = kNone, gw = -1;
+        for (unsigned q = lane; q < C; q += 32) {
+            const long long k = cand_key[par][q], r = cand_row[par][q];
+            if (key_better(k, r, gk, gr)) { gk = k; gr = r; gw = (long long)q; }
         }
-        __syncthreads();
-        const long long p = s_p;
-        const double piv = s_piv[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            long long ok = __shfl_xor_sync(0xffffffffu, gk, off);
+            long long orr = __shfl_xor_sync(0xffffffffu, gr, off);
+            long long ow = __shfl_xor_sync(0xffffffffu, gw, off);
+            if (key_better(ok, orr, gk, gr)) { gk = ok; gr = orr; gw = ow; }
+        }
+        if (gr == kNone) { gr = rowj; gw = -1; }         // only NaN in the column: keep the diagonal row
+        const double* diagrow = pub_diag[par];
+        const double* pivrow = gw >= 0 ? cand_vals[par][gw] : diagrow;
+        const long long p = gr;
+        const double piv = pivrow[j];
         if (me == 0 && tid == 0) {
             ipiv[rowj] = (int32_t)p;
             if (piv == 0.0) atomicCAS((unsigned long long*)&info->info, 0ull, (unsigned long long)(rowj + 1));
@@ -423,13 +416,13 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
         // below when there is one), scale the column below the diagonal with one
         // true division per row, interchange in the panel's other columns
         if (swap && tid < w) {
-            if (rp >= 0 && rp < nloc && (tid != j || piv == 0.0)) sm[rp * S + tid] = s_diag[tid];
-            if (rd >= 0 && rd < nloc) sm[rd * S + tid] = s_piv[tid];
+            if (rp >= 0 && rp < nloc && (tid != j || piv == 0.0)) sm[rp * S + tid] = diagrow[tid];
+            if (rd >= 0 && rd < nloc) sm[rd * S + tid] = pivrow[tid];
         }
         const int rs = (int)max((int64_t)0, (int64_t)(rowj + 1 - grow0));
         if (piv != 0.0)
             for (int r = rs + tid; r < nloc; r += kLeafThreads) {
-                const double v = (swap && r == rp) ? s_diag[j] : sm[r * S + j];
+                const double v = (swap && r == rp) ? diagrow[j] : sm[r * S + j];
                 sm[r * S + j] = v / piv;
             }
         if (swap)
@@ -452,7 +445,7 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
                 const int dq = kLeafThreads / ncol, dc = kLeafThreads - dq * ncol;
                 while (q < nr) {
                     const int r = rs + q, c = j + 1 + cc;
-                    const double a = fma(-sm[r * S + j], s_piv[c], sm[r * S + c]);
+                    const double a = fma(-sm[r * S + j], pivrow[c], sm[r * S + c]);
                     sm[r * S + c] = a;
                     if (cc == 0) {
                         long long k = mag_key(a);
