@@ -402,6 +402,18 @@ int hplgb_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
 int hplgb_gemm_config(int what, long long value);
 
 /*
+ * hplgb_lu_config — measurement switch of the FP64 LU (not in the paper).
+ * what = 0: the TRSM of the block row, U12 = L11^-1 A12, as one kernel
+ * (value 0) or blocked by 64 (value 1, the default: each 64 x 64 diagonal
+ * block solved in shared memory, the rows below it updated by the DFMA
+ * product kernel). Both
+ * apply the same fused multiply-adds to every entry in the same order, so
+ * the factors are bit-identical. Process-wide, not thread-safe;
+ * HPL_ERR_INVALID for an unknown switch or value.
+ */
+int hplgb_lu_config(int what, long long value);
+
+/*
  * hplgb_batched_config — residency switch of the batched solver, for
  * measurement (not in the paper). what = 0: value 0 (default) runs a plan
  * whose systems all use 16-wide panels with two CTAs per SM (its shared

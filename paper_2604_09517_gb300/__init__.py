@@ -115,6 +115,7 @@ def load():
             "hplgb_gemm_config": (i32, [i32, ctypes.c_longlong]),
             "hpl_upload": (i32, [i64, i64, vp, i64, vp, i64, vp]),
             "hpl_download": (i32, [i64, i64, vp, i64, vp, i64, vp]),
+            "hplgb_lu_config": (i32, [i32, ctypes.c_longlong]),
             "hplgb_batched_config": (i32, [i32, ctypes.c_longlong]),
             "hplgb_phase_times": (i32, [vp, vp, vp]),
             "hplgb_phase_records": (i32, [vp, vp, vp, vp, vp, ctypes.c_longlong, vp]),
@@ -584,6 +585,14 @@ GEMM_PAIR_ATOMS = 3
 def gemm_config(what: int, value: int) -> None:
     """Tuning switch of the tensor-core product (see include/hplgb.h)."""
     _check(load().hplgb_gemm_config(int(what), int(value)), "hplgb_gemm_config")
+
+
+LU_TRSM_BLOCKED = 0       # hplgb_lu_config switch
+
+
+def lu_config(what: int, value: int) -> None:
+    """Measurement switch of the FP64 LU (see include/hplgb.h)."""
+    _check(load().hplgb_lu_config(int(what), int(value)), "hplgb_lu_config")
 
 
 def batched_config(what: int, value: int) -> None:
