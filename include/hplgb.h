@@ -177,9 +177,13 @@ int lu_factor_noalloc(int64_t n, double* A, int64_t lda, int32_t* ipiv, const hp
  * (Sec. III-A.1). trans = 0 solves A X = B: the interchanges are applied to B,
  * then L (unit lower) forward and U backward substitution. trans = 1 solves
  * A^T X = B (U^T, then L^T, then the interchanges in reverse order).
- * B (n x nrhs, ldb) holds b on entry and x on exit. ws must hold
- * lu_solve_workspace_size(n, nrhs) bytes. A zero on the diagonal of U sets
- * info->status = HPL_ERR_SINGULAR (the solve still runs; x has Inf/NaN).
+ * B (n x nrhs, ldb) holds b on entry and x on exit. ws (256-byte aligned)
+ * must hold lu_solve_workspace_size(n, nrhs) bytes. One right-hand side
+ * without transpose runs both triangles in one persistent launch, 64-row
+ * diagonal blocks applied through their inverses (the same solution as
+ * substitution up to rounding). A zero on the diagonal of U sets
+ * info->status = HPL_ERR_SINGULAR (the solve still runs; x has Inf/NaN); a
+ * device-side wait that expires sets HPL_ERR_TIMEOUT.
  */
 size_t lu_solve_workspace_size(int64_t n, int64_t nrhs);
 int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const int32_t* ipiv, int trans,
@@ -402,14 +406,21 @@ int hplgb_gemm_tf32(int64_t M, int64_t N, int64_t K, const float* A, int64_t lda
 int hplgb_gemm_config(int what, long long value);
 
 /*
- * hplgb_lu_config — measurement switch of the FP64 LU (not in the paper).
+ * hplgb_lu_config — measurement switches of the FP64 LU and its solve (not
+ * in the paper).
  * what = 0: the TRSM of the block row, U12 = L11^-1 A12, as one kernel
  * (value 0) or blocked by 64 (value 1, the default: each 64 x 64 diagonal
  * block solved in shared memory, the rows below it updated by the DFMA
- * product kernel). Both
- * apply the same fused multiply-adds to every entry in the same order, so
- * the factors are bit-identical. Process-wide, not thread-safe;
- * HPL_ERR_INVALID for an unknown switch or value.
+ * product kernel). Both apply the same fused multiply-adds to every entry in
+ * the same order, so the factors are bit-identical.
+ * what = 1: lu_solve of one right-hand side (trans = 0) as one persistent
+ * launch for both triangles (value 1, the default) or as per-block
+ * launches (value 0). The two sum in different orders (the same solution to
+ * rounding).
+ * what = 2: CTAs of that persistent launch, 0 (default) = one per SM, else
+ * at most value (1 .. 4096); the result is the same bits for every value.
+ * Process-wide, not thread-safe; HPL_ERR_INVALID for an unknown switch or
+ * value.
  */
 int hplgb_lu_config(int what, long long value);
 

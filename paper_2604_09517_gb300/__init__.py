@@ -587,11 +587,13 @@ def gemm_config(what: int, value: int) -> None:
     _check(load().hplgb_gemm_config(int(what), int(value)), "hplgb_gemm_config")
 
 
-LU_TRSM_BLOCKED = 0       # hplgb_lu_config switch
+LU_TRSM_BLOCKED = 0       # hplgb_lu_config switches
+LU_SOLVE_WAVE = 1
+LU_SOLVE_WAVE_GRID = 2
 
 
 def lu_config(what: int, value: int) -> None:
-    """Measurement switch of the FP64 LU (see include/hplgb.h)."""
+    """Measurement switch of the FP64 LU and its solve (see include/hplgb.h)."""
     _check(load().hplgb_lu_config(int(what), int(value)), "hplgb_lu_config")
 
 

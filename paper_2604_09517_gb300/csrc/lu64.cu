@@ -1251,11 +1251,24 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
     return HPL_OK;
 }
 
+namespace hplgb {
+extern int g_solve_wave;         // solve64.cu
+extern int g_solve_wave_grid;
+}  // namespace hplgb
+
 extern "C" int hplgb_lu_config(int what, long long value) {
     switch (what) {
         case 0:
             if (value < 0 || value > 1) return HPL_ERR_INVALID;
             hplgb::g_trsm_blocked = (int)value;
+            return HPL_OK;
+        case 1:
+            if (value < 0 || value > 1) return HPL_ERR_INVALID;
+            hplgb::g_solve_wave = (int)value;
+            return HPL_OK;
+        case 2:
+            if (value < 0 || value > 4096) return HPL_ERR_INVALID;
+            hplgb::g_solve_wave_grid = (int)value;
             return HPL_OK;
         default:
             return HPL_ERR_INVALID;
