@@ -86,6 +86,17 @@ enum Phase {
 int phase_begin(cudaStream_t s);                                   // -1 when timing is off
 void phase_end(int slot, cudaStream_t s, int phase, double work, int step = -1);  // work: flops or bytes
 
+// k_perm_pairs (lu64.cu): size of its table of rows beyond the block (a power
+// of two >= 2 pb) and its dynamic shared memory, for blocks of pb pivots.
+__host__ __device__ inline int perm_pairs_table(int pb) {
+    int h = 1;
+    while (h < 2 * pb) h <<= 1;
+    return h;
+}
+inline size_t perm_pairs_smem(int pb) {
+    return sizeof(int) * (5 * (size_t)pb + 2 * (size_t)perm_pairs_table(pb));
+}
+
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;
     asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));

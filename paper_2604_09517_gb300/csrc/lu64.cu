@@ -472,58 +472,72 @@ __global__ void __launch_bounds__(kLeafThreads) k_panel_leaf_cl(
 }
 
 // ---------------------------------------------------------------------------
-// SWAP: the sequential interchanges ipiv[k0 .. k0+kb) as a gather. One warp
-// replays them on a list of touched positions and emits (dst, src) pairs with
-// new[dst] = old[src]; the gather kernel then moves whole rows.
+// SWAP: the sequential interchanges ipiv[k0 .. k0+kb) as a gather. One lane
+// replays them on a list of touched positions (the block's own rows first,
+// then every row beyond the block that a pivot names, found through an
+// open-addressing table in shared memory) and the warp emits (dst, src) pairs
+// with new[dst] = old[src]; the gather kernel then moves whole rows.
 // Block b of the launch handles ipiv[k0_base + b*pb, ... + pb) (clipped at
-// n_end) and writes cnt[b], dst/src + b*2*pb.
+// n_end) and writes cnt[b], dst/src + b*2*pb. Shared memory:
+// perm_pairs_smem(pb) bytes.
 // Entries outside [k, n_total) are not interchanges and are skipped.
 __global__ void k_perm_pairs(const int32_t* __restrict__ ipiv, int64_t k0_base, int pb, int64_t n_end,
                              int64_t n_total, int* __restrict__ cnt, int* __restrict__ dst, int* __restrict__ src) {
     extern __shared__ int psm[];
+    __shared__ int s_len;
     const int64_t k0 = k0_base + (int64_t)blockIdx.x * pb;
     const int kb = (int)min((int64_t)pb, n_end - k0);
     cnt += blockIdx.x;
     dst += (int64_t)blockIdx.x * 2 * pb;
     src += (int64_t)blockIdx.x * 2 * pb;
-    int* pos = psm;               // [2*pb]
-    int* con = psm + 2 * pb;      // [2*pb]
+    const int H = perm_pairs_table(pb);
+    int* pos = psm;               // [2*pb] touched positions
+    int* con = psm + 2 * pb;      // [2*pb] their contents (original row numbers)
     int* pv = psm + 4 * pb;       // [pb] the block's pivots, read once (coalesced)
+    int* hkey = psm + 5 * pb;     // [H] rows beyond the block seen so far (-1: free)
+    int* hslot = hkey + H;        // [H] their index in pos / con
     const int lane = threadIdx.x;
     for (int i = lane; i < kb; i += 32) {
         pos[i] = (int)(k0 + i);
         con[i] = (int)(k0 + i);
         pv[i] = ipiv[k0 + i];
     }
+    for (int h = lane; h < H; h += 32) hkey[h] = -1;
     __syncwarp();
-    int L = kb;
-    for (int i = 0; i < kb; i++) {
-        int p = pv[i];
-        if (p <= k0 + i || p >= n_total) continue;
-        int q;
-        if (p < k0 + kb) {
-            q = (int)(p - k0);
-        } else {
-            q = -1;
-            for (int base = kb; base < L && q < 0; base += 32) {
-                int e = base + lane;
-                unsigned b = __ballot_sync(0xffffffffu, e < L && pos[e] == p);
-                if (b) q = base + __ffs(b) - 1;
+    if (lane == 0) {
+        int L = kb;
+        for (int i = 0; i < kb; i++) {
+            const int p = pv[i];
+            if (p <= k0 + i || p >= n_total) continue;
+            int q;
+            if (p < k0 + kb) {
+                q = (int)(p - k0);
+            } else {
+                // at most pb rows beyond the block, H >= 2 pb: a free entry always exists
+                for (int h = p & (H - 1);; h = (h + 1) & (H - 1)) {
+                    const int key = hkey[h];
+                    if (key == p) {
+                        q = hslot[h];
+                        break;
+                    }
+                    if (key < 0) {
+                        q = L++;
+                        hkey[h] = p;
+                        hslot[h] = q;
+                        pos[q] = p;
+                        con[q] = p;
+                        break;
+                    }
+                }
             }
-            if (q < 0) {
-                q = L;
-                if (lane == 0) { pos[L] = p; con[L] = p; }
-                L++;
-            }
-        }
-        __syncwarp();
-        if (lane == 0) {
-            int t = con[i];
+            const int t = con[i];
             con[i] = con[q];
             con[q] = t;
         }
-        __syncwarp();
+        s_len = L;
     }
+    __syncwarp();
+    const int L = s_len;
     // compact the pairs that move something
     int base_out = 0;
     for (int b = 0; b < L; b += 32) {
@@ -1170,7 +1184,7 @@ extern "C" int lu_factor(int64_t n, double* A, int64_t lda, int32_t* ipiv, const
         int r = panel_rec(n, A, lda, c0, kb, c0, kb, ipiv, w, info, o.timeout_ns, pp, ps);
         if (r) return r;
         int par = (int)(k & 1);
-        k_perm_pairs<<<1, 32, sizeof(int) * 5 * kb, ps>>>(ipiv, c0, kb, c0 + kb, n, w.perm_cnt + par,
+        k_perm_pairs<<<1, 32, perm_pairs_smem(kb), ps>>>(ipiv, c0, kb, c0 + kb, n, w.perm_cnt + par,
                                                            w.perm_dst + par * 2 * nb, w.perm_src + par * 2 * nb);
         HPL_LAUNCH_CHECK();
         // getrf of an m x kb panel: m kb^2 - kb^3/3 flops (leading terms)

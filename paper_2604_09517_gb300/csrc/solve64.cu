@@ -652,7 +652,7 @@ extern "C" int lu_solve(int64_t n, int64_t nrhs, const double* LU, int64_t lda, 
     solve_ws_layout(n, &w, (char*)ws);
     int *cnt = w.cnt, *dst = w.dst, *src = w.src;
     const int nblk = (int)((n + kPivBlock - 1) / kPivBlock);
-    k_perm_pairs<<<nblk, 32, sizeof(int) * 5 * kPivBlock, s>>>(ipiv, 0, kPivBlock, n, n, cnt, dst, src);
+    k_perm_pairs<<<nblk, 32, perm_pairs_smem(kPivBlock), s>>>(ipiv, 0, kPivBlock, n, n, cnt, dst, src);
     HPL_LAUNCH_CHECK();
     if (info) {
         k_check_udiag<<<(unsigned)std::min<int64_t>((n + 255) / 256, 1024), 256, 0, s>>>(n, LU, lda, info);
