@@ -198,7 +198,9 @@ static size_t solve_ws_layout(int64_t n, SolveWs* w, char* base) {
 // word (and info->status = HPL_ERR_TIMEOUT); every other waiter sees it, and
 // the CTA returns at its next barrier.
 constexpr int kWaveThreads = 256;
-constexpr int kWaveUEarly = 8;         // CTAs from here on invert their last U block before the forward sweep
+constexpr int kWaveUEarly = 12;        // CTAs from here on invert their last U block before the forward
+                                       // sweep (about 3 us per block reaches CTA c after c blocks; an
+                                       // inverse takes about 33 us)
 constexpr int kInvLd = kTB + 1;
 constexpr unsigned long long kWaveEmpty = ~0ull;   // bit pattern of a block not yet published
 
