@@ -27,7 +27,11 @@
  *       exact-rational diagonal sums, distribution moments.
  *   orc_getrf / orc_getrs : exact rational elimination (n <= 6), Cramer's rule,
  *       LAPACK getrf via scipy, closed forms, ||PA-LU|| invariant.
- *   orc_scaled_residual(_gen) : closed forms and a hand-computed case.
+ *   orc_scaled_residual(_gen) : closed forms and a hand-computed case; NaN for
+ *       a NaN or infinite x.
+ *   orc_mxp_refine(_plain) iteration counts : the same GMRES-IR around scipy's
+ *       GMRES with the preconditioner restated in numpy (equal corrections,
+ *       GMRES steps within one per cycle), every operand precision.
  *   orc_round_bf16 / orc_round_e4m3 : PyTorch's RNE casts (library routine),
  *       normals, ties, FP32 subnormals and the overflow threshold.
  *   orc_round_fp16 : NumPy's float16 cast (library routine).
@@ -45,7 +49,7 @@
  *   FP8 and FP16 operand encodings (prec = 1, 2): element rounding pinned;
  *       the per-row / per-column scale choice is a reading (the paper fixes
  *       none), pinned by a brute-force check of its defining property;
- *       iteration counts for FP8 are unpinned (only convergence is checked).
+ *       their iteration counts as for every precision (above).
  */
 #include <math.h>
 #include <stdint.h>
@@ -249,15 +253,23 @@ void orc_getrs(int64_t n, int64_t nrhs, const double* LU, int64_t lda, const int
 /* HPL scaled residual (the acceptance test; the paper prints no formula, this
  * is the standard HPL check): ||Ax-b||_inf / (eps (||A||_inf ||x||_inf +
  * ||b||_inf) n) with eps = 2^-53. Each r_i = sum_j a_ij x_j - b_i in FP64. */
+/* max |v_i|; NaN if any entry is NaN (a comparison would skip it) */
 static double orc_norm_inf_vec(int64_t n, const double* v) {
     double m = 0.0;
-    for (int64_t i = 0; i < n; i++) if (fabs(v[i]) > m) m = fabs(v[i]);
+    for (int64_t i = 0; i < n; i++) {
+        double a = fabs(v[i]);
+        if (a != a) return a;
+        if (a > m) m = a;
+    }
     return m;
 }
 
+/* The HPL acceptance quantity. A NaN residual entry makes the result NaN
+ * (it is no pass), as does a NaN in x or b. */
 double orc_scaled_residual(int64_t n, const double* A, int64_t lda, const double* x, const double* b) {
     double rmax = 0.0, amax = 0.0;
-#pragma omp parallel for schedule(static) reduction(max : rmax, amax)
+    int bad = 0;
+#pragma omp parallel for schedule(static) reduction(max : rmax, amax) reduction(| : bad)
     for (int64_t i = 0; i < n; i++) {
         double r = 0.0, s = 0.0;
         for (int64_t j = 0; j < n; j++) {
@@ -266,9 +278,11 @@ double orc_scaled_residual(int64_t n, const double* A, int64_t lda, const double
             s += fabs(a);
         }
         r -= b[i];
+        if (r != r) bad = 1;
         if (fabs(r) > rmax) rmax = fabs(r);
         if (s > amax) amax = s;
     }
+    if (bad) return NAN;
     double eps = 0x1p-53;
     return rmax / (eps * (amax * orc_norm_inf_vec(n, x) + orc_norm_inf_vec(n, b)) * (double)n);
 }
@@ -278,7 +292,8 @@ double orc_scaled_residual(int64_t n, const double* A, int64_t lda, const double
 double orc_scaled_residual_gen(uint64_t seed, int64_t n, int dominant, const double* x, const double* b) {
     uint64_t key = orc_stream_key(seed, 0);
     double rmax = 0.0, amax = 0.0;
-#pragma omp parallel for schedule(dynamic, 16) reduction(max : rmax, amax)
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 16) reduction(max : rmax, amax) reduction(| : bad)
     for (int64_t i = 0; i < n; i++) {
         double r = 0.0, s = 0.0;
         double dii = dominant ? orc_row_diag(key, n, i) : 0.0;
@@ -288,9 +303,11 @@ double orc_scaled_residual_gen(uint64_t seed, int64_t n, int dominant, const dou
             s += fabs(a);
         }
         r -= b[i];
+        if (r != r) bad = 1;
         if (fabs(r) > rmax) rmax = fabs(r);
         if (s > amax) amax = s;
     }
+    if (bad) return NAN;
     double eps = 0x1p-53;
     return rmax / (eps * (amax * orc_norm_inf_vec(n, x) + orc_norm_inf_vec(n, b)) * (double)n);
 }
@@ -862,6 +879,7 @@ static int orc_refine_impl(int64_t n, const double* A, int64_t lda, const orc_pr
         for (int64_t i = 0; i < n; i++) r[i] = b[i] - r[i];
         sr = orc_norm_inf_vec(n, r) / (eps * (anorm * orc_norm_inf_vec(n, x) + bnorm) * (double)n);
         if (hist) hist[it] = sr;
+        if (!isfinite(sr)) { status = 3; break; }   /* NaN or Inf: no pass, no further correction */
         if (sr < tol) { status = 0; break; }
         if (it >= max_iter) break;
         if (refine == 0) {

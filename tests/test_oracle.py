@@ -950,3 +950,136 @@ def test_mxp_tf32_operands(orc):
     assert out["status"] == 0 and out["sr"] < 16
     x64, _ = orc.solve(A, b)
     assert np.abs(out["x"] - x64).max() / np.abs(x64).max() < 2 * 16 * n * EPS * np.linalg.cond(A, np.inf)
+
+
+def _block_prec(F, Dinv, nb):
+    """M^-1 of the block factor, restated in numpy from its definition: block
+    forward substitution with the block unit lower L (the blocks of F below
+    the diagonal), then block backward substitution with U (the blocks of F on
+    and above it), each diagonal block D_k applied through its approximate
+    inverse Dinv_k. Computed in FP64 on the factor's values so that it is
+    linear to rounding (scipy's GMRES forms M^-1 of a combination of basis
+    vectors, the oracle the combination of M^-1 of each)."""
+    F64 = np.asarray(F, dtype=np.float64)
+    D64 = np.asarray(Dinv, dtype=np.float64)
+    n = F64.shape[0]
+    blocks = [(k0, min(n, k0 + nb)) for k0 in range(0, n, nb)]
+
+    def apply(v):
+        y = np.array(v, dtype=np.float64)
+        for k0, k1 in blocks:
+            for j0, j1 in blocks:
+                if j0 >= k0:
+                    break
+                y[k0:k1] -= F64[k0:k1, j0:j1] @ y[j0:j1]
+        x = np.zeros(n)
+        for k0, k1 in reversed(blocks):
+            x[k0:k1] = D64[k0:k1, :k1 - k0] @ (y[k0:k1] - F64[k0:k1, k1:] @ x[k1:])
+        return x
+    return apply
+
+
+def _plain_prec(F):
+    """M^-1 of the plain factor (L unit lower, U upper, both in F): two
+    triangular solves (LAPACK through scipy), in FP64 on the factor's values
+    for the same reason."""
+    from scipy.linalg import solve_triangular
+    F64 = np.asarray(F, dtype=np.float64)
+
+    def apply(v):
+        y = solve_triangular(F64, np.asarray(v, dtype=np.float64), lower=True, unit_diagonal=True)
+        return solve_triangular(F64, y, lower=False)
+    return apply
+
+
+def _gmres_ir_scipy(A, b, apply_minv, m=30, tol=16.0, max_iter=50):
+    """GMRES-based iterative refinement (Sec. II-B) around scipy's GMRES: x0 =
+    M^-1 b; while the HPL scaled residual of the FP64 residual r = b - A x is
+    16 or more, one restart cycle of GMRES on A M^-1 u = r (at most m steps,
+    stopping at a residual of 1e-10 |r|) and x += M^-1 u. Returns (outer
+    corrections, GMRES steps, final scaled residual)."""
+    from scipy.sparse.linalg import LinearOperator, gmres
+    A = np.asarray(A, dtype=np.float64)
+    n = A.shape[0]
+    anorm = np.abs(A).sum(axis=1).max()
+    bnorm = np.abs(b).max()
+    B = LinearOperator((n, n), matvec=lambda u: A @ apply_minv(np.ravel(u)), dtype=np.float64)
+    x = apply_minv(b)
+    outer = steps = 0
+    while True:
+        r = b - A @ x
+        sr = np.abs(r).max() / (EPS * (anorm * np.abs(x).max() + bnorm) * n)
+        if sr < tol or outer >= max_iter:
+            return outer, steps, sr
+        seen = []
+        u, _ = gmres(B, r, rtol=1e-10, atol=0.0, restart=m, maxiter=1, callback=seen.append,
+                     callback_type="pr_norm")
+        steps += len(seen)
+        x = x + apply_minv(u)
+        outer += 1
+
+
+@pytest.mark.parametrize("prec", ["PREC_BF16", "PREC_FP16", "PREC_FP8"])
+@pytest.mark.parametrize("case", ["dominant", "weak"])
+def test_mxp_refinement_counts_match_scipy_gmres(orc, prec, case):
+    """The oracle's GMRES-IR iteration counts (outer corrections and GMRES
+    steps), for the block factor and for the plain factor, against the same
+    refinement written around scipy's GMRES with each preconditioner restated
+    in numpy (in FP64 where the oracle applies it in FP32, a 1e-7 difference
+    against the factor's own 2^-8 .. 2^-4): the same outcome and number of
+    corrections and at most one GMRES step apart per restart cycle (rounding
+    can move the 1e-10 crossing by one step). Cases: the HPL-MxP matrix with
+    restarts of 30, and a weakly dominant one (diagonal 0.1 of the absolute
+    row sum) with restarts of 3, several cycles. This pins the FP8 counts,
+    which no closed form gives."""
+    pytest.importorskip("scipy")
+    p = getattr(orc, prec)
+    n, nb = 384, 64
+    b = orc.generate(12, orc.STREAM_B, n, 1)[:, 0]
+    if case == "dominant":
+        A, m = orc.generate(12, orc.STREAM_A, n, n, dominant=True), 30
+    else:
+        R = orc.generate(12, orc.STREAM_A, n, n)
+        A, m = R + 0.1 * np.diag(np.abs(R).sum(axis=1)), 3
+    F, Dinv, info = orc.mxp_factor(A, nb, p)
+    assert info == 0
+    Fp, info = orc.mxp_lu_plain(A, nb, p)
+    assert info == 0
+    for out, minv in ((orc.mxp_refine(A, F, Dinv, nb, b, refine=1, gmres_m=m), _block_prec(F, Dinv, nb)),
+                      (orc.mxp_refine_plain(A, Fp, b, refine=1, gmres_m=m), _plain_prec(Fp))):
+        outer, steps, sr = _gmres_ir_scipy(A, b, minv, m=m)
+        assert out["status"] == 0 and sr < 16
+        assert out["iters"] == outer, (out["iters"], outer)
+        assert abs(out["inner"] - steps) <= outer, (out["inner"], steps)
+
+
+def test_scaled_residual_is_nan_for_nonfinite_solution(orc):
+    """A NaN in x (or a NaN residual entry) is no pass of the acceptance test:
+    the scaled residual is NaN, never below 16."""
+    n = 64
+    A = orc.generate(3, orc.STREAM_A, n, n)
+    b = orc.generate(3, orc.STREAM_B, n, 1)[:, 0]
+    x, _ = orc.solve(A, b)
+    assert orc.scaled_residual(A, x, b) < 16
+    for bad in (np.nan, np.inf):
+        y = x.copy()
+        y[17] = bad
+        assert np.isnan(orc.scaled_residual(A, y, b))
+        assert np.isnan(orc.scaled_residual_gen(3, n, False, y, b))
+
+
+def test_mxp_refinement_reports_nonfinite(orc):
+    """Where the unpivoted low-precision factor is a useless preconditioner
+    (a matrix far from diagonal dominance), refinement ends with status 3
+    (non-finite) once its iterate overflows, instead of reading the NaN
+    residual as a pass."""
+    n, nb = 384, 64
+    R = orc.generate(12, orc.STREAM_A, n, n)
+    b = orc.generate(12, orc.STREAM_B, n, 1)[:, 0]
+    F, Dinv, _ = orc.mxp_factor(R, nb, orc.PREC_FP8)
+    out = orc.mxp_refine(R, F, Dinv, nb, b, refine=0)
+    assert out["status"] == 3 and not np.isfinite(out["x"]).all()
+    A = R + 0.05 * np.diag(np.abs(R).sum(axis=1))     # I - M^-1 A has spectral radius ~ 10: IR diverges
+    F, Dinv, _ = orc.mxp_factor(A, nb, orc.PREC_FP8)
+    assert orc.mxp_refine(A, F, Dinv, nb, b, refine=0)["status"] == 3
+    assert orc.mxp_refine(A, F, Dinv, nb, b, refine=1)["status"] == 4     # GMRES: no blow-up, no convergence
