@@ -137,3 +137,43 @@ def test_profiles_are_short_text_with_their_command():
         assert len(text) < 16384, p
         assert "Command" in text and "ncu" in text, p
         assert "_work" not in text and "gpurun" not in text, p
+
+
+def test_measurement_switches_accept_documented_values_only(lib):
+    """hplgb_gemm_config, hplgb_lu_config and hplgb_batched_config take the
+    values include/hplgb.h documents and refuse others with HPL_ERR_INVALID
+    (1). They only set host state, so this runs without a GPU. The defaults
+    are restored at the end."""
+    ok = {
+        "hplgb_gemm_config": [(0, 0), (0, 1), (1, 0), (1, 16), (1, 4096), (2, 0), (2, -1), (2, 1 << 30), (3, 1),
+                              (3, 2)],
+        "hplgb_lu_config": [(0, 0), (0, 1), (1, 0), (1, 1), (2, 0), (2, 1), (2, 4096)],
+        "hplgb_batched_config": [(0, 0), (0, 1)],
+    }
+    bad = {
+        "hplgb_gemm_config": [(0, 2), (0, -1), (1, -1), (1, 4097), (3, 0), (3, 3), (4, 0), (-1, 0)],
+        "hplgb_lu_config": [(0, 2), (0, -1), (1, 2), (1, -1), (2, -1), (2, 4097), (3, 0), (-1, 0)],
+        "hplgb_batched_config": [(0, 2), (0, -1), (1, 0)],
+    }
+    defaults = {
+        "hplgb_gemm_config": [(0, 0), (1, 0), (2, 0), (3, 2)],
+        "hplgb_lu_config": [(0, 1), (1, 1), (2, 0)],
+        "hplgb_batched_config": [(0, 0)],
+    }
+    fn = {}
+    for name in ok:
+        f = getattr(lib, name)
+        f.argtypes = [ctypes.c_int, ctypes.c_longlong]
+        f.restype = ctypes.c_int
+        fn[name] = f
+    try:
+        for name, cases in ok.items():
+            for what, value in cases:
+                assert fn[name](what, value) == 0, (name, what, value)
+        for name, cases in bad.items():
+            for what, value in cases:
+                assert fn[name](what, value) == 1, (name, what, value)
+    finally:
+        for name, cases in defaults.items():
+            for what, value in cases:
+                assert fn[name](what, value) == 0
