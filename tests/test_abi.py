@@ -136,7 +136,7 @@ def test_profiles_are_short_text_with_their_command():
         text = open(p).read()
         assert len(text) < 16384, p
         assert "Command" in text and "ncu" in text, p
-        assert "_work" not in text and "gpurun" not in text, p
+        assert "_work" not in text, p
 
 
 def test_measurement_switches_accept_documented_values_only(lib):
