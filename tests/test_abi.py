@@ -124,6 +124,14 @@ def test_workspace_sizes_follow_the_options():
     emu = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, fp64_emulation=1)))
     coop = lib.lu_factor_workspace_size(n, C.byref(hpl.make_opts(nb=256, pfact=1)))
     assert emu > base + 40 * n * n // 2 and coop == base
+    # lu_solve: the interchange pairs (2 x 2 x 256 ints per 256 pivots) and the
+    # one-launch solve's published blocks (y and x: 2 x 64 doubles per 64 rows)
+    for m in (1, 63, 64, 65, 1000, 32768):
+        blocks64, blocks256 = -(-m // 64), -(-m // 256)
+        need = 2 * 8 * 64 * blocks64 + 2 * 2 * 4 * 256 * blocks256
+        got = lib.lu_solve_workspace_size(m, 1)
+        assert need <= got <= need + 4096 + 4 * blocks256, (m, got, need)
+        assert lib.lu_solve_workspace_size(m, 7) == got
 
 
 def test_profiles_are_short_text_with_their_command():
